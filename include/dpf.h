@@ -1,0 +1,231 @@
+/*
+ * dpf.h -- C ABI of the GB300 (sm_103a) Differentiable Power-Flow hot path.
+ *
+ * Differentiable Power-Flow (DPF) solves the AC power-flow problem of
+ * Sec. 2.1 (Eq. powerbalance, Eq. pf_equation_full) by gradient descent on
+ * the squared power mismatch (Eq. pf_optimization_problem, Sec. 4, Alg. 1):
+ * each iteration forms S_calc = V (Y_bus V)^*, the mismatch
+ * f = [dP(pv,pq), dQ(pq)], the loss L = (1/m)||f||^2 with m = |pv| + 2|pq|,
+ * its gradient with respect to theta(pv,pq) and |V|(pq), and an Adam step
+ * with a learning-rate scheduler.  This library runs that iteration for many
+ * cases at once on one GPU, sharing one Y_bus (Sec. 4.2 batching; N-1 cases
+ * as a per-case correction of the shared matrix).
+ *
+ * Conventions
+ *   - All functions return an int status: DPF_OK (0) or a negative DPF_E_*.
+ *     Nothing aborts or throws across the ABI; dpf_last_error() returns a
+ *     human-readable message for the most recent failure on the calling
+ *     thread.
+ *   - Units: per unit (p.u.) and radians.  Injections are net
+ *     (generation - load).
+ *   - Layouts: per-case arrays are case-major, [n_case][n_bus] row-major
+ *     (case k, bus i at k*n_bus + i).  Branch arrays are [n_branch].
+ *   - Ownership: every pointer argument stays owned by the caller and is
+ *     read or written only during the call (or, for device pointers, by work
+ *     enqueued on `stream` by the call).  Handles (dpf_ybus, dpf_workspace)
+ *     are owned by the library and released with their *_free function.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Work is enqueued on it; functions that return host
+ *     values synchronise that stream (stated per function).
+ *   - Device pointers must be 8-byte aligned (16 for double2-viewed data is
+ *     not required: complex values are passed as separate re/im arrays).
+ */
+#ifndef DPF_H
+#define DPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+enum {
+  DPF_OK = 0,
+  DPF_E_INVALID = -1,     /* bad argument: NULL, size, index or bus type    */
+  DPF_E_ISLANDED = -2,    /* an outage disconnects the grid                 */
+  DPF_E_CUDA = -3,        /* a CUDA runtime call failed (message has detail) */
+  DPF_E_OOM = -4,         /* device or host allocation failed               */
+  DPF_E_UNSUPPORTED = -5, /* e.g. a phase-shifting transformer              */
+  DPF_E_STATE = -6        /* call out of order (e.g. iterate before begin)  */
+};
+
+/* per-case outcome written to dpf_batch.status */
+enum {
+  DPF_CASE_CONVERGED = 0, /* FP64 max |f| <= tol                             */
+  DPF_CASE_MAX_ITER = 1,  /* iteration budget spent above tol                */
+  DPF_CASE_DIVERGED = 2   /* loss became NaN/Inf                             */
+};
+
+enum { DPF_PQ = 0, DPF_PV = 1, DPF_SLACK = 2 };            /* bus types (Sec. 2.1) */
+enum { DPF_FP32 = 0, DPF_FP64 = 1 };                        /* iteration precision */
+enum { DPF_SCHED_CONST = 0, DPF_SCHED_PLATEAU = 1, DPF_SCHED_STEP = 2 };
+
+/* ---- grid description (host arrays, caller-owned, read-only) -------------
+ * The problem statement of Sec. 2.1 / Alg. 1 inputs: bus types with exactly
+ * one slack, specified P (pv, pq), Q (pq), |V| (pv, slack), the slack angle,
+ * and the branch table from which Y_bus is built with the pi-model (the
+ * MATPOWER model the paper's Eq. powerbalance footnote refers to):
+ *   y_s = 1/(r + jx); Y_ff += (y_s + j b_ch/2)/tap^2; Y_tt += y_s + j b_ch/2;
+ *   Y_ft += -y_s/tap; Y_tf += -y_s/tap.
+ * tap = 0 is read as 1 (no transformer).  shift may be NULL; a nonzero shift
+ * is rejected with DPF_E_UNSUPPORTED.  Parallel branches are rejected with
+ * DPF_E_UNSUPPORTED (each CSR off-diagonal entry maps to one branch). */
+typedef struct {
+  int32_t n_bus, n_branch;
+  const uint8_t* bus_type;   /* [n_bus] DPF_PQ / DPF_PV / DPF_SLACK            */
+  const double* p_spec;      /* [n_bus] net active injection                   */
+  const double* q_spec;      /* [n_bus] net reactive injection (used at PQ)    */
+  const double* vm_set;      /* [n_bus] |V| set-point (used at PV and slack)   */
+  double va_slack;           /* slack angle                                    */
+  const int32_t* f_bus;      /* [n_branch] 0-based from-bus (tap side)         */
+  const int32_t* t_bus;      /* [n_branch] 0-based to-bus                      */
+  const double *r, *x, *b_ch, *tap;  /* [n_branch]                              */
+  const double* shift;       /* [n_branch] or NULL; must be 0                  */
+} dpf_grid;
+
+typedef struct dpf_ybus dpf_ybus;           /* Y_bus in CSR (host + device)   */
+typedef struct dpf_workspace dpf_workspace; /* device state of one batch      */
+
+/* Build Y_bus on the host (CSR, FP64, sorted columns, every diagonal
+ * present) and validate the grid.  No CUDA call is made; a GPU is not needed.
+ * Errors: DPF_E_INVALID (sizes, indices, not exactly one slack, f == t,
+ * non-finite or zero impedance), DPF_E_UNSUPPORTED (shift, parallel branch). */
+int dpf_build_ybus_host(const dpf_grid* g, dpf_ybus** out);
+
+/* Copy a host-built Y_bus to the current device (FP32 and FP64 values, CSR
+ * indices, branch data), enqueued on `stream`, which is then synchronised. */
+int dpf_ybus_upload(dpf_ybus* y, void* stream);
+
+/* dpf_build_ybus_host followed by dpf_ybus_upload. */
+int dpf_build_ybus(const dpf_grid* g, void* stream, dpf_ybus** out);
+int dpf_ybus_free(dpf_ybus* y);
+
+/* Sizes of a built Y_bus (host values). */
+int dpf_ybus_info(const dpf_ybus* y, int32_t* n_bus, int32_t* n_branch, int32_t* nnz);
+
+/* Host copies of the FP64 CSR: row_ptr [n_bus+1], col [nnz], val_re/val_im
+ * [nnz].  Any output may be NULL.  No CUDA call. */
+int dpf_ybus_export(const dpf_ybus* y, int32_t* row_ptr, int32_t* col,
+                    double* val_re, double* val_im);
+
+/* bridge[l] = 1 if removing branch l disconnects the grid (Tarjan low-link on
+ * the host).  N-1 outages of bridges are rejected with DPF_E_ISLANDED.
+ * No CUDA call. */
+int dpf_ybus_bridges(const dpf_ybus* y, uint8_t* bridge);
+
+/* ---- batched solve ---------------------------------------------------------
+ * One case = one power-flow problem on the shared grid, possibly with its own
+ * injections / set-points (time series) and one branch outage (N-1).
+ * All pointers are device pointers unless host_io = 1, in which case they are
+ * host pointers (pinned memory gives the best transfer rate) and the library
+ * copies them through its workspace inside the call, on `stream`. */
+typedef struct {
+  int32_t n_case;
+  int32_t host_io;           /* 0: device pointers; 1: host pointers          */
+  const double* p_spec;      /* [n_case][n_bus] or NULL = the grid's          */
+  const double* q_spec;      /* [n_case][n_bus] or NULL = the grid's          */
+  const double* vm_set;      /* [n_case][n_bus] or NULL = the grid's          */
+  const int32_t* outage;     /* [n_case] branch index or -1, NULL = none      */
+  double* va;                /* [n_case][n_bus] in: warm start (if flat_start
+                                = 0); out: solution angles                   */
+  double* vm;                /* [n_case][n_bus] in/out: magnitudes            */
+  int32_t* iters;            /* [n_case] out: optimizer steps taken           */
+  int32_t* status;           /* [n_case] out: DPF_CASE_*                      */
+  double* max_mismatch;      /* [n_case] out: FP64 max |f| of the returned V  */
+  double* loss;              /* [n_case] out: FP64 loss of the returned V     */
+} dpf_batch;
+
+/* Iteration options.  Defaults (dpf_default_opts): Table 2 of the paper --
+ * Adam betas (0.979, 0.963), eps 1e-8, ReduceLROnPlateau factor 0.547,
+ * patience 41, threshold 0.0673 (relative), cooldown 97, max_iter 1000 --
+ * with lr 1e-2, tol 1e-6 p.u., check_every 25, FP32 iterations. */
+typedef struct {
+  double lr, beta1, beta2, eps;
+  int32_t sched;             /* DPF_SCHED_*                                    */
+  double factor, threshold, min_lr;
+  int32_t patience, cooldown;
+  int32_t step_size;         /* StepLR                                         */
+  double gamma;
+  int32_t max_iter;          /* optimizer steps per case                       */
+  int32_t check_every;       /* FP64 convergence test every k steps (>= 1)     */
+  double tol;                /* stop when FP64 max |f| <= tol                  */
+  int32_t flat_start;        /* 1: ignore va/vm inputs, start flat             */
+  int32_t precision;         /* DPF_FP32 (FP64 master + FP64 test) / DPF_FP64  */
+  int32_t lanes;             /* cases per row group 1..32 (power of 2); 0=auto */
+  int32_t warps;             /* warps per CTA (1..32); 0 = auto                */
+  int32_t row_blocks;        /* CTAs along the bus dimension; 0 = auto         */
+  int32_t use_graph;         /* 1: replay iterations from a CUDA graph         */
+} dpf_solve_opts;
+
+void dpf_default_opts(dpf_solve_opts* o);
+
+/* Workspace: device buffers for up to `max_case` cases of one Y_bus.  All
+ * device memory the solve needs is allocated here (and grown on demand by
+ * dpf_solve_begin); nothing is allocated per iteration. */
+int dpf_workspace_create(const dpf_ybus* y, int32_t max_case, dpf_workspace** out);
+int dpf_workspace_free(dpf_workspace* ws);
+
+/* Full solve (Alg. 1 for every case): dpf_solve_begin, iterations until every
+ * case has converged, diverged or spent max_iter, dpf_solve_end.  Polls the
+ * active-case count from the host every few check intervals (synchronises
+ * `stream` at those points and at the end).  ws may be NULL (a temporary
+ * workspace is created and freed inside the call). */
+int dpf_solve_batch(const dpf_ybus* y, dpf_workspace* ws, const dpf_batch* b,
+                    const dpf_solve_opts* o, void* stream);
+
+/* Step-wise driving of the same solve.  begin: validate, copy inputs, set the
+ * initial state (flat or warm start; fixed |V| and slack angle enforced),
+ * compute the N-1 corrections.  iterate: n_iter DPF iterations of every
+ * active case -- FP64 test (when due), forward SpMV + mismatch + loss, adjoint
+ * SpMV + gradient + Adam, scheduler -- with no host synchronisation.  end:
+ * final FP64 evaluation, statuses and solution written to the batch outputs
+ * (synchronises `stream` when host_io = 1). */
+int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* ws, const dpf_batch* b,
+                    const dpf_solve_opts* o, void* stream);
+int dpf_solve_iterate(dpf_workspace* ws, int32_t n_iter, void* stream);
+int dpf_solve_end(dpf_workspace* ws, const dpf_batch* b, void* stream);
+/* Number of cases still iterating (synchronises `stream`). */
+int dpf_active_count(dpf_workspace* ws, int32_t* n_active, void* stream);
+/* Steps taken so far by the batch (host counter, no synchronisation). */
+int dpf_iterations_done(const dpf_workspace* ws, int32_t* n_iter);
+
+/* ---- forward evaluation (Eq. powerbalance) --------------------------------
+ * S_calc = V (Y V)^* for n_case voltage vectors (case-major device arrays),
+ * optional per-case outage (NULL = none).  precision selects the FP32 or
+ * FP64 kernels; outputs are FP64 either way. */
+int dpf_power(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
+              const double* va, const double* vm, const int32_t* outage,
+              int32_t precision, double* p_calc, double* q_calc, void* stream);
+
+/* ---- loss and its adjoint (Sec. 4.1: dL/dx = J^T F, scaled by the MSE) ----
+ * For n_case states (va, vm) and specified injections (p_spec/q_spec, NULL =
+ * the grid's; case-major device arrays) computes the FP64 loss per case and,
+ * through the hand-written adjoint kernels in `precision`:
+ *   d_va, d_vm [n_case][n_bus]  dL/dtheta (0 off pv,pq), dL/d|V| (0 off pq);
+ *   d_p, d_q   [n_case][n_bus]  dL/dP_spec, dL/dQ_spec;
+ *   d_g, d_b, d_bch [n_branch]  dL/d(series g), dL/d(series b), dL/d(b_ch),
+ *                               summed over the cases (parameter
+ *                               identification over operating points).
+ * g_series / b_series ([n_branch] device, FP64) replace the branches' series
+ * admittance g + jb (NULL = as built); charging and taps stay as built.
+ * Any output pointer may be NULL to skip it.  outage may be NULL. */
+int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
+                      const double* va, const double* vm,
+                      const double* p_spec, const double* q_spec,
+                      const int32_t* outage,
+                      const double* g_series, const double* b_series,
+                      int32_t precision,
+                      double* loss, double* d_va, double* d_vm,
+                      double* d_p, double* d_q,
+                      double* d_g, double* d_b, double* d_bch, void* stream);
+
+/* Message of the most recent failure on this thread ("" if none). */
+const char* dpf_last_error(void);
+/* Static description of a status code. */
+const char* dpf_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPF_H */
