@@ -123,8 +123,8 @@ int dpf_ybus_bridges(const dpf_ybus* y, uint8_t* bridge);
 typedef struct {
   int32_t n_case;
   int32_t host_io;           /* 0: device pointers; 1: host pointers          */
-  const double* p_spec;      /* [n_case][n_bus] or NULL = the grid's          */
-  const double* q_spec;      /* [n_case][n_bus] or NULL = the grid's          */
+  const double* p_spec;      /* [n_case][n_bus] or NULL = the grid's; p_spec  */
+  const double* q_spec;      /* and q_spec are given together or not at all   */
   const double* vm_set;      /* [n_case][n_bus] or NULL = the grid's          */
   const int32_t* outage;     /* [n_case] branch index or -1, NULL = none      */
   double* va;                /* [n_case][n_bus] in: warm start (if flat_start
@@ -156,6 +156,11 @@ typedef struct {
   int32_t warps;             /* warps per CTA (1..32); 0 = auto                */
   int32_t row_blocks;        /* CTAs along the bus dimension; 0 = auto         */
   int32_t use_graph;         /* 1: replay iterations from a CUDA graph         */
+  int32_t plain;             /* 1: the plain form of Alg. 1 -- one case at a
+                                time, separate launches per iteration and a
+                                host stop test (FP64 check + device-to-host
+                                read) after every iteration; check_every is
+                                taken as 1.  Used as the unbatched baseline. */
 } dpf_solve_opts;
 
 void dpf_default_opts(dpf_solve_opts* o);

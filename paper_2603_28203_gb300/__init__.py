@@ -1,0 +1,18 @@
+"""GB300-native Differentiable Power-Flow (DPF) hot path.
+
+The CUDA library (csrc/, C ABI in include/dpf.h) runs batched DPF iterations
+(Alg. 1): complex CSR SpMV I = Y V with the mismatch and loss fused in its
+epilogue, the hand-written adjoint (Y applied to the mismatch-weighted
+voltages), a fused Adam step with per-case schedulers, N-1 outages as a
+per-case correction of one shared Y_bus, and an FP64 convergence test.
+`dpf` is the ctypes binding (same names as the C functions), `autograd` the
+torch.autograd.Function over the adjoint.
+"""
+from . import _abi
+from ._abi import (CASE_CONVERGED, CASE_DIVERGED, CASE_MAX_ITER, FP32, FP64, PQ, PV, SCHED_CONST,
+                   SCHED_PLATEAU, SCHED_STEP, SLACK)
+from .dpf import (DPFError, SolveOpts, Workspace, Ybus, dpf_active_count, dpf_build_ybus,
+                  dpf_build_ybus_host, dpf_default_opts, dpf_iterations_done, dpf_last_error,
+                  dpf_loss_backward, dpf_power, dpf_solve_batch, dpf_solve_begin, dpf_solve_end,
+                  dpf_solve_iterate, dpf_status_str, dpf_workspace_create, dpf_ybus_bridges,
+                  dpf_ybus_export, dpf_ybus_upload, lib)

@@ -1,0 +1,1087 @@
+// CUDA part of libdpf: device copies of Y_bus, workspaces, launch
+// configuration, the batched solve (Alg. 1 for every case) and the
+// evaluation entry points (S_calc; loss + adjoint gradients).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dpf_internal.h"
+#include "dpf_kernels.cuh"
+
+using namespace dpf;
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(e_ == cudaErrorMemoryAllocation ? DPF_E_OOM : DPF_E_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+  } while (0)
+
+#define CKLAUNCH()                                                                            \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(DPF_E_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                  \
+  } while (0)
+
+#define TRY(x)               \
+  do {                       \
+    int s_ = (x);            \
+    if (s_ != DPF_OK) return s_; \
+  } while (0)
+
+namespace {
+
+template <class T>
+int dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? DPF_E_OOM : DPF_E_CUDA, "cudaMalloc(%zu bytes): %s",
+                n * sizeof(T), cudaGetErrorString(e));
+  }
+  return DPF_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+template <class T>
+int upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
+  TRY(dalloc(dst, src.size()));
+  if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return DPF_OK;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+int pow2ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Y_bus upload
+// ---------------------------------------------------------------------------
+static void free_device(DeviceYbus& d) {
+  dfree(d.ent32); dfree(d.row_ptr); dfree(d.col); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
+  dfree(d.type); dfree(d.p64); dfree(d.q64); dfree(d.vmset); dfree(d.p32); dfree(d.q32);
+  dfree(d.perm); dfree(d.iperm); dfree(d.br_f); dfree(d.br_t); dfree(d.br_r); dfree(d.br_x);
+  dfree(d.br_bch); dfree(d.br_tap); dfree(d.bridge);
+  d.ready = false;
+}
+
+extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
+  clear_error();
+  if (!y) return fail(DPF_E_INVALID, "dpf_ybus_upload: NULL handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceYbus& d = y->dev;
+  if (d.ready) free_device(d);
+  const int n = y->n, m = y->m, nnz = y->nnz;
+  std::vector<int4> ent(nnz);
+  std::vector<double2> v64(nnz);
+  for (int p = 0; p < nnz; ++p) {
+    const float re = (float)y->ival_re[p], im = (float)y->ival_im[p];
+    int4 e;
+    e.x = y->icol[p];
+    memcpy(&e.y, &re, 4);
+    memcpy(&e.z, &im, 4);
+    e.w = 0;
+    ent[p] = e;
+    v64[p] = make_double2(y->ival_re[p], y->ival_im[p]);
+  }
+  std::vector<uint8_t> type(n);
+  std::vector<double> p64(n), q64(n), vms(n);
+  std::vector<float> p32(n), q32(n);
+  for (int i = 0; i < n; ++i) {
+    const int o = y->perm[i];
+    type[i] = y->bus_type[o];
+    p64[i] = y->p_spec[o];
+    q64[i] = y->q_spec[o];
+    vms[i] = y->vm_set[o];
+    p32[i] = (float)p64[i];
+    q32[i] = (float)q64[i];
+  }
+  std::vector<int32_t> bf(m), bt(m);
+  for (int e = 0; e < m; ++e) {
+    bf[e] = y->iperm[y->f_bus[e]];
+    bt[e] = y->iperm[y->t_bus[e]];
+  }
+  int rc = DPF_OK;
+  do {
+    if ((rc = upload(&d.ent32, ent, s))) break;
+    if ((rc = upload(&d.row_ptr, y->irow_ptr, s))) break;
+    if ((rc = upload(&d.col, y->icol, s))) break;
+    if ((rc = upload(&d.val64, v64, s))) break;
+    if ((rc = upload(&d.ebr, y->iebr, s))) break;
+    if ((rc = upload(&d.dpos, y->idpos, s))) break;
+    if ((rc = upload(&d.type, type, s))) break;
+    if ((rc = upload(&d.p64, p64, s))) break;
+    if ((rc = upload(&d.q64, q64, s))) break;
+    if ((rc = upload(&d.vmset, vms, s))) break;
+    if ((rc = upload(&d.p32, p32, s))) break;
+    if ((rc = upload(&d.q32, q32, s))) break;
+    if ((rc = upload(&d.perm, y->perm, s))) break;
+    if ((rc = upload(&d.iperm, y->iperm, s))) break;
+    if ((rc = upload(&d.br_f, bf, s))) break;
+    if ((rc = upload(&d.br_t, bt, s))) break;
+    if ((rc = upload(&d.br_r, y->r, s))) break;
+    if ((rc = upload(&d.br_x, y->x, s))) break;
+    if ((rc = upload(&d.br_bch, y->b_ch, s))) break;
+    if ((rc = upload(&d.br_tap, y->tap, s))) break;
+    if ((rc = upload(&d.bridge, y->bridge, s))) break;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { rc = fail(DPF_E_CUDA, "upload sync: %s", cudaGetErrorString(e)); break; }
+  } while (0);
+  if (rc != DPF_OK) {
+    free_device(d);
+    return rc;
+  }
+  cudaGetDevice(&d.device);
+  d.ready = true;
+  return DPF_OK;
+}
+
+extern "C" int dpf_build_ybus(const dpf_grid* g, void* stream, dpf_ybus** out) {
+  if (!out) return fail(DPF_E_INVALID, "dpf_build_ybus: NULL out");
+  *out = nullptr;
+  dpf_ybus* y = nullptr;
+  TRY(dpf_build_ybus_host(g, &y));
+  const int rc = dpf_ybus_upload(y, stream);
+  if (rc != DPF_OK) {
+    delete y;
+    return rc;
+  }
+  *out = y;
+  return DPF_OK;
+}
+
+extern "C" int dpf_ybus_free(dpf_ybus* y) {
+  if (!y) return DPF_OK;
+  if (y->dev.ready) free_device(y->dev);
+  delete y;
+  return DPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+struct dpf_workspace {
+  const dpf_ybus* y = nullptr;
+  size_t cap_elems = 0;   // N * Kp capacity
+  int cap_cases = 0;      // Kp capacity
+  size_t cap_stage = 0;   // K * N capacity of the user-layout staging buffers
+  // element buffers (sized for FP64; FP32 mode uses the front half)
+  void *V = nullptr, *W = nullptr, *G0 = nullptr, *th = nullptr, *vm = nullptr;
+  void *mth = nullptr, *vth = nullptr, *mvm = nullptr, *vvm = nullptr, *p = nullptr, *q = nullptr;
+  double *p64 = nullptr, *q64 = nullptr, *tmp_a = nullptr, *tmp_b = nullptr, *tmp_c = nullptr;
+  double2* V64 = nullptr;
+  void *sbuf = nullptr, *cbuf = nullptr;
+  // Y values rebuilt from caller branch parameters
+  int4* ent_loc = nullptr;
+  double2* val_loc = nullptr;
+  // per-case buffers
+  int32_t *active = nullptr, *iters = nullptr, *status = nullptr, *of = nullptr, *ot = nullptr;
+  int32_t *bad = nullptr, *cool = nullptr;
+  double *lr = nullptr, *best = nullptr, *out_max = nullptr, *out_loss = nullptr, *loss64 = nullptr;
+  void *loss_acc = nullptr, *step_size = nullptr, *isbc2 = nullptr, *yff = nullptr, *yft = nullptr, *ytt = nullptr;
+  double2 *yff64 = nullptr, *yft64 = nullptr, *ytt64 = nullptr;
+  unsigned long long* maxmis = nullptr;
+  int32_t* outage_dev = nullptr;
+  int32_t* n_active = nullptr;
+  int32_t* h_n_active = nullptr;  // pinned
+  // user-layout staging for host_io
+  double *st_a = nullptr, *st_b = nullptr, *st_c = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  // solve state
+  bool begun = false;
+  int K = 0, Kp = 0, lanes = 1, warps = 8, gx = 1, gy = 1, precision = DPF_FP32;
+  bool spec_per_case = false, has_outage = false;
+  dpf_solve_opts opts;
+  int t_done = 0;
+  cudaGraphExec_t gexec = nullptr;
+  bool use_local_y = false;
+};
+
+static void ws_free_buffers(dpf_workspace* w) {
+  void** ptrs[] = {&w->V, &w->W, &w->G0, &w->th, &w->vm, &w->mth, &w->vth, &w->mvm, &w->vvm, &w->p, &w->q,
+                   &w->sbuf, &w->cbuf, &w->loss_acc, &w->step_size, &w->isbc2, &w->yff, &w->yft, &w->ytt};
+  for (void** p : ptrs) dfree(*p);
+  dfree(w->p64); dfree(w->q64); dfree(w->tmp_a); dfree(w->tmp_b); dfree(w->tmp_c); dfree(w->V64);
+  dfree(w->ent_loc); dfree(w->val_loc);
+  dfree(w->active); dfree(w->iters); dfree(w->status); dfree(w->of); dfree(w->ot); dfree(w->bad); dfree(w->cool);
+  dfree(w->lr); dfree(w->best); dfree(w->out_max); dfree(w->out_loss); dfree(w->loss64);
+  dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
+  dfree(w->st_a); dfree(w->st_b); dfree(w->st_c);
+  w->cap_elems = 0;
+  w->cap_cases = 0;
+  w->cap_stage = 0;
+}
+
+static void ws_drop_graph(dpf_workspace* w) {
+  if (w->gexec) cudaGraphExecDestroy(w->gexec);
+  w->gexec = nullptr;
+}
+
+// Grow the buffers to hold Kp cases (N * Kp elements) and K*N staging.
+static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
+  const dpf_ybus* y = w->y;
+  const size_t E = (size_t)y->n * Kp;
+  if (E > w->cap_elems || Kp > w->cap_cases) {
+    ws_drop_graph(w);
+    dfree(w->V); dfree(w->W); dfree(w->G0); dfree(w->th); dfree(w->vm); dfree(w->mth); dfree(w->vth);
+    dfree(w->mvm); dfree(w->vvm); dfree(w->p); dfree(w->q); dfree(w->sbuf); dfree(w->cbuf);
+    dfree(w->p64); dfree(w->q64); dfree(w->tmp_a); dfree(w->tmp_b); dfree(w->tmp_c); dfree(w->V64);
+    dfree(w->loss_acc); dfree(w->step_size); dfree(w->isbc2); dfree(w->yff); dfree(w->yft); dfree(w->ytt);
+    dfree(w->active); dfree(w->iters); dfree(w->status); dfree(w->of); dfree(w->ot); dfree(w->bad);
+    dfree(w->cool); dfree(w->lr); dfree(w->best); dfree(w->out_max); dfree(w->out_loss); dfree(w->loss64);
+    dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
+    w->cap_elems = 0;
+    w->cap_cases = 0;
+    char** bufs16[] = {(char**)&w->V, (char**)&w->W, (char**)&w->G0, (char**)&w->V64, (char**)&w->sbuf,
+                       (char**)&w->cbuf};
+    for (char** b : bufs16) TRY(dalloc(b, E * 16));
+    char** bufs8[] = {(char**)&w->th, (char**)&w->vm, (char**)&w->mth, (char**)&w->vth, (char**)&w->mvm,
+                      (char**)&w->vvm, (char**)&w->p, (char**)&w->q, (char**)&w->p64, (char**)&w->q64,
+                      (char**)&w->tmp_a, (char**)&w->tmp_b, (char**)&w->tmp_c};
+    for (char** b : bufs8) TRY(dalloc(b, E * 8));
+    TRY(dalloc((char**)&w->loss_acc, (size_t)Kp * 8));
+    TRY(dalloc((char**)&w->step_size, (size_t)Kp * 8));
+    TRY(dalloc((char**)&w->isbc2, (size_t)Kp * 8));
+    TRY(dalloc((char**)&w->yff, (size_t)Kp * 16));
+    TRY(dalloc((char**)&w->yft, (size_t)Kp * 16));
+    TRY(dalloc((char**)&w->ytt, (size_t)Kp * 16));
+    TRY(dalloc(&w->active, Kp)); TRY(dalloc(&w->iters, Kp)); TRY(dalloc(&w->status, Kp));
+    TRY(dalloc(&w->of, Kp)); TRY(dalloc(&w->ot, Kp)); TRY(dalloc(&w->bad, Kp)); TRY(dalloc(&w->cool, Kp));
+    TRY(dalloc(&w->lr, Kp)); TRY(dalloc(&w->best, Kp)); TRY(dalloc(&w->out_max, Kp));
+    TRY(dalloc(&w->out_loss, Kp)); TRY(dalloc(&w->loss64, Kp));
+    TRY(dalloc(&w->yff64, Kp)); TRY(dalloc(&w->yft64, Kp)); TRY(dalloc(&w->ytt64, Kp));
+    TRY(dalloc(&w->maxmis, Kp)); TRY(dalloc(&w->outage_dev, Kp));
+    CK(cudaMemset(w->p64, 0, E * 8));
+    CK(cudaMemset(w->q64, 0, E * 8));
+    w->cap_elems = E;
+    w->cap_cases = Kp;
+  }
+  if (stage > w->cap_stage) {
+    dfree(w->st_a); dfree(w->st_b); dfree(w->st_c);
+    w->cap_stage = 0;
+    TRY(dalloc(&w->st_a, stage));
+    TRY(dalloc(&w->st_b, stage));
+    TRY(dalloc(&w->st_c, stage));
+    w->cap_stage = stage;
+  }
+  if (!w->ent_loc && y->nnz > 0) {
+    TRY(dalloc(&w->ent_loc, y->nnz));
+    TRY(dalloc(&w->val_loc, y->nnz));
+  }
+  return DPF_OK;
+}
+
+extern "C" int dpf_workspace_create(const dpf_ybus* y, int32_t max_case, dpf_workspace** out) {
+  clear_error();
+  if (!y || !out) return fail(DPF_E_INVALID, "dpf_workspace_create: NULL argument");
+  if (!y->dev.ready) return fail(DPF_E_STATE, "Y_bus is not on the device (dpf_ybus_upload)");
+  if (max_case < 1) return fail(DPF_E_INVALID, "max_case must be >= 1");
+  dpf_workspace* w = new (std::nothrow) dpf_workspace();
+  if (!w) return fail(DPF_E_OOM, "out of host memory");
+  w->y = y;
+  dpf_default_opts(&w->opts);
+  int rc = DPF_OK;
+  do {
+    if ((rc = dalloc(&w->n_active, 1))) break;
+    cudaError_t e = cudaMallocHost((void**)&w->h_n_active, sizeof(int32_t));
+    if (e != cudaSuccess) { rc = fail(DPF_E_OOM, "cudaMallocHost: %s", cudaGetErrorString(e)); break; }
+    e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { rc = fail(DPF_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); break; }
+    const int Kp = max_case <= 16 ? pow2ceil(max_case) : (max_case + 31) / 32 * 32;
+    if ((rc = ws_reserve(w, Kp, 0))) break;
+  } while (0);
+  if (rc != DPF_OK) {
+    dpf_workspace_free(w);
+    return rc;
+  }
+  *out = w;
+  return DPF_OK;
+}
+
+extern "C" int dpf_workspace_free(dpf_workspace* w) {
+  if (!w) return DPF_OK;
+  ws_drop_graph(w);
+  ws_free_buffers(w);
+  dfree(w->n_active);
+  if (w->h_n_active) cudaFreeHost(w->h_n_active);
+  if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
+  delete w;
+  return DPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch plumbing, one instance per precision
+// ---------------------------------------------------------------------------
+template <class R>
+struct Plan {
+  using C = typename Prec<R>::C;
+  using M = typename Prec<R>::M;
+  IterArgs<R> it;
+  SchedArgs<R> sc;
+  Check64Args<M> ck;
+  ApplyArgs ap;
+  dim3 grid, block;
+  int sched_blocks;
+  bool need_volt64;
+};
+
+template <class R>
+static Plan<R> make_plan(dpf_workspace* w) {
+  using C = typename Prec<R>::C;
+  using M = typename Prec<R>::M;
+  const dpf_ybus* y = w->y;
+  const DeviceYbus& d = y->dev;
+  Plan<R> P;
+  memset(&P.it, 0, sizeof(P.it));
+  memset(&P.sc, 0, sizeof(P.sc));
+  memset(&P.ck, 0, sizeof(P.ck));
+  memset(&P.ap, 0, sizeof(P.ap));
+  IterArgs<R>& a = P.it;
+  a.N = y->n;
+  a.Kp = w->Kp;
+  a.lanes = w->lanes;
+  a.rp = d.row_ptr;
+  const int4* ent = w->use_local_y ? w->ent_loc : d.ent32;
+  const double2* v64 = w->use_local_y ? w->val_loc : d.val64;
+  if constexpr (sizeof(R) == 4) {
+    a.Y.ent = ent;
+  } else {
+    a.Y.col = d.col;
+    a.Y.val = v64;
+  }
+  a.type = d.type;
+  a.V = (C*)w->V;
+  a.W = (C*)w->W;
+  a.G0 = (C*)w->G0;
+  a.th = (M*)w->th;
+  a.vm = (M*)w->vm;
+  a.mth = (R*)w->mth;
+  a.vth = (R*)w->vth;
+  a.mvm = (R*)w->mvm;
+  a.vvm = (R*)w->vvm;
+  a.spec_per_case = w->spec_per_case ? 1 : 0;
+  if (w->spec_per_case) {
+    a.pspec = (const R*)w->p;
+    a.qspec = (const R*)w->q;
+  } else if constexpr (sizeof(R) == 4) {
+    a.pspec = (const R*)d.p32;
+    a.qspec = (const R*)d.q32;
+  } else {
+    a.pspec = (const R*)d.p64;
+    a.qspec = (const R*)d.q64;
+  }
+  a.active = w->active;
+  a.of = w->of;
+  a.ot = w->ot;
+  a.yff = (const C*)w->yff;
+  a.yft = (const C*)w->yft;
+  a.ytt = (const C*)w->ytt;
+  a.has_outage = w->has_outage ? 1 : 0;
+  a.loss_acc = (R*)w->loss_acc;
+  a.step_size = (const R*)w->step_size;
+  a.isbc2 = (const R*)w->isbc2;
+  a.beta1 = (R)w->opts.beta1;
+  a.beta2 = (R)w->opts.beta2;
+  a.eps = (R)w->opts.eps;
+  a.inv_m2 = (R)(y->m_loss > 0 ? 2.0 / y->m_loss : 0.0);
+  a.n_active = w->n_active;
+
+  SchedArgs<R>& s = P.sc;
+  s.Kp = w->Kp;
+  s.active = w->active;
+  s.iters = w->iters;
+  s.status = w->status;
+  s.loss_acc = (R*)w->loss_acc;
+  s.lr = w->lr;
+  s.best = w->best;
+  s.bad = w->bad;
+  s.cool = w->cool;
+  s.step_size = (R*)w->step_size;
+  s.isbc2 = (R*)w->isbc2;
+  s.n_active = w->n_active;
+  s.inv_m = y->m_loss > 0 ? 1.0 / y->m_loss : 0.0;
+  s.beta1 = w->opts.beta1;
+  s.beta2 = w->opts.beta2;
+  s.factor = w->opts.factor;
+  s.threshold = w->opts.threshold;
+  s.min_lr = w->opts.min_lr;
+  s.gamma = w->opts.gamma;
+  s.lr0 = w->opts.lr;
+  s.sched = w->opts.sched;
+  s.patience = w->opts.patience;
+  s.cooldown = w->opts.cooldown;
+  s.step_every = std::max(1, w->opts.step_size);
+
+  Check64Args<M>& c = P.ck;
+  c.N = y->n;
+  c.Kp = w->Kp;
+  c.lanes = w->lanes;
+  c.all_cases = 0;
+  c.rp = d.row_ptr;
+  c.col = d.col;
+  c.val = v64;
+  c.type = d.type;
+  c.th = (const M*)w->th;
+  c.vm = (const M*)w->vm;
+  P.need_volt64 = (sizeof(R) == 4);
+  c.V64 = P.need_volt64 ? w->V64 : (double2*)w->V;
+  c.pspec = w->spec_per_case ? w->p64 : d.p64;
+  c.qspec = w->spec_per_case ? w->q64 : d.q64;
+  c.spec_per_case = w->spec_per_case ? 1 : 0;
+  c.active = w->active;
+  c.of = w->of;
+  c.ot = w->ot;
+  c.yff = w->yff64;
+  c.yft = w->yft64;
+  c.ytt = w->ytt64;
+  c.has_outage = w->has_outage ? 1 : 0;
+  c.maxmis = w->maxmis;
+  c.loss64 = w->loss64;
+  c.n_active = w->n_active;
+
+  ApplyArgs& p = P.ap;
+  p.K = w->K;
+  p.Kp = w->Kp;
+  p.final_pass = 0;
+  p.tol = w->opts.tol;
+  p.inv_m = s.inv_m;
+  p.active = w->active;
+  p.status = w->status;
+  p.maxmis = w->maxmis;
+  p.loss64 = w->loss64;
+  p.out_max = w->out_max;
+  p.out_loss = w->out_loss;
+  p.n_active = w->n_active;
+
+  P.grid = dim3(w->gx, w->gy);
+  P.block = dim3(w->warps * 32);
+  P.sched_blocks = (w->Kp + 255) / 256;
+  return P;
+}
+
+template <class R>
+static int launch_check(dpf_workspace* w, cudaStream_t s, bool final_pass) {
+  Plan<R> P = make_plan<R>(w);
+  P.ck.all_cases = final_pass ? 1 : 0;
+  P.ap.final_pass = final_pass ? 1 : 0;
+  using M = typename Prec<R>::M;
+  if (P.need_volt64) k_volt64<M><<<P.grid, P.block, 0, s>>>(P.ck);
+  k_check64<M><<<P.grid, P.block, 0, s>>>(P.ck);
+  k_apply<<<1, 1024, 0, s>>>(P.ap);
+  CKLAUNCH();
+  return DPF_OK;
+}
+
+template <class R>
+static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
+  if (with_check) TRY(launch_check<R>(w, s, false));
+  Plan<R> P = make_plan<R>(w);
+  k_fwd<R><<<P.grid, P.block, 0, s>>>(P.it);
+  k_adj<R><<<P.grid, P.block, 0, s>>>(P.it);
+  k_sched<R><<<P.sched_blocks, 256, 0, s>>>(P.sc);
+  CKLAUNCH();
+  return DPF_OK;
+}
+
+static int launch_iteration_any(dpf_workspace* w, cudaStream_t s, bool with_check) {
+  return w->precision == DPF_FP64 ? launch_iteration<double>(w, s, with_check)
+                                  : launch_iteration<float>(w, s, with_check);
+}
+static int launch_check_any(dpf_workspace* w, cudaStream_t s, bool final_pass) {
+  return w->precision == DPF_FP64 ? launch_check<double>(w, s, final_pass)
+                                  : launch_check<float>(w, s, final_pass);
+}
+
+// Capture one check interval (FP64 test + check_every iterations) as a graph.
+static int build_graph(dpf_workspace* w) {
+  ws_drop_graph(w);
+  cudaStream_t cs = w->cap_stream;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int rc = DPF_OK;
+  for (int i = 0; i < w->opts.check_every && rc == DPF_OK; ++i) rc = launch_iteration_any(w, cs, i == 0);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (rc != DPF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(DPF_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&w->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    w->gexec = nullptr;
+    return fail(DPF_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  return DPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// State set-up shared by the solve and the evaluation entry points
+// ---------------------------------------------------------------------------
+struct StateIn {
+  int K;
+  bool host_io;
+  const double *va, *vm, *vmset, *p, *q;  // user layout [K][N] or NULL
+  const int32_t* outage;
+};
+
+static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
+  int lanes = (o && o->lanes > 0) ? o->lanes : std::min(32, pow2ceil(K));
+  if (lanes > 32) lanes = 32;
+  lanes = pow2ceil(lanes);
+  w->lanes = lanes;
+  w->Kp = (K + lanes - 1) / lanes * lanes;
+  w->warps = (o && o->warps > 0) ? std::min(o->warps, 32) : 8;
+  const int rpw = 32 / lanes;
+  w->gx = w->Kp / lanes;
+  const int rows_per_cta = w->warps * rpw;
+  const int gy_max = std::max(1, (w->y->n + rows_per_cta - 1) / rows_per_cta);
+  int gy;
+  if (o && o->row_blocks > 0) gy = o->row_blocks;
+  else gy = (num_sms() * 8 + w->gx - 1) / w->gx;
+  w->gy = std::max(1, std::min(std::min(gy, gy_max), 65535));
+}
+
+// Copy an input (user layout) into the internal layout buffer `dst`.
+static int to_internal(dpf_workspace* w, const double* src, bool host_io, double* stage, double* dst,
+                       cudaStream_t s) {
+  const dpf_ybus* y = w->y;
+  const double* dsrc = src;
+  if (host_io) {
+    CK(cudaMemcpyAsync(stage, src, (size_t)w->K * y->n * 8, cudaMemcpyHostToDevice, s));
+    dsrc = stage;
+  }
+  dim3 g((y->n + 31) / 32, (w->K + 31) / 32), b(32, 8);
+  k_to_internal<<<g, b, 0, s>>>(dsrc, dst, w->K, y->n, w->Kp, y->dev.iperm);
+  CKLAUNCH();
+  return DPF_OK;
+}
+
+static int to_user(dpf_workspace* w, const double* src, bool host_io, double* stage, double* dst,
+                   cudaStream_t s) {
+  const dpf_ybus* y = w->y;
+  double* ddst = host_io ? stage : dst;
+  dim3 g((y->n + 31) / 32, (w->K + 31) / 32), b(32, 8);
+  k_to_user<<<g, b, 0, s>>>(src, ddst, w->K, y->n, w->Kp, y->dev.iperm);
+  CKLAUNCH();
+  if (host_io) CK(cudaMemcpyAsync(dst, stage, (size_t)w->K * y->n * 8, cudaMemcpyDeviceToHost, s));
+  return DPF_OK;
+}
+
+// Validate an outage list against the grid (copies it to the host).
+static int check_outages(dpf_workspace* w, const int32_t* outage, bool host_io, cudaStream_t s) {
+  const dpf_ybus* y = w->y;
+  std::vector<int32_t> h(w->K);
+  if (host_io) {
+    memcpy(h.data(), outage, (size_t)w->K * 4);
+  } else {
+    CK(cudaMemcpyAsync(h.data(), outage, (size_t)w->K * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  for (int k = 0; k < w->K; ++k) {
+    const int l = h[k];
+    if (l < -1 || l >= y->m) return fail(DPF_E_INVALID, "case %d: outage index %d out of range", k, l);
+    if (l >= 0 && y->bridge[l]) return fail(DPF_E_ISLANDED, "case %d: removing branch %d islands the grid", k, l);
+  }
+  return DPF_OK;
+}
+
+template <class R>
+static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
+  const dpf_ybus* y = w->y;
+  const DeviceYbus& d = y->dev;
+  const bool hio = in.host_io;
+  // inputs to the internal layout
+  double* va_t = nullptr;
+  double* vm_t = nullptr;
+  double* vms_t = nullptr;
+  if (in.va && in.vm) {
+    TRY(to_internal(w, in.va, hio, w->st_a, w->tmp_a, s));
+    TRY(to_internal(w, in.vm, hio, w->st_b, w->tmp_b, s));
+    va_t = w->tmp_a;
+    vm_t = w->tmp_b;
+  }
+  if (in.vmset) {
+    TRY(to_internal(w, in.vmset, hio, w->st_c, w->tmp_c, s));
+    vms_t = w->tmp_c;
+  }
+  if ((in.p == nullptr) != (in.q == nullptr))
+    return fail(DPF_E_INVALID, "p_spec and q_spec must be given together");
+  w->spec_per_case = (in.p != nullptr);
+  if (w->spec_per_case) {
+    TRY(to_internal(w, in.p, hio, w->st_a, w->p64, s));
+    TRY(to_internal(w, in.q, hio, w->st_b, w->q64, s));
+  }
+  InitArgs<R> ia;
+  memset(&ia, 0, sizeof ia);
+  ia.N = y->n;
+  ia.K = w->K;
+  ia.Kp = w->Kp;
+  ia.type = d.type;
+  ia.vmset_grid = d.vmset;
+  ia.vms_t = vms_t;
+  ia.va_t = va_t;
+  ia.vm_t = vm_t;
+  ia.va_slack = y->va_slack;
+  ia.p64 = w->spec_per_case ? w->p64 : nullptr;
+  ia.q64 = w->spec_per_case ? w->q64 : nullptr;
+  ia.p = (R*)w->p;
+  ia.q = (R*)w->q;
+  ia.th = (typename Prec<R>::M*)w->th;
+  ia.vm = (typename Prec<R>::M*)w->vm;
+  ia.V = (typename Prec<R>::C*)w->V;
+  ia.mth = (R*)w->mth;
+  ia.vth = (R*)w->vth;
+  ia.mvm = (R*)w->mvm;
+  ia.vvm = (R*)w->vvm;
+  const size_t E = (size_t)y->n * w->Kp;
+  const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+  k_init<R><<<std::max(nb, 1), 256, 0, s>>>(ia);
+  CKLAUNCH();
+
+  // per-case state and N-1 corrections
+  w->has_outage = (in.outage != nullptr);
+  const int32_t* outage_dev = nullptr;
+  if (in.outage) {
+    TRY(check_outages(w, in.outage, hio, s));
+    if (hio) {
+      CK(cudaMemcpyAsync(w->outage_dev, in.outage, (size_t)w->K * 4, cudaMemcpyHostToDevice, s));
+      outage_dev = w->outage_dev;
+    } else {
+      outage_dev = in.outage;
+    }
+  }
+  CaseInitArgs<R> ca;
+  memset(&ca, 0, sizeof ca);
+  ca.K = w->K;
+  ca.Kp = w->Kp;
+  ca.outage = outage_dev;
+  ca.br_f = d.br_f;
+  ca.br_t = d.br_t;
+  ca.br_r = d.br_r;
+  ca.br_x = d.br_x;
+  ca.br_bch = d.br_bch;
+  ca.br_tap = d.br_tap;
+  ca.of = w->of;
+  ca.ot = w->ot;
+  ca.yff = (typename Prec<R>::C*)w->yff;
+  ca.yft = (typename Prec<R>::C*)w->yft;
+  ca.ytt = (typename Prec<R>::C*)w->ytt;
+  ca.yff64 = w->yff64;
+  ca.yft64 = w->yft64;
+  ca.ytt64 = w->ytt64;
+  ca.active = w->active;
+  ca.iters = w->iters;
+  ca.status = w->status;
+  ca.lr = w->lr;
+  ca.best = w->best;
+  ca.bad = w->bad;
+  ca.cool = w->cool;
+  ca.loss_acc = (R*)w->loss_acc;
+  ca.step_size = (R*)w->step_size;
+  ca.isbc2 = (R*)w->isbc2;
+  ca.maxmis = w->maxmis;
+  ca.loss64 = w->loss64;
+  ca.lr0 = w->opts.lr;
+  ca.beta1 = w->opts.beta1;
+  ca.beta2 = w->opts.beta2;
+  k_case_init<R><<<(w->Kp + 255) / 256, 256, 0, s>>>(ca);
+  CKLAUNCH();
+  CK(cudaMemcpyAsync(w->n_active, &w->K, 4, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // &w->K is host memory that may change later
+  return DPF_OK;
+}
+
+static int validate_opts(const dpf_solve_opts* o) {
+  if (!(o->lr > 0) || !(o->beta1 >= 0 && o->beta1 < 1) || !(o->beta2 >= 0 && o->beta2 < 1) || !(o->eps >= 0))
+    return fail(DPF_E_INVALID, "invalid Adam parameters");
+  if (o->sched < DPF_SCHED_CONST || o->sched > DPF_SCHED_STEP) return fail(DPF_E_INVALID, "unknown scheduler");
+  if (o->sched == DPF_SCHED_PLATEAU && (!(o->factor > 0 && o->factor < 1) || o->patience < 0 || o->cooldown < 0))
+    return fail(DPF_E_INVALID, "invalid plateau parameters");
+  if (o->sched == DPF_SCHED_STEP && (o->step_size < 1 || !(o->gamma > 0)))
+    return fail(DPF_E_INVALID, "invalid StepLR parameters");
+  if (o->max_iter < 0 || o->check_every < 1 || !(o->tol >= 0))
+    return fail(DPF_E_INVALID, "invalid max_iter / check_every / tol");
+  if (o->precision != DPF_FP32 && o->precision != DPF_FP64) return fail(DPF_E_INVALID, "unknown precision");
+  if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 32 || o->row_blocks < 0)
+    return fail(DPF_E_INVALID, "invalid launch shape");
+  return DPF_OK;
+}
+
+static int common_checks(const dpf_ybus* y, dpf_workspace* w, int K) {
+  if (!y || !w) return fail(DPF_E_INVALID, "NULL handle");
+  if (w->y != y) return fail(DPF_E_INVALID, "workspace was created for another Y_bus");
+  if (!y->dev.ready) return fail(DPF_E_STATE, "Y_bus is not on the device");
+  if (K < 1) return fail(DPF_E_INVALID, "n_case must be >= 1");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != y->dev.device) return fail(DPF_E_STATE, "current device %d differs from the Y_bus device %d", dev, y->dev.device);
+  return DPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solve
+// ---------------------------------------------------------------------------
+extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b,
+                               const dpf_solve_opts* o, void* stream) {
+  clear_error();
+  if (!b || !o) return fail(DPF_E_INVALID, "dpf_solve_begin: NULL argument");
+  TRY(common_checks(y, w, b->n_case));
+  TRY(validate_opts(o));
+  if (!o->flat_start && (!b->va || !b->vm)) return fail(DPF_E_INVALID, "warm start needs va and vm");
+  cudaStream_t s = (cudaStream_t)stream;
+  w->begun = false;
+  ws_drop_graph(w);
+  w->opts = *o;
+  w->K = b->n_case;
+  w->precision = o->precision;
+  w->use_local_y = false;
+  choose_shape(w, o, w->K);
+  TRY(ws_reserve(w, w->Kp, b->host_io ? (size_t)w->K * y->n : 0));
+  StateIn in;
+  memset(&in, 0, sizeof in);
+  in.K = w->K;
+  in.host_io = b->host_io != 0;
+  if (!o->flat_start) {
+    in.va = b->va;
+    in.vm = b->vm;
+  }
+  in.vmset = b->vm_set;
+  in.p = b->p_spec;
+  in.q = b->q_spec;
+  in.outage = b->outage;
+  TRY(w->precision == DPF_FP64 ? init_state<double>(w, in, s) : init_state<float>(w, in, s));
+  w->t_done = 0;
+  w->begun = true;
+  return DPF_OK;
+}
+
+extern "C" int dpf_solve_iterate(dpf_workspace* w, int32_t n_iter, void* stream) {
+  clear_error();
+  if (!w || !w->begun) return fail(DPF_E_STATE, "dpf_solve_iterate before dpf_solve_begin");
+  if (n_iter < 0) return fail(DPF_E_INVALID, "n_iter must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  n_iter = std::min(n_iter, w->opts.max_iter - w->t_done);
+  const int ce = w->opts.check_every;
+  while (n_iter > 0) {
+    if (w->opts.use_graph && w->t_done % ce == 0 && n_iter >= ce) {
+      if (!w->gexec) TRY(build_graph(w));
+      CK(cudaGraphLaunch(w->gexec, s));
+      w->t_done += ce;
+      n_iter -= ce;
+    } else {
+      TRY(launch_iteration_any(w, s, w->t_done % ce == 0));
+      w->t_done += 1;
+      n_iter -= 1;
+    }
+  }
+  return DPF_OK;
+}
+
+extern "C" int dpf_active_count(dpf_workspace* w, int32_t* n_active, void* stream) {
+  if (!w || !n_active) return fail(DPF_E_INVALID, "dpf_active_count: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(w->h_n_active, w->n_active, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *n_active = *w->h_n_active;
+  return DPF_OK;
+}
+
+extern "C" int dpf_iterations_done(const dpf_workspace* w, int32_t* n_iter) {
+  if (!w || !n_iter) return fail(DPF_E_INVALID, "dpf_iterations_done: NULL argument");
+  *n_iter = w->t_done;
+  return DPF_OK;
+}
+
+extern "C" int dpf_solve_end(dpf_workspace* w, const dpf_batch* b, void* stream) {
+  clear_error();
+  if (!w || !w->begun) return fail(DPF_E_STATE, "dpf_solve_end before dpf_solve_begin");
+  if (!b || b->n_case != w->K) return fail(DPF_E_INVALID, "dpf_solve_end: batch differs from dpf_solve_begin");
+  cudaStream_t s = (cudaStream_t)stream;
+  const dpf_ybus* y = w->y;
+  const bool hio = b->host_io != 0;
+  TRY(launch_check_any(w, s, true));
+  const size_t E = (size_t)y->n * w->Kp;
+  const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+  if (b->va || b->vm) {
+    if (w->precision == DPF_FP64) {
+      k_master64<double><<<nb, 256, 0, s>>>((const double*)w->th, w->tmp_a, E);
+      k_master64<double><<<nb, 256, 0, s>>>((const double*)w->vm, w->tmp_b, E);
+    } else {
+      k_master64<float2><<<nb, 256, 0, s>>>((const float2*)w->th, w->tmp_a, E);
+      k_master64<float2><<<nb, 256, 0, s>>>((const float2*)w->vm, w->tmp_b, E);
+    }
+    CKLAUNCH();
+    if (b->va) TRY(to_user(w, w->tmp_a, hio, w->st_a, b->va, s));
+    if (b->vm) TRY(to_user(w, w->tmp_b, hio, w->st_b, b->vm, s));
+  }
+  const cudaMemcpyKind kind = hio ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (b->iters) CK(cudaMemcpyAsync(b->iters, w->iters, (size_t)w->K * 4, kind, s));
+  if (b->status) CK(cudaMemcpyAsync(b->status, w->status, (size_t)w->K * 4, kind, s));
+  if (b->max_mismatch) CK(cudaMemcpyAsync(b->max_mismatch, w->out_max, (size_t)w->K * 8, kind, s));
+  if (b->loss) CK(cudaMemcpyAsync(b->loss, w->out_loss, (size_t)w->K * 8, kind, s));
+  if (hio) CK(cudaStreamSynchronize(s));
+  w->begun = false;
+  return DPF_OK;
+}
+
+static int solve_batched(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b, const dpf_solve_opts* o,
+                         cudaStream_t s) {
+  TRY(dpf_solve_begin(y, w, b, o, s));
+  const int ce = o->check_every;
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  bool pending = false;
+  int rc = DPF_OK;
+  while (w->t_done < o->max_iter) {
+    const int n = std::min(ce - (w->t_done % ce), o->max_iter - w->t_done);
+    if ((rc = dpf_solve_iterate(w, n, s))) break;
+    // non-blocking poll of the active count, one interval behind
+    if (pending && cudaEventQuery(ev) == cudaSuccess) {
+      pending = false;
+      if (*w->h_n_active == 0) break;
+    }
+    if (!pending) {
+      cudaMemcpyAsync(w->h_n_active, w->n_active, 4, cudaMemcpyDeviceToHost, s);
+      cudaEventRecord(ev, s);
+      pending = true;
+    }
+  }
+  if (pending) cudaEventSynchronize(ev);
+  cudaEventDestroy(ev);
+  if (rc != DPF_OK) return rc;
+  return dpf_solve_end(w, b, s);
+}
+
+// The plain form: one case at a time, one iteration per host round trip.
+static int solve_plain(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b, const dpf_solve_opts* o,
+                       cudaStream_t s) {
+  dpf_solve_opts po = *o;
+  po.check_every = 1;
+  po.use_graph = 0;
+  po.lanes = 1;
+  const size_t N = (size_t)y->n;
+  for (int k = 0; k < b->n_case; ++k) {
+    dpf_batch one;
+    memset(&one, 0, sizeof one);
+    one.n_case = 1;
+    one.host_io = b->host_io;
+    auto off = [&](const double* p) { return p ? p + (size_t)k * N : nullptr; };
+    one.p_spec = off(b->p_spec);
+    one.q_spec = off(b->q_spec);
+    one.vm_set = off(b->vm_set);
+    one.outage = b->outage ? b->outage + k : nullptr;
+    one.va = b->va ? b->va + (size_t)k * N : nullptr;
+    one.vm = b->vm ? b->vm + (size_t)k * N : nullptr;
+    one.iters = b->iters ? b->iters + k : nullptr;
+    one.status = b->status ? b->status + k : nullptr;
+    one.max_mismatch = b->max_mismatch ? b->max_mismatch + k : nullptr;
+    one.loss = b->loss ? b->loss + k : nullptr;
+    TRY(dpf_solve_begin(y, w, &one, &po, s));
+    while (w->t_done < po.max_iter) {
+      TRY(dpf_solve_iterate(w, 1, s));
+      // host stop test of Alg. 1 (the FP64 test runs at the start of each iteration)
+      int32_t act = 0;
+      TRY(dpf_active_count(w, &act, s));
+      if (act == 0) break;
+    }
+    TRY(dpf_solve_end(w, &one, s));
+  }
+  return DPF_OK;
+}
+
+extern "C" int dpf_solve_batch(const dpf_ybus* y, dpf_workspace* ws, const dpf_batch* b,
+                               const dpf_solve_opts* o, void* stream) {
+  clear_error();
+  if (!y || !b || !o) return fail(DPF_E_INVALID, "dpf_solve_batch: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  dpf_workspace* w = ws;
+  if (!w) TRY(dpf_workspace_create(y, b->n_case, &w));
+  const int rc = o->plain ? solve_plain(y, w, b, o, s) : solve_batched(y, w, b, o, s);
+  if (!ws) {
+    cudaStreamSynchronize(s);
+    dpf_workspace_free(w);
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Evaluation entry points
+// ---------------------------------------------------------------------------
+static int eval_setup(const dpf_ybus* y, dpf_workspace* w, int K, int precision, const double* va,
+                      const double* vm, const double* p, const double* q, const int32_t* outage,
+                      cudaStream_t s) {
+  TRY(common_checks(y, w, K));
+  if (precision != DPF_FP32 && precision != DPF_FP64) return fail(DPF_E_INVALID, "unknown precision");
+  if (!va || !vm) return fail(DPF_E_INVALID, "va and vm are required");
+  w->begun = false;
+  ws_drop_graph(w);
+  dpf_default_opts(&w->opts);
+  w->opts.precision = precision;
+  w->precision = precision;
+  w->K = K;
+  choose_shape(w, nullptr, K);
+  TRY(ws_reserve(w, w->Kp, 0));
+  StateIn in;
+  memset(&in, 0, sizeof in);
+  in.K = K;
+  in.va = va;
+  in.vm = vm;
+  in.p = p;
+  in.q = q;
+  in.outage = outage;
+  return precision == DPF_FP64 ? init_state<double>(w, in, s) : init_state<float>(w, in, s);
+}
+
+template <class R>
+static int power_impl(dpf_workspace* w, double* p_calc, double* q_calc, cudaStream_t s) {
+  Plan<R> P = make_plan<R>(w);
+  P.it.sbuf = (typename Prec<R>::C*)w->sbuf;
+  P.it.loss_acc = nullptr;
+  P.it.n_active = nullptr;
+  k_fwd<R><<<P.grid, P.block, 0, s>>>(P.it);
+  const size_t E = (size_t)w->y->n * w->Kp;
+  const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+  k_widen<R><<<nb, 256, 0, s>>>((const R*)w->sbuf, w->tmp_a, E, 2, 1.0);
+  k_widen<R><<<nb, 256, 0, s>>>((const R*)w->sbuf + 1, w->tmp_b, E, 2, 1.0);
+  CKLAUNCH();
+  if (p_calc) TRY(to_user(w, w->tmp_a, false, nullptr, p_calc, s));
+  if (q_calc) TRY(to_user(w, w->tmp_b, false, nullptr, q_calc, s));
+  return DPF_OK;
+}
+
+extern "C" int dpf_power(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* va,
+                         const double* vm, const int32_t* outage, int32_t precision, double* p_calc,
+                         double* q_calc, void* stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(eval_setup(y, w, n_case, precision, va, vm, nullptr, nullptr, outage, s));
+  return precision == DPF_FP64 ? power_impl<double>(w, p_calc, q_calc, s) : power_impl<float>(w, p_calc, q_calc, s);
+}
+
+template <class R>
+static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, double* d_vm, double* d_p,
+                              double* d_q, double* d_g, double* d_b, double* d_bch, cudaStream_t s) {
+  using C = typename Prec<R>::C;
+  const dpf_ybus* y = w->y;
+  Plan<R> P = make_plan<R>(w);
+  P.it.cbuf = (C*)w->cbuf;
+  P.it.n_active = nullptr;
+  k_fwd<R><<<P.grid, P.block, 0, s>>>(P.it);
+  P.it.gva = (R*)w->tmp_c;  // reuse as gradient scratch: [N][Kp] R each
+  P.it.gvm = (R*)w->sbuf;
+  k_adj<R><<<P.grid, P.block, 0, s>>>(P.it);
+  CKLAUNCH();
+  const size_t E = (size_t)y->n * w->Kp;
+  const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+  if (d_va) {
+    k_widen<R><<<nb, 256, 0, s>>>((const R*)w->tmp_c, w->tmp_a, E, 1, 1.0);
+    CKLAUNCH();
+    TRY(to_user(w, w->tmp_a, false, nullptr, d_va, s));
+  }
+  if (d_vm) {
+    k_widen<R><<<nb, 256, 0, s>>>((const R*)w->sbuf, w->tmp_a, E, 1, 1.0);
+    CKLAUNCH();
+    TRY(to_user(w, w->tmp_a, false, nullptr, d_vm, s));
+  }
+  if (d_p) {
+    k_widen<R><<<nb, 256, 0, s>>>((const R*)w->cbuf, w->tmp_a, E, 2, -1.0);
+    CKLAUNCH();
+    TRY(to_user(w, w->tmp_a, false, nullptr, d_p, s));
+  }
+  if (d_q) {
+    k_widen<R><<<nb, 256, 0, s>>>((const R*)w->cbuf + 1, w->tmp_a, E, 2, -1.0);
+    CKLAUNCH();
+    TRY(to_user(w, w->tmp_a, false, nullptr, d_q, s));
+  }
+  if (d_g || d_b || d_bch) {
+    if (d_g) CK(cudaMemsetAsync(d_g, 0, (size_t)y->m * 8, s));
+    if (d_b) CK(cudaMemsetAsync(d_b, 0, (size_t)y->m * 8, s));
+    if (d_bch) CK(cudaMemsetAsync(d_bch, 0, (size_t)y->m * 8, s));
+    EdgeArgs<R> ea;
+    memset(&ea, 0, sizeof ea);
+    ea.M = y->m;
+    ea.K = w->K;
+    ea.Kp = w->Kp;
+    ea.lanes = w->lanes;
+    ea.br_f = y->dev.br_f;
+    ea.br_t = y->dev.br_t;
+    ea.tap = y->dev.br_tap;
+    ea.V = (const C*)w->V;
+    ea.W = (const C*)w->W;
+    ea.d_g = d_g;
+    ea.d_b = d_b;
+    ea.d_bch = d_bch;
+    const int rpw = 32 / w->lanes;
+    const int gy = std::max(1, std::min((y->m + w->warps * rpw - 1) / (w->warps * rpw), 65535));
+    k_edge_grad<R><<<dim3(w->gx, gy), P.block, 0, s>>>(ea);
+    CKLAUNCH();
+  }
+  if (loss) {
+    TRY(launch_check<R>(w, s, true));
+    CK(cudaMemcpyAsync(loss, w->out_loss, (size_t)w->K * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  return DPF_OK;
+}
+
+extern "C" int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* va,
+                                 const double* vm, const double* p_spec, const double* q_spec,
+                                 const int32_t* outage, const double* g_series, const double* b_series,
+                                 int32_t precision, double* loss, double* d_va, double* d_vm, double* d_p,
+                                 double* d_q, double* d_g, double* d_b, double* d_bch, void* stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((g_series == nullptr) != (b_series == nullptr))
+    return fail(DPF_E_INVALID, "g_series and b_series must be given together");
+  TRY(eval_setup(y, w, n_case, precision, va, vm, p_spec, q_spec, outage, s));
+  if (g_series) {
+    YValArgs ya;
+    ya.N = y->n;
+    ya.rp = y->dev.row_ptr;
+    ya.col = y->dev.col;
+    ya.ebr = y->dev.ebr;
+    ya.br_f = y->dev.br_f;
+    ya.g = g_series;
+    ya.b = b_series;
+    ya.bch = y->dev.br_bch;
+    ya.tap = y->dev.br_tap;
+    ya.ent32 = w->ent_loc;
+    ya.val64 = w->val_loc;
+    k_ybus_values<<<(y->n + 127) / 128, 128, 0, s>>>(ya);
+    CKLAUNCH();
+    w->use_local_y = true;
+  }
+  const int rc = precision == DPF_FP64
+                     ? loss_backward_impl<double>(w, loss, d_va, d_vm, d_p, d_q, d_g, d_b, d_bch, s)
+                     : loss_backward_impl<float>(w, loss, d_va, d_vm, d_p, d_q, d_g, d_b, d_bch, s);
+  w->use_local_y = false;
+  return rc;
+}

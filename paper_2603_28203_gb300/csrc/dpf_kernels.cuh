@@ -1,0 +1,819 @@
+// Device kernels of the DPF hot path (sm_103a).
+//
+// Layout: per-case state is stored case-minor, element (bus i, case k) at
+// i*Kp + k, with Kp the case count padded to the lane group.  A warp covers
+// `lanes` consecutive cases of 32/lanes consecutive buses, so for a batch of
+// >= 32 cases all 32 lanes work on one bus: the Y_bus row is read once per
+// warp (a broadcast 16-byte load per nonzero) and every gather of a
+// neighbour's voltage is one coalesced 256-byte (FP32) access.  For a single
+// case (lanes = 1) the same code is a thread-per-row CSR SpMV.
+//
+// One DPF iteration (Alg. 1) is three launches:
+//   k_fwd   I = Y V (+ N-1 correction), S = V conj(I), dP/dQ, loss partials,
+//           w = c conj(V), g0 = conj(c) S      (Eq. powerbalance, Alg. 1)
+//   k_adj   z = Y w (+ N-1 correction), h = g0 + V z,
+//           dL/dtheta = -Im h, dL/d|V| = Re h / |V|, Adam update, new V
+//   k_sched per-case loss, scheduler (ReduceLROnPlateau / StepLR), bias terms
+// and every `check_every` iterations the FP64 test k_volt64 + k_check64 +
+// k_apply (max |f| per case <= tol -> the case stops).
+//
+// The adjoint identity used by k_adj: with c_i = (2/m)(dP_i + j dQ_i),
+// dL = Re sum_i conj(c_i) dS_i and dS_i = dV_i conj(I_i) + V_i conj((Y dV)_i),
+// so dL = Re sum_k dV_k (conj(c_k I_k) + (Y^T w)_k) with w = c conj(V).  Y is
+// symmetric (no phase shifters), and dV_k = V_k (j dtheta_k + d|V_k|/|V_k|).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dpf {
+
+enum { BUS_PQ = 0, BUS_PV = 1, BUS_SLACK = 2 };
+enum { CASE_CONVERGED = 0, CASE_MAX_ITER = 1, CASE_DIVERGED = 2 };
+enum { SCHED_CONST = 0, SCHED_PLATEAU = 1, SCHED_STEP = 2 };
+
+template <class R> struct Prec;
+template <> struct Prec<float> { using C = float2; using M = float2; };   // M: (hi, lo) master
+template <> struct Prec<double> { using C = double2; using M = double; };
+
+__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float sqrtT(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqrtT(double a) { return sqrt(a); }
+
+// acc += y * v (complex)
+template <class C> __device__ __forceinline__ void cfma(C& acc, const C y, const C v) {
+  acc.x = fmaT(y.x, v.x, fmaT(-y.y, v.y, acc.x));
+  acc.y = fmaT(y.x, v.y, fmaT(y.y, v.x, acc.y));
+}
+// acc -= y * v (complex)
+template <class C> __device__ __forceinline__ void cfms(C& acc, const C y, const C v) {
+  acc.x = fmaT(-y.x, v.x, fmaT(y.y, v.y, acc.x));
+  acc.y = fmaT(-y.x, v.y, fmaT(-y.y, v.x, acc.y));
+}
+
+// ---- master values ---------------------------------------------------------
+// FP32 mode keeps theta and |V| as an unevaluated sum hi + lo of two floats
+// (~48 significant bits) and updates them with an error-free two-sum, so the
+// per-iteration path needs no FP64 instruction.
+__device__ __forceinline__ double mval(float2 m) { return (double)m.x + (double)m.y; }
+__device__ __forceinline__ double mval(double m) { return m; }
+__device__ __forceinline__ float mwork(float2 m) { return m.x + m.y; }
+__device__ __forceinline__ double mwork(double m) { return m; }
+
+__device__ __forceinline__ float2 msub(float2 a, float d) {
+  const float nd = -d;
+  const float s = __fadd_rn(a.x, nd);
+  const float bp = __fsub_rn(s, a.x);
+  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bp)), __fsub_rn(nd, bp));
+  const float lo = __fadd_rn(a.y, err);
+  const float hi = __fadd_rn(s, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+}
+__device__ __forceinline__ double msub(double a, double d) { return a - d; }
+
+template <class M> __device__ __forceinline__ M mfrom(double v);
+template <> __device__ __forceinline__ float2 mfrom<float2>(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+template <> __device__ __forceinline__ double mfrom<double>(double v) { return v; }
+
+// V = |V| e^{j theta} in working precision.  FP32: sincos of the high word,
+// first-order correction for the low word (|lo| <= 2^-24 |hi|).
+__device__ __forceinline__ float2 volt(float2 th, float2 vm) {
+  float s, c;
+  sincosf(th.x, &s, &c);
+  const float s2 = fmaf(th.y, c, s), c2 = fmaf(-th.y, s, c);
+  const float m = vm.x + vm.y;
+  return make_float2(m * c2, m * s2);
+}
+__device__ __forceinline__ double2 volt(double th, double vm) {
+  double s, c;
+  sincos(th, &s, &c);
+  return make_double2(vm * c, vm * s);
+}
+// V in FP64 from a master value (the convergence test).
+template <class M> __device__ __forceinline__ double2 volt64(M th, M vm) {
+  double s, c;
+  sincos(mval(th), &s, &c);
+  const double m = mval(vm);
+  return make_double2(m * c, m * s);
+}
+
+// ---- Y_bus views -----------------------------------------------------------
+template <class R> struct YView;
+template <> struct YView<float> {
+  const int4* __restrict__ ent;  // {col, re bits, im bits, 0}
+  __device__ __forceinline__ void get(int p, int& j, float2& y) const {
+    const int4 e = __ldg(ent + p);
+    j = e.x;
+    y = make_float2(__int_as_float(e.y), __int_as_float(e.z));
+  }
+};
+template <> struct YView<double> {
+  const int32_t* __restrict__ col;
+  const double2* __restrict__ val;
+  __device__ __forceinline__ void get(int p, int& j, double2& y) const {
+    j = __ldg(col + p);
+    y = __ldg(val + p);
+  }
+};
+
+// ---- thread -> (case, rows) map ------------------------------------------
+struct Map {
+  int k, row0, rstride, kl, rsub;
+};
+__device__ __forceinline__ Map thread_map(int lanes) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int rpw = 32 / lanes;
+  Map mp;
+  mp.kl = lane & (lanes - 1);
+  mp.rsub = lane / lanes;
+  mp.k = blockIdx.x * lanes + mp.kl;
+  mp.row0 = (blockIdx.y * wpb + warp) * rpw + mp.rsub;
+  mp.rstride = gridDim.y * wpb * rpw;
+  return mp;
+}
+
+// Sum `v` over all threads of the CTA that share a case, then one atomic per
+// case per CTA.  Every thread of the CTA must call it.
+template <class R>
+__device__ __forceinline__ void case_sum_atomic(R v, int lanes, R* out, int Kp) {
+  __shared__ R red[32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int off = 16; off >= lanes; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (lane < lanes) red[warp][lane] = v;
+  __syncthreads();
+  if (threadIdx.x < lanes) {
+    R s = 0;
+    for (int w = 0; w < wpb; ++w) s += red[w][threadIdx.x];
+    const int k = blockIdx.x * lanes + threadIdx.x;
+    if (k < Kp && s != R(0)) atomicAdd(out + k, s);
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v) {
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+// Per-case max and sum over the CTA (convergence test), one atomic each.
+__device__ __forceinline__ void case_max_sum_atomic(double mx, double sq, int lanes,
+                                                    unsigned long long* omax, double* osum, int Kp) {
+  __shared__ double rmax[32][32];
+  __shared__ double rsum[32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int off = 16; off >= lanes; off >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    sq += __shfl_xor_sync(0xffffffffu, sq, off);
+  }
+  if (lane < lanes) { rmax[warp][lane] = mx; rsum[warp][lane] = sq; }
+  __syncthreads();
+  if (threadIdx.x < lanes) {
+    double m = 0.0, s = 0.0;
+    for (int w = 0; w < wpb; ++w) { m = fmax(m, rmax[w][threadIdx.x]); s += rsum[w][threadIdx.x]; }
+    const int k = blockIdx.x * lanes + threadIdx.x;
+    if (k < Kp) {
+      atomic_max_nonneg(omax + k, m);
+      if (s != 0.0) atomicAdd(osum + k, s);
+    }
+  }
+}
+
+// ---- arguments -------------------------------------------------------------
+template <class R> struct IterArgs {
+  using C = typename Prec<R>::C;
+  using M = typename Prec<R>::M;
+  int N, Kp, lanes;
+  const int32_t* __restrict__ rp;
+  YView<R> Y;
+  const uint8_t* __restrict__ type;
+  C* V;
+  C* W;
+  C* G0;
+  M* th;
+  M* vm;
+  R* mth;
+  R* vth;
+  R* mvm;
+  R* vvm;
+  const R* pspec;
+  const R* qspec;
+  int spec_per_case;
+  const int32_t* active;
+  const int32_t* of;
+  const int32_t* ot;
+  const C* yff;
+  const C* yft;
+  const C* ytt;
+  int has_outage;
+  R* loss_acc;
+  const R* step_size;
+  const R* isbc2;
+  R beta1, beta2, eps, inv_m2;
+  const int32_t* n_active;
+  // optional outputs (evaluation entry points); NULL in the solve loop
+  C* sbuf;   // S_calc
+  C* cbuf;   // c = (2/m)(dP + j dQ)
+  R* gva;    // gradient mode of k_adj: write dL/dtheta, dL/d|V| instead of stepping
+  R* gvm;
+};
+
+// ---- forward: SpMV + power + mismatch + loss --------------------------------
+template <class R>
+__global__ void __launch_bounds__(1024) k_fwd(IterArgs<R> a) {
+  using C = typename Prec<R>::C;
+  if (a.n_active && *a.n_active == 0) return;
+  const Map mp = thread_map(a.lanes);
+  const int k = mp.k;
+  const bool on = (k < a.Kp) && a.active[k];
+  R acc = 0;
+  if (on) {
+    int of = -1, ot = -1;
+    C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
+    if (a.has_outage) {
+      of = a.of[k];
+      ot = a.ot[k];
+      if (of >= 0) { yff = a.yff[k]; yft = a.yft[k]; ytt = a.ytt[k]; }
+    }
+    const size_t Kp = (size_t)a.Kp;
+    const C* __restrict__ V = a.V;
+    for (int i = mp.row0; i < a.N; i += mp.rstride) {
+      const size_t e = (size_t)i * Kp + k;
+      C I = mkc(R(0), R(0));
+      const int p1 = __ldg(a.rp + i + 1);
+      for (int p = __ldg(a.rp + i); p < p1; ++p) {
+        int j;
+        C y;
+        a.Y.get(p, j, y);
+        cfma(I, y, V[(size_t)j * Kp + k]);
+      }
+      const C vi = V[e];
+      if (i == of) {
+        cfms(I, yff, vi);
+        cfms(I, yft, V[(size_t)ot * Kp + k]);
+      } else if (i == ot) {
+        cfms(I, yft, V[(size_t)of * Kp + k]);
+        cfms(I, ytt, vi);
+      }
+      const R P = vi.x * I.x + vi.y * I.y;
+      const R Q = vi.y * I.x - vi.x * I.y;
+      const int ty = __ldg(a.type + i);
+      const size_t si = a.spec_per_case ? e : (size_t)i;
+      const R dP = (ty != BUS_SLACK) ? P - a.pspec[si] : R(0);
+      const R dQ = (ty == BUS_PQ) ? Q - a.qspec[si] : R(0);
+      const R ca = a.inv_m2 * dP, cb = a.inv_m2 * dQ;
+      a.W[e] = mkc(ca * vi.x + cb * vi.y, cb * vi.x - ca * vi.y);
+      a.G0[e] = mkc(ca * P + cb * Q, ca * Q - cb * P);
+      if (a.sbuf) a.sbuf[e] = mkc(P, Q);
+      if (a.cbuf) a.cbuf[e] = mkc(ca, cb);
+      acc += dP * dP + dQ * dQ;
+    }
+  }
+  if (a.loss_acc) case_sum_atomic(acc, a.lanes, a.loss_acc, a.Kp);
+}
+
+// ---- adjoint SpMV + gradient + Adam ----------------------------------------
+template <class R>
+__global__ void __launch_bounds__(1024) k_adj(IterArgs<R> a) {
+  using C = typename Prec<R>::C;
+  using M = typename Prec<R>::M;
+  if (a.n_active && *a.n_active == 0) return;
+  const Map mp = thread_map(a.lanes);
+  const int k = mp.k;
+  if (k >= a.Kp || !a.active[k]) return;
+  int of = -1, ot = -1;
+  C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
+  if (a.has_outage) {
+    of = a.of[k];
+    ot = a.ot[k];
+    if (of >= 0) { yff = a.yff[k]; yft = a.yft[k]; ytt = a.ytt[k]; }
+  }
+  const bool grad_only = (a.gva != nullptr);
+  R step = 0, isb = 1;
+  if (!grad_only) { step = a.step_size[k]; isb = a.isbc2[k]; }
+  const R b1 = a.beta1, b2 = a.beta2, eps = a.eps;
+  const size_t Kp = (size_t)a.Kp;
+  const C* __restrict__ W = a.W;
+  for (int i = mp.row0; i < a.N; i += mp.rstride) {
+    const size_t e = (size_t)i * Kp + k;
+    const int ty = __ldg(a.type + i);
+    if (ty == BUS_SLACK) {
+      if (grad_only) { a.gva[e] = R(0); a.gvm[e] = R(0); }
+      continue;
+    }
+    C z = mkc(R(0), R(0));
+    const int p1 = __ldg(a.rp + i + 1);
+    for (int p = __ldg(a.rp + i); p < p1; ++p) {
+      int j;
+      C y;
+      a.Y.get(p, j, y);
+      cfma(z, y, W[(size_t)j * Kp + k]);
+    }
+    if (i == of) {
+      cfms(z, yff, W[e]);
+      cfms(z, yft, W[(size_t)ot * Kp + k]);
+    } else if (i == ot) {
+      cfms(z, yft, W[(size_t)of * Kp + k]);
+      cfms(z, ytt, W[e]);
+    }
+    M th = a.th[e];
+    M vm = a.vm[e];
+    const C vi = volt(th, vm);
+    const C g0 = a.G0[e];
+    const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
+    const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
+    const R g_th = -hi;
+    const R g_vm = (ty == BUS_PQ) ? hr / mwork(vm) : R(0);
+    if (grad_only) {
+      a.gva[e] = g_th;
+      a.gvm[e] = g_vm;
+      continue;
+    }
+    {  // Adam on theta (pv and pq buses)
+      R m1 = a.mth[e], v1 = a.vth[e];
+      m1 = b1 * m1 + (R(1) - b1) * g_th;
+      v1 = b2 * v1 + (R(1) - b2) * g_th * g_th;
+      a.mth[e] = m1;
+      a.vth[e] = v1;
+      th = msub(th, step * m1 / (sqrtT(v1) * isb + eps));
+      a.th[e] = th;
+    }
+    if (ty == BUS_PQ) {  // Adam on |V| (pq buses)
+      R m1 = a.mvm[e], v1 = a.vvm[e];
+      m1 = b1 * m1 + (R(1) - b1) * g_vm;
+      v1 = b2 * v1 + (R(1) - b2) * g_vm * g_vm;
+      a.mvm[e] = m1;
+      a.vvm[e] = v1;
+      vm = msub(vm, step * m1 / (sqrtT(v1) * isb + eps));
+      a.vm[e] = vm;
+    }
+    a.V[e] = volt(th, vm);
+  }
+}
+
+// ---- scheduler (one thread per case) ---------------------------------------
+template <class R> struct SchedArgs {
+  int Kp;
+  int32_t* active;
+  int32_t* iters;
+  int32_t* status;
+  R* loss_acc;
+  double* lr;
+  double* best;
+  int32_t* bad;
+  int32_t* cool;
+  R* step_size;
+  R* isbc2;
+  int32_t* n_active;
+  double inv_m, beta1, beta2, factor, threshold, min_lr, gamma, lr0;
+  int sched, patience, cooldown, step_every;
+};
+
+template <class R>
+__global__ void k_sched(SchedArgs<R> a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.Kp || !a.active[k]) return;
+  const double L = (double)a.loss_acc[k] * a.inv_m;  // MSE of the iterate the step came from
+  a.loss_acc[k] = R(0);
+  const int it = a.iters[k] + 1;
+  a.iters[k] = it;
+  if (!isfinite(L)) {
+    a.status[k] = CASE_DIVERGED;
+    a.active[k] = 0;
+    atomicSub(a.n_active, 1);
+    return;
+  }
+  double lr = a.lr[k];
+  if (a.sched == SCHED_PLATEAU) {
+    double best = a.best[k];
+    int bad = a.bad[k], cool = a.cool[k];
+    if (L < best * (1.0 - a.threshold)) { best = L; bad = 0; }
+    else bad += 1;
+    if (cool > 0) { cool -= 1; bad = 0; }
+    if (bad > a.patience) {
+      const double nl = fmax(lr * a.factor, a.min_lr);
+      if (lr - nl > 1e-8) lr = nl;
+      cool = a.cooldown;
+      bad = 0;
+    }
+    a.best[k] = best;
+    a.bad[k] = bad;
+    a.cool[k] = cool;
+  } else if (a.sched == SCHED_STEP) {
+    lr = a.lr0 * pow(a.gamma, (double)(it / a.step_every));
+  }
+  a.lr[k] = lr;
+  const double t1 = (double)(it + 1);  // Adam step number of the next update
+  a.step_size[k] = (R)(lr / (1.0 - pow(a.beta1, t1)));
+  a.isbc2[k] = (R)(1.0 / sqrt(1.0 - pow(a.beta2, t1)));
+}
+
+// ---- FP64 convergence test --------------------------------------------------
+template <class M> struct Check64Args {
+  int N, Kp, lanes, all_cases;
+  const int32_t* __restrict__ rp;
+  const int32_t* __restrict__ col;
+  const double2* __restrict__ val;
+  const uint8_t* __restrict__ type;
+  const M* th;
+  const M* vm;
+  double2* V64;
+  const double* pspec;
+  const double* qspec;
+  int spec_per_case;
+  const int32_t* active;
+  const int32_t* of;
+  const int32_t* ot;
+  const double2* yff;
+  const double2* yft;
+  const double2* ytt;
+  int has_outage;
+  unsigned long long* maxmis;
+  double* loss64;
+  const int32_t* n_active;
+};
+
+// V64 = |V| e^{j theta} from the master state (FP64 sincos).
+template <class M>
+__global__ void __launch_bounds__(1024) k_volt64(Check64Args<M> a) {
+  if (!a.all_cases && *a.n_active == 0) return;
+  const Map mp = thread_map(a.lanes);
+  const int k = mp.k;
+  if (k >= a.Kp || !(a.all_cases || a.active[k])) return;
+  for (int i = mp.row0; i < a.N; i += mp.rstride) {
+    const size_t e = (size_t)i * a.Kp + k;
+    a.V64[e] = volt64(a.th[e], a.vm[e]);
+  }
+}
+
+template <class M>
+__global__ void __launch_bounds__(1024) k_check64(Check64Args<M> a) {
+  if (!a.all_cases && *a.n_active == 0) return;
+  const Map mp = thread_map(a.lanes);
+  const int k = mp.k;
+  const bool on = (k < a.Kp) && (a.all_cases || a.active[k]);
+  double mx = 0.0, sq = 0.0;
+  if (on) {
+    int of = -1, ot = -1;
+    double2 yff = make_double2(0, 0), yft = yff, ytt = yff;
+    if (a.has_outage) {
+      of = a.of[k];
+      ot = a.ot[k];
+      if (of >= 0) { yff = a.yff[k]; yft = a.yft[k]; ytt = a.ytt[k]; }
+    }
+    const size_t Kp = (size_t)a.Kp;
+    const double2* __restrict__ V = a.V64;
+    for (int i = mp.row0; i < a.N; i += mp.rstride) {
+      const size_t e = (size_t)i * Kp + k;
+      double2 I = make_double2(0.0, 0.0);
+      const int p1 = __ldg(a.rp + i + 1);
+      for (int p = __ldg(a.rp + i); p < p1; ++p)
+        cfma(I, __ldg(a.val + p), V[(size_t)__ldg(a.col + p) * Kp + k]);
+      const double2 vi = V[e];
+      if (i == of) {
+        cfms(I, yff, vi);
+        cfms(I, yft, V[(size_t)ot * Kp + k]);
+      } else if (i == ot) {
+        cfms(I, yft, V[(size_t)of * Kp + k]);
+        cfms(I, ytt, vi);
+      }
+      const double P = vi.x * I.x + vi.y * I.y;
+      const double Q = vi.y * I.x - vi.x * I.y;
+      const int ty = __ldg(a.type + i);
+      const size_t si = a.spec_per_case ? e : (size_t)i;
+      const double dP = (ty != BUS_SLACK) ? P - a.pspec[si] : 0.0;
+      const double dQ = (ty == BUS_PQ) ? Q - a.qspec[si] : 0.0;
+      // a NaN mismatch is recorded as +inf so that it survives the max reduction
+      const double am = (isnan(dP) || isnan(dQ)) ? __longlong_as_double(0x7ff0000000000000LL)
+                                                 : fmax(fabs(dP), fabs(dQ));
+      mx = fmax(mx, am);
+      sq += dP * dP + dQ * dQ;
+    }
+  }
+  case_max_sum_atomic(mx, sq, a.lanes, a.maxmis, a.loss64, a.Kp);
+}
+
+// Apply a convergence test (single CTA): stop converged cases, record their
+// mismatch, reset the accumulators and recount the active cases.  With
+// `final_pass` every real case gets its outputs and final status.
+struct ApplyArgs {
+  int K, Kp, final_pass;
+  double tol, inv_m;
+  int32_t* active;
+  int32_t* status;
+  unsigned long long* maxmis;
+  double* loss64;
+  double* out_max;
+  double* out_loss;
+  int32_t* n_active;
+};
+
+__global__ void k_apply(ApplyArgs a) {
+  __shared__ int cnt[32];
+  int c = 0;
+  for (int k = threadIdx.x; k < a.Kp; k += blockDim.x) {
+    if (k < a.K) {
+      const double mx = __longlong_as_double((long long)a.maxmis[k]);
+      const double L = a.loss64[k] * a.inv_m;
+      if (a.final_pass) {
+        a.out_max[k] = mx;
+        a.out_loss[k] = L;
+        if (a.active[k]) a.status[k] = (mx <= a.tol) ? CASE_CONVERGED : CASE_MAX_ITER;
+        a.active[k] = 0;
+      } else if (a.active[k] && mx <= a.tol) {
+        a.active[k] = 0;
+        a.status[k] = CASE_CONVERGED;
+        a.out_max[k] = mx;
+        a.out_loss[k] = L;
+      }
+      c += a.active[k];
+    }
+    a.maxmis[k] = 0ULL;
+    a.loss64[k] = 0.0;
+  }
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0) cnt[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += cnt[w];
+    *a.n_active = s;
+  }
+}
+
+// ---- set-up / tear-down ----------------------------------------------------
+// Tiled transpose of a case-major [K][N] user-order FP64 array into the
+// case-minor internal layout [N][Kp] (row iperm[u] for user bus u).
+__global__ void k_to_internal(const double* __restrict__ src, double* __restrict__ dst, int K, int N,
+                              int Kp, const int32_t* __restrict__ iperm) {
+  __shared__ double tile[32][33];
+  const int u0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, u = u0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < K && u < N) ? src[(size_t)k * N + u] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int u = u0 + r, k = k0 + threadIdx.x;
+    if (u < N && k < K) dst[(size_t)iperm[u] * Kp + k] = tile[threadIdx.x][r];
+  }
+}
+
+// Inverse of k_to_internal.
+__global__ void k_to_user(const double* __restrict__ src, double* __restrict__ dst, int K, int N, int Kp,
+                          const int32_t* __restrict__ iperm) {
+  __shared__ double tile[32][33];
+  const int u0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int u = u0 + r, k = k0 + threadIdx.x;
+    tile[r][threadIdx.x] = (u < N && k < K) ? src[(size_t)iperm[u] * Kp + k] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, u = u0 + threadIdx.x;
+    if (k < K && u < N) dst[(size_t)k * N + u] = tile[threadIdx.x][r];
+  }
+}
+
+// Initial state of every (bus, case) element.  va_t / vm_t / vms_t are
+// case-minor FP64 inputs or NULL (flat start / the grid's set-points).
+template <class R> struct InitArgs {
+  using C = typename Prec<R>::C;
+  using M = typename Prec<R>::M;
+  int N, K, Kp;
+  const uint8_t* type;
+  const double* vmset_grid;  // [N]
+  const double* vms_t;       // [N][Kp] or NULL
+  const double* va_t;        // [N][Kp] or NULL
+  const double* vm_t;
+  double va_slack;
+  const double* p64;         // per-case spec (FP64, [N][Kp]) or NULL
+  const double* q64;
+  R* p;                      // per-case working-precision copies
+  R* q;
+  M* th;
+  M* vm;
+  C* V;
+  R* mth;
+  R* vth;
+  R* mvm;
+  R* vvm;
+};
+
+template <class R>
+__global__ void k_init(InitArgs<R> a) {
+  using M = typename Prec<R>::M;
+  const size_t n = (size_t)a.N * a.Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / a.Kp), k = (int)(e % a.Kp);
+    const int ty = a.type[i];
+    double th = 0.0, vm = 1.0;
+    if (k < a.K) {
+      if (a.va_t) { th = a.va_t[e]; vm = a.vm_t[e]; }
+      const double set = a.vms_t ? a.vms_t[e] : a.vmset_grid[i];
+      if (ty != BUS_PQ) vm = set;
+      if (ty == BUS_SLACK) th = a.va_slack;
+    }
+    const M mth = mfrom<M>(th), mvm = mfrom<M>(vm);
+    a.th[e] = mth;
+    a.vm[e] = mvm;
+    a.V[e] = volt(mth, mvm);
+    a.mth[e] = R(0);
+    a.vth[e] = R(0);
+    a.mvm[e] = R(0);
+    a.vvm[e] = R(0);
+    if (a.p64) {
+      a.p[e] = (R)a.p64[e];
+      a.q[e] = (R)a.q64[e];
+    }
+  }
+}
+
+// Per-case scalar state and N-1 corrections.  outage (user branch index or
+// -1) may be NULL.  Branch data are FP64 in internal bus order.
+template <class R> struct CaseInitArgs {
+  using C = typename Prec<R>::C;
+  int K, Kp;
+  const int32_t* outage;
+  const int32_t* br_f;
+  const int32_t* br_t;
+  const double* br_r;
+  const double* br_x;
+  const double* br_bch;
+  const double* br_tap;
+  int32_t* of;
+  int32_t* ot;
+  C* yff;
+  C* yft;
+  C* ytt;
+  double2* yff64;
+  double2* yft64;
+  double2* ytt64;
+  int32_t* active;
+  int32_t* iters;
+  int32_t* status;
+  double* lr;
+  double* best;
+  int32_t* bad;
+  int32_t* cool;
+  R* loss_acc;
+  R* step_size;
+  R* isbc2;
+  unsigned long long* maxmis;
+  double* loss64;
+  double lr0, beta1, beta2;
+};
+
+template <class R>
+__global__ void k_case_init(CaseInitArgs<R> a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.Kp) return;
+  const bool real = k < a.K;
+  a.active[k] = real ? 1 : 0;
+  a.iters[k] = 0;
+  a.status[k] = CASE_MAX_ITER;
+  a.lr[k] = a.lr0;
+  a.best[k] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+  a.bad[k] = 0;
+  a.cool[k] = 0;
+  a.loss_acc[k] = R(0);
+  a.step_size[k] = (R)(a.lr0 / (1.0 - a.beta1));
+  a.isbc2[k] = (R)(1.0 / sqrt(1.0 - a.beta2));
+  a.maxmis[k] = 0ULL;
+  a.loss64[k] = 0.0;
+  int ell = (real && a.outage) ? a.outage[k] : -1;
+  if (ell < 0) {
+    a.of[k] = -1;
+    a.ot[k] = -1;
+    return;
+  }
+  // pi-model block of the outaged branch (removed from the shared Y_bus)
+  const double r = a.br_r[ell], x = a.br_x[ell], bch = a.br_bch[ell];
+  const double tau = (a.br_tap[ell] == 0.0) ? 1.0 : a.br_tap[ell];
+  const double d = r * r + x * x, gs = r / d, bs = -x / d, t2 = tau * tau;
+  const double2 ff = make_double2(gs / t2, (bs + 0.5 * bch) / t2);
+  const double2 ft = make_double2(-gs / tau, -bs / tau);
+  const double2 tt = make_double2(gs, bs + 0.5 * bch);
+  a.of[k] = a.br_f[ell];
+  a.ot[k] = a.br_t[ell];
+  a.yff64[k] = ff;
+  a.yft64[k] = ft;
+  a.ytt64[k] = tt;
+  a.yff[k] = mkc((R)ff.x, (R)ff.y);
+  a.yft[k] = mkc((R)ft.x, (R)ft.y);
+  a.ytt[k] = mkc((R)tt.x, (R)tt.y);
+}
+
+// master -> FP64 (for the solution output)
+template <class M>
+__global__ void k_master64(const M* __restrict__ src, double* __restrict__ dst, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = mval(src[e]);
+}
+
+// working precision -> FP64, optional scale (outputs of the evaluation calls)
+template <class R>
+__global__ void k_widen(const R* __restrict__ src, double* __restrict__ dst, size_t n, size_t stride, double scale) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = scale * (double)src[e * stride];
+}
+
+// Y_bus values from per-branch series admittance (g + jb), charging and taps,
+// one thread per internal row: off-diagonal entries -y_s/tau, diagonal the
+// sum of the incident branches' end contributions.
+struct YValArgs {
+  int N;
+  const int32_t* rp;
+  const int32_t* col;
+  const int32_t* ebr;
+  const int32_t* br_f;  // internal from-bus
+  const double* g;      // [M] user branch order
+  const double* b;
+  const double* bch;
+  const double* tap;
+  int4* ent32;
+  double2* val64;
+};
+
+__global__ void k_ybus_values(YValArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  double dr = 0.0, di = 0.0;
+  int pd = -1;
+  for (int p = a.rp[i]; p < a.rp[i + 1]; ++p) {
+    const int ell = a.ebr[p];
+    if (ell < 0) { pd = p; continue; }
+    const double tau = (a.tap[ell] == 0.0) ? 1.0 : a.tap[ell];
+    const double gs = a.g[ell], bs = a.b[ell], sh = 0.5 * a.bch[ell];
+    const double vr = -gs / tau, vi = -bs / tau;
+    a.val64[p] = make_double2(vr, vi);
+    a.ent32[p] = make_int4(a.col[p], __float_as_int((float)vr), __float_as_int((float)vi), 0);
+    if (a.br_f[ell] == i) { dr += gs / (tau * tau); di += (bs + sh) / (tau * tau); }
+    else { dr += gs; di += bs + sh; }
+  }
+  if (pd >= 0) {
+    a.val64[pd] = make_double2(dr, di);
+    a.ent32[pd] = make_int4(i, __float_as_int((float)dr), __float_as_int((float)di), 0);
+  }
+}
+
+// Branch-parameter gradients, summed over cases (one thread per
+// (branch, case)): with H_ik = w_i V_k (w = c conj V),
+//   E = H_ff/tau^2 + H_tt - (H_ft + H_tf)/tau,
+//   dL/dg = Re E, dL/db = -Im E, dL/db_ch = -Im(H_ff/tau^2 + H_tt)/2.
+template <class R> struct EdgeArgs {
+  using C = typename Prec<R>::C;
+  int M, K, Kp, lanes;
+  const int32_t* br_f;
+  const int32_t* br_t;
+  const double* tap;
+  const C* V;
+  const C* W;
+  double* d_g;
+  double* d_b;
+  double* d_bch;
+};
+
+template <class R>
+__global__ void __launch_bounds__(1024) k_edge_grad(EdgeArgs<R> a) {
+  using C = typename Prec<R>::C;
+  const Map mp = thread_map(a.lanes);
+  const int k = mp.k;
+  for (int ell0 = mp.row0 - mp.rsub; ell0 < a.M; ell0 += mp.rstride) {
+    const int ell = ell0 + mp.rsub;
+    R eg = 0, eb = 0, ec = 0;
+    if (ell < a.M && k < a.K) {
+      const int f = a.br_f[ell], t = a.br_t[ell];
+      const double tau = (a.tap[ell] == 0.0) ? 1.0 : a.tap[ell];
+      const R it = (R)(1.0 / tau), it2 = (R)(1.0 / (tau * tau));
+      const size_t Kp = (size_t)a.Kp;
+      const C wf = a.W[(size_t)f * Kp + k], wt = a.W[(size_t)t * Kp + k];
+      const C vf = a.V[(size_t)f * Kp + k], vt = a.V[(size_t)t * Kp + k];
+      const C hff = mkc(wf.x * vf.x - wf.y * vf.y, wf.x * vf.y + wf.y * vf.x);
+      const C htt = mkc(wt.x * vt.x - wt.y * vt.y, wt.x * vt.y + wt.y * vt.x);
+      const C hft = mkc(wf.x * vt.x - wf.y * vt.y, wf.x * vt.y + wf.y * vt.x);
+      const C htf = mkc(wt.x * vf.x - wt.y * vf.y, wt.x * vf.y + wt.y * vf.x);
+      const R er = hff.x * it2 + htt.x - (hft.x + htf.x) * it;
+      const R ei = hff.y * it2 + htt.y - (hft.y + htf.y) * it;
+      eg = er;
+      eb = -ei;
+      ec = -(hff.y * it2 + htt.y) * R(0.5);
+    }
+    for (int off = 1; off < a.lanes; off <<= 1) {
+      eg += __shfl_xor_sync(0xffffffffu, eg, off);
+      eb += __shfl_xor_sync(0xffffffffu, eb, off);
+      ec += __shfl_xor_sync(0xffffffffu, ec, off);
+    }
+    if (mp.kl == 0 && ell < a.M) {
+      if (a.d_g) atomicAdd(a.d_g + ell, (double)eg);
+      if (a.d_b) atomicAdd(a.d_b + ell, (double)eb);
+      if (a.d_bch) atomicAdd(a.d_bch + ell, (double)ec);
+    }
+  }
+}
+
+}  // namespace dpf

@@ -1,0 +1,303 @@
+"""Python binding of libdpf (include/dpf.h): argument marshalling only.
+
+Every function keeps the C name.  Device arrays are torch CUDA tensors
+(float64 / int32, contiguous); their data pointers and the current torch
+stream are passed straight to the library, which does all the work in its own
+CUDA kernels.  There is no fallback: if libdpf.so is missing or a call fails,
+an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+from . import _abi
+from .build import LIB
+
+_lib = None
+
+
+class DPFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdpf error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libdpf.so (built in-tree by `build.build()`); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libdpf.so not found at {LIB}; build it with paper_2603_28203_gb300.build.build()")
+        L = C.CDLL(LIB)
+        for name, (res, args) in _abi.SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != _abi.DPF_OK:
+        raise DPFError(rc, lib().dpf_last_error().decode())
+
+
+def _ptr(t):
+    """Data pointer of a contiguous tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return t.ctypes.data
+    assert t.is_contiguous(), "tensors passed to libdpf must be contiguous"
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---- grid / Y_bus -----------------------------------------------------------
+class Ybus:
+    """Owner of a dpf_ybus handle."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+        n, m, z = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().dpf_ybus_info(handle, C.byref(n), C.byref(m), C.byref(z)))
+        self.n_bus, self.n_branch, self.nnz = n.value, m.value, z.value
+
+    def free(self):
+        if self.handle:
+            lib().dpf_ybus_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _grid_struct(grid):
+    arrs = dict(
+        bus_type=np.ascontiguousarray(grid.bus_type, np.uint8),
+        p_spec=np.ascontiguousarray(grid.p_spec, np.float64),
+        q_spec=np.ascontiguousarray(grid.q_spec, np.float64),
+        vm_set=np.ascontiguousarray(grid.vm_set, np.float64),
+        f_bus=np.ascontiguousarray(grid.f_bus, np.int32),
+        t_bus=np.ascontiguousarray(grid.t_bus, np.int32),
+        r=np.ascontiguousarray(grid.r, np.float64),
+        x=np.ascontiguousarray(grid.x, np.float64),
+        b_ch=np.ascontiguousarray(grid.b_ch, np.float64),
+        tap=np.ascontiguousarray(grid.tap, np.float64),
+    )
+    shift = getattr(grid, "shift", None)
+    if shift is not None:
+        arrs["shift"] = np.ascontiguousarray(shift, np.float64)
+    g = _abi.DpfGrid()
+    g.n_bus = arrs["bus_type"].size
+    g.n_branch = arrs["f_bus"].size
+    for k, v in arrs.items():
+        setattr(g, k, v.ctypes.data)
+    g.va_slack = float(getattr(grid, "va_slack", 0.0))
+    return g, arrs
+
+
+def dpf_build_ybus_host(grid) -> Ybus:
+    g, keep = _grid_struct(grid)
+    h = C.c_void_p()
+    _check(lib().dpf_build_ybus_host(C.byref(g), C.byref(h)))
+    return Ybus(h, keep)
+
+
+def dpf_ybus_upload(y: Ybus, stream=None):
+    _check(lib().dpf_ybus_upload(y.handle, _stream(stream)))
+
+
+def dpf_build_ybus(grid, stream=None) -> Ybus:
+    g, keep = _grid_struct(grid)
+    h = C.c_void_p()
+    _check(lib().dpf_build_ybus(C.byref(g), _stream(stream), C.byref(h)))
+    return Ybus(h, keep)
+
+
+def dpf_ybus_export(y: Ybus):
+    """(row_ptr, col, val) of the FP64 CSR in user bus order (numpy)."""
+    rp = np.empty(y.n_bus + 1, np.int32)
+    col = np.empty(y.nnz, np.int32)
+    re = np.empty(y.nnz, np.float64)
+    im = np.empty(y.nnz, np.float64)
+    _check(lib().dpf_ybus_export(y.handle, rp.ctypes.data, col.ctypes.data, re.ctypes.data, im.ctypes.data))
+    return rp, col, re + 1j * im
+
+
+def dpf_ybus_bridges(y: Ybus) -> np.ndarray:
+    out = np.empty(max(y.n_branch, 1), np.uint8)
+    _check(lib().dpf_ybus_bridges(y.handle, out.ctypes.data))
+    return out[: y.n_branch].astype(bool)
+
+
+# ---- options / workspace ----------------------------------------------------
+@dataclasses.dataclass
+class SolveOpts:
+    """Mirror of dpf_solve_opts; None keeps the library default (Table 2 etc.)."""
+    lr: float | None = None
+    beta1: float | None = None
+    beta2: float | None = None
+    eps: float | None = None
+    sched: int | None = None
+    factor: float | None = None
+    threshold: float | None = None
+    min_lr: float | None = None
+    patience: int | None = None
+    cooldown: int | None = None
+    step_size: int | None = None
+    gamma: float | None = None
+    max_iter: int | None = None
+    check_every: int | None = None
+    tol: float | None = None
+    flat_start: int | None = None
+    precision: int | None = None
+    lanes: int | None = None
+    warps: int | None = None
+    row_blocks: int | None = None
+    use_graph: int | None = None
+    plain: int | None = None
+
+    def to_c(self) -> _abi.DpfSolveOpts:
+        o = _abi.DpfSolveOpts()
+        lib().dpf_default_opts(C.byref(o))
+        for f in dataclasses.fields(self):
+            v = getattr(self, f.name)
+            if v is not None:
+                setattr(o, f.name, v)
+        return o
+
+
+def dpf_default_opts() -> _abi.DpfSolveOpts:
+    o = _abi.DpfSolveOpts()
+    lib().dpf_default_opts(C.byref(o))
+    return o
+
+
+class Workspace:
+    def __init__(self, y: Ybus, max_case: int):
+        self.ybus = y
+        h = C.c_void_p()
+        _check(lib().dpf_workspace_create(y.handle, int(max_case), C.byref(h)))
+        self.handle = h
+
+    def free(self):
+        if self.handle:
+            lib().dpf_workspace_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dpf_workspace_create(y: Ybus, max_case: int) -> Workspace:
+    return Workspace(y, max_case)
+
+
+# ---- batched solve -----------------------------------------------------------
+def _batch_struct(n_case, host_io=False, p_spec=None, q_spec=None, vm_set=None, outage=None, va=None,
+                  vm=None, iters=None, status=None, max_mismatch=None, loss=None):
+    b = _abi.DpfBatch()
+    b.n_case = int(n_case)
+    b.host_io = 1 if host_io else 0
+    for name, t in dict(p_spec=p_spec, q_spec=q_spec, vm_set=vm_set, outage=outage, va=va, vm=vm,
+                        iters=iters, status=status, max_mismatch=max_mismatch, loss=loss).items():
+        setattr(b, name, _ptr(t))
+    return b
+
+
+def _opts(opts):
+    if opts is None:
+        return dpf_default_opts()
+    if isinstance(opts, SolveOpts):
+        return opts.to_c()
+    return opts
+
+
+def dpf_solve_batch(y: Ybus, ws: Workspace | None, opts=None, stream=None, **batch):
+    """Solve every case; `batch` holds the dpf_batch fields as tensors."""
+    b = _batch_struct(**batch)
+    o = _opts(opts)
+    _check(lib().dpf_solve_batch(y.handle, ws.handle if ws else None, C.byref(b), C.byref(o), _stream(stream)))
+
+
+def dpf_solve_begin(y: Ybus, ws: Workspace, opts=None, stream=None, **batch):
+    b = _batch_struct(**batch)
+    o = _opts(opts)
+    _check(lib().dpf_solve_begin(y.handle, ws.handle, C.byref(b), C.byref(o), _stream(stream)))
+
+
+def dpf_solve_iterate(ws: Workspace, n_iter: int, stream=None):
+    _check(lib().dpf_solve_iterate(ws.handle, int(n_iter), _stream(stream)))
+
+
+def dpf_solve_end(ws: Workspace, stream=None, **batch):
+    b = _batch_struct(**batch)
+    _check(lib().dpf_solve_end(ws.handle, C.byref(b), _stream(stream)))
+
+
+def dpf_active_count(ws: Workspace, stream=None) -> int:
+    n = C.c_int32()
+    _check(lib().dpf_active_count(ws.handle, C.byref(n), _stream(stream)))
+    return n.value
+
+
+def dpf_iterations_done(ws: Workspace) -> int:
+    n = C.c_int32()
+    _check(lib().dpf_iterations_done(ws.handle, C.byref(n)))
+    return n.value
+
+
+# ---- evaluation ----------------------------------------------------------------
+def dpf_power(y: Ybus, ws: Workspace, va, vm, outage=None, precision=_abi.FP32, stream=None):
+    """(P_calc, Q_calc) [K][N] float64 CUDA tensors."""
+    import torch
+    p = torch.empty_like(va)
+    q = torch.empty_like(va)
+    _check(lib().dpf_power(y.handle, ws.handle, int(va.shape[0]), _ptr(va), _ptr(vm), _ptr(outage),
+                           int(precision), _ptr(p), _ptr(q), _stream(stream)))
+    return p, q
+
+
+def dpf_loss_backward(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, outage=None,
+                      g_series=None, b_series=None, precision=_abi.FP32, want=("loss", "d_va", "d_vm"),
+                      stream=None):
+    """Loss per case and the requested gradients, as float64 CUDA tensors (dict)."""
+    import torch
+    K, N = va.shape
+    M = y.n_branch
+    out = {}
+    shapes = dict(loss=(K,), d_va=(K, N), d_vm=(K, N), d_p=(K, N), d_q=(K, N), d_g=(M,), d_b=(M,), d_bch=(M,))
+    for name in want:
+        out[name] = torch.empty(shapes[name], dtype=torch.float64, device=va.device)
+    g = [out.get(n) for n in ("loss", "d_va", "d_vm", "d_p", "d_q", "d_g", "d_b", "d_bch")]
+    _check(lib().dpf_loss_backward(y.handle, ws.handle, int(K), _ptr(va), _ptr(vm), _ptr(p_spec), _ptr(q_spec),
+                                   _ptr(outage), _ptr(g_series), _ptr(b_series), int(precision),
+                                   *[_ptr(t) for t in g], _stream(stream)))
+    return out
+
+
+def dpf_last_error() -> str:
+    return lib().dpf_last_error().decode()
+
+
+def dpf_status_str(code: int) -> str:
+    return lib().dpf_status_str(int(code)).decode()

@@ -1,0 +1,119 @@
+"""CPU checks of the C ABI library: it loads, exports every declared symbol,
+and its host-side logic (Y_bus assembly, validation, bridges, defaults) is
+right.  No GPU call is made."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+
+import gridgen
+import oracle
+from oracle.ybus import grid_ybus
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dpf():
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as m
+    m.lib()
+    return m
+
+
+def test_exports_every_declared_symbol(dpf):
+    src = open(os.path.join(ROOT, "include", "dpf.h")).read()
+    names = set(re.findall(r"\b(dpf_[a-z0-9_]+)\s*\(", src))
+    assert len(names) >= 15
+    L = dpf.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("name", ["c1_30bus_fp64", "c3_n1_2kbus"])
+def test_host_ybus_matches_oracle(dpf, name):
+    g = gridgen.config_grid(name)
+    y = dpf.dpf_build_ybus_host(g)
+    rp, col, val = dpf.dpf_ybus_export(y)
+    Y = grid_ybus(g)
+    Y.sort_indices()
+    np.testing.assert_array_equal(rp, Y.indptr)       # index work: bit-exact
+    np.testing.assert_array_equal(col, Y.indices)
+    assert np.abs(val - Y.data).max() <= 1e-15 * np.abs(Y.data).max()
+
+
+def _bridges_brute(g):
+    out = np.zeros(g.n_branch, bool)
+    for e in range(g.n_branch):
+        keep = np.arange(g.n_branch) != e
+        a = sp.coo_matrix((np.ones(keep.sum()), (g.f_bus[keep], g.t_bus[keep])), shape=(g.n_bus, g.n_bus))
+        out[e] = connected_components(a, directed=False)[0] > 1
+    return out
+
+
+@pytest.mark.parametrize("n,seed", [(30, 0), (120, 3)])
+def test_bridges_brute_force(dpf, n, seed):
+    g = gridgen.make_grid(n, seed, n_branch=int(1.2 * n))
+    y = dpf.dpf_build_ybus_host(g)
+    np.testing.assert_array_equal(dpf.dpf_ybus_bridges(y), _bridges_brute(g))
+
+
+def _bad(g, **changes):
+    h = g.copy()
+    for k, v in changes.items():
+        setattr(h, k, v)
+    return h
+
+
+def test_validation_errors(dpf):
+    g = gridgen.config_grid("c1_30bus_fp64")
+    cases = {
+        -1: [
+            _bad(g, bus_type=np.where(np.arange(g.n_bus) < 2, 2, g.bus_type).astype(np.uint8)),  # two slacks
+            _bad(g, bus_type=np.where(g.bus_type == 2, 0, g.bus_type).astype(np.uint8)),          # none
+            _bad(g, f_bus=np.where(np.arange(g.n_branch) == 3, g.n_bus, g.f_bus).astype(np.int32)),
+            _bad(g, t_bus=np.where(np.arange(g.n_branch) == 3, g.f_bus, g.t_bus).astype(np.int32)),
+            _bad(g, r=np.where(np.arange(g.n_branch) == 0, 0.0, g.r), x=np.where(np.arange(g.n_branch) == 0, 0.0, g.x)),
+            _bad(g, p_spec=np.where(np.arange(g.n_bus) == 1, np.nan, g.p_spec)),
+            _bad(g, tap=np.where(np.arange(g.n_branch) == 0, -1.0, g.tap)),
+        ],
+        -5: [
+            _bad(g, shift=np.where(np.arange(g.n_branch) == 0, 0.1, 0.0)),
+            _bad(g, f_bus=np.concatenate([g.f_bus, g.f_bus[:1]]), t_bus=np.concatenate([g.t_bus, g.t_bus[:1]]),
+                 r=np.concatenate([g.r, g.r[:1]]), x=np.concatenate([g.x, g.x[:1]]),
+                 b_ch=np.concatenate([g.b_ch, g.b_ch[:1]]), tap=np.concatenate([g.tap, g.tap[:1]]),
+                 shift=np.zeros(g.n_branch + 1)),
+        ],
+    }
+    for code, grids in cases.items():
+        for h in grids:
+            with pytest.raises(dpf.DPFError) as e:
+                dpf.dpf_build_ybus_host(h)
+            assert e.value.code == code, dpf.dpf_last_error()
+
+
+def test_tap_zero_means_none(dpf):
+    g = gridgen.config_grid("c1_30bus_fp64")
+    h = _bad(g, tap=np.where(g.tap == 1.0, 0.0, g.tap))
+    a = dpf.dpf_ybus_export(dpf.dpf_build_ybus_host(g))[2]
+    b = dpf.dpf_ybus_export(dpf.dpf_build_ybus_host(h))[2]
+    np.testing.assert_array_equal(a, b)
+
+
+def test_default_opts_are_table2(dpf):
+    t2 = json.load(open(os.path.join(ROOT, "tests", "golden", "hyperparameters.json")))["table2_static"]
+    o = dpf.dpf_default_opts()
+    assert (o.beta1, o.beta2) == tuple(t2["betas"])
+    assert (o.factor, o.patience, o.threshold, o.cooldown) == (t2["factor"], t2["patience"], t2["threshold"], t2["cooldown"])
+    assert o.max_iter == t2["max_iter"] and o.sched == dpf.SCHED_PLATEAU
+
+
+def test_status_strings(dpf):
+    for c in (0, -1, -2, -3, -4, -5, -6):
+        assert dpf.dpf_status_str(c) and dpf.dpf_status_str(c) != "unknown status"
