@@ -139,7 +139,7 @@ typedef struct {
 /* Iteration options.  Defaults (dpf_default_opts): Table 2 of the paper --
  * Adam betas (0.979, 0.963), eps 1e-8, ReduceLROnPlateau factor 0.547,
  * patience 41, threshold 0.0673 (relative), cooldown 97, max_iter 1000 --
- * with lr 1e-2, tol 1e-6 p.u., check_every 25, FP32 iterations. */
+ * with lr 1e-2, tol 1e-6 p.u., check_every 25, gate 1e-3, FP32 iterations. */
 typedef struct {
   double lr, beta1, beta2, eps;
   int32_t sched;             /* DPF_SCHED_*                                    */
@@ -150,10 +150,15 @@ typedef struct {
   int32_t max_iter;          /* optimizer steps per case                       */
   int32_t check_every;       /* FP64 convergence test every k steps (>= 1)     */
   double tol;                /* stop when FP64 max |f| <= tol                  */
+  double gate;               /* FP32 mode: the FP64 test examines only cases
+                                whose FP32 max |f| from the latest forward pass
+                                is <= gate (0 = every case).  It only skips
+                                tests that cannot pass; a case is marked
+                                converged by the FP64 test alone.             */
   int32_t flat_start;        /* 1: ignore va/vm inputs, start flat             */
   int32_t precision;         /* DPF_FP32 (FP64 master + FP64 test) / DPF_FP64  */
   int32_t lanes;             /* cases per row group 1..32 (power of 2); 0=auto */
-  int32_t warps;             /* warps per CTA (1..32); 0 = auto                */
+  int32_t warps;             /* warps per CTA (1..8); 0 = auto                 */
   int32_t row_blocks;        /* CTAs along the bus dimension; 0 = auto         */
   int32_t use_graph;         /* 1: replay iterations from a CUDA graph         */
   int32_t plain;             /* 1: the plain form of Alg. 1 -- one case at a
@@ -195,7 +200,21 @@ int dpf_active_count(dpf_workspace* ws, int32_t* n_active, void* stream);
 /* Steps taken so far by the batch (host counter, no synchronisation). */
 int dpf_iterations_done(const dpf_workspace* ws, int32_t* n_iter);
 
+/* ---- measurement ----------------------------------------------------------
+ * dpf_profile_enable(ws, 1): from now on dpf_solve_iterate launches without a
+ * CUDA graph and brackets every forward (k_fwd) and adjoint (k_adj) launch
+ * with CUDA events on the caller's stream; 0 switches back to graph replay.
+ * dpf_kernel_times: summed durations (ms) and launch counts of the
+ * bracketed launches since the last enable (synchronises `stream`).
+ * dpf_kernel_launches: number of kernels the workspace has enqueued since it
+ * was created (graph replays count their kernel nodes). */
+int dpf_profile_enable(dpf_workspace* ws, int32_t on);
+int dpf_kernel_times(dpf_workspace* ws, double* fwd_ms, double* adj_ms, int32_t* n_fwd, int32_t* n_adj,
+                     void* stream);
+int dpf_kernel_launches(const dpf_workspace* ws, int64_t* n);
+
 /* ---- forward evaluation (Eq. powerbalance) --------------------------------
+ * The evaluation entry points take (va, vm) verbatim, set-points included.
  * S_calc = V (Y V)^* for n_case voltage vectors (case-major device arrays),
  * optional per-case outage (NULL = none).  precision selects the FP32 or
  * FP64 kernels; outputs are FP64 either way. */

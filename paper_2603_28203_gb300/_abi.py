@@ -43,7 +43,7 @@ class DpfSolveOpts(C.Structure):
         ("factor", C.c_double), ("threshold", C.c_double), ("min_lr", C.c_double),
         ("patience", C.c_int32), ("cooldown", C.c_int32),
         ("step_size", C.c_int32), ("gamma", C.c_double),
-        ("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double),
+        ("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double), ("gate", C.c_double),
         ("flat_start", C.c_int32), ("precision", C.c_int32),
         ("lanes", C.c_int32), ("warps", C.c_int32), ("row_blocks", C.c_int32),
         ("use_graph", C.c_int32), ("plain", C.c_int32),
@@ -74,6 +74,9 @@ SIGNATURES = {
     "dpf_power": (C.c_int, [VP, VP, I32, VP, VP, VP, I32, VP, VP, VP]),
     "dpf_loss_backward": (C.c_int, [VP, VP, I32, VP, VP, VP, VP, VP, VP, VP, I32,
                                     VP, VP, VP, VP, VP, VP, VP, VP, VP]),
+    "dpf_profile_enable": (C.c_int, [VP, I32]),
+    "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),
+    "dpf_kernel_launches": (C.c_int, [VP, C.POINTER(C.c_int64)]),
     "dpf_last_error": (C.c_char_p, []),
     "dpf_status_str": (C.c_char_p, [C.c_int]),
 }

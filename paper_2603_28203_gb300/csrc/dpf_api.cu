@@ -208,6 +208,9 @@ struct dpf_workspace {
   double *lr = nullptr, *best = nullptr, *out_max = nullptr, *out_loss = nullptr, *loss64 = nullptr;
   void *loss_acc = nullptr, *step_size = nullptr, *isbc2 = nullptr, *yff = nullptr, *yft = nullptr, *ytt = nullptr;
   double2 *yff64 = nullptr, *yft64 = nullptr, *ytt64 = nullptr;
+  double *b1t = nullptr, *b2t = nullptr;
+  int32_t* cand = nullptr;
+  unsigned int* mx32 = nullptr;
   unsigned long long* maxmis = nullptr;
   int32_t* outage_dev = nullptr;
   int32_t* n_active = nullptr;
@@ -217,12 +220,19 @@ struct dpf_workspace {
   cudaStream_t cap_stream = nullptr;
   // solve state
   bool begun = false;
-  int K = 0, Kp = 0, lanes = 1, warps = 8, gx = 1, gy = 1, precision = DPF_FP32;
+  int K = 0, Kp = 0, lanes = 1, warps = 8, gx = 1, gy = 1, rpb = 1, smem = 0, precision = DPF_FP32;
   bool spec_per_case = false, has_outage = false;
   dpf_solve_opts opts;
   int t_done = 0;
   cudaGraphExec_t gexec = nullptr;
+  int graph_kernels = 0;  // kernel nodes per replay
   bool use_local_y = false;
+  long long launches = 0;
+  // per-kernel timing
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_fwd, ev_adj;  // (start, stop) indices into ev_pool
+  size_t ev_used = 0;
 };
 
 static void ws_free_buffers(dpf_workspace* w) {
@@ -234,6 +244,7 @@ static void ws_free_buffers(dpf_workspace* w) {
   dfree(w->active); dfree(w->iters); dfree(w->status); dfree(w->of); dfree(w->ot); dfree(w->bad); dfree(w->cool);
   dfree(w->lr); dfree(w->best); dfree(w->out_max); dfree(w->out_loss); dfree(w->loss64);
   dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
+  dfree(w->b1t); dfree(w->b2t); dfree(w->cand); dfree(w->mx32);
   dfree(w->st_a); dfree(w->st_b); dfree(w->st_c);
   w->cap_elems = 0;
   w->cap_cases = 0;
@@ -243,6 +254,17 @@ static void ws_free_buffers(dpf_workspace* w) {
 static void ws_drop_graph(dpf_workspace* w) {
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
   w->gexec = nullptr;
+  w->graph_kernels = 0;
+}
+
+static int ev_take(dpf_workspace* w, cudaEvent_t* e) {
+  if (w->ev_used == w->ev_pool.size()) {
+    cudaEvent_t n;
+    CK(cudaEventCreate(&n));
+    w->ev_pool.push_back(n);
+  }
+  *e = w->ev_pool[w->ev_used++];
+  return DPF_OK;
 }
 
 // Grow the buffers to hold Kp cases (N * Kp elements) and K*N staging.
@@ -258,6 +280,7 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     dfree(w->active); dfree(w->iters); dfree(w->status); dfree(w->of); dfree(w->ot); dfree(w->bad);
     dfree(w->cool); dfree(w->lr); dfree(w->best); dfree(w->out_max); dfree(w->out_loss); dfree(w->loss64);
     dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
+    dfree(w->b1t); dfree(w->b2t); dfree(w->cand); dfree(w->mx32);
     w->cap_elems = 0;
     w->cap_cases = 0;
     char** bufs16[] = {(char**)&w->V, (char**)&w->W, (char**)&w->G0, (char**)&w->V64, (char**)&w->sbuf,
@@ -279,6 +302,7 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     TRY(dalloc(&w->out_loss, Kp)); TRY(dalloc(&w->loss64, Kp));
     TRY(dalloc(&w->yff64, Kp)); TRY(dalloc(&w->yft64, Kp)); TRY(dalloc(&w->ytt64, Kp));
     TRY(dalloc(&w->maxmis, Kp)); TRY(dalloc(&w->outage_dev, Kp));
+    TRY(dalloc(&w->b1t, Kp)); TRY(dalloc(&w->b2t, Kp)); TRY(dalloc(&w->cand, Kp)); TRY(dalloc(&w->mx32, Kp));
     CK(cudaMemset(w->p64, 0, E * 8));
     CK(cudaMemset(w->q64, 0, E * 8));
     w->cap_elems = E;
@@ -329,6 +353,8 @@ extern "C" int dpf_workspace_create(const dpf_ybus* y, int32_t max_case, dpf_wor
 extern "C" int dpf_workspace_free(dpf_workspace* w) {
   if (!w) return DPF_OK;
   ws_drop_graph(w);
+  for (auto e : w->ev_pool) cudaEventDestroy(e);
+  w->ev_pool.clear();
   ws_free_buffers(w);
   dfree(w->n_active);
   if (w->h_n_active) cudaFreeHost(w->h_n_active);
@@ -349,6 +375,7 @@ struct Plan {
   Check64Args<M> ck;
   ApplyArgs ap;
   dim3 grid, block;
+  int smem;
   int sched_blocks;
   bool need_volt64;
 };
@@ -368,6 +395,9 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.N = y->n;
   a.Kp = w->Kp;
   a.lanes = w->lanes;
+  a.rpb = w->rpb;
+  // FP32 iterations gate the FP64 test with the forward pass's FP32 mismatch
+  const bool gated = (sizeof(R) == 4) && w->opts.gate > 0.0;
   a.rp = d.row_ptr;
   const int4* ent = w->use_local_y ? w->ent_loc : d.ent32;
   const double2* v64 = w->use_local_y ? w->val_loc : d.val64;
@@ -406,6 +436,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.ytt = (const C*)w->ytt;
   a.has_outage = w->has_outage ? 1 : 0;
   a.loss_acc = (R*)w->loss_acc;
+  a.mx32 = gated ? w->mx32 : nullptr;
   a.step_size = (const R*)w->step_size;
   a.isbc2 = (const R*)w->isbc2;
   a.beta1 = (R)w->opts.beta1;
@@ -420,6 +451,11 @@ static Plan<R> make_plan(dpf_workspace* w) {
   s.iters = w->iters;
   s.status = w->status;
   s.loss_acc = (R*)w->loss_acc;
+  s.mx32 = gated ? w->mx32 : nullptr;
+  s.cand = w->cand;
+  s.gate = w->opts.gate;
+  s.b1t = w->b1t;
+  s.b2t = w->b2t;
   s.lr = w->lr;
   s.best = w->best;
   s.bad = w->bad;
@@ -457,6 +493,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   c.qspec = w->spec_per_case ? w->q64 : d.q64;
   c.spec_per_case = w->spec_per_case ? 1 : 0;
   c.active = w->active;
+  c.cand = gated ? w->cand : nullptr;
   c.of = w->of;
   c.ot = w->ot;
   c.yff = w->yff64;
@@ -474,6 +511,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   p.tol = w->opts.tol;
   p.inv_m = s.inv_m;
   p.active = w->active;
+  p.cand = gated ? w->cand : nullptr;
   p.status = w->status;
   p.maxmis = w->maxmis;
   p.loss64 = w->loss64;
@@ -483,6 +521,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
 
   P.grid = dim3(w->gx, w->gy);
   P.block = dim3(w->warps * 32);
+  P.smem = w->smem;
   P.sched_blocks = (w->Kp + 255) / 256;
   return P;
 }
@@ -493,9 +532,13 @@ static int launch_check(dpf_workspace* w, cudaStream_t s, bool final_pass) {
   P.ck.all_cases = final_pass ? 1 : 0;
   P.ap.final_pass = final_pass ? 1 : 0;
   using M = typename Prec<R>::M;
-  if (P.need_volt64) k_volt64<M><<<P.grid, P.block, 0, s>>>(P.ck);
+  if (P.need_volt64) {
+    k_volt64<M><<<P.grid, P.block, 0, s>>>(P.ck);
+    w->launches++;
+  }
   k_check64<M><<<P.grid, P.block, 0, s>>>(P.ck);
   k_apply<<<1, 1024, 0, s>>>(P.ap);
+  w->launches += 2;
   CKLAUNCH();
   return DPF_OK;
 }
@@ -504,9 +547,24 @@ template <class R>
 static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
   if (with_check) TRY(launch_check<R>(w, s, false));
   Plan<R> P = make_plan<R>(w);
-  k_fwd<R><<<P.grid, P.block, 0, s>>>(P.it);
-  k_adj<R><<<P.grid, P.block, 0, s>>>(P.it);
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (w->profile) {
+    TRY(ev_take(w, &e0));
+    TRY(ev_take(w, &e1));
+    TRY(ev_take(w, &e2));
+    CK(cudaEventRecord(e0, s));
+  }
+  k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  if (w->profile) CK(cudaEventRecord(e1, s));
+  k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  if (w->profile) {
+    CK(cudaEventRecord(e2, s));
+    const int i2 = (int)w->ev_used - 1;
+    w->ev_fwd.push_back({i2 - 2, i2 - 1});
+    w->ev_adj.push_back({i2 - 1, i2});
+  }
   k_sched<R><<<P.sched_blocks, 256, 0, s>>>(P.sc);
+  w->launches += 3;
   CKLAUNCH();
   return DPF_OK;
 }
@@ -524,6 +582,9 @@ static int launch_check_any(dpf_workspace* w, cudaStream_t s, bool final_pass) {
 static int build_graph(dpf_workspace* w) {
   ws_drop_graph(w);
   cudaStream_t cs = w->cap_stream;
+  const long long launches_before = w->launches;
+  const bool prof = w->profile;
+  w->profile = false;
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   int rc = DPF_OK;
   for (int i = 0; i < w->opts.check_every && rc == DPF_OK; ++i) rc = launch_iteration_any(w, cs, i == 0);
@@ -534,6 +595,21 @@ static int build_graph(dpf_workspace* w) {
     return rc;
   }
   if (e != cudaSuccess) return fail(DPF_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int kn = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nd, &ty);
+      kn += (ty == cudaGraphNodeTypeKernel);
+    }
+    w->graph_kernels = kn;
+  }
+  w->launches = launches_before;
+  w->profile = prof;
   e = cudaGraphInstantiate(&w->gexec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
@@ -549,6 +625,7 @@ static int build_graph(dpf_workspace* w) {
 struct StateIn {
   int K;
   bool host_io;
+  bool enforce_fixed;  // solve: set-points override the given state; evaluation: state as given
   const double *va, *vm, *vmset, *p, *q;  // user layout [K][N] or NULL
   const int32_t* outage;
 };
@@ -559,7 +636,7 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   lanes = pow2ceil(lanes);
   w->lanes = lanes;
   w->Kp = (K + lanes - 1) / lanes * lanes;
-  w->warps = (o && o->warps > 0) ? std::min(o->warps, 32) : 8;
+  w->warps = (o && o->warps > 0) ? std::min(o->warps, 8) : 8;
   const int rpw = 32 / lanes;
   w->gx = w->Kp / lanes;
   const int rows_per_cta = w->warps * rpw;
@@ -567,7 +644,33 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   int gy;
   if (o && o->row_blocks > 0) gy = o->row_blocks;
   else gy = (num_sms() * 8 + w->gx - 1) / w->gx;
-  w->gy = std::max(1, std::min(std::min(gy, gy_max), 65535));
+  gy = std::max(1, std::min(std::min(gy, gy_max), 65535));
+  const int n = w->y->n;
+  const std::vector<int32_t>& rp = w->y->irow_ptr;
+  const bool fp64 = (o ? o->precision : w->precision) == DPF_FP64;
+  // shrink row blocks until the staged Y rows of every block fit in shared memory
+  for (;;) {
+    const int rpb = (n + gy - 1) / gy;
+    int mx = 0;
+    for (int r0 = 0; r0 < n; r0 += rpb) mx = std::max(mx, rp[std::min(n, r0 + rpb)] - rp[r0]);
+    const int bytes = ysmem_bytes(rpb, mx, fp64);
+    if (bytes <= 96 * 1024 || gy >= 65535 || rpb <= 1) {
+      w->gy = (n + rpb - 1) / rpb;
+      w->rpb = rpb;
+      w->smem = bytes;
+      break;
+    }
+    gy = std::min(65535, gy * 2);
+  }
+}
+
+template <class R>
+static int set_smem_attr(int bytes) {
+  if (bytes > 48 * 1024) {
+    CK(cudaFuncSetAttribute(k_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CK(cudaFuncSetAttribute(k_adj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  }
+  return DPF_OK;
 }
 
 // Copy an input (user layout) into the internal layout buffer `dst`.
@@ -645,6 +748,7 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   ia.N = y->n;
   ia.K = w->K;
   ia.Kp = w->Kp;
+  ia.enforce_fixed = in.enforce_fixed ? 1 : 0;
   ia.type = d.type;
   ia.vmset_grid = d.vmset;
   ia.vms_t = vms_t;
@@ -708,6 +812,10 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   ca.loss_acc = (R*)w->loss_acc;
   ca.step_size = (R*)w->step_size;
   ca.isbc2 = (R*)w->isbc2;
+  ca.b1t = w->b1t;
+  ca.b2t = w->b2t;
+  ca.cand = w->cand;
+  ca.mx32 = w->mx32;
   ca.maxmis = w->maxmis;
   ca.loss64 = w->loss64;
   ca.lr0 = w->opts.lr;
@@ -731,8 +839,9 @@ static int validate_opts(const dpf_solve_opts* o) {
   if (o->max_iter < 0 || o->check_every < 1 || !(o->tol >= 0))
     return fail(DPF_E_INVALID, "invalid max_iter / check_every / tol");
   if (o->precision != DPF_FP32 && o->precision != DPF_FP64) return fail(DPF_E_INVALID, "unknown precision");
-  if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 32 || o->row_blocks < 0)
-    return fail(DPF_E_INVALID, "invalid launch shape");
+  if (!(o->gate >= 0.0)) return fail(DPF_E_INVALID, "gate must be >= 0");
+  if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 8 || o->row_blocks < 0)
+    return fail(DPF_E_INVALID, "invalid launch shape (lanes 0..32, warps 0..8, row_blocks >= 0)");
   return DPF_OK;
 }
 
@@ -765,11 +874,13 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   w->precision = o->precision;
   w->use_local_y = false;
   choose_shape(w, o, w->K);
+  TRY(w->precision == DPF_FP64 ? set_smem_attr<double>(w->smem) : set_smem_attr<float>(w->smem));
   TRY(ws_reserve(w, w->Kp, b->host_io ? (size_t)w->K * y->n : 0));
   StateIn in;
   memset(&in, 0, sizeof in);
   in.K = w->K;
   in.host_io = b->host_io != 0;
+  in.enforce_fixed = true;
   if (!o->flat_start) {
     in.va = b->va;
     in.vm = b->vm;
@@ -792,9 +903,10 @@ extern "C" int dpf_solve_iterate(dpf_workspace* w, int32_t n_iter, void* stream)
   n_iter = std::min(n_iter, w->opts.max_iter - w->t_done);
   const int ce = w->opts.check_every;
   while (n_iter > 0) {
-    if (w->opts.use_graph && w->t_done % ce == 0 && n_iter >= ce) {
+    if (w->opts.use_graph && !w->profile && w->t_done % ce == 0 && n_iter >= ce) {
       if (!w->gexec) TRY(build_graph(w));
       CK(cudaGraphLaunch(w->gexec, s));
+      w->launches += w->graph_kernels;
       w->t_done += ce;
       n_iter -= ce;
     } else {
@@ -812,6 +924,43 @@ extern "C" int dpf_active_count(dpf_workspace* w, int32_t* n_active, void* strea
   CK(cudaMemcpyAsync(w->h_n_active, w->n_active, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *n_active = *w->h_n_active;
+  return DPF_OK;
+}
+
+extern "C" int dpf_profile_enable(dpf_workspace* w, int32_t on) {
+  if (!w) return fail(DPF_E_INVALID, "dpf_profile_enable: NULL workspace");
+  w->profile = on != 0;
+  w->ev_used = 0;
+  w->ev_fwd.clear();
+  w->ev_adj.clear();
+  return DPF_OK;
+}
+
+extern "C" int dpf_kernel_times(dpf_workspace* w, double* fwd_ms, double* adj_ms, int32_t* n_fwd, int32_t* n_adj,
+                                void* stream) {
+  if (!w) return fail(DPF_E_INVALID, "dpf_kernel_times: NULL workspace");
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  double tf = 0.0, ta = 0.0;
+  for (auto& pr : w->ev_fwd) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, w->ev_pool[pr.first], w->ev_pool[pr.second]));
+    tf += ms;
+  }
+  for (auto& pr : w->ev_adj) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, w->ev_pool[pr.first], w->ev_pool[pr.second]));
+    ta += ms;
+  }
+  if (fwd_ms) *fwd_ms = tf;
+  if (adj_ms) *adj_ms = ta;
+  if (n_fwd) *n_fwd = (int32_t)w->ev_fwd.size();
+  if (n_adj) *n_adj = (int32_t)w->ev_adj.size();
+  return DPF_OK;
+}
+
+extern "C" int dpf_kernel_launches(const dpf_workspace* w, int64_t* n) {
+  if (!w || !n) return fail(DPF_E_INVALID, "dpf_kernel_launches: NULL argument");
+  *n = w->launches;
   return DPF_OK;
 }
 
@@ -949,6 +1098,7 @@ static int eval_setup(const dpf_ybus* y, dpf_workspace* w, int K, int precision,
   w->precision = precision;
   w->K = K;
   choose_shape(w, nullptr, K);
+  TRY(precision == DPF_FP64 ? set_smem_attr<double>(w->smem) : set_smem_attr<float>(w->smem));
   TRY(ws_reserve(w, w->Kp, 0));
   StateIn in;
   memset(&in, 0, sizeof in);
@@ -967,7 +1117,7 @@ static int power_impl(dpf_workspace* w, double* p_calc, double* q_calc, cudaStre
   P.it.sbuf = (typename Prec<R>::C*)w->sbuf;
   P.it.loss_acc = nullptr;
   P.it.n_active = nullptr;
-  k_fwd<R><<<P.grid, P.block, 0, s>>>(P.it);
+  k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
   const size_t E = (size_t)w->y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
   k_widen<R><<<nb, 256, 0, s>>>((const R*)w->sbuf, w->tmp_a, E, 2, 1.0);
@@ -995,10 +1145,10 @@ static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, doub
   Plan<R> P = make_plan<R>(w);
   P.it.cbuf = (C*)w->cbuf;
   P.it.n_active = nullptr;
-  k_fwd<R><<<P.grid, P.block, 0, s>>>(P.it);
+  k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
   P.it.gva = (R*)w->tmp_c;  // reuse as gradient scratch: [N][Kp] R each
   P.it.gvm = (R*)w->sbuf;
-  k_adj<R><<<P.grid, P.block, 0, s>>>(P.it);
+  k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
   CKLAUNCH();
   const size_t E = (size_t)y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);

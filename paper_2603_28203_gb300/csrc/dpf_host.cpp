@@ -337,6 +337,7 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->max_iter = 1000;
   o->check_every = 25;
   o->tol = 1e-6;
+  o->gate = 1e-3;
   o->flat_start = 1;
   o->precision = DPF_FP32;
   o->lanes = 0;

@@ -139,23 +139,6 @@ __device__ __forceinline__ Map thread_map(int lanes) {
   return mp;
 }
 
-// Sum `v` over all threads of the CTA that share a case, then one atomic per
-// case per CTA.  Every thread of the CTA must call it.
-template <class R>
-__device__ __forceinline__ void case_sum_atomic(R v, int lanes, R* out, int Kp) {
-  __shared__ R red[32][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  for (int off = 16; off >= lanes; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if (lane < lanes) red[warp][lane] = v;
-  __syncthreads();
-  if (threadIdx.x < lanes) {
-    R s = 0;
-    for (int w = 0; w < wpb; ++w) s += red[w][threadIdx.x];
-    const int k = blockIdx.x * lanes + threadIdx.x;
-    if (k < Kp && s != R(0)) atomicAdd(out + k, s);
-  }
-}
-
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
@@ -183,11 +166,123 @@ __device__ __forceinline__ void case_max_sum_atomic(double mx, double sq, int la
   }
 }
 
+// ---- row-block map and shared-memory Y_bus ----------------------------------
+// CTA (bx, by) owns cases [bx*lanes, bx*lanes + lanes) and the contiguous bus
+// rows [by*rpb, by*rpb + rpb).  Buses are RCM-ordered, so a row block is a
+// compact patch of the grid: its Y_bus rows are staged once in shared memory
+// (one coalesced copy) and the neighbour gathers of its warps hit the same
+// cache lines.
+struct BMap {
+  int k, kl, rsub, i0, istride, r0, r1;
+};
+__device__ __forceinline__ BMap block_map(int lanes, int N, int rpb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int rpw = 32 / lanes;
+  BMap mp;
+  mp.kl = lane & (lanes - 1);
+  mp.rsub = lane / lanes;
+  mp.k = blockIdx.x * lanes + mp.kl;
+  mp.r0 = blockIdx.y * rpb;
+  mp.r1 = min(N, mp.r0 + rpb);
+  mp.i0 = mp.r0 + warp * rpw + mp.rsub;
+  mp.istride = wpb * rpw;
+  return mp;
+}
+
+// Bytes of dynamic shared memory for a row block of `rows` rows and `nnz`
+// nonzeros (same formula on host and device).
+__host__ __device__ __forceinline__ int ysmem_bytes(int rows, int nnz, bool fp64) {
+  const int rp = ((rows + 1) * 4 + 15) & ~15;
+  return fp64 ? rp + ((nnz * 4 + 15) & ~15) + nnz * 16 : rp + nnz * 16;
+}
+
+template <class R> struct YSmem;
+template <> struct YSmem<float> {
+  const int* rp;
+  const int4* ent;
+  __device__ __forceinline__ void stage(const int32_t* __restrict__ grp, const YView<float>& Y, int r0, int r1,
+                                        unsigned char* sm) {
+    const int nrow = max(0, r1 - r0);
+    int* srp = (int*)sm;
+    int4* sent = (int4*)(sm + (((nrow + 1) * 4 + 15) & ~15));
+    const int base = nrow ? __ldg(grp + r0) : 0;
+    const int cnt = nrow ? __ldg(grp + r1) - base : 0;
+    for (int t = threadIdx.x; t <= nrow; t += blockDim.x) srp[t] = (nrow ? __ldg(grp + r0 + t) : 0) - base;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) sent[t] = __ldg(Y.ent + base + t);
+    __syncthreads();
+    rp = srp - r0;  // index by global row
+    ent = sent;
+  }
+  __device__ __forceinline__ void get(int p, int& j, float2& y) const {
+    const int4 e = ent[p];
+    j = e.x;
+    y = make_float2(__int_as_float(e.y), __int_as_float(e.z));
+  }
+};
+template <> struct YSmem<double> {
+  const int* rp;
+  const int* col;
+  const double2* val;
+  __device__ __forceinline__ void stage(const int32_t* __restrict__ grp, const YView<double>& Y, int r0, int r1,
+                                        unsigned char* sm) {
+    const int nrow = max(0, r1 - r0);
+    int* srp = (int*)sm;
+    const int base = nrow ? __ldg(grp + r0) : 0;
+    const int cnt = nrow ? __ldg(grp + r1) - base : 0;
+    int* scol = (int*)(sm + (((nrow + 1) * 4 + 15) & ~15));
+    double2* sval = (double2*)((unsigned char*)scol + ((cnt * 4 + 15) & ~15));
+    for (int t = threadIdx.x; t <= nrow; t += blockDim.x) srp[t] = (nrow ? __ldg(grp + r0 + t) : 0) - base;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      scol[t] = __ldg(Y.col + base + t);
+      sval[t] = __ldg(Y.val + base + t);
+    }
+    __syncthreads();
+    rp = srp - r0;
+    col = scol;
+    val = sval;
+  }
+  __device__ __forceinline__ void get(int p, int& j, double2& y) const {
+    j = col[p];
+    y = val[p];
+  }
+};
+
+// acc_row = sum_p Y[p] * X[col(p)*Kp + k] over the row's nonzeros [p0, p1).
+// Four nonzeros per step with predicated loads, so up to four independent
+// gathers are in flight per thread.
+template <class R, class YS>
+__device__ __forceinline__ typename Prec<R>::C row_spmv(const YS& ys, int p0, int p1,
+                                                        const typename Prec<R>::C* __restrict__ X, size_t Kp,
+                                                        int k) {
+  using C = typename Prec<R>::C;
+  C a0 = mkc(R(0), R(0)), a1 = a0;
+  for (int p = p0; p < p1; p += 4) {
+    int j[4];
+    C y[4], x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (p + u < p1) {
+        ys.get(p + u, j[u], y[u]);
+      } else {
+        j[u] = -1;
+        y[u] = mkc(R(0), R(0));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = (j[u] >= 0) ? X[(size_t)j[u] * Kp + k] : mkc(R(0), R(0));
+    cfma(a0, y[0], x[0]);
+    cfma(a1, y[1], x[1]);
+    cfma(a0, y[2], x[2]);
+    cfma(a1, y[3], x[3]);
+  }
+  return mkc(a0.x + a1.x, a0.y + a1.y);
+}
+
 // ---- arguments -------------------------------------------------------------
 template <class R> struct IterArgs {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
-  int N, Kp, lanes;
+  int N, Kp, lanes, rpb;
   const int32_t* __restrict__ rp;
   YView<R> Y;
   const uint8_t* __restrict__ type;
@@ -211,6 +306,7 @@ template <class R> struct IterArgs {
   const C* ytt;
   int has_outage;
   R* loss_acc;
+  unsigned int* mx32;  // per-case max |dP|,|dQ| (float bits) or NULL
   const R* step_size;
   const R* isbc2;
   R beta1, beta2, eps, inv_m2;
@@ -222,15 +318,51 @@ template <class R> struct IterArgs {
   R* gvm;
 };
 
+// Per-case sum and max over the CTA, one atomic each per case.  Every thread
+// of the CTA must call it.
+template <class R>
+__device__ __forceinline__ void case_sum_max_atomic(R v, float mx, int lanes, R* sum_out, unsigned int* max_out,
+                                                    int Kp) {
+  __shared__ R red[32][32];
+  __shared__ float redm[32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int off = 16; off >= lanes; off >>= 1) {
+    v += __shfl_xor_sync(0xffffffffu, v, off);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  if (lane < lanes) {
+    red[warp][lane] = v;
+    redm[warp][lane] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x < lanes) {
+    R s = 0;
+    float m = 0.f;
+    for (int w = 0; w < wpb; ++w) {
+      s += red[w][threadIdx.x];
+      m = fmaxf(m, redm[w][threadIdx.x]);
+    }
+    const int k = blockIdx.x * lanes + threadIdx.x;
+    if (k < Kp) {
+      if (sum_out && s != R(0)) atomicAdd(sum_out + k, s);
+      if (max_out && m > 0.f) atomicMax(max_out + k, __float_as_uint(m));
+    }
+  }
+}
+
 // ---- forward: SpMV + power + mismatch + loss --------------------------------
 template <class R>
-__global__ void __launch_bounds__(1024) k_fwd(IterArgs<R> a) {
+__global__ void __launch_bounds__(256) k_fwd(IterArgs<R> a) {
   using C = typename Prec<R>::C;
+  extern __shared__ __align__(16) unsigned char smem[];
   if (a.n_active && *a.n_active == 0) return;
-  const Map mp = thread_map(a.lanes);
+  const BMap mp = block_map(a.lanes, a.N, a.rpb);
+  YSmem<R> ys;
+  ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
   const int k = mp.k;
   const bool on = (k < a.Kp) && a.active[k];
   R acc = 0;
+  float mx = 0.f;
   if (on) {
     int of = -1, ot = -1;
     C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
@@ -241,17 +373,13 @@ __global__ void __launch_bounds__(1024) k_fwd(IterArgs<R> a) {
     }
     const size_t Kp = (size_t)a.Kp;
     const C* __restrict__ V = a.V;
-    for (int i = mp.row0; i < a.N; i += mp.rstride) {
+    for (int i = mp.i0; i < mp.r1; i += mp.istride) {
       const size_t e = (size_t)i * Kp + k;
-      C I = mkc(R(0), R(0));
-      const int p1 = __ldg(a.rp + i + 1);
-      for (int p = __ldg(a.rp + i); p < p1; ++p) {
-        int j;
-        C y;
-        a.Y.get(p, j, y);
-        cfma(I, y, V[(size_t)j * Kp + k]);
-      }
+      const int ty = __ldg(a.type + i);
+      const size_t si = a.spec_per_case ? e : (size_t)i;
       const C vi = V[e];
+      const R ps = a.pspec[si], qs = a.qspec[si];
+      C I = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], V, Kp, k);
       if (i == of) {
         cfms(I, yff, vi);
         cfms(I, yft, V[(size_t)ot * Kp + k]);
@@ -261,28 +389,31 @@ __global__ void __launch_bounds__(1024) k_fwd(IterArgs<R> a) {
       }
       const R P = vi.x * I.x + vi.y * I.y;
       const R Q = vi.y * I.x - vi.x * I.y;
-      const int ty = __ldg(a.type + i);
-      const size_t si = a.spec_per_case ? e : (size_t)i;
-      const R dP = (ty != BUS_SLACK) ? P - a.pspec[si] : R(0);
-      const R dQ = (ty == BUS_PQ) ? Q - a.qspec[si] : R(0);
+      const R dP = (ty != BUS_SLACK) ? P - ps : R(0);
+      const R dQ = (ty == BUS_PQ) ? Q - qs : R(0);
       const R ca = a.inv_m2 * dP, cb = a.inv_m2 * dQ;
       a.W[e] = mkc(ca * vi.x + cb * vi.y, cb * vi.x - ca * vi.y);
       a.G0[e] = mkc(ca * P + cb * Q, ca * Q - cb * P);
       if (a.sbuf) a.sbuf[e] = mkc(P, Q);
       if (a.cbuf) a.cbuf[e] = mkc(ca, cb);
       acc += dP * dP + dQ * dQ;
+      const float am = fmaxf(fabsf((float)dP), fabsf((float)dQ));
+      mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);  // NaN -> +inf
     }
   }
-  if (a.loss_acc) case_sum_atomic(acc, a.lanes, a.loss_acc, a.Kp);
+  if (a.loss_acc || a.mx32) case_sum_max_atomic(acc, mx, a.lanes, a.loss_acc, a.mx32, a.Kp);
 }
 
 // ---- adjoint SpMV + gradient + Adam ----------------------------------------
 template <class R>
-__global__ void __launch_bounds__(1024) k_adj(IterArgs<R> a) {
+__global__ void __launch_bounds__(256) k_adj(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
+  extern __shared__ __align__(16) unsigned char smem[];
   if (a.n_active && *a.n_active == 0) return;
-  const Map mp = thread_map(a.lanes);
+  const BMap mp = block_map(a.lanes, a.N, a.rpb);
+  YSmem<R> ys;
+  ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
   const int k = mp.k;
   if (k >= a.Kp || !a.active[k]) return;
   int of = -1, ot = -1;
@@ -298,21 +429,24 @@ __global__ void __launch_bounds__(1024) k_adj(IterArgs<R> a) {
   const R b1 = a.beta1, b2 = a.beta2, eps = a.eps;
   const size_t Kp = (size_t)a.Kp;
   const C* __restrict__ W = a.W;
-  for (int i = mp.row0; i < a.N; i += mp.rstride) {
+  for (int i = mp.i0; i < mp.r1; i += mp.istride) {
     const size_t e = (size_t)i * Kp + k;
     const int ty = __ldg(a.type + i);
     if (ty == BUS_SLACK) {
       if (grad_only) { a.gva[e] = R(0); a.gvm[e] = R(0); }
       continue;
     }
-    C z = mkc(R(0), R(0));
-    const int p1 = __ldg(a.rp + i + 1);
-    for (int p = __ldg(a.rp + i); p < p1; ++p) {
-      int j;
-      C y;
-      a.Y.get(p, j, y);
-      cfma(z, y, W[(size_t)j * Kp + k]);
+    // this element's operands first: they do not depend on the gather chain
+    const C g0 = a.G0[e];
+    M th = a.th[e];
+    M vm = a.vm[e];
+    R m1 = 0, v1 = 0, m2 = 0, v2 = 0;
+    if (!grad_only) {
+      m1 = a.mth[e];
+      v1 = a.vth[e];
+      if (ty == BUS_PQ) { m2 = a.mvm[e]; v2 = a.vvm[e]; }
     }
+    C z = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], W, Kp, k);
     if (i == of) {
       cfms(z, yff, W[e]);
       cfms(z, yft, W[(size_t)ot * Kp + k]);
@@ -320,10 +454,7 @@ __global__ void __launch_bounds__(1024) k_adj(IterArgs<R> a) {
       cfms(z, yft, W[(size_t)of * Kp + k]);
       cfms(z, ytt, W[e]);
     }
-    M th = a.th[e];
-    M vm = a.vm[e];
     const C vi = volt(th, vm);
-    const C g0 = a.G0[e];
     const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
     const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
     const R g_th = -hi;
@@ -333,22 +464,19 @@ __global__ void __launch_bounds__(1024) k_adj(IterArgs<R> a) {
       a.gvm[e] = g_vm;
       continue;
     }
-    {  // Adam on theta (pv and pq buses)
-      R m1 = a.mth[e], v1 = a.vth[e];
-      m1 = b1 * m1 + (R(1) - b1) * g_th;
-      v1 = b2 * v1 + (R(1) - b2) * g_th * g_th;
-      a.mth[e] = m1;
-      a.vth[e] = v1;
-      th = msub(th, step * m1 / (sqrtT(v1) * isb + eps));
-      a.th[e] = th;
-    }
+    // Adam on theta (pv and pq buses)
+    m1 = b1 * m1 + (R(1) - b1) * g_th;
+    v1 = b2 * v1 + (R(1) - b2) * g_th * g_th;
+    a.mth[e] = m1;
+    a.vth[e] = v1;
+    th = msub(th, step * m1 / (sqrtT(v1) * isb + eps));
+    a.th[e] = th;
     if (ty == BUS_PQ) {  // Adam on |V| (pq buses)
-      R m1 = a.mvm[e], v1 = a.vvm[e];
-      m1 = b1 * m1 + (R(1) - b1) * g_vm;
-      v1 = b2 * v1 + (R(1) - b2) * g_vm * g_vm;
-      a.mvm[e] = m1;
-      a.vvm[e] = v1;
-      vm = msub(vm, step * m1 / (sqrtT(v1) * isb + eps));
+      m2 = b1 * m2 + (R(1) - b1) * g_vm;
+      v2 = b2 * v2 + (R(1) - b2) * g_vm * g_vm;
+      a.mvm[e] = m2;
+      a.vvm[e] = v2;
+      vm = msub(vm, step * m2 / (sqrtT(v2) * isb + eps));
       a.vm[e] = vm;
     }
     a.V[e] = volt(th, vm);
@@ -362,10 +490,15 @@ template <class R> struct SchedArgs {
   int32_t* iters;
   int32_t* status;
   R* loss_acc;
+  unsigned int* mx32;  // FP32 max mismatch of the last forward pass (or NULL)
+  int32_t* cand;       // 1: the next FP64 test examines the case
+  double gate;         // FP32 max mismatch below which the FP64 test runs (<= 0: always)
   double* lr;
   double* best;
   int32_t* bad;
   int32_t* cool;
+  double* b1t;         // beta1^t, beta2^t of the next Adam step (running products)
+  double* b2t;
   R* step_size;
   R* isbc2;
   int32_t* n_active;
@@ -379,6 +512,11 @@ __global__ void k_sched(SchedArgs<R> a) {
   if (k >= a.Kp || !a.active[k]) return;
   const double L = (double)a.loss_acc[k] * a.inv_m;  // MSE of the iterate the step came from
   a.loss_acc[k] = R(0);
+  if (a.mx32) {
+    const float mxf = __uint_as_float(a.mx32[k]);
+    a.mx32[k] = 0u;
+    a.cand[k] = (a.gate <= 0.0 || (double)mxf <= a.gate) ? 1 : 0;
+  }
   const int it = a.iters[k] + 1;
   a.iters[k] = it;
   if (!isfinite(L)) {
@@ -404,12 +542,20 @@ __global__ void k_sched(SchedArgs<R> a) {
     a.bad[k] = bad;
     a.cool[k] = cool;
   } else if (a.sched == SCHED_STEP) {
-    lr = a.lr0 * pow(a.gamma, (double)(it / a.step_every));
+    double gk = 1.0;  // gamma^(it / step_every) by repeated squaring (no pow: FP64 is slow here)
+    double base = a.gamma;
+    for (int e = it / a.step_every; e > 0; e >>= 1) {
+      if (e & 1) gk *= base;
+      base *= base;
+    }
+    lr = a.lr0 * gk;
   }
   a.lr[k] = lr;
-  const double t1 = (double)(it + 1);  // Adam step number of the next update
-  a.step_size[k] = (R)(lr / (1.0 - pow(a.beta1, t1)));
-  a.isbc2[k] = (R)(1.0 / sqrt(1.0 - pow(a.beta2, t1)));
+  const double b1t = a.b1t[k] * a.beta1, b2t = a.b2t[k] * a.beta2;  // beta^(it+1)
+  a.b1t[k] = b1t;
+  a.b2t[k] = b2t;
+  a.step_size[k] = (R)(lr / (1.0 - b1t));
+  a.isbc2[k] = (R)(1.0 / sqrt(1.0 - b2t));
 }
 
 // ---- FP64 convergence test --------------------------------------------------
@@ -426,6 +572,7 @@ template <class M> struct Check64Args {
   const double* qspec;
   int spec_per_case;
   const int32_t* active;
+  const int32_t* cand;  // NULL: every active case; else only cases with cand[k] = 1
   const int32_t* of;
   const int32_t* ot;
   const double2* yff;
@@ -443,7 +590,7 @@ __global__ void __launch_bounds__(1024) k_volt64(Check64Args<M> a) {
   if (!a.all_cases && *a.n_active == 0) return;
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
-  if (k >= a.Kp || !(a.all_cases || a.active[k])) return;
+  if (k >= a.Kp || !(a.all_cases || (a.active[k] && (!a.cand || a.cand[k])))) return;
   for (int i = mp.row0; i < a.N; i += mp.rstride) {
     const size_t e = (size_t)i * a.Kp + k;
     a.V64[e] = volt64(a.th[e], a.vm[e]);
@@ -455,7 +602,7 @@ __global__ void __launch_bounds__(1024) k_check64(Check64Args<M> a) {
   if (!a.all_cases && *a.n_active == 0) return;
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
-  const bool on = (k < a.Kp) && (a.all_cases || a.active[k]);
+  const bool on = (k < a.Kp) && (a.all_cases || (a.active[k] && (!a.cand || a.cand[k])));
   double mx = 0.0, sq = 0.0;
   if (on) {
     int of = -1, ot = -1;
@@ -504,6 +651,7 @@ struct ApplyArgs {
   int K, Kp, final_pass;
   double tol, inv_m;
   int32_t* active;
+  const int32_t* cand;
   int32_t* status;
   unsigned long long* maxmis;
   double* loss64;
@@ -524,7 +672,7 @@ __global__ void k_apply(ApplyArgs a) {
         a.out_loss[k] = L;
         if (a.active[k]) a.status[k] = (mx <= a.tol) ? CASE_CONVERGED : CASE_MAX_ITER;
         a.active[k] = 0;
-      } else if (a.active[k] && mx <= a.tol) {
+      } else if (a.active[k] && (!a.cand || a.cand[k]) && mx <= a.tol) {
         a.active[k] = 0;
         a.status[k] = CASE_CONVERGED;
         a.out_max[k] = mx;
@@ -585,6 +733,7 @@ template <class R> struct InitArgs {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
   int N, K, Kp;
+  int enforce_fixed;         // 1: slack angle and pv/slack |V| set from the specification
   const uint8_t* type;
   const double* vmset_grid;  // [N]
   const double* vms_t;       // [N][Kp] or NULL
@@ -614,9 +763,11 @@ __global__ void k_init(InitArgs<R> a) {
     double th = 0.0, vm = 1.0;
     if (k < a.K) {
       if (a.va_t) { th = a.va_t[e]; vm = a.vm_t[e]; }
-      const double set = a.vms_t ? a.vms_t[e] : a.vmset_grid[i];
-      if (ty != BUS_PQ) vm = set;
-      if (ty == BUS_SLACK) th = a.va_slack;
+      if (a.enforce_fixed || !a.va_t) {
+        const double set = a.vms_t ? a.vms_t[e] : a.vmset_grid[i];
+        if (ty != BUS_PQ) vm = set;
+        if (ty == BUS_SLACK) th = a.va_slack;
+      }
     }
     const M mth = mfrom<M>(th), mvm = mfrom<M>(vm);
     a.th[e] = mth;
@@ -663,6 +814,10 @@ template <class R> struct CaseInitArgs {
   R* loss_acc;
   R* step_size;
   R* isbc2;
+  double* b1t;
+  double* b2t;
+  int32_t* cand;
+  unsigned int* mx32;
   unsigned long long* maxmis;
   double* loss64;
   double lr0, beta1, beta2;
@@ -683,6 +838,10 @@ __global__ void k_case_init(CaseInitArgs<R> a) {
   a.loss_acc[k] = R(0);
   a.step_size[k] = (R)(a.lr0 / (1.0 - a.beta1));
   a.isbc2[k] = (R)(1.0 / sqrt(1.0 - a.beta2));
+  a.b1t[k] = a.beta1;  // beta^1: bias correction of the first step
+  a.b2t[k] = a.beta2;
+  a.cand[k] = 1;
+  a.mx32[k] = 0u;
   a.maxmis[k] = 0ULL;
   a.loss64[k] = 0.0;
   int ell = (real && a.outage) ? a.outage[k] : -1;

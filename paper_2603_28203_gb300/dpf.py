@@ -165,6 +165,7 @@ class SolveOpts:
     max_iter: int | None = None
     check_every: int | None = None
     tol: float | None = None
+    gate: float | None = None
     flat_start: int | None = None
     precision: int | None = None
     lanes: int | None = None
@@ -257,6 +258,24 @@ def dpf_solve_end(ws: Workspace, stream=None, **batch):
 def dpf_active_count(ws: Workspace, stream=None) -> int:
     n = C.c_int32()
     _check(lib().dpf_active_count(ws.handle, C.byref(n), _stream(stream)))
+    return n.value
+
+
+def dpf_profile_enable(ws: Workspace, on: bool = True):
+    _check(lib().dpf_profile_enable(ws.handle, 1 if on else 0))
+
+
+def dpf_kernel_times(ws: Workspace, stream=None):
+    """(fwd_ms_total, adj_ms_total, n_fwd, n_adj) of the bracketed launches."""
+    f, a = C.c_double(), C.c_double()
+    nf, na = C.c_int32(), C.c_int32()
+    _check(lib().dpf_kernel_times(ws.handle, C.byref(f), C.byref(a), C.byref(nf), C.byref(na), _stream(stream)))
+    return f.value, a.value, nf.value, na.value
+
+
+def dpf_kernel_launches(ws: Workspace) -> int:
+    n = C.c_int64()
+    _check(lib().dpf_kernel_launches(ws.handle, C.byref(n)))
     return n.value
 
 

@@ -50,7 +50,7 @@ def _t(a, dtype=torch.float64):
 
 GRIDS = {
     "c1": lambda: gridgen.config_grid("c1_30bus_fp64"),
-    "g300": lambda: gridgen.make_grid(300, 5, load_scale=0.3),
+    "g300": lambda: gridgen.make_grid(300, 5, load_scale=0.1),
     "c3": lambda: gridgen.config_grid("c3_n1_2kbus"),
 }
 
