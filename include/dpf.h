@@ -222,6 +222,29 @@ int dpf_power(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
               const double* va, const double* vm, const int32_t* outage,
               int32_t precision, double* p_calc, double* q_calc, void* stream);
 
+/* ---- forward evaluation without device allocation ---------------------------
+ * No counterpart in the paper: a deployment variant of dpf_power for callers
+ * that cannot allocate device memory -- code running inside an application
+ * that owns the whole device memory budget through its own pool (a raw
+ * cudaMalloc there fails or bypasses the application's accounting) and
+ * latency-critical loops that cannot afford the implicit synchronisation of
+ * cudaMalloc/cudaFree.  Same result as dpf_power with precision DPF_FP64
+ * (va, vm taken verbatim; no outages), but it needs no workspace and calls
+ * no allocating routine.  Its scratch is a fixed array inside the library of
+ * DPF_NOALLOC_MAX_ELEMS complex values (4 MiB), which every GPU that loads
+ * the library holds until the process exits; n_case * n_bus above that limit
+ * is rejected with DPF_E_INVALID.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array,
+ * so calls whose work overlaps on the GPU (different streams, or host threads
+ * without ordering) race: serialise them, e.g. on one stream.  The scratch
+ * is fully rewritten by each call before it is read.  Inputs va, vm
+ * [n_case][n_bus] and outputs p_calc, q_calc (either may be NULL) are
+ * caller-owned device arrays. */
+#define DPF_NOALLOC_MAX_ELEMS (1 << 18)
+int dpf_power_noalloc(const dpf_ybus* y, int32_t n_case, const double* va, const double* vm,
+                      double* p_calc, double* q_calc, void* stream);
+
 /* ---- loss and its adjoint (Sec. 4.1: dL/dx = J^T F, scaled by the MSE) ----
  * For n_case states (va, vm) and specified injections (p_spec/q_spec, NULL =
  * the grid's; case-major device arrays) computes the FP64 loss per case and,

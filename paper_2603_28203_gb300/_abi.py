@@ -9,6 +9,7 @@ CASE_CONVERGED, CASE_MAX_ITER, CASE_DIVERGED = 0, 1, 2
 PQ, PV, SLACK = 0, 1, 2
 FP32, FP64 = 0, 1
 SCHED_CONST, SCHED_PLATEAU, SCHED_STEP = 0, 1, 2
+NOALLOC_MAX_ELEMS = 1 << 18
 
 p_i32 = C.POINTER(C.c_int32)
 p_u8 = C.POINTER(C.c_uint8)
@@ -74,6 +75,7 @@ SIGNATURES = {
     "dpf_power": (C.c_int, [VP, VP, I32, VP, VP, VP, I32, VP, VP, VP]),
     "dpf_loss_backward": (C.c_int, [VP, VP, I32, VP, VP, VP, VP, VP, VP, VP, I32,
                                     VP, VP, VP, VP, VP, VP, VP, VP, VP]),
+    "dpf_power_noalloc": (C.c_int, [VP, I32, VP, VP, VP, VP, VP]),
     "dpf_profile_enable": (C.c_int, [VP, I32]),
     "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),
     "dpf_kernel_launches": (C.c_int, [VP, C.POINTER(C.c_int64)]),

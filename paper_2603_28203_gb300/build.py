@@ -1,4 +1,4 @@
-"""Build libdpf.so in-tree for sm_103a (nvcc + g++, two translation units in parallel)."""
+"""Build libdpf.so in-tree for sm_103a (nvcc + g++, translation units compiled in parallel)."""
 from __future__ import annotations
 
 import os
@@ -33,18 +33,23 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
-    api_o = os.path.join(OUT_DIR, "dpf_api.o")
+    objs, cmds = [], []
+    for src in ("dpf_api.cu", "dpf_noalloc.cu"):
+        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        cu = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-I" + INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        if ptxas_info:
+            cu.insert(1, "-Xptxas=-v")
+        objs.append(obj)
+        cmds.append(cu)
     host_o = os.path.join(OUT_DIR, "dpf_host.o")
-    cu = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-          "-I" + INCLUDE, "-c", os.path.join(CSRC, "dpf_api.cu"), "-o", api_o]
-    if ptxas_info:
-        cu.insert(1, "-Xptxas=-v")
-    cxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE,
-           "-I" + os.path.join(cuda, "include"), "-c", os.path.join(CSRC, "dpf_host.cpp"), "-o", host_o]
-    with ThreadPoolExecutor(2) as ex:
-        outs = list(ex.map(_run, [cu, cxx]))
+    cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE,
+                 "-I" + os.path.join(cuda, "include"), "-c", os.path.join(CSRC, "dpf_host.cpp"), "-o", host_o])
+    objs.append(host_o)
+    with ThreadPoolExecutor(len(cmds)) as ex:
+        outs = list(ex.map(_run, cmds))
     tmp = LIB + ".tmp"
-    outs.append(_run([nvcc, *ARCH, "-shared", api_o, host_o, "-o", tmp]))
+    outs.append(_run([nvcc, *ARCH, "-shared", *objs, "-o", tmp]))
     os.replace(tmp, LIB)
     if verbose:
         for o in outs:

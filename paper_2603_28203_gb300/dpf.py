@@ -296,6 +296,16 @@ def dpf_power(y: Ybus, ws: Workspace, va, vm, outage=None, precision=_abi.FP32, 
     return p, q
 
 
+def dpf_power_noalloc(y: Ybus, va, vm, p_calc, q_calc, stream=None):
+    """FP64 S_calc into caller-provided tensors without any device allocation.
+
+    For callers that cannot allocate device memory (see include/dpf.h); the
+    library's fixed scratch limits n_case * n_bus to NOALLOC_MAX_ELEMS.
+    """
+    _check(lib().dpf_power_noalloc(y.handle, int(va.shape[0]), _ptr(va), _ptr(vm), _ptr(p_calc), _ptr(q_calc),
+                                   _stream(stream)))
+
+
 def dpf_loss_backward(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, outage=None,
                       g_series=None, b_series=None, precision=_abi.FP32, want=("loss", "d_va", "d_vm"),
                       stream=None):
