@@ -13,6 +13,12 @@ Here the element-wise rules are written as sparse matrix products: the
 off-diagonal rule applied to every (i, j) of Y's pattern is
 diag(V) conj(Y) diag(conj(V)/|V|) (resp. -j diag(V) conj(Y) diag(conj(V))), and
 the diagonal rule adds diag(V/|V| conj(I)) (resp. j diag(V conj(I))).
+
+|V| in these denominators is the magnitude variable itself (Alg. 1: the
+learnable real factor in V = |V| e^{j theta}), not the modulus of V: the two
+agree while the variable is positive, and using the variable keeps the
+partials those of S with respect to the learnable when an iterate's
+magnitude turns negative.
 """
 from __future__ import annotations
 
@@ -24,11 +30,12 @@ from .power import learnable_sets, voltage
 
 def dS_dVm_dVa(Y, va, vm):
     """(dS/d|V|, dS/dtheta) as complex sparse matrices (Alg. 2)."""
+    vm = np.asarray(vm, np.float64)
     V = voltage(va, vm)
     I = Y @ V
     Yc = Y.conj()
     dV = sp.diags(V)
-    d_vm = dV @ Yc @ sp.diags(np.conj(V) / np.abs(V)) + sp.diags(V / np.abs(V) * np.conj(I))
+    d_vm = dV @ Yc @ sp.diags(np.conj(V) / vm) + sp.diags(V / vm * np.conj(I))
     d_va = -1j * (dV @ Yc @ sp.diags(np.conj(V))) + sp.diags(1j * V * np.conj(I))
     return d_vm.tocsr(), d_va.tocsr()
 

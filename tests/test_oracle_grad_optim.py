@@ -27,11 +27,14 @@ def _rand_state(g, seed):
     return va, vm
 
 
-@pytest.mark.parametrize("n,seed,npv", [(3, 1, 1), (4, 2, 1), (5, 3, 2), (5, 9, 1)])
-def test_voltage_gradient_fd(n, seed, npv):
+@pytest.mark.parametrize("n,seed,npv,neg", [(3, 1, 1, False), (4, 2, 1, False), (5, 3, 2, False),
+                                            (5, 9, 1, False), (5, 9, 1, True)])
+def test_voltage_gradient_fd(n, seed, npv, neg):
     g = small_grid(n, seed, n_pv=npv)
     Y = grid_ybus(g)
     va, vm = _rand_state(g, seed)
+    if neg:  # an iterate whose magnitude variable went negative
+        vm[g.pq[0]] = -0.3
     L, d_va, d_vm = oracle.loss_grad(Y, va, vm, g.p_spec, g.q_spec, g.bus_type)
     h = 1e-6
     pvpq, pq = oracle.learnable_sets(g.bus_type)
