@@ -23,6 +23,7 @@ bounded sample of the same workload, on the host cores.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -239,6 +240,9 @@ def run_ours(args):
     opts = dpf.SolveOpts(lr=LR, tol=TOL, check_every=CHECK_EVERY, precision=dpf.FP32,
                          max_iter=args.warmup + args.steps + args.profile_steps + 8 * CHECK_EVERY,
                          lanes=args.lanes or None, warps=args.warps or None, row_blocks=args.row_blocks or None)
+    if not (args.lanes or args.warps or args.row_blocks or args.no_autotune):
+        with torch.cuda.stream(stream):
+            opts = dpf.dpf_autotune(y, ws, opts, iters=50, stream=stream, n_case=K, outage=out_dev)
     res = dict(va=torch.empty((K, N), dtype=torch.float64, device=dev),
                vm=torch.empty((K, N), dtype=torch.float64, device=dev),
                iters=torch.empty(K, dtype=torch.int32, device=dev),
@@ -301,7 +305,7 @@ def run_ours(args):
     # end-to-end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(dpf, y, ws, g, outages, stream, args)
+        e2e = run_e2e(dpf, y, ws, g, outages, stream, args, opts)
 
     if rank == 0:
         line = {
@@ -329,6 +333,10 @@ def run_ours(args):
                 "step": "one DPF iteration of the whole batch",
                 "l2": "per-iteration working set ~0.5 GB >> 129 MB L2 (no flush needed)",
                 "parallelism": f"replicas x{world} (independent cases, no data-path collective)",
+                "launch_shape": {"lanes": opts.lanes, "warps": opts.warps, "row_blocks": opts.row_blocks,
+                                 "pair_cases": opts.pair_cases, "chosen_by": "dpf_autotune"
+                                 if not (args.lanes or args.warps or args.row_blocks or args.no_autotune)
+                                 else "command line"},
             },
             "case_iterations_per_s": case_iters / (t_max / 1e3),
             "converged_frac": float((st == 0).mean()),
@@ -357,7 +365,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(dpf, y, ws, g, outages, stream, args):
+def run_e2e(dpf, y, ws, g, outages, stream, args, opts):
     """Full solves through dpf_solve_batch with pinned host buffers (H2D/D2H inside)."""
     import torch
     K, N = outages.size, g.n_bus
@@ -368,8 +376,7 @@ def run_e2e(dpf, y, ws, g, outages, stream, args):
              status=torch.empty(K, dtype=torch.int32).pin_memory(),
              max_mismatch=torch.empty(K, dtype=torch.float64).pin_memory(),
              loss=torch.empty(K, dtype=torch.float64).pin_memory())
-    opts = dpf.SolveOpts(lr=LR, tol=TOL, check_every=CHECK_EVERY, precision=dpf.FP32, max_iter=ITERS_PER_SOLVE,
-                         lanes=args.lanes or None, warps=args.warps or None, row_blocks=args.row_blocks or None)
+    opts = dataclasses.replace(opts, max_iter=ITERS_PER_SOLVE)
     times = []
     for rep in range(1 + args.e2e_steps):
         torch.cuda.synchronize()
@@ -445,6 +452,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

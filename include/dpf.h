@@ -161,6 +161,10 @@ typedef struct {
   int32_t warps;             /* warps per CTA (1..8); 0 = auto                 */
   int32_t row_blocks;        /* CTAs along the bus dimension; 0 = auto         */
   int32_t use_graph;         /* 1: replay iterations from a CUDA graph         */
+  int32_t pair_cases;        /* FP32 batches of >= 64 cases at 32 lanes: bit 0
+                                runs the forward pass, bit 1 the adjoint pass
+                                with two cases per thread (16-byte accesses);
+                                0: one case per thread                        */
   int32_t plain;             /* 1: the plain form of Alg. 1 -- one case at a
                                 time, separate launches per iteration and a
                                 host stop test (FP64 check + device-to-host
@@ -195,6 +199,18 @@ int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* ws, const dpf_batch* b,
                     const dpf_solve_opts* o, void* stream);
 int dpf_solve_iterate(dpf_workspace* ws, int32_t n_iter, void* stream);
 int dpf_solve_end(dpf_workspace* ws, const dpf_batch* b, void* stream);
+/* Autotuner.  Times candidate launch shapes of the solve loop on this batch
+ * -- cases per row group (`lanes`, i.e. rows per warp = 32/lanes), warps per
+ * CTA, row blocks, and the two-cases-per-thread variants -- for `iters`
+ * iterations each (plus one warm-up check interval), and writes the fastest
+ * into o->lanes, o->warps, o->row_blocks and o->pair_cases.  The batch's
+ * inputs are read (as in dpf_solve_begin) but no output is written; a later
+ * dpf_solve_begin starts from scratch.  Results are cached in the workspace
+ * per (n_case, precision, grid, outage/injection layout).  Synchronises
+ * `stream`. */
+int dpf_autotune(const dpf_ybus* y, dpf_workspace* ws, const dpf_batch* b, dpf_solve_opts* o,
+                 int32_t iters, void* stream);
+
 /* Number of cases still iterating (synchronises `stream`). */
 int dpf_active_count(dpf_workspace* ws, int32_t* n_active, void* stream);
 /* Steps taken so far by the batch (host counter, no synchronisation). */

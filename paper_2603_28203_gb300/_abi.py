@@ -47,7 +47,7 @@ class DpfSolveOpts(C.Structure):
         ("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double), ("gate", C.c_double),
         ("flat_start", C.c_int32), ("precision", C.c_int32),
         ("lanes", C.c_int32), ("warps", C.c_int32), ("row_blocks", C.c_int32),
-        ("use_graph", C.c_int32), ("plain", C.c_int32),
+        ("use_graph", C.c_int32), ("pair_cases", C.c_int32), ("plain", C.c_int32),
     ]
 
 
@@ -71,6 +71,7 @@ SIGNATURES = {
     "dpf_solve_iterate": (C.c_int, [VP, I32, VP]),
     "dpf_solve_end": (C.c_int, [VP, C.POINTER(DpfBatch), VP]),
     "dpf_active_count": (C.c_int, [VP, p_i32, VP]),
+    "dpf_autotune": (C.c_int, [VP, VP, C.POINTER(DpfBatch), C.POINTER(DpfSolveOpts), I32, VP]),
     "dpf_iterations_done": (C.c_int, [VP, p_i32]),
     "dpf_power": (C.c_int, [VP, VP, I32, VP, VP, VP, I32, VP, VP, VP]),
     "dpf_loss_backward": (C.c_int, [VP, VP, I32, VP, VP, VP, VP, VP, VP, VP, I32,

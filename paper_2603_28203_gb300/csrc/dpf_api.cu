@@ -221,6 +221,9 @@ struct dpf_workspace {
   // solve state
   bool begun = false;
   int K = 0, Kp = 0, lanes = 1, warps = 8, gx = 1, gy = 1, rpb = 1, smem = 0, precision = DPF_FP32;
+  bool pairs = false;   // FP32 solve loop, Kp a multiple of 64: two cases per thread possible
+  bool pair_fwd = false, pair_adj = false;
+  std::vector<std::pair<std::vector<long long>, std::vector<int>>> tune_cache;  // key -> (lanes, warps, rb, pairs)
   bool spec_per_case = false, has_outage = false;
   dpf_solve_opts opts;
   int t_done = 0;
@@ -374,7 +377,9 @@ struct Plan {
   SchedArgs<R> sc;
   Check64Args<M> ck;
   ApplyArgs ap;
-  dim3 grid, block;
+  dim3 grid, block;   // one case per thread
+  dim3 cgrid;         // (the same; check and evaluation kernels)
+  dim3 pgrid;         // two cases per thread
   int smem;
   int sched_blocks;
   bool need_volt64;
@@ -519,7 +524,9 @@ static Plan<R> make_plan(dpf_workspace* w) {
   p.out_loss = w->out_loss;
   p.n_active = w->n_active;
 
-  P.grid = dim3(w->gx, w->gy);
+  P.cgrid = dim3(w->Kp / w->lanes, w->gy);
+  P.grid = P.cgrid;
+  P.pgrid = dim3(w->Kp / 64, w->gy);
   P.block = dim3(w->warps * 32);
   P.smem = w->smem;
   P.sched_blocks = (w->Kp + 255) / 256;
@@ -533,10 +540,10 @@ static int launch_check(dpf_workspace* w, cudaStream_t s, bool final_pass) {
   P.ap.final_pass = final_pass ? 1 : 0;
   using M = typename Prec<R>::M;
   if (P.need_volt64) {
-    k_volt64<M><<<P.grid, P.block, 0, s>>>(P.ck);
+    k_volt64<M><<<P.cgrid, P.block, 0, s>>>(P.ck);
     w->launches++;
   }
-  k_check64<M><<<P.grid, P.block, 0, s>>>(P.ck);
+  k_check64<M><<<P.cgrid, P.block, 0, s>>>(P.ck);
   k_apply<<<1, 1024, 0, s>>>(P.ap);
   w->launches += 2;
   CKLAUNCH();
@@ -554,9 +561,19 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
     TRY(ev_take(w, &e2));
     CK(cudaEventRecord(e0, s));
   }
-  k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  if constexpr (sizeof(R) == 4) {
+    if (w->pair_fwd) k_fwd2<<<P.pgrid, P.block, P.smem, s>>>(P.it);
+    else k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  } else {
+    k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  }
   if (w->profile) CK(cudaEventRecord(e1, s));
-  k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  if constexpr (sizeof(R) == 4) {
+    if (w->pair_adj) k_adj2<<<P.pgrid, P.block, P.smem, s>>>(P.it);
+    else k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  } else {
+    k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  }
   if (w->profile) {
     CK(cudaEventRecord(e2, s));
     const int i2 = (int)w->ev_used - 1;
@@ -635,7 +652,12 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   if (lanes > 32) lanes = 32;
   lanes = pow2ceil(lanes);
   w->lanes = lanes;
-  w->Kp = (K + lanes - 1) / lanes * lanes;
+  // FP32 solve loop over >= 64 cases at 32 lanes: two cases per thread
+  w->pairs = o && o->precision == DPF_FP32 && lanes == 32 && K >= 64 && o->pair_cases != 0;
+  w->pair_fwd = w->pairs && (o->pair_cases & 1);
+  w->pair_adj = w->pairs && (o->pair_cases & 2);
+  const int tile = w->pairs ? 64 : lanes;
+  w->Kp = (K + tile - 1) / tile * tile;
   w->warps = (o && o->warps > 0) ? std::min(o->warps, 8) : 8;
   const int rpw = 32 / lanes;
   w->gx = w->Kp / lanes;
@@ -669,6 +691,10 @@ static int set_smem_attr(int bytes) {
   if (bytes > 48 * 1024) {
     CK(cudaFuncSetAttribute(k_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     CK(cudaFuncSetAttribute(k_adj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if constexpr (sizeof(R) == 4) {
+      CK(cudaFuncSetAttribute(k_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_adj2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    }
   }
   return DPF_OK;
 }
@@ -1080,6 +1106,86 @@ extern "C" int dpf_solve_batch(const dpf_ybus* y, dpf_workspace* ws, const dpf_b
     dpf_workspace_free(w);
   }
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: launch shape of the solve loop, timed on the caller's batch
+// ---------------------------------------------------------------------------
+extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b, dpf_solve_opts* o,
+                            int32_t iters, void* stream) {
+  clear_error();
+  if (!y || !w || !b || !o) return fail(DPF_E_INVALID, "dpf_autotune: NULL argument");
+  if (iters < 1) return fail(DPF_E_INVALID, "iters must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::vector<long long> key = {b->n_case, o->precision, (long long)y->n, y->nnz, b->outage != nullptr,
+                                      b->p_spec != nullptr};
+  for (auto& kv : w->tune_cache)
+    if (kv.first == key) {
+      o->lanes = kv.second[0];
+      o->warps = kv.second[1];
+      o->row_blocks = kv.second[2];
+      o->pair_cases = kv.second[3];
+      return DPF_OK;
+    }
+  const int K = b->n_case;
+  const int auto_lanes = std::min(32, pow2ceil(K));
+  std::vector<int> lanes_c = {auto_lanes};
+  if (auto_lanes >= 8) { lanes_c.push_back(auto_lanes / 2); lanes_c.push_back(auto_lanes / 4); }
+  std::vector<int> pair_c = {0};
+  if (o->precision == DPF_FP32 && K >= 64) pair_c = {0, 1, 2, 3};
+  // row blocks: the automatic choice and multiples of it
+  dpf_solve_opts base = *o;
+  base.max_iter = 2 * iters + 4 * std::max(1, o->check_every) + 8;
+  base.lanes = auto_lanes;
+  base.warps = 8;
+  base.row_blocks = 0;
+  base.pair_cases = 0;
+  choose_shape(w, &base, K);
+  const int gy_auto = w->gy;
+  std::vector<int> rb_c = {gy_auto, 2 * gy_auto, 4 * gy_auto};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  dpf_solve_opts best = base;
+  int rc = DPF_OK;
+  for (int ln : lanes_c)
+    for (int pc : pair_c)
+      for (int wp : {4, 8})
+        for (int rb : rb_c) {
+          if (pc && ln != 32) continue;
+          dpf_solve_opts c = base;
+          c.lanes = ln;
+          c.pair_cases = pc;
+          c.warps = wp;
+          c.row_blocks = rb;
+          if ((rc = dpf_solve_begin(y, w, b, &c, s)) != DPF_OK) break;
+          const int ce = std::max(1, c.check_every);
+          if ((rc = dpf_solve_iterate(w, ce, s)) != DPF_OK) break;  // warm-up, builds the graph
+          cudaEventRecord(e0, s);
+          const int n = (iters + ce - 1) / ce * ce;
+          if ((rc = dpf_solve_iterate(w, n, s)) != DPF_OK) break;
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= n;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+          }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  w->begun = false;
+  ws_drop_graph(w);
+  if (rc != DPF_OK) return rc;
+  o->lanes = best.lanes;
+  o->warps = best.warps;
+  o->row_blocks = best.row_blocks;
+  o->pair_cases = best.pair_cases;
+  w->tune_cache.push_back({key, {best.lanes, best.warps, best.row_blocks, best.pair_cases}});
+  return DPF_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -344,5 +344,6 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->warps = 0;
   o->row_blocks = 0;
   o->use_graph = 1;
+  o->pair_cases = 1;  /* forward pass two cases per thread */
   o->plain = 0;
 }

@@ -43,6 +43,13 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float sqrtT(float a) { return sqrtf(a); }
 __device__ __forceinline__ double sqrtT(double a) { return sqrt(a); }
+// Optimiser arithmetic: in FP32 an approximate sqrt (rsqrt, ~1 ulp) and a
+// fast division (~2 ulp); the result only scales an optimiser step.  FP64
+// keeps IEEE operations.
+__device__ __forceinline__ float sqrt_step(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
+__device__ __forceinline__ double sqrt_step(double v) { return sqrt(v); }
+__device__ __forceinline__ float div_step(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_step(double a, double b) { return a / b; }
 
 // acc += y * v (complex)
 template <class C> __device__ __forceinline__ void cfma(C& acc, const C y, const C v) {
@@ -352,7 +359,7 @@ __device__ __forceinline__ void case_sum_max_atomic(R v, float mx, int lanes, R*
 
 // ---- forward: SpMV + power + mismatch + loss --------------------------------
 template <class R>
-__global__ void __launch_bounds__(256) k_fwd(IterArgs<R> a) {
+__global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.n_active && *a.n_active == 0) return;
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(256) k_fwd(IterArgs<R> a) {
 
 // ---- adjoint SpMV + gradient + Adam ----------------------------------------
 template <class R>
-__global__ void __launch_bounds__(256) k_adj(IterArgs<R> a) {
+__global__ void __launch_bounds__(256, 5) k_adj(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -458,7 +465,7 @@ __global__ void __launch_bounds__(256) k_adj(IterArgs<R> a) {
     const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
     const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
     const R g_th = -hi;
-    const R g_vm = (ty == BUS_PQ) ? hr / mwork(vm) : R(0);
+    const R g_vm = (ty == BUS_PQ) ? div_step(hr, mwork(vm)) : R(0);
     if (grad_only) {
       a.gva[e] = g_th;
       a.gvm[e] = g_vm;
@@ -469,17 +476,260 @@ __global__ void __launch_bounds__(256) k_adj(IterArgs<R> a) {
     v1 = b2 * v1 + (R(1) - b2) * g_th * g_th;
     a.mth[e] = m1;
     a.vth[e] = v1;
-    th = msub(th, step * m1 / (sqrtT(v1) * isb + eps));
+    th = msub(th, div_step(step * m1, sqrt_step(v1) * isb + eps));
     a.th[e] = th;
     if (ty == BUS_PQ) {  // Adam on |V| (pq buses)
       m2 = b1 * m2 + (R(1) - b1) * g_vm;
       v2 = b2 * v2 + (R(1) - b2) * g_vm * g_vm;
       a.mvm[e] = m2;
       a.vvm[e] = v2;
-      vm = msub(vm, step * m2 / (sqrtT(v2) * isb + eps));
+      vm = msub(vm, div_step(step * m2, sqrt_step(v2) * isb + eps));
       a.vm[e] = vm;
     }
     a.V[e] = volt(th, vm);
+  }
+}
+
+// ---- two cases per thread (FP32 solve loop, batches of >= 64 cases) --------
+// Thread t of CTA bx handles the adjacent cases k0 = 2 (bx*32 + lane) and
+// k0 + 1: the row's Y entries, bus type and address arithmetic serve both,
+// and every per-element access is one 16-byte (two-case) load or store.
+struct Pair {
+  int k0;
+  bool on0, on1;
+  int of0, ot0, of1, ot1;
+  float2 yff0, yft0, ytt0, yff1, yft1, ytt1;
+};
+
+__device__ __forceinline__ Pair load_pair(const IterArgs<float>& a, int k0) {
+  Pair q;
+  q.k0 = k0;
+  q.on0 = (k0 < a.Kp) && a.active[k0];
+  q.on1 = (k0 + 1 < a.Kp) && a.active[k0 + 1];
+  q.of0 = q.ot0 = q.of1 = q.ot1 = -1;
+  q.yff0 = q.yft0 = q.ytt0 = q.yff1 = q.yft1 = q.ytt1 = make_float2(0.f, 0.f);
+  if (a.has_outage && (q.on0 || q.on1)) {
+    q.of0 = a.of[k0];
+    q.ot0 = a.ot[k0];
+    q.of1 = a.of[k0 + 1];
+    q.ot1 = a.ot[k0 + 1];
+    if (q.of0 >= 0) { q.yff0 = a.yff[k0]; q.yft0 = a.yft[k0]; q.ytt0 = a.ytt[k0]; }
+    if (q.of1 >= 0) { q.yff1 = a.yff[k0 + 1]; q.yft1 = a.yft[k0 + 1]; q.ytt1 = a.ytt[k0 + 1]; }
+  }
+  return q;
+}
+
+// sum_p Y[p] X[col(p)] for two adjacent cases (X as float4 pairs).
+__device__ __forceinline__ void row_spmv2(const YSmem<float>& ys, int p0, int p1, const float4* __restrict__ X,
+                                          unsigned hKp, unsigned h0, float2& r0, float2& r1) {
+  // two accumulators per case, alternating like row_spmv: the same sums
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+  for (int p = p0; p < p1; p += 4) {
+    int j[4];
+    float2 y[4];
+    float4 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (p + u < p1) {
+        ys.get(p + u, j[u], y[u]);
+      } else {
+        j[u] = -1;
+        y[u] = make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = (j[u] >= 0) ? X[(unsigned)j[u] * hKp + h0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    cfma(a0, y[0], make_float2(x[0].x, x[0].y));
+    cfma(b0, y[0], make_float2(x[0].z, x[0].w));
+    cfma(a1, y[1], make_float2(x[1].x, x[1].y));
+    cfma(b1, y[1], make_float2(x[1].z, x[1].w));
+    cfma(a0, y[2], make_float2(x[2].x, x[2].y));
+    cfma(b0, y[2], make_float2(x[2].z, x[2].w));
+    cfma(a1, y[3], make_float2(x[3].x, x[3].y));
+    cfma(b1, y[3], make_float2(x[3].z, x[3].w));
+  }
+  r0 = make_float2(a0.x + a1.x, a0.y + a1.y);
+  r1 = make_float2(b0.x + b1.x, b0.y + b1.y);
+}
+
+// Per-case sum and max for two cases per thread, one atomic each per case.
+__device__ __forceinline__ void pair_sum_max_atomic(float s0, float s1, float m0, float m1, float* sum_out,
+                                                    unsigned int* max_out, int Kp) {
+  __shared__ float rs[8][64];
+  __shared__ float rm[8][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  rs[warp][2 * lane] = s0;
+  rs[warp][2 * lane + 1] = s1;
+  rm[warp][2 * lane] = m0;
+  rm[warp][2 * lane + 1] = m1;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    float s = 0.f, m = 0.f;
+    for (int w = 0; w < wpb; ++w) {
+      s += rs[w][threadIdx.x];
+      m = fmaxf(m, rm[w][threadIdx.x]);
+    }
+    const int k = blockIdx.x * 64 + threadIdx.x;
+    if (k < Kp) {
+      if (sum_out && s != 0.f) atomicAdd(sum_out + k, s);
+      if (max_out && m > 0.f) atomicMax(max_out + k, __float_as_uint(m));
+    }
+  }
+}
+
+// Forward epilogue of one case (the same arithmetic as k_fwd).
+__device__ __forceinline__ void fwd_epilogue(float2 vi, float2 I, int ty, float ps, float qs, float inv_m2,
+                                             float2& w, float2& g0, float& acc, float& mx) {
+  const float P = vi.x * I.x + vi.y * I.y;
+  const float Q = vi.y * I.x - vi.x * I.y;
+  const float dP = (ty != BUS_SLACK) ? P - ps : 0.f;
+  const float dQ = (ty == BUS_PQ) ? Q - qs : 0.f;
+  const float ca = inv_m2 * dP, cb = inv_m2 * dQ;
+  w = make_float2(ca * vi.x + cb * vi.y, cb * vi.x - ca * vi.y);
+  g0 = make_float2(ca * P + cb * Q, ca * Q - cb * P);
+  acc += dP * dP + dQ * dQ;
+  const float am = fmaxf(fabsf(dP), fabsf(dQ));
+  mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);
+}
+
+__global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (a.n_active && *a.n_active == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int r0 = blockIdx.y * a.rpb, r1 = min(a.N, r0 + a.rpb);
+  YSmem<float> ys;
+  ys.stage(a.rp, a.Y, r0, r1, smem);
+  const int k0 = 2 * (blockIdx.x * 32 + lane);
+  const Pair q = load_pair(a, k0);
+  float acc0 = 0.f, acc1 = 0.f, mx0 = 0.f, mx1 = 0.f;
+  if (q.on0 || q.on1) {
+    const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
+    const float4* __restrict__ V = (const float4*)a.V;
+    float4* W = (float4*)a.W;
+    float4* G = (float4*)a.G0;
+    for (int i = r0 + warp; i < r1; i += wpb) {
+      const unsigned e = (unsigned)i * hKp + h0;  // pair index
+      const int ty = __ldg(a.type + i);
+      const float4 v = V[e];
+      float ps0, ps1, qs0, qs1;
+      if (a.spec_per_case) {
+        const float2 pp = ((const float2*)a.pspec)[e], qq = ((const float2*)a.qspec)[e];
+        ps0 = pp.x; ps1 = pp.y; qs0 = qq.x; qs1 = qq.y;
+      } else {
+        ps0 = ps1 = a.pspec[i];
+        qs0 = qs1 = a.qspec[i];
+      }
+      float2 I0, I1;
+      row_spmv2(ys, ys.rp[i], ys.rp[i + 1], V, hKp, h0, I0, I1);
+      const float2 vi0 = make_float2(v.x, v.y), vi1 = make_float2(v.z, v.w);
+      if (i == q.of0) {
+        cfms(I0, q.yff0, vi0);
+        const float4 t = V[(unsigned)q.ot0 * hKp + h0];
+        cfms(I0, q.yft0, make_float2(t.x, t.y));
+      } else if (i == q.ot0) {
+        const float4 t = V[(unsigned)q.of0 * hKp + h0];
+        cfms(I0, q.yft0, make_float2(t.x, t.y));
+        cfms(I0, q.ytt0, vi0);
+      }
+      if (i == q.of1) {
+        cfms(I1, q.yff1, vi1);
+        const float4 t = V[(unsigned)q.ot1 * hKp + h0];
+        cfms(I1, q.yft1, make_float2(t.z, t.w));
+      } else if (i == q.ot1) {
+        const float4 t = V[(unsigned)q.of1 * hKp + h0];
+        cfms(I1, q.yft1, make_float2(t.z, t.w));
+        cfms(I1, q.ytt1, vi1);
+      }
+      float2 w0, w1, g0, g1;
+      fwd_epilogue(vi0, I0, ty, ps0, qs0, a.inv_m2, w0, g0, acc0, mx0);
+      fwd_epilogue(vi1, I1, ty, ps1, qs1, a.inv_m2, w1, g1, acc1, mx1);
+      W[e] = make_float4(w0.x, w0.y, w1.x, w1.y);
+      G[e] = make_float4(g0.x, g0.y, g1.x, g1.y);
+    }
+    if (!q.on0) { acc0 = 0.f; mx0 = 0.f; }
+    if (!q.on1) { acc1 = 0.f; mx1 = 0.f; }
+  }
+  pair_sum_max_atomic(acc0, acc1, mx0, mx1, a.loss_acc, a.mx32, a.Kp);
+}
+
+// Adam update of one double-float master value.
+__device__ __forceinline__ float2 adam_step(float2 x, float g, float& m, float& v, float b1, float b2, float step,
+                                           float isb, float eps) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  return msub(x, div_step(step * m, sqrt_step(v) * isb + eps));
+}
+
+__global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (a.n_active && *a.n_active == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int r0 = blockIdx.y * a.rpb, r1 = min(a.N, r0 + a.rpb);
+  YSmem<float> ys;
+  ys.stage(a.rp, a.Y, r0, r1, smem);
+  const int k0 = 2 * (blockIdx.x * 32 + lane);
+  const Pair q = load_pair(a, k0);
+  if (!(q.on0 || q.on1)) return;
+  const float st0 = a.step_size[k0], st1 = a.step_size[k0 + 1];
+  const float ib0 = a.isbc2[k0], ib1 = a.isbc2[k0 + 1];
+  const float b1 = a.beta1, b2 = a.beta2, eps = a.eps;
+  const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
+  const float4* __restrict__ W = (const float4*)a.W;
+  for (int i = r0 + warp; i < r1; i += wpb) {
+    const int ty = __ldg(a.type + i);
+    if (ty == BUS_SLACK) continue;
+    const unsigned e = (unsigned)i * hKp + h0;
+    // this element's operands first: they do not depend on the gather chain
+    const float4 g = ((const float4*)a.G0)[e];
+    float4 th = ((const float4*)a.th)[e];  // (hi, lo) of case k0, then of k0 + 1
+    float4 vm = ((const float4*)a.vm)[e];
+    float2 mt = ((const float2*)a.mth)[e], vt = ((const float2*)a.vth)[e];
+    float2 mv = make_float2(0.f, 0.f), vv = mv;
+    if (ty == BUS_PQ) {
+      mv = ((const float2*)a.mvm)[e];
+      vv = ((const float2*)a.vvm)[e];
+    }
+    float2 z0, z1;
+    row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W, hKp, h0, z0, z1);
+    const float4 wi = W[e];
+    if (i == q.of0) {
+      cfms(z0, q.yff0, make_float2(wi.x, wi.y));
+      const float4 t = W[(unsigned)q.ot0 * hKp + h0];
+      cfms(z0, q.yft0, make_float2(t.x, t.y));
+    } else if (i == q.ot0) {
+      const float4 t = W[(unsigned)q.of0 * hKp + h0];
+      cfms(z0, q.yft0, make_float2(t.x, t.y));
+      cfms(z0, q.ytt0, make_float2(wi.x, wi.y));
+    }
+    if (i == q.of1) {
+      cfms(z1, q.yff1, make_float2(wi.z, wi.w));
+      const float4 t = W[(unsigned)q.ot1 * hKp + h0];
+      cfms(z1, q.yft1, make_float2(t.z, t.w));
+    } else if (i == q.ot1) {
+      const float4 t = W[(unsigned)q.of1 * hKp + h0];
+      cfms(z1, q.yft1, make_float2(t.z, t.w));
+      cfms(z1, q.ytt1, make_float2(wi.z, wi.w));
+    }
+    float2 th0 = make_float2(th.x, th.y), th1 = make_float2(th.z, th.w);
+    float2 vm0 = make_float2(vm.x, vm.y), vm1 = make_float2(vm.z, vm.w);
+    const float2 v0 = volt(th0, vm0), v1 = volt(th1, vm1);
+    const float hr0 = g.x + (v0.x * z0.x - v0.y * z0.y), hi0 = g.y + (v0.x * z0.y + v0.y * z0.x);
+    const float hr1 = g.z + (v1.x * z1.x - v1.y * z1.y), hi1 = g.w + (v1.x * z1.y + v1.y * z1.x);
+    // Adam on theta (pv and pq buses); an inactive case keeps its state
+    if (q.on0) th0 = adam_step(th0, -hi0, mt.x, vt.x, b1, b2, st0, ib0, eps);
+    if (q.on1) th1 = adam_step(th1, -hi1, mt.y, vt.y, b1, b2, st1, ib1, eps);
+    ((float2*)a.mth)[e] = mt;
+    ((float2*)a.vth)[e] = vt;
+    ((float4*)a.th)[e] = make_float4(th0.x, th0.y, th1.x, th1.y);
+    if (ty == BUS_PQ) {  // Adam on |V| (pq buses)
+      if (q.on0) vm0 = adam_step(vm0, div_step(hr0, mwork(vm0)), mv.x, vv.x, b1, b2, st0, ib0, eps);
+      if (q.on1) vm1 = adam_step(vm1, div_step(hr1, mwork(vm1)), mv.y, vv.y, b1, b2, st1, ib1, eps);
+      ((float2*)a.mvm)[e] = mv;
+      ((float2*)a.vvm)[e] = vv;
+      ((float4*)a.vm)[e] = make_float4(vm0.x, vm0.y, vm1.x, vm1.y);
+    }
+    const float2 n0 = q.on0 ? volt(th0, vm0) : v0, n1 = q.on1 ? volt(th1, vm1) : v1;
+    ((float4*)a.V)[e] = make_float4(n0.x, n0.y, n1.x, n1.y);
   }
 }
 

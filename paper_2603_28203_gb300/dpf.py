@@ -172,6 +172,7 @@ class SolveOpts:
     warps: int | None = None
     row_blocks: int | None = None
     use_graph: int | None = None
+    pair_cases: int | None = None
     plain: int | None = None
 
     def to_c(self) -> _abi.DpfSolveOpts:
@@ -244,6 +245,17 @@ def dpf_solve_begin(y: Ybus, ws: Workspace, opts=None, stream=None, **batch):
     b = _batch_struct(**batch)
     o = _opts(opts)
     _check(lib().dpf_solve_begin(y.handle, ws.handle, C.byref(b), C.byref(o), _stream(stream)))
+
+
+def dpf_autotune(y: Ybus, ws: Workspace, opts=None, iters: int = 25, stream=None, **batch) -> SolveOpts:
+    """Launch shape picked by the library's autotuner for this batch (returned as SolveOpts)."""
+    b = _batch_struct(**batch)
+    o = _opts(opts)
+    _check(lib().dpf_autotune(y.handle, ws.handle, C.byref(b), C.byref(o), int(iters), _stream(stream)))
+    out = SolveOpts(**{f.name: getattr(opts, f.name) for f in dataclasses.fields(SolveOpts)}) \
+        if isinstance(opts, SolveOpts) else SolveOpts()
+    out.lanes, out.warps, out.row_blocks, out.pair_cases = o.lanes, o.warps, o.row_blocks, o.pair_cases
+    return out
 
 
 def dpf_solve_iterate(ws: Workspace, n_iter: int, stream=None):

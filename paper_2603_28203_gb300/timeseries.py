@@ -1,0 +1,63 @@
+"""Time-series power flows with warm starts (Sec. 5.4.2, Table 3).
+
+Snapshots are solved in windows of `window` cases per batched call.  The
+first window starts flat with the t = 0 settings of Table 3 (Adam lr 0.03564,
+betas (0.9802, 0.9440), StepLR step 100 / gamma 0.773, <= 1,000 iterations);
+every later window starts from the solutions of the previous window,
+snapshot by snapshot (snapshot t from snapshot t - window, the same hour of
+day for a 96-hour window), with the t > 0 settings (Adam lr 0.00027, betas
+(0.7847, 0.6624), ReduceLROnPlateau 0.8 / 2 / 0.0388 / 4, <= 300 iterations).
+The solutions stay on the device between windows; only the window's
+injections are copied in.  All arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _abi
+from .dpf import SolveOpts, Workspace, Ybus, dpf_solve_batch
+
+TABLE3_T0 = dict(lr=0.03564, beta1=0.9802, beta2=0.9440, sched=_abi.SCHED_STEP, step_size=100, gamma=0.773,
+                 max_iter=1000)
+TABLE3_T1 = dict(lr=0.00027, beta1=0.7847, beta2=0.6624, sched=_abi.SCHED_PLATEAU, factor=0.8, patience=2,
+                 threshold=0.0388, cooldown=4, max_iter=300)
+
+
+def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 96, precision=_abi.FP32,
+                      first=None, later=None, check_every: int = 25, tol: float = 1e-6, stream=None):
+    """Solve T snapshots ([T][N] injections, numpy or torch); returns numpy arrays.
+
+    `first` / `later` override the Table 3 settings (dicts of SolveOpts fields).
+    """
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P = torch.as_tensor(np.asarray(p_series, np.float64) if not torch.is_tensor(p_series) else p_series,
+                        dtype=torch.float64)
+    Q = torch.as_tensor(np.asarray(q_series, np.float64) if not torch.is_tensor(q_series) else q_series,
+                        dtype=torch.float64)
+    T, N = P.shape
+    out = {k: np.empty((T, N)) for k in ("va", "vm")}
+    out.update(iters=np.empty(T, np.int32), status=np.empty(T, np.int32), max_mismatch=np.empty(T),
+               loss=np.empty(T))
+    va = torch.zeros((window, N), dtype=torch.float64, device=dev)
+    vm = torch.zeros((window, N), dtype=torch.float64, device=dev)
+    res = dict(iters=torch.zeros(window, dtype=torch.int32, device=dev),
+               status=torch.zeros(window, dtype=torch.int32, device=dev),
+               max_mismatch=torch.zeros(window, dtype=torch.float64, device=dev),
+               loss=torch.zeros(window, dtype=torch.float64, device=dev))
+    for w0 in range(0, T, window):
+        K = min(window, T - w0)
+        p = P[w0:w0 + K].to(dev).contiguous()
+        q = Q[w0:w0 + K].to(dev).contiguous()
+        settings = dict(TABLE3_T0 if w0 == 0 else TABLE3_T1)
+        settings.update((first if w0 == 0 else later) or {})
+        opts = SolveOpts(precision=precision, check_every=check_every, tol=tol, flat_start=1 if w0 == 0 else 0,
+                         **settings)
+        dpf_solve_batch(y, ws, opts, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
+                        **{k: v[:K] for k, v in res.items()})
+        out["va"][w0:w0 + K] = va[:K].cpu().numpy()
+        out["vm"][w0:w0 + K] = vm[:K].cpu().numpy()
+        for k, v in res.items():
+            out[k][w0:w0 + K] = v[:K].cpu().numpy()
+    return out

@@ -252,6 +252,42 @@ def test_fp32_iterations_track_fp64():
         assert abs(b["max_mismatch"][k] - np.abs(f).max()) <= 1e-12 * np.abs(f).max()
 
 
+@pytest.mark.parametrize("outages", [False, True])
+def test_pair_kernels_match_single(outages):
+    """FP32 batches >= 64 cases run two cases per thread; same iterates as one per thread."""
+    g = GRIDS["c3"]()
+    K = 100
+    kw = {}
+    if outages:
+        ells = np.concatenate([[-1], np.random.default_rng(8).choice(gridgen.n1_outages(g), K - 1, replace=False)])
+        kw["outage"] = _t(ells.astype(np.int32), torch.int32)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    base = dict(precision=dpf.FP32, max_iter=100, check_every=10, lr=1e-3)
+    a = _solve(y, ws, K, dpf.SolveOpts(pair_cases=1, **base), **kw)
+    b = _solve(y, ws, K, dpf.SolveOpts(pair_cases=0, **base), **kw)
+    assert np.abs(a["va"] - b["va"]).max() < 1e-4 and np.abs(a["vm"] - b["vm"]).max() < 1e-4
+    assert np.abs(a["max_mismatch"] - b["max_mismatch"]).max() < 1e-4 * np.abs(b["max_mismatch"]).max()
+    assert (a["iters"] == b["iters"]).all()
+
+
+def test_autotune_shape_is_valid_and_equivalent():
+    g = GRIDS["c3"]()
+    K = 130
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    base = dpf.SolveOpts(precision=dpf.FP32, max_iter=60, check_every=10, lr=1e-3)
+    tuned = dpf.dpf_autotune(y, ws, base, iters=10, n_case=K)
+    assert tuned.lanes in (8, 16, 32) and tuned.warps in (4, 8) and tuned.row_blocks >= 1
+    assert tuned.pair_cases in (0, 1, 2, 3)
+    again = dpf.dpf_autotune(y, ws, base, iters=10, n_case=K)  # cached
+    assert (again.lanes, again.warps, again.row_blocks, again.pair_cases) == \
+        (tuned.lanes, tuned.warps, tuned.row_blocks, tuned.pair_cases)
+    a = _solve(y, ws, K, tuned)
+    b = _solve(y, ws, K, base)
+    assert np.abs(a["va"] - b["va"]).max() < 1e-4 and np.abs(a["vm"] - b["vm"]).max() < 1e-4
+
+
 def test_warm_start_and_host_io():
     g = GRIDS["g300"]()
     K = 3
