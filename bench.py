@@ -306,6 +306,9 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(dpf, y, ws, g, outages, stream, args, opts)
+    plain = None
+    if not args.no_plain:
+        plain = run_plain(dpf, y, g, outages, stream, args)
 
     if rank == 0:
         line = {
@@ -357,6 +360,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": e2e,
+            "plain_form": plain,
+            "speedup_vs_plain_form": (value / plain["value"]) if plain else None,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -391,6 +396,34 @@ def run_e2e(dpf, y, ws, g, outages, stream, args, opts):
     return {"value": K / t, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "step": "one dpf_solve_batch call (host_io) over all cases, up to 1,000 iterations",
             "steps": len(times), "ms_per_step": 1e3 * t}
+
+
+def run_plain(dpf, y, g, outages, stream, args):
+    """The plain form on the same GPU: Alg. 1 case by case in FP64, separate
+    launches per iteration and a host stop test (device-to-host read) after
+    every iteration; `--plain-cases` cases of the N-1 batch, 1,000 iterations."""
+    import torch
+    n = args.plain_cases
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws1 = dpf.dpf_workspace_create(y, 1)
+    out = torch.tensor(outages[:n], dtype=torch.int32, device=dev)
+    va = torch.zeros((n, g.n_bus), dtype=torch.float64, device=dev)
+    vm = torch.zeros_like(va)
+    it = torch.zeros(n, dtype=torch.int32, device=dev)
+    opts = dpf.SolveOpts(lr=LR, tol=TOL, precision=dpf.FP64, max_iter=ITERS_PER_SOLVE, plain=1)
+    with torch.cuda.stream(stream):
+        dpf.dpf_solve_batch(y, ws1, opts, stream=stream, n_case=1, outage=out[:1], va=va[:1], vm=vm[:1],
+                            iters=it[:1])  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dpf.dpf_solve_batch(y, ws1, opts, stream=stream, n_case=n, outage=out, va=va, vm=vm, iters=it)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    iters = int(it.sum().item())
+    ws1.free()
+    return {"value": iters / ITERS_PER_SOLVE / t, "unit": "solves/s", "cases": n, "precision": "fp64",
+            "ms_per_iteration": 1e3 * t / max(iters, 1),
+            "form": "one case at a time, separate launches per iteration, host stop test every iteration"}
 
 
 # ---------------------------------------------------------------------------
@@ -453,6 +486,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain-cases", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -306,6 +306,19 @@ def perturb_branches(grid: Grid, seed: int, rel: float = 0.10) -> Grid:
     return g
 
 
+def concat_grids(grids) -> Grid:
+    """Block-diagonal batch of grids (one island each), bus indices offset."""
+    off = np.cumsum([0] + [g.n_bus for g in grids])
+    cat = lambda name: np.concatenate([getattr(g, name) for g in grids])
+    return Grid(bus_type=cat("bus_type"), p_spec=cat("p_spec"), q_spec=cat("q_spec"), vm_set=cat("vm_set"),
+                va_slack=0.0,
+                f_bus=np.concatenate([g.f_bus + o for g, o in zip(grids, off)]).astype(np.int32),
+                t_bus=np.concatenate([g.t_bus + o for g, o in zip(grids, off)]).astype(np.int32),
+                r=cat("r"), x=cat("x"), b_ch=cat("b_ch"), tap=cat("tap"), shift=cat("shift"),
+                pos=cat("pos"), p_load=cat("p_load"), q_load=cat("q_load"), gen_w=cat("gen_w"),
+                dispatch=grids[0].dispatch)
+
+
 def uneven_sizes(n_grids: int, seed: int, lo: int = 300, hi: int = 80_000) -> np.ndarray:
     """Grid sizes log-uniform in [lo, hi]."""
     rng = np.random.default_rng(seed)

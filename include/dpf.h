@@ -63,7 +63,9 @@ enum { DPF_SCHED_CONST = 0, DPF_SCHED_PLATEAU = 1, DPF_SCHED_STEP = 2 };
 
 /* ---- grid description (host arrays, caller-owned, read-only) -------------
  * The problem statement of Sec. 2.1 / Alg. 1 inputs: bus types with exactly
- * one slack, specified P (pv, pq), Q (pq), |V| (pv, slack), the slack angle,
+ * one slack per connected island (a block-diagonal batch of grids, Sec. 4.2,
+ * is one grid with one island per member), specified P (pv, pq), Q (pq),
+ * |V| (pv, slack), the slack angle (the same for every island),
  * and the branch table from which Y_bus is built with the pi-model (the
  * MATPOWER model the paper's Eq. powerbalance footnote refers to):
  *   y_s = 1/(r + jx); Y_ff += (y_s + j b_ch/2)/tap^2; Y_tt += y_s + j b_ch/2;
@@ -89,7 +91,7 @@ typedef struct dpf_workspace dpf_workspace; /* device state of one batch      */
 
 /* Build Y_bus on the host (CSR, FP64, sorted columns, every diagonal
  * present) and validate the grid.  No CUDA call is made; a GPU is not needed.
- * Errors: DPF_E_INVALID (sizes, indices, not exactly one slack, f == t,
+ * Errors: DPF_E_INVALID (sizes, indices, an island without exactly one slack, f == t,
  * non-finite or zero impedance), DPF_E_UNSUPPORTED (shift, parallel branch). */
 int dpf_build_ybus_host(const dpf_grid* g, dpf_ybus** out);
 
@@ -282,6 +284,17 @@ int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
                       double* loss, double* d_va, double* d_vm,
                       double* d_p, double* d_q,
                       double* d_g, double* d_b, double* d_bch, void* stream);
+
+/* ---- Adam on a parameter vector -------------------------------------------
+ * One Adam step (the optimiser of Sec. 5.3, Kingma & Ba with bias correction)
+ * on n FP64 parameters, e.g. the branch admittances g, b of parameter
+ * identification driven by dpf_loss_backward's d_g, d_b.  All arrays are
+ * device [n]: x (updated in place), grad, and the caller-owned moments m, v
+ * (zero before step 1).  t is the 1-based step number.  lr_scale (or NULL)
+ * gives a per-entry learning-rate factor (step_i = lr * lr_scale[i]), e.g.
+ * the parameters' magnitudes for relative steps. */
+int dpf_adam_update(int32_t n, double* x, const double* grad, double* m, double* v, const double* lr_scale,
+                    int32_t t, double lr, double beta1, double beta2, double eps, void* stream);
 
 /* Message of the most recent failure on this thread ("" if none). */
 const char* dpf_last_error(void);

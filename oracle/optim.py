@@ -28,15 +28,19 @@ class Adam:
         self.v = np.zeros(n)
         self.t = 0
 
-    def step(self, x, g):
-        """Return the updated parameter vector (x is not modified)."""
+    def step(self, x, g, lr_scale=None):
+        """Return the updated parameter vector (x is not modified).
+
+        lr_scale (optional, per entry) multiplies the learning rate.
+        """
         self.t += 1
         b1, b2 = self.beta1, self.beta2
         self.m = b1 * self.m + (1.0 - b1) * g
         self.v = b2 * self.v + (1.0 - b2) * g * g
         m_hat = self.m / (1.0 - b1 ** self.t)
         v_hat = self.v / (1.0 - b2 ** self.t)
-        return x - self.lr * m_hat / (np.sqrt(v_hat) + self.eps)
+        lr = self.lr if lr_scale is None else self.lr * lr_scale
+        return x - lr * m_hat / (np.sqrt(v_hat) + self.eps)
 
 
 class ReduceLROnPlateau:

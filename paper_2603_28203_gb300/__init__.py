@@ -11,7 +11,7 @@ torch.autograd.Function over the adjoint.
 from . import _abi
 from ._abi import (CASE_CONVERGED, CASE_DIVERGED, CASE_MAX_ITER, FP32, FP64, PQ, PV, SCHED_CONST,
                    SCHED_PLATEAU, SCHED_STEP, SLACK)
-from .dpf import (DPFError, SolveOpts, Workspace, Ybus, dpf_active_count, dpf_autotune, dpf_build_ybus,
+from .dpf import (DPFError, SolveOpts, Workspace, Ybus, dpf_active_count, dpf_adam_update, dpf_autotune, dpf_build_ybus,
                   dpf_build_ybus_host, dpf_default_opts, dpf_iterations_done, dpf_kernel_launches, dpf_kernel_times,
                   dpf_last_error, dpf_profile_enable,
                   dpf_loss_backward, dpf_power, dpf_power_noalloc, dpf_solve_batch, dpf_solve_begin, dpf_solve_end,

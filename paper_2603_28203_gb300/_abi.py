@@ -80,6 +80,8 @@ SIGNATURES = {
     "dpf_profile_enable": (C.c_int, [VP, I32]),
     "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),
     "dpf_kernel_launches": (C.c_int, [VP, C.POINTER(C.c_int64)]),
+    "dpf_adam_update": (C.c_int, [I32, VP, VP, VP, VP, VP, I32, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  VP]),
     "dpf_last_error": (C.c_char_p, []),
     "dpf_status_str": (C.c_char_p, [C.c_int]),
 }

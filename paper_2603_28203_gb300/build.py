@@ -37,7 +37,8 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     for src in ("dpf_api.cu", "dpf_noalloc.cu"):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         cu = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-              "-I" + INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+              "-I" + INCLUDE, *os.environ.get("DPF_NVCC_FLAGS", "").split(), "-c", os.path.join(CSRC, src),
+              "-o", obj]
         if ptxas_info:
             cu.insert(1, "-Xptxas=-v")
         objs.append(obj)

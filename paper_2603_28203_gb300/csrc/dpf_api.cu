@@ -529,7 +529,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   P.pgrid = dim3(w->Kp / 64, w->gy);
   P.block = dim3(w->warps * 32);
   P.smem = w->smem;
-  P.sched_blocks = (w->Kp + 255) / 256;
+  P.sched_blocks = (w->Kp + 63) / 64;
   return P;
 }
 
@@ -580,7 +580,7 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
     w->ev_fwd.push_back({i2 - 2, i2 - 1});
     w->ev_adj.push_back({i2 - 1, i2});
   }
-  k_sched<R><<<P.sched_blocks, 256, 0, s>>>(P.sc);
+  k_sched<R><<<P.sched_blocks, 64, 0, s>>>(P.sc);
   w->launches += 3;
   CKLAUNCH();
   return DPF_OK;
@@ -1106,6 +1106,39 @@ extern "C" int dpf_solve_batch(const dpf_ybus* y, dpf_workspace* ws, const dpf_b
     dpf_workspace_free(w);
   }
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Adam on a parameter vector (parameter identification)
+// ---------------------------------------------------------------------------
+__global__ void k_adam_params(int n, double* __restrict__ x, const double* __restrict__ g, double* __restrict__ m,
+                              double* __restrict__ v, const double* __restrict__ lr_scale, double lr, double b1,
+                              double b2, double eps, double bc1, double bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double gi = g[i];
+  const double mi = b1 * m[i] + (1.0 - b1) * gi;
+  const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const double step = lr * (lr_scale ? lr_scale[i] : 1.0);
+  x[i] -= step * (mi / bc1) / (sqrt(vi / bc2) + eps);
+}
+
+extern "C" int dpf_adam_update(int32_t n, double* x, const double* grad, double* m, double* v,
+                               const double* lr_scale, int32_t t, double lr, double beta1, double beta2, double eps,
+                               void* stream) {
+  clear_error();
+  if (n < 0 || (n > 0 && (!x || !grad || !m || !v))) return fail(DPF_E_INVALID, "dpf_adam_update: bad arguments");
+  if (t < 1 || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps >= 0))
+    return fail(DPF_E_INVALID, "dpf_adam_update: invalid step or hyper-parameters");
+  if (n == 0) return DPF_OK;
+  double b1t = 1.0, b2t = 1.0;  // host powers: one scalar each per call
+  for (int k = 0; k < t; ++k) { b1t *= beta1; b2t *= beta2; }
+  k_adam_params<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, x, grad, m, v, lr_scale, lr, beta1, beta2,
+                                                                    eps, 1.0 - b1t, 1.0 - b2t);
+  CKLAUNCH();
+  return DPF_OK;
 }
 
 // ---------------------------------------------------------------------------

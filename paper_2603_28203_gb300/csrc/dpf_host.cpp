@@ -164,7 +164,7 @@ extern "C" int dpf_build_ybus_host(const dpf_grid* g, dpf_ybus** out) {
     if (ty != DPF_PQ && !(g->vm_set[i] > 0.0))
       return fail(DPF_E_INVALID, "bus %d: |V| set-point must be > 0", i);
   }
-  if (n_slack != 1) return fail(DPF_E_INVALID, "need exactly one slack bus (got %d)", n_slack);
+  if (n_slack < 1) return fail(DPF_E_INVALID, "need a slack bus");
   std::set<std::pair<int, int>> pairs;
   for (int e = 0; e < m; ++e) {
     const int f = g->f_bus[e], t = g->t_bus[e];
@@ -181,6 +181,22 @@ extern "C" int dpf_build_ybus_host(const dpf_grid* g, dpf_ybus** out) {
       return fail(DPF_E_UNSUPPORTED, "branch %d is parallel to an earlier branch", e);
   }
 
+  {  // a block-diagonal batch of grids (Sec. 4.2) has several islands: one slack each
+    std::vector<int32_t> parent(n);
+    for (int i = 0; i < n; ++i) parent[i] = i;
+    auto find = [&](int v) {
+      while (parent[v] != v) v = parent[v] = parent[parent[v]];
+      return v;
+    };
+    for (int e = 0; e < m; ++e) parent[find(g->f_bus[e])] = find(g->t_bus[e]);
+    std::vector<int32_t> slacks(n, 0);
+    for (int i = 0; i < n; ++i)
+      if (g->bus_type[i] == DPF_SLACK) slacks[find(i)]++;
+    for (int i = 0; i < n; ++i)
+      if (find(i) == i && slacks[i] != 1)
+        return fail(DPF_E_INVALID, "each island needs exactly one slack bus (island of bus %d has %d)", i,
+                    slacks[i]);
+  }
   dpf_ybus* y = new (std::nothrow) dpf_ybus();
   if (!y) return fail(DPF_E_OOM, "out of host memory");
   y->n = n;

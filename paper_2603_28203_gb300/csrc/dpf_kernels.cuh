@@ -412,8 +412,11 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
 }
 
 // ---- adjoint SpMV + gradient + Adam ----------------------------------------
+#ifndef DPF_ADJ_MINB
+#define DPF_ADJ_MINB 5
+#endif
 template <class R>
-__global__ void __launch_bounds__(256, 5) k_adj(IterArgs<R> a) {
+__global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -804,8 +807,10 @@ __global__ void k_sched(SchedArgs<R> a) {
   const double b1t = a.b1t[k] * a.beta1, b2t = a.b2t[k] * a.beta2;  // beta^(it+1)
   a.b1t[k] = b1t;
   a.b2t[k] = b2t;
-  a.step_size[k] = (R)(lr / (1.0 - b1t));
-  a.isbc2[k] = (R)(1.0 / sqrt(1.0 - b2t));
+  // bias-corrected step terms in working precision (FP64 division and square
+  // root are slow on this GPU; FP32 runs only consume them in FP32)
+  a.step_size[k] = (R)lr / (R(1) - (R)b1t);
+  a.isbc2[k] = R(1) / sqrtT(R(1) - (R)b2t);
 }
 
 // ---- FP64 convergence test --------------------------------------------------

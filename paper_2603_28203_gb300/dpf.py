@@ -336,6 +336,12 @@ def dpf_loss_backward(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, 
     return out
 
 
+def dpf_adam_update(x, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, lr_scale=None, stream=None):
+    """One Adam step on device float64 vectors (in place on x, m, v)."""
+    _check(lib().dpf_adam_update(int(x.numel()), _ptr(x), _ptr(grad), _ptr(m), _ptr(v), _ptr(lr_scale), int(t),
+                                 float(lr), float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
 def dpf_last_error() -> str:
     return lib().dpf_last_error().decode()
 

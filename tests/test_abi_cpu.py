@@ -98,6 +98,18 @@ def test_validation_errors(dpf):
             assert e.value.code == code, dpf.dpf_last_error()
 
 
+def test_islands_need_one_slack_each(dpf):
+    a = gridgen.make_grid(30, 1, load_scale=0.5)
+    b = gridgen.make_grid(40, 2, load_scale=0.5)
+    cat = gridgen.concat_grids([a, b])
+    y = dpf.dpf_build_ybus_host(cat)  # two islands, one slack each
+    assert y.n_bus == 70 and y.nnz == 70 + 2 * (a.n_branch + b.n_branch)
+    bad = _bad(cat, bus_type=np.where(np.arange(70) == b.slack + 30, 0, cat.bus_type).astype(np.uint8))
+    with pytest.raises(dpf.DPFError) as e:
+        dpf.dpf_build_ybus_host(bad)
+    assert e.value.code == -1 and "island" in dpf.dpf_last_error()
+
+
 def test_tap_zero_means_none(dpf):
     g = gridgen.config_grid("c1_30bus_fp64")
     h = _bad(g, tap=np.where(g.tap == 1.0, 0.0, g.tap))
