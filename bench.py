@@ -163,16 +163,18 @@ class ClockSampler:
 def algorithmic_bytes(n_bus, n_pv, n_pq, nnz, n_case):
     """Bytes each kernel must move per launch (every array element once).
 
-    k_fwd, per case: read V (8 B/bus), write w and g0 (16 B/bus);
-    k_adj, per case: read w (8 B/bus); for every pv/pq bus read g0 (8),
-      read+write theta (16, double-float), read |V| (8), read+write the two
-      Adam moments of theta (16), write V (8); for pq buses also write |V|
-      (8) and read+write its moments (16).
-    Shared per launch: Y in CSR (16 B per nonzero + 4 B row pointers + bus types).
+    k_fwd, per case: read V (8 B/bus), write w (8 B/bus), write Q_calc at pv
+      buses (4 B);
+    k_adj, per case: read w (8 B/bus); at pv buses read Q_calc (4); at every
+      pv/pq bus read+write theta (16, double-float), read |V| (8), read+write
+      the two Adam moments of theta (16), write V (8); at pq buses also write
+      |V| (8) and read+write its moments (16).
+    Shared per launch: Y in CSR (16 B per nonzero + 4 B row pointers + bus
+    types) and the shared specified P, Q (8 B/bus).
     """
-    shared = 16 * nnz + 4 * (n_bus + 1) + n_bus
-    fwd = n_case * 24 * n_bus + shared
-    adj = n_case * (8 * n_bus + 56 * (n_pv + n_pq) + 24 * n_pq) + shared
+    shared = 16 * nnz + 4 * (n_bus + 1) + n_bus + 8 * n_bus
+    fwd = n_case * (16 * n_bus + 4 * n_pv) + shared
+    adj = n_case * (8 * n_bus + 52 * n_pv + 72 * n_pq) + shared
     return fwd, adj
 
 
@@ -337,7 +339,7 @@ def run_ours(args):
                 "l2": "per-iteration working set ~0.5 GB >> 129 MB L2 (no flush needed)",
                 "parallelism": f"replicas x{world} (independent cases, no data-path collective)",
                 "launch_shape": {"lanes": opts.lanes, "warps": opts.warps, "row_blocks": opts.row_blocks,
-                                 "pair_cases": opts.pair_cases, "chosen_by": "dpf_autotune"
+                                 "pair_cases": opts.pair_cases, "stage_v": opts.stage_v, "chosen_by": "dpf_autotune"
                                  if not (args.lanes or args.warps or args.row_blocks or args.no_autotune)
                                  else "command line"},
             },

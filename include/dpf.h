@@ -167,6 +167,9 @@ typedef struct {
                                 runs the forward pass, bit 1 the adjoint pass
                                 with two cases per thread (16-byte accesses);
                                 0: one case per thread                        */
+  int32_t stage_v;           /* 1: the forward pass first copies the rows of V
+                                its row block references into shared memory
+                                and gathers from there (lanes = 32 only)      */
   int32_t plain;             /* 1: the plain form of Alg. 1 -- one case at a
                                 time, separate launches per iteration and a
                                 host stop test (FP64 check + device-to-host
@@ -203,9 +206,10 @@ int dpf_solve_iterate(dpf_workspace* ws, int32_t n_iter, void* stream);
 int dpf_solve_end(dpf_workspace* ws, const dpf_batch* b, void* stream);
 /* Autotuner.  Times candidate launch shapes of the solve loop on this batch
  * -- cases per row group (`lanes`, i.e. rows per warp = 32/lanes), warps per
- * CTA, row blocks, and the two-cases-per-thread variants -- for `iters`
+ * CTA, row blocks, the two-cases-per-thread variants and shared-memory V
+ * staging -- for `iters`
  * iterations each (plus one warm-up check interval), and writes the fastest
- * into o->lanes, o->warps, o->row_blocks and o->pair_cases.  The batch's
+ * into o->lanes, o->warps, o->row_blocks, o->pair_cases and o->stage_v.  The batch's
  * inputs are read (as in dpf_solve_begin) but no output is written; a later
  * dpf_solve_begin starts from scratch.  Results are cached in the workspace
  * per (n_case, precision, grid, outage/injection layout).  Synchronises

@@ -222,6 +222,13 @@ struct dpf_workspace {
   bool begun = false;
   int K = 0, Kp = 0, lanes = 1, warps = 8, gx = 1, gy = 1, rpb = 1, smem = 0, precision = DPF_FP32;
   bool pairs = false;   // FP32 solve loop, Kp a multiple of 64: two cases per thread possible
+  // shared-memory windows of V for the forward pass: per row block the first
+  // and last row referenced (host copy + device copy)
+  std::vector<int32_t> h_wlo, h_whi;
+  int32_t *d_wlo = nullptr, *d_whi = nullptr;
+  int cap_wblocks = 0;
+  bool staged = false;
+  int ysmem = 0;
   bool pair_fwd = false, pair_adj = false;
   std::vector<std::pair<std::vector<long long>, std::vector<int>>> tune_cache;  // key -> (lanes, warps, rb, pairs)
   bool spec_per_case = false, has_outage = false;
@@ -249,6 +256,8 @@ static void ws_free_buffers(dpf_workspace* w) {
   dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
   dfree(w->b1t); dfree(w->b2t); dfree(w->cand); dfree(w->mx32);
   dfree(w->st_a); dfree(w->st_b); dfree(w->st_c);
+  dfree(w->d_wlo); dfree(w->d_whi);
+  w->cap_wblocks = 0;
   w->cap_elems = 0;
   w->cap_cases = 0;
   w->cap_stage = 0;
@@ -381,6 +390,7 @@ struct Plan {
   dim3 cgrid;         // (the same; check and evaluation kernels)
   dim3 pgrid;         // two cases per thread
   int smem;
+  int ysmem;
   int sched_blocks;
   bool need_volt64;
 };
@@ -401,6 +411,9 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.Kp = w->Kp;
   a.lanes = w->lanes;
   a.rpb = w->rpb;
+  a.wlo = w->staged ? w->d_wlo : nullptr;
+  a.whi = w->staged ? w->d_whi : nullptr;
+  a.ysmem = w->ysmem;
   // FP32 iterations gate the FP64 test with the forward pass's FP32 mismatch
   const bool gated = (sizeof(R) == 4) && w->opts.gate > 0.0;
   a.rp = d.row_ptr;
@@ -415,7 +428,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.type = d.type;
   a.V = (C*)w->V;
   a.W = (C*)w->W;
-  a.G0 = (C*)w->G0;
+  a.qpv = (R*)w->G0;  // the buffer holds Q_calc at pv buses
   a.th = (M*)w->th;
   a.vm = (M*)w->vm;
   a.mth = (R*)w->mth;
@@ -448,6 +461,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.beta2 = (R)w->opts.beta2;
   a.eps = (R)w->opts.eps;
   a.inv_m2 = (R)(y->m_loss > 0 ? 2.0 / y->m_loss : 0.0);
+  a.m_half = (R)(0.5 * y->m_loss);
   a.n_active = w->n_active;
 
   SchedArgs<R>& s = P.sc;
@@ -528,7 +542,8 @@ static Plan<R> make_plan(dpf_workspace* w) {
   P.grid = P.cgrid;
   P.pgrid = dim3(w->Kp / 64, w->gy);
   P.block = dim3(w->warps * 32);
-  P.smem = w->smem;
+  P.smem = w->smem;    // forward pass: Y rows + (optional) V window
+  P.ysmem = w->ysmem;  // adjoint and evaluation passes: Y rows only
   P.sched_blocks = (w->Kp + 63) / 64;
   return P;
 }
@@ -569,10 +584,10 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
   }
   if (w->profile) CK(cudaEventRecord(e1, s));
   if constexpr (sizeof(R) == 4) {
-    if (w->pair_adj) k_adj2<<<P.pgrid, P.block, P.smem, s>>>(P.it);
-    else k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+    if (w->pair_adj) k_adj2<<<P.pgrid, P.block, P.ysmem, s>>>(P.it);
+    else k_adj<R><<<P.grid, P.block, P.ysmem, s>>>(P.it);
   } else {
-    k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+    k_adj<R><<<P.grid, P.block, P.ysmem, s>>>(P.it);
   }
   if (w->profile) {
     CK(cudaEventRecord(e2, s));
@@ -669,21 +684,60 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   gy = std::max(1, std::min(std::min(gy, gy_max), 65535));
   const int n = w->y->n;
   const std::vector<int32_t>& rp = w->y->irow_ptr;
+  const std::vector<int32_t>& col = w->y->icol;
   const bool fp64 = (o ? o->precision : w->precision) == DPF_FP64;
-  // shrink row blocks until the staged Y rows of every block fit in shared memory
-  for (;;) {
+  // bytes of one staged window row: the case tile's line of V
+  const bool stage_v = o && o->stage_v;
+  const int line = !stage_v ? 0 : w->pair_fwd ? 512 : (lanes == 32 ? 32 * (fp64 ? 16 : 8) : 0);
+  // shrink row blocks until the staged Y rows (and the V window) fit
+  for (int tries = 0;; ++tries) {
     const int rpb = (n + gy - 1) / gy;
-    int mx = 0;
-    for (int r0 = 0; r0 < n; r0 += rpb) mx = std::max(mx, rp[std::min(n, r0 + rpb)] - rp[r0]);
-    const int bytes = ysmem_bytes(rpb, mx, fp64);
-    if (bytes <= 96 * 1024 || gy >= 65535 || rpb <= 1) {
+    int mx = 0, wmax = 0;
+    for (int r0 = 0; r0 < n; r0 += rpb) {
+      const int r1 = std::min(n, r0 + rpb);
+      mx = std::max(mx, rp[r1] - rp[r0]);
+      int lo = r0, hi = r1 - 1;
+      for (int q = rp[r0]; q < rp[r1]; ++q) { lo = std::min(lo, col[q]); hi = std::max(hi, col[q]); }
+      wmax = std::max(wmax, hi - lo + 1);
+    }
+    const int ybytes = ysmem_bytes(rpb, mx, fp64);
+    const int wbytes = line * wmax;
+    const bool fits = ybytes + wbytes <= 150 * 1024;
+    if ((fits && line > 0) || (line == 0 && ybytes <= 96 * 1024) || gy >= 65535 || rpb <= 1 || tries >= 6) {
       w->gy = (n + rpb - 1) / rpb;
       w->rpb = rpb;
-      w->smem = bytes;
+      w->ysmem = ybytes;
+      w->staged = line > 0 && fits;
+      w->smem = ybytes + (w->staged ? wbytes : 0);
       break;
     }
     gy = std::min(65535, gy * 2);
   }
+  w->h_wlo.assign(w->gy, 0);
+  w->h_whi.assign(w->gy, 0);
+  for (int b = 0; b < w->gy; ++b) {
+    const int r0 = b * w->rpb, r1 = std::min(n, r0 + w->rpb);
+    int lo = r0, hi = r1 - 1;
+    for (int q = rp[r0]; q < rp[r1]; ++q) { lo = std::min(lo, col[q]); hi = std::max(hi, col[q]); }
+    w->h_wlo[b] = lo;
+    w->h_whi[b] = hi;
+  }
+}
+
+// Device copies of the row-block windows (after choose_shape).
+static int upload_windows(dpf_workspace* w, cudaStream_t s) {
+  if (w->gy > w->cap_wblocks) {
+    dfree(w->d_wlo);
+    dfree(w->d_whi);
+    w->cap_wblocks = 0;
+    TRY(dalloc(&w->d_wlo, w->gy));
+    TRY(dalloc(&w->d_whi, w->gy));
+    w->cap_wblocks = w->gy;
+  }
+  CK(cudaMemcpyAsync(w->d_wlo, w->h_wlo.data(), w->gy * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w->d_whi, w->h_whi.data(), w->gy * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // host vectors may change at the next choose_shape
+  return DPF_OK;
 }
 
 template <class R>
@@ -900,6 +954,7 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   w->precision = o->precision;
   w->use_local_y = false;
   choose_shape(w, o, w->K);
+  TRY(upload_windows(w, s));
   TRY(w->precision == DPF_FP64 ? set_smem_attr<double>(w->smem) : set_smem_attr<float>(w->smem));
   TRY(ws_reserve(w, w->Kp, b->host_io ? (size_t)w->K * y->n : 0));
   StateIn in;
@@ -1158,6 +1213,7 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
       o->warps = kv.second[1];
       o->row_blocks = kv.second[2];
       o->pair_cases = kv.second[3];
+      o->stage_v = kv.second[4];
       return DPF_OK;
     }
   const int K = b->n_case;
@@ -1173,6 +1229,7 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
   base.warps = 8;
   base.row_blocks = 0;
   base.pair_cases = 0;
+  base.stage_v = 0;
   choose_shape(w, &base, K);
   const int gy_auto = w->gy;
   std::vector<int> rb_c = {gy_auto, 2 * gy_auto, 4 * gy_auto};
@@ -1185,13 +1242,16 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
   for (int ln : lanes_c)
     for (int pc : pair_c)
       for (int wp : {4, 8})
-        for (int rb : rb_c) {
+        for (int rb : rb_c)
+          for (int sv : {0, 1}) {
           if (pc && ln != 32) continue;
+          if (sv && ln != 32) continue;
           dpf_solve_opts c = base;
           c.lanes = ln;
           c.pair_cases = pc;
           c.warps = wp;
           c.row_blocks = rb;
+          c.stage_v = sv;
           if ((rc = dpf_solve_begin(y, w, b, &c, s)) != DPF_OK) break;
           const int ce = std::max(1, c.check_every);
           if ((rc = dpf_solve_iterate(w, ce, s)) != DPF_OK) break;  // warm-up, builds the graph
@@ -1217,7 +1277,8 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
   o->warps = best.warps;
   o->row_blocks = best.row_blocks;
   o->pair_cases = best.pair_cases;
-  w->tune_cache.push_back({key, {best.lanes, best.warps, best.row_blocks, best.pair_cases}});
+  o->stage_v = best.stage_v;
+  w->tune_cache.push_back({key, {best.lanes, best.warps, best.row_blocks, best.pair_cases, best.stage_v}});
   return DPF_OK;
 }
 
@@ -1237,6 +1298,7 @@ static int eval_setup(const dpf_ybus* y, dpf_workspace* w, int K, int precision,
   w->precision = precision;
   w->K = K;
   choose_shape(w, nullptr, K);
+  TRY(upload_windows(w, s));
   TRY(precision == DPF_FP64 ? set_smem_attr<double>(w->smem) : set_smem_attr<float>(w->smem));
   TRY(ws_reserve(w, w->Kp, 0));
   StateIn in;

@@ -361,5 +361,6 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->row_blocks = 0;
   o->use_graph = 1;
   o->pair_cases = 1;  /* forward pass two cases per thread */
+  o->stage_v = 0;
   o->plain = 0;
 }

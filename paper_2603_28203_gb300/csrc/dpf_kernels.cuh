@@ -292,10 +292,13 @@ template <class R> struct IterArgs {
   int N, Kp, lanes, rpb;
   const int32_t* __restrict__ rp;
   YView<R> Y;
+  const int32_t* wlo;  // per row block: first and last row its nonzeros reference
+  const int32_t* whi;  //   (NULL: neighbour gathers read global memory)
+  int ysmem;           // bytes of the staged Y rows (the V/W window follows)
   const uint8_t* __restrict__ type;
   C* V;
   C* W;
-  C* G0;
+  R* qpv;    // Q_calc at pv buses (the rows k_adj cannot rebuild from w)
   M* th;
   M* vm;
   R* mth;
@@ -316,7 +319,7 @@ template <class R> struct IterArgs {
   unsigned int* mx32;  // per-case max |dP|,|dQ| (float bits) or NULL
   const R* step_size;
   const R* isbc2;
-  R beta1, beta2, eps, inv_m2;
+  R beta1, beta2, eps, inv_m2, m_half;
   const int32_t* n_active;
   // optional outputs (evaluation entry points); NULL in the solve loop
   C* sbuf;   // S_calc
@@ -357,6 +360,19 @@ __device__ __forceinline__ void case_sum_max_atomic(R v, float mx, int lanes, R*
   }
 }
 
+// Copy rows [lo, hi] of a case-minor array, restricted to this CTA's case
+// tile, into shared memory: `per_row` 16-byte words per row, row-major.
+// Coalesced 16-byte loads, all threads; ends with a barrier.
+__device__ __forceinline__ void stage_window(const float4* __restrict__ src, unsigned row_words, unsigned base,
+                                             int lo, int hi, int per_row, float4* __restrict__ dst) {
+  const int n = (hi - lo + 1) * per_row;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int r = t / per_row, c = t - r * per_row;
+    dst[t] = __ldg(src + (unsigned)(lo + r) * row_words + base + c);
+  }
+  __syncthreads();
+}
+
 // ---- forward: SpMV + power + mismatch + loss --------------------------------
 template <class R>
 __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
@@ -367,6 +383,16 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   YSmem<R> ys;
   ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
   const int k = mp.k;
+  // window of V in shared memory (lanes = 32: one 32-case line per row)
+  const bool staged = a.wlo && a.lanes == 32 && mp.r0 < mp.r1;
+  const int wlo = staged ? a.wlo[blockIdx.y] : 0;
+  C* vt = (C*)(smem + a.ysmem);
+  if (staged) {
+    constexpr int per_row = 32 * (int)sizeof(C) / 16;
+    stage_window((const float4*)a.V, (unsigned)(a.Kp * sizeof(C) / 16), blockIdx.x * per_row, wlo,
+                 a.whi[blockIdx.y], per_row, (float4*)vt);
+  }
+  const C* __restrict__ Vsh = vt - (size_t)wlo * 32 + (k & 31);
   const bool on = (k < a.Kp) && a.active[k];
   R acc = 0;
   float mx = 0.f;
@@ -384,9 +410,10 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
       const size_t e = (size_t)i * Kp + k;
       const int ty = __ldg(a.type + i);
       const size_t si = a.spec_per_case ? e : (size_t)i;
-      const C vi = V[e];
+      const C vi = staged ? Vsh[(size_t)i * 32] : V[e];
       const R ps = a.pspec[si], qs = a.qspec[si];
-      C I = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], V, Kp, k);
+      C I = staged ? row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], Vsh, 32, 0)
+                   : row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], V, Kp, k);
       if (i == of) {
         cfms(I, yff, vi);
         cfms(I, yft, V[(size_t)ot * Kp + k]);
@@ -400,7 +427,7 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
       const R dQ = (ty == BUS_PQ) ? Q - qs : R(0);
       const R ca = a.inv_m2 * dP, cb = a.inv_m2 * dQ;
       a.W[e] = mkc(ca * vi.x + cb * vi.y, cb * vi.x - ca * vi.y);
-      a.G0[e] = mkc(ca * P + cb * Q, ca * Q - cb * P);
+      if (ty == BUS_PV) a.qpv[e] = Q;
       if (a.sbuf) a.sbuf[e] = mkc(P, Q);
       if (a.cbuf) a.cbuf[e] = mkc(ca, cb);
       acc += dP * dP + dQ * dQ;
@@ -409,6 +436,19 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
     }
   }
   if (a.loss_acc || a.mx32) case_sum_max_atomic(acc, mx, a.lanes, a.loss_acc, a.mx32, a.Kp);
+}
+
+// conj(c_i) S_i rebuilt from w_i = c_i conj(V_i):  c = w V / |V|^2;
+// P = P_spec + (m/2) Re c (pv, pq);  Q = Q_spec + (m/2) Im c (pq), or the
+// forward pass's Q_calc at pv buses (c is real there).
+template <class C, class R>
+__device__ __forceinline__ C conj_c_s(C w, C v, int ty, R ps, R qs, R qpv, R m_half) {
+  const R inv = R(1) / (v.x * v.x + v.y * v.y);
+  const R ca = (w.x * v.x - w.y * v.y) * inv;
+  const R cb = (ty == BUS_PQ) ? (w.x * v.y + w.y * v.x) * inv : R(0);
+  const R P = ps + m_half * ca;
+  const R Q = (ty == BUS_PQ) ? qs + m_half * cb : qpv;
+  return mkc(ca * P + cb * Q, ca * Q - cb * P);
 }
 
 // ---- adjoint SpMV + gradient + Adam ----------------------------------------
@@ -447,7 +487,10 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
       continue;
     }
     // this element's operands first: they do not depend on the gather chain
-    const C g0 = a.G0[e];
+    const C wi = W[e];
+    const size_t si = a.spec_per_case ? e : (size_t)i;
+    const R ps = a.pspec[si], qs = a.qspec[si];
+    const R qp = (ty == BUS_PV) ? a.qpv[e] : R(0);
     M th = a.th[e];
     M vm = a.vm[e];
     R m1 = 0, v1 = 0, m2 = 0, v2 = 0;
@@ -458,13 +501,14 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
     }
     C z = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], W, Kp, k);
     if (i == of) {
-      cfms(z, yff, W[e]);
+      cfms(z, yff, wi);
       cfms(z, yft, W[(size_t)ot * Kp + k]);
     } else if (i == ot) {
       cfms(z, yft, W[(size_t)of * Kp + k]);
-      cfms(z, ytt, W[e]);
+      cfms(z, ytt, wi);
     }
     const C vi = volt(th, vm);
+    const C g0 = conj_c_s(wi, vi, ty, ps, qs, qp, a.m_half);
     const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
     const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
     const R g_th = -hi;
@@ -582,14 +626,14 @@ __device__ __forceinline__ void pair_sum_max_atomic(float s0, float s1, float m0
 
 // Forward epilogue of one case (the same arithmetic as k_fwd).
 __device__ __forceinline__ void fwd_epilogue(float2 vi, float2 I, int ty, float ps, float qs, float inv_m2,
-                                             float2& w, float2& g0, float& acc, float& mx) {
+                                             float2& w, float& q, float& acc, float& mx) {
   const float P = vi.x * I.x + vi.y * I.y;
   const float Q = vi.y * I.x - vi.x * I.y;
   const float dP = (ty != BUS_SLACK) ? P - ps : 0.f;
   const float dQ = (ty == BUS_PQ) ? Q - qs : 0.f;
   const float ca = inv_m2 * dP, cb = inv_m2 * dQ;
   w = make_float2(ca * vi.x + cb * vi.y, cb * vi.x - ca * vi.y);
-  g0 = make_float2(ca * P + cb * Q, ca * Q - cb * P);
+  q = Q;
   acc += dP * dP + dQ * dQ;
   const float am = fmaxf(fabsf(dP), fabsf(dQ));
   mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);
@@ -603,17 +647,22 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
   YSmem<float> ys;
   ys.stage(a.rp, a.Y, r0, r1, smem);
   const int k0 = 2 * (blockIdx.x * 32 + lane);
+  const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
+  // this block's window of V (the rows its nonzeros reference), one
+  // 512-byte line of 64 cases per row
+  const int wlo = (a.wlo && r0 < r1) ? a.wlo[blockIdx.y] : 0;
+  float4* vt = (float4*)(smem + a.ysmem);
+  if (a.wlo && r0 < r1) stage_window((const float4*)a.V, hKp, blockIdx.x * 32, wlo, a.whi[blockIdx.y], 32, vt);
+  const float4* __restrict__ Vs = vt - (size_t)wlo * 32 + lane;  // Vs[j * 32]: row j, this thread's pair
   const Pair q = load_pair(a, k0);
   float acc0 = 0.f, acc1 = 0.f, mx0 = 0.f, mx1 = 0.f;
   if (q.on0 || q.on1) {
-    const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
     const float4* __restrict__ V = (const float4*)a.V;
     float4* W = (float4*)a.W;
-    float4* G = (float4*)a.G0;
     for (int i = r0 + warp; i < r1; i += wpb) {
       const unsigned e = (unsigned)i * hKp + h0;  // pair index
       const int ty = __ldg(a.type + i);
-      const float4 v = V[e];
+      const float4 v = a.wlo ? Vs[(size_t)i * 32] : V[e];
       float ps0, ps1, qs0, qs1;
       if (a.spec_per_case) {
         const float2 pp = ((const float2*)a.pspec)[e], qq = ((const float2*)a.qspec)[e];
@@ -623,7 +672,8 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
         qs0 = qs1 = a.qspec[i];
       }
       float2 I0, I1;
-      row_spmv2(ys, ys.rp[i], ys.rp[i + 1], V, hKp, h0, I0, I1);
+      if (a.wlo) row_spmv2(ys, ys.rp[i], ys.rp[i + 1], Vs, 32u, 0u, I0, I1);
+      else row_spmv2(ys, ys.rp[i], ys.rp[i + 1], V, hKp, h0, I0, I1);
       const float2 vi0 = make_float2(v.x, v.y), vi1 = make_float2(v.z, v.w);
       if (i == q.of0) {
         cfms(I0, q.yff0, vi0);
@@ -643,11 +693,12 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
         cfms(I1, q.yft1, make_float2(t.z, t.w));
         cfms(I1, q.ytt1, vi1);
       }
-      float2 w0, w1, g0, g1;
-      fwd_epilogue(vi0, I0, ty, ps0, qs0, a.inv_m2, w0, g0, acc0, mx0);
-      fwd_epilogue(vi1, I1, ty, ps1, qs1, a.inv_m2, w1, g1, acc1, mx1);
+      float2 w0, w1;
+      float q0, q1;
+      fwd_epilogue(vi0, I0, ty, ps0, qs0, a.inv_m2, w0, q0, acc0, mx0);
+      fwd_epilogue(vi1, I1, ty, ps1, qs1, a.inv_m2, w1, q1, acc1, mx1);
       W[e] = make_float4(w0.x, w0.y, w1.x, w1.y);
-      G[e] = make_float4(g0.x, g0.y, g1.x, g1.y);
+      if (ty == BUS_PV) ((float2*)a.qpv)[e] = make_float2(q0, q1);
     }
     if (!q.on0) { acc0 = 0.f; mx0 = 0.f; }
     if (!q.on1) { acc1 = 0.f; mx1 = 0.f; }
@@ -683,7 +734,16 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     if (ty == BUS_SLACK) continue;
     const unsigned e = (unsigned)i * hKp + h0;
     // this element's operands first: they do not depend on the gather chain
-    const float4 g = ((const float4*)a.G0)[e];
+    const float4 wi = W[e];
+    float ps0, ps1, qs0, qs1;
+    if (a.spec_per_case) {
+      const float2 pp = ((const float2*)a.pspec)[e], qq = ((const float2*)a.qspec)[e];
+      ps0 = pp.x; ps1 = pp.y; qs0 = qq.x; qs1 = qq.y;
+    } else {
+      ps0 = ps1 = a.pspec[i];
+      qs0 = qs1 = a.qspec[i];
+    }
+    const float2 qp = (ty == BUS_PV) ? ((const float2*)a.qpv)[e] : make_float2(0.f, 0.f);
     float4 th = ((const float4*)a.th)[e];  // (hi, lo) of case k0, then of k0 + 1
     float4 vm = ((const float4*)a.vm)[e];
     float2 mt = ((const float2*)a.mth)[e], vt = ((const float2*)a.vth)[e];
@@ -694,7 +754,6 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     }
     float2 z0, z1;
     row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W, hKp, h0, z0, z1);
-    const float4 wi = W[e];
     if (i == q.of0) {
       cfms(z0, q.yff0, make_float2(wi.x, wi.y));
       const float4 t = W[(unsigned)q.ot0 * hKp + h0];
@@ -716,8 +775,10 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     float2 th0 = make_float2(th.x, th.y), th1 = make_float2(th.z, th.w);
     float2 vm0 = make_float2(vm.x, vm.y), vm1 = make_float2(vm.z, vm.w);
     const float2 v0 = volt(th0, vm0), v1 = volt(th1, vm1);
-    const float hr0 = g.x + (v0.x * z0.x - v0.y * z0.y), hi0 = g.y + (v0.x * z0.y + v0.y * z0.x);
-    const float hr1 = g.z + (v1.x * z1.x - v1.y * z1.y), hi1 = g.w + (v1.x * z1.y + v1.y * z1.x);
+    const float2 g0 = conj_c_s(make_float2(wi.x, wi.y), v0, ty, ps0, qs0, qp.x, a.m_half);
+    const float2 g1 = conj_c_s(make_float2(wi.z, wi.w), v1, ty, ps1, qs1, qp.y, a.m_half);
+    const float hr0 = g0.x + (v0.x * z0.x - v0.y * z0.y), hi0 = g0.y + (v0.x * z0.y + v0.y * z0.x);
+    const float hr1 = g1.x + (v1.x * z1.x - v1.y * z1.y), hi1 = g1.y + (v1.x * z1.y + v1.y * z1.x);
     // Adam on theta (pv and pq buses); an inactive case keeps its state
     if (q.on0) th0 = adam_step(th0, -hi0, mt.x, vt.x, b1, b2, st0, ib0, eps);
     if (q.on1) th1 = adam_step(th1, -hi1, mt.y, vt.y, b1, b2, st1, ib1, eps);

@@ -173,6 +173,7 @@ class SolveOpts:
     row_blocks: int | None = None
     use_graph: int | None = None
     pair_cases: int | None = None
+    stage_v: int | None = None
     plain: int | None = None
 
     def to_c(self) -> _abi.DpfSolveOpts:
@@ -254,7 +255,8 @@ def dpf_autotune(y: Ybus, ws: Workspace, opts=None, iters: int = 25, stream=None
     _check(lib().dpf_autotune(y.handle, ws.handle, C.byref(b), C.byref(o), int(iters), _stream(stream)))
     out = SolveOpts(**{f.name: getattr(opts, f.name) for f in dataclasses.fields(SolveOpts)}) \
         if isinstance(opts, SolveOpts) else SolveOpts()
-    out.lanes, out.warps, out.row_blocks, out.pair_cases = o.lanes, o.warps, o.row_blocks, o.pair_cases
+    out.lanes, out.warps, out.row_blocks, out.pair_cases, out.stage_v = (o.lanes, o.warps, o.row_blocks,
+                                                                        o.pair_cases, o.stage_v)
     return out
 
 
