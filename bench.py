@@ -167,14 +167,14 @@ def algorithmic_bytes(n_bus, n_pv, n_pq, nnz, n_case):
       buses (4 B);
     k_adj, per case: read w (8 B/bus); at pv buses read Q_calc (4); at every
       pv/pq bus read+write theta (16, double-float), read |V| (8), read+write
-      the two Adam moments of theta (16), write V (8); at pq buses also write
-      |V| (8) and read+write its moments (16).
+      V (16), read+write the two Adam moments of theta (16); at pq buses also
+      write |V| (8) and read+write its moments (16).
     Shared per launch: Y in CSR (16 B per nonzero + 4 B row pointers + bus
     types) and the shared specified P, Q (8 B/bus).
     """
     shared = 16 * nnz + 4 * (n_bus + 1) + n_bus + 8 * n_bus
     fwd = n_case * (16 * n_bus + 4 * n_pv) + shared
-    adj = n_case * (8 * n_bus + 52 * n_pv + 72 * n_pq) + shared
+    adj = n_case * (8 * n_bus + 60 * n_pv + 80 * n_pq) + shared
     return fwd, adj
 
 

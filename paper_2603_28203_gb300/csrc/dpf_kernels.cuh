@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
 // forward pass's Q_calc at pv buses (c is real there).
 template <class C, class R>
 __device__ __forceinline__ C conj_c_s(C w, C v, int ty, R ps, R qs, R qpv, R m_half) {
-  const R inv = R(1) / (v.x * v.x + v.y * v.y);
+  const R inv = div_step(R(1), v.x * v.x + v.y * v.y);
   const R ca = (w.x * v.x - w.y * v.y) * inv;
   const R cb = (ty == BUS_PQ) ? (w.x * v.y + w.y * v.x) * inv : R(0);
   const R P = ps + m_half * ca;
@@ -493,6 +493,7 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
     const R qp = (ty == BUS_PV) ? a.qpv[e] : R(0);
     M th = a.th[e];
     M vm = a.vm[e];
+    const C vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
     R m1 = 0, v1 = 0, m2 = 0, v2 = 0;
     if (!grad_only) {
       m1 = a.mth[e];
@@ -507,7 +508,6 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
       cfms(z, yft, W[(size_t)of * Kp + k]);
       cfms(z, ytt, wi);
     }
-    const C vi = volt(th, vm);
     const C g0 = conj_c_s(wi, vi, ty, ps, qs, qp, a.m_half);
     const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
     const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
@@ -746,6 +746,7 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     const float2 qp = (ty == BUS_PV) ? ((const float2*)a.qpv)[e] : make_float2(0.f, 0.f);
     float4 th = ((const float4*)a.th)[e];  // (hi, lo) of case k0, then of k0 + 1
     float4 vm = ((const float4*)a.vm)[e];
+    const float4 vv4 = ((const float4*)a.V)[e];  // current V of both cases (no second sincos)
     float2 mt = ((const float2*)a.mth)[e], vt = ((const float2*)a.vth)[e];
     float2 mv = make_float2(0.f, 0.f), vv = mv;
     if (ty == BUS_PQ) {
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     }
     float2 th0 = make_float2(th.x, th.y), th1 = make_float2(th.z, th.w);
     float2 vm0 = make_float2(vm.x, vm.y), vm1 = make_float2(vm.z, vm.w);
-    const float2 v0 = volt(th0, vm0), v1 = volt(th1, vm1);
+    const float2 v0 = make_float2(vv4.x, vv4.y), v1 = make_float2(vv4.z, vv4.w);
     const float2 g0 = conj_c_s(make_float2(wi.x, wi.y), v0, ty, ps0, qs0, qp.x, a.m_half);
     const float2 g1 = conj_c_s(make_float2(wi.z, wi.w), v1, ty, ps1, qs1, qp.y, a.m_half);
     const float hr0 = g0.x + (v0.x * z0.x - v0.y * z0.y), hi0 = g0.y + (v0.x * z0.y + v0.y * z0.x);
