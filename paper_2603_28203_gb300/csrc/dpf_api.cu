@@ -221,6 +221,7 @@ struct dpf_workspace {
   // solve state
   bool begun = false;
   int K = 0, Kp = 0, lanes = 1, warps = 8, gx = 1, gy = 1, rpb = 1, smem = 0, precision = DPF_FP32;
+  int gy_b = 1, rpb_b = 1, ysmem_b = 0;  // the adjoint pass's row blocks (may differ from the forward's)
   bool pairs = false;   // FP32 solve loop, Kp a multiple of 64: two cases per thread possible
   // shared-memory windows of V for the forward pass: per row block the first
   // and last row referenced (host copy + device copy)
@@ -389,6 +390,8 @@ struct Plan {
   dim3 grid, block;   // one case per thread
   dim3 cgrid;         // (the same; check and evaluation kernels)
   dim3 pgrid;         // two cases per thread
+  IterArgs<R> itb;    // the adjoint pass (its own row blocks)
+  dim3 gridb, pgridb;
   int smem;
   int ysmem;
   int sched_blocks;
@@ -541,9 +544,15 @@ static Plan<R> make_plan(dpf_workspace* w) {
   P.cgrid = dim3(w->Kp / w->lanes, w->gy);
   P.grid = P.cgrid;
   P.pgrid = dim3(w->Kp / 64, w->gy);
+  P.itb = P.it;
+  P.itb.rpb = w->rpb_b;
+  P.itb.wlo = nullptr;
+  P.itb.whi = nullptr;
+  P.gridb = dim3(w->Kp / w->lanes, w->gy_b);
+  P.pgridb = dim3(w->Kp / 64, w->gy_b);
   P.block = dim3(w->warps * 32);
-  P.smem = w->smem;    // forward pass: Y rows + (optional) V window
-  P.ysmem = w->ysmem;  // adjoint and evaluation passes: Y rows only
+  P.smem = w->smem;      // forward pass: Y rows + (optional) V window
+  P.ysmem = w->ysmem_b;  // adjoint pass: its Y rows only
   P.sched_blocks = (w->Kp + 63) / 64;
   return P;
 }
@@ -584,10 +593,10 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
   }
   if (w->profile) CK(cudaEventRecord(e1, s));
   if constexpr (sizeof(R) == 4) {
-    if (w->pair_adj) k_adj2<<<P.pgrid, P.block, P.ysmem, s>>>(P.it);
-    else k_adj<R><<<P.grid, P.block, P.ysmem, s>>>(P.it);
+    if (w->pair_adj) k_adj2<<<P.pgridb, P.block, P.ysmem, s>>>(P.itb);
+    else k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
   } else {
-    k_adj<R><<<P.grid, P.block, P.ysmem, s>>>(P.it);
+    k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
   }
   if (w->profile) {
     CK(cudaEventRecord(e2, s));
@@ -713,6 +722,45 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
     }
     gy = std::min(65535, gy * 2);
   }
+  // Row blocks per pass, sized so that each grid is a whole number of waves
+  // of resident CTAs (a partial last wave leaves SMs idle at the tail).
+  auto seg_nnz = [&](int rpb_) {
+    int mx = 0;
+    for (int r0 = 0; r0 < n; r0 += rpb_) mx = std::max(mx, rp[std::min(n, r0 + rpb_)] - rp[r0]);
+    return mx;
+  };
+  auto aligned = [&](int gx_k, int slots, int gy0) {
+    if (slots <= 0) return gy0;
+    const int waves = std::max(1, (int)((double)gx_k * gy0 / slots + 0.5));
+    int g_ = std::max(1, std::min(n, (int)((long long)waves * slots / gx_k)));
+    const int rpb_ = (n + g_ - 1) / g_;
+    return (n + rpb_ - 1) / rpb_;
+  };
+  const bool auto_rb = !(o && o->row_blocks > 0);
+  const int block = w->warps * 32;
+  const int sms = num_sms();
+  w->gy_b = w->gy;
+  if (auto_rb && !w->staged) {
+    int occ_f = 0, occ_b = 0;
+    const void* kf = fp64 ? (const void*)k_fwd<double> : w->pair_fwd ? (const void*)k_fwd2 : (const void*)k_fwd<float>;
+    const void* kb = fp64 ? (const void*)k_adj<double> : w->pair_adj ? (const void*)k_adj2 : (const void*)k_adj<float>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, block, w->smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, kb, block, w->smem);
+    cudaGetLastError();  // a failed query only disables the alignment
+    const int gxf = w->pair_fwd ? w->Kp / 64 : w->gx;
+    const int gxb = w->pair_adj ? w->Kp / 64 : w->gx;
+    const int gyf = aligned(gxf, occ_f * sms, w->gy);
+    w->gy_b = aligned(gxb, occ_b * sms, w->gy);
+    if (gyf != w->gy) {
+      w->rpb = (n + gyf - 1) / gyf;
+      w->gy = (n + w->rpb - 1) / w->rpb;
+      w->ysmem = ysmem_bytes(w->rpb, seg_nnz(w->rpb), fp64);
+      w->smem = w->ysmem;
+    }
+  }
+  w->rpb_b = (n + w->gy_b - 1) / w->gy_b;
+  w->gy_b = (n + w->rpb_b - 1) / w->rpb_b;
+  w->ysmem_b = ysmem_bytes(w->rpb_b, seg_nnz(w->rpb_b), fp64);
   w->h_wlo.assign(w->gy, 0);
   w->h_whi.assign(w->gy, 0);
   for (int b = 0; b < w->gy; ++b) {
@@ -955,7 +1003,8 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   w->use_local_y = false;
   choose_shape(w, o, w->K);
   TRY(upload_windows(w, s));
-  TRY(w->precision == DPF_FP64 ? set_smem_attr<double>(w->smem) : set_smem_attr<float>(w->smem));
+  TRY(w->precision == DPF_FP64 ? set_smem_attr<double>(std::max(w->smem, w->ysmem_b))
+                               : set_smem_attr<float>(std::max(w->smem, w->ysmem_b)));
   TRY(ws_reserve(w, w->Kp, b->host_io ? (size_t)w->K * y->n : 0));
   StateIn in;
   memset(&in, 0, sizeof in);
@@ -1232,7 +1281,7 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
   base.stage_v = 0;
   choose_shape(w, &base, K);
   const int gy_auto = w->gy;
-  std::vector<int> rb_c = {gy_auto, 2 * gy_auto, 4 * gy_auto};
+  std::vector<int> rb_c = {0, gy_auto, 2 * gy_auto, 4 * gy_auto};  // 0: wave-aligned automatic choice
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1299,7 +1348,8 @@ static int eval_setup(const dpf_ybus* y, dpf_workspace* w, int K, int precision,
   w->K = K;
   choose_shape(w, nullptr, K);
   TRY(upload_windows(w, s));
-  TRY(precision == DPF_FP64 ? set_smem_attr<double>(w->smem) : set_smem_attr<float>(w->smem));
+  TRY(precision == DPF_FP64 ? set_smem_attr<double>(std::max(w->smem, w->ysmem_b))
+                            : set_smem_attr<float>(std::max(w->smem, w->ysmem_b)));
   TRY(ws_reserve(w, w->Kp, 0));
   StateIn in;
   memset(&in, 0, sizeof in);
@@ -1349,7 +1399,9 @@ static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, doub
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
   P.it.gva = (R*)w->tmp_c;  // reuse as gradient scratch: [N][Kp] R each
   P.it.gvm = (R*)w->sbuf;
-  k_adj<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  P.itb = P.it;
+  P.itb.rpb = w->rpb_b;
+  k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
   CKLAUNCH();
   const size_t E = (size_t)y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
