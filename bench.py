@@ -241,8 +241,9 @@ def run_ours(args):
     out_dev = torch.tensor(outages, dtype=torch.int32, device=dev)
     opts = dpf.SolveOpts(lr=LR, tol=TOL, check_every=CHECK_EVERY, precision=dpf.FP32,
                          max_iter=args.warmup + args.steps + args.profile_steps + 8 * CHECK_EVERY,
-                         lanes=args.lanes or None, warps=args.warps or None, row_blocks=args.row_blocks or None)
-    if not (args.lanes or args.warps or args.row_blocks or args.no_autotune):
+                         lanes=args.lanes or None, warps=args.warps or None, row_blocks=args.row_blocks or None,
+                         pdl=0 if args.no_pdl else None)
+    if not (args or args.warps or args.row_blocks or args.no_autotune):
         with torch.cuda.stream(stream):
             opts = dpf.dpf_autotune(y, ws, opts, iters=50, stream=stream, n_case=K, outage=out_dev)
     res = dict(va=torch.empty((K, N), dtype=torch.float64, device=dev),
@@ -489,6 +490,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-pdl", action="store_true")
     ap.add_argument("--plain-cases", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

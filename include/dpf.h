@@ -167,6 +167,10 @@ typedef struct {
                                 runs the forward pass, bit 1 the adjoint pass
                                 with two cases per thread (16-byte accesses);
                                 0: one case per thread                        */
+  int32_t pdl;               /* 1: iteration kernels use programmatic dependent
+                                launch (each may start while its predecessor
+                                drains; it waits for it before touching the
+                                state)                                         */
   int32_t stage_v;           /* 1: the forward pass first copies the rows of V
                                 its row block references into shared memory
                                 and gathers from there (lanes = 32 only)      */

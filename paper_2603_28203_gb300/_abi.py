@@ -47,7 +47,8 @@ class DpfSolveOpts(C.Structure):
         ("max_iter", C.c_int32), ("check_every", C.c_int32), ("tol", C.c_double), ("gate", C.c_double),
         ("flat_start", C.c_int32), ("precision", C.c_int32),
         ("lanes", C.c_int32), ("warps", C.c_int32), ("row_blocks", C.c_int32),
-        ("use_graph", C.c_int32), ("pair_cases", C.c_int32), ("stage_v", C.c_int32), ("plain", C.c_int32),
+        ("use_graph", C.c_int32), ("pair_cases", C.c_int32), ("pdl", C.c_int32), ("stage_v", C.c_int32),
+        ("plain", C.c_int32),
     ]
 
 

@@ -37,6 +37,24 @@ using namespace dpf;
 
 namespace {
 
+// Launch with programmatic stream serialisation when `pdl` (see pdl_wait /
+// pdl_release in the kernels), else as a plain stream-ordered launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                   Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <class T>
 int dalloc(T** p, size_t n) {
   *p = nullptr;
@@ -563,14 +581,14 @@ static int launch_check(dpf_workspace* w, cudaStream_t s, bool final_pass) {
   P.ck.all_cases = final_pass ? 1 : 0;
   P.ap.final_pass = final_pass ? 1 : 0;
   using M = typename Prec<R>::M;
+  const bool pdl = w->opts.pdl != 0;
   if (P.need_volt64) {
-    k_volt64<M><<<P.cgrid, P.block, 0, s>>>(P.ck);
+    CK(launch(k_volt64<M>, P.cgrid, P.block, 0, s, pdl, P.ck));
     w->launches++;
   }
-  k_check64<M><<<P.cgrid, P.block, 0, s>>>(P.ck);
-  k_apply<<<1, 1024, 0, s>>>(P.ap);
+  CK(launch(k_check64<M>, P.cgrid, P.block, 0, s, pdl, P.ck));
+  CK(launch(k_apply, dim3(1), dim3(1024), 0, s, pdl, P.ap));
   w->launches += 2;
-  CKLAUNCH();
   return DPF_OK;
 }
 
@@ -578,6 +596,8 @@ template <class R>
 static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
   if (with_check) TRY(launch_check<R>(w, s, false));
   Plan<R> P = make_plan<R>(w);
+  // event-bracketed (profiled) launches keep plain stream order
+  const bool pdl = w->opts.pdl != 0 && !w->profile;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (w->profile) {
     TRY(ev_take(w, &e0));
@@ -586,17 +606,17 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
     CK(cudaEventRecord(e0, s));
   }
   if constexpr (sizeof(R) == 4) {
-    if (w->pair_fwd) k_fwd2<<<P.pgrid, P.block, P.smem, s>>>(P.it);
-    else k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+    if (w->pair_fwd) CK(launch(k_fwd2, P.pgrid, P.block, P.smem, s, pdl, P.it));
+    else CK(launch(k_fwd<R>, P.grid, P.block, P.smem, s, pdl, P.it));
   } else {
-    k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+    CK(launch(k_fwd<R>, P.grid, P.block, P.smem, s, pdl, P.it));
   }
   if (w->profile) CK(cudaEventRecord(e1, s));
   if constexpr (sizeof(R) == 4) {
-    if (w->pair_adj) k_adj2<<<P.pgridb, P.block, P.ysmem, s>>>(P.itb);
-    else k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
+    if (w->pair_adj) CK(launch(k_adj2, P.pgridb, P.block, P.ysmem, s, pdl, P.itb));
+    else CK(launch(k_adj<R>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
   } else {
-    k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
+    CK(launch(k_adj<R>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
   }
   if (w->profile) {
     CK(cudaEventRecord(e2, s));
@@ -604,9 +624,8 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
     w->ev_fwd.push_back({i2 - 2, i2 - 1});
     w->ev_adj.push_back({i2 - 1, i2});
   }
-  k_sched<R><<<P.sched_blocks, 64, 0, s>>>(P.sc);
+  CK(launch(k_sched<R>, dim3(P.sched_blocks), dim3(64), 0, s, pdl, P.sc));
   w->launches += 3;
-  CKLAUNCH();
   return DPF_OK;
 }
 
@@ -968,6 +987,7 @@ static int validate_opts(const dpf_solve_opts* o) {
     return fail(DPF_E_INVALID, "invalid max_iter / check_every / tol");
   if (o->precision != DPF_FP32 && o->precision != DPF_FP64) return fail(DPF_E_INVALID, "unknown precision");
   if (!(o->gate >= 0.0)) return fail(DPF_E_INVALID, "gate must be >= 0");
+  if (o->pdl != 0 && o->pdl != 1) return fail(DPF_E_INVALID, "pdl must be 0 or 1");
   if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 8 || o->row_blocks < 0)
     return fail(DPF_E_INVALID, "invalid launch shape (lanes 0..32, warps 0..8, row_blocks >= 0)");
   return DPF_OK;

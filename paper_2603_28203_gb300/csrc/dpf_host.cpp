@@ -362,5 +362,6 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->use_graph = 1;
   o->pair_cases = 1;  /* forward pass two cases per thread */
   o->stage_v = 0;
+  o->pdl = 1;
   o->plain = 0;
 }

@@ -62,6 +62,16 @@ template <class C> __device__ __forceinline__ void cfms(C& acc, const C y, const
   acc.y = fmaT(-y.x, v.y, fmaT(-y.y, v.x, acc.y));
 }
 
+// ---- programmatic dependent launch -------------------------------------------
+// A kernel launched with programmatic stream serialisation may start while its
+// predecessor drains.  pdl_wait() blocks until the predecessor grid has
+// completed and its memory is visible; pdl_release() lets the successor be
+// scheduled.  Both are no-ops for a kernel launched without the attribute.
+// Everything before pdl_wait() may read only data no kernel of the iteration
+// writes (Y_bus, bus types).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- master values ---------------------------------------------------------
 // FP32 mode keeps theta and |V| as an unevaluated sum hi + lo of two floats
 // (~48 significant bits) and updates them with an error-free two-sum, so the
@@ -378,10 +388,12 @@ template <class R>
 __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   extern __shared__ __align__(16) unsigned char smem[];
-  if (a.n_active && *a.n_active == 0) return;
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
   YSmem<R> ys;
   ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
+  pdl_wait();
+  pdl_release();
+  if (a.n_active && *a.n_active == 0) return;
   const int k = mp.k;
   // window of V in shared memory (lanes = 32: one 32-case line per row)
   const bool staged = a.wlo && a.lanes == 32 && mp.r0 < mp.r1;
@@ -452,6 +464,101 @@ __device__ __forceinline__ C conj_c_s(C w, C v, int ty, R ps, R qs, R qpv, R m_h
 }
 
 // ---- adjoint SpMV + gradient + Adam ----------------------------------------
+#ifndef DPF_ADJ_ROWS
+#define DPF_ADJ_ROWS 1
+#endif
+
+// One row of the adjoint pass for one case: operands, adjoint SpMV, update.
+template <class R> struct AdjRow {
+  using C = typename Prec<R>::C;
+  using M = typename Prec<R>::M;
+  bool live;  // row exists and is not the slack
+  int i, ty;
+  size_t e;
+  C wi, vi, z;
+  R ps, qs, qp, m1, v1, m2, v2;
+  M th, vm;
+};
+
+template <class R>
+__device__ __forceinline__ void adj_load(const IterArgs<R>& a, AdjRow<R>& r, int i, int r1, int k, size_t Kp,
+                                         bool grad_only) {
+  r.live = false;
+  if (i >= r1) return;
+  r.i = i;
+  r.e = (size_t)i * Kp + k;
+  r.ty = __ldg(a.type + i);
+  if (r.ty == BUS_SLACK) {
+    if (grad_only) { a.gva[r.e] = R(0); a.gvm[r.e] = R(0); }
+    return;
+  }
+  r.live = true;
+  const size_t e = r.e;
+  r.wi = a.W[e];
+  const size_t si = a.spec_per_case ? e : (size_t)i;
+  r.ps = a.pspec[si];
+  r.qs = a.qspec[si];
+  r.qp = (r.ty == BUS_PV) ? a.qpv[e] : R(0);
+  r.th = a.th[e];
+  r.vm = a.vm[e];
+  r.vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
+  r.m1 = r.v1 = r.m2 = r.v2 = R(0);
+  if (!grad_only) {
+    r.m1 = a.mth[e];
+    r.v1 = a.vth[e];
+    if (r.ty == BUS_PQ) { r.m2 = a.mvm[e]; r.v2 = a.vvm[e]; }
+  }
+}
+
+template <class R, class YS>
+__device__ __forceinline__ void adj_gather(const IterArgs<R>& a, const YS& ys, AdjRow<R>& r, int k, size_t Kp,
+                                           int of, int ot, typename Prec<R>::C yff, typename Prec<R>::C yft,
+                                           typename Prec<R>::C ytt) {
+  const int i = r.i;
+  r.z = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], a.W, Kp, k);
+  if (i == of) {
+    cfms(r.z, yff, r.wi);
+    cfms(r.z, yft, a.W[(size_t)ot * Kp + k]);
+  } else if (i == ot) {
+    cfms(r.z, yft, a.W[(size_t)of * Kp + k]);
+    cfms(r.z, ytt, r.wi);
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, bool grad_only, R step, R isb, R b1,
+                                           R b2, R eps) {
+  using C = typename Prec<R>::C;
+  const size_t e = r.e;
+  const C vi = r.vi, z = r.z;
+  const C g0 = conj_c_s(r.wi, vi, r.ty, r.ps, r.qs, r.qp, a.m_half);
+  const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
+  const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
+  const R g_th = -hi;
+  const R g_vm = (r.ty == BUS_PQ) ? div_step(hr, mwork(r.vm)) : R(0);
+  if (grad_only) {
+    a.gva[e] = g_th;
+    a.gvm[e] = g_vm;
+    return;
+  }
+  // Adam on theta (pv and pq buses)
+  r.m1 = b1 * r.m1 + (R(1) - b1) * g_th;
+  r.v1 = b2 * r.v1 + (R(1) - b2) * g_th * g_th;
+  a.mth[e] = r.m1;
+  a.vth[e] = r.v1;
+  r.th = msub(r.th, div_step(step * r.m1, sqrt_step(r.v1) * isb + eps));
+  a.th[e] = r.th;
+  if (r.ty == BUS_PQ) {  // Adam on |V| (pq buses)
+    r.m2 = b1 * r.m2 + (R(1) - b1) * g_vm;
+    r.v2 = b2 * r.v2 + (R(1) - b2) * g_vm * g_vm;
+    a.mvm[e] = r.m2;
+    a.vvm[e] = r.v2;
+    r.vm = msub(r.vm, div_step(step * r.m2, sqrt_step(r.v2) * isb + eps));
+    a.vm[e] = r.vm;
+  }
+  a.V[e] = volt(r.th, r.vm);
+}
+
 #ifndef DPF_ADJ_MINB
 #define DPF_ADJ_MINB 5
 #endif
@@ -460,10 +567,12 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
   extern __shared__ __align__(16) unsigned char smem[];
-  if (a.n_active && *a.n_active == 0) return;
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
   YSmem<R> ys;
   ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
+  pdl_wait();
+  pdl_release();
+  if (a.n_active && *a.n_active == 0) return;
   const int k = mp.k;
   if (k >= a.Kp || !a.active[k]) return;
   int of = -1, ot = -1;
@@ -479,61 +588,19 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   const R b1 = a.beta1, b2 = a.beta2, eps = a.eps;
   const size_t Kp = (size_t)a.Kp;
   const C* __restrict__ W = a.W;
-  for (int i = mp.i0; i < mp.r1; i += mp.istride) {
-    const size_t e = (size_t)i * Kp + k;
-    const int ty = __ldg(a.type + i);
-    if (ty == BUS_SLACK) {
-      if (grad_only) { a.gva[e] = R(0); a.gvm[e] = R(0); }
-      continue;
-    }
-    // this element's operands first: they do not depend on the gather chain
-    const C wi = W[e];
-    const size_t si = a.spec_per_case ? e : (size_t)i;
-    const R ps = a.pspec[si], qs = a.qspec[si];
-    const R qp = (ty == BUS_PV) ? a.qpv[e] : R(0);
-    M th = a.th[e];
-    M vm = a.vm[e];
-    const C vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
-    R m1 = 0, v1 = 0, m2 = 0, v2 = 0;
-    if (!grad_only) {
-      m1 = a.mth[e];
-      v1 = a.vth[e];
-      if (ty == BUS_PQ) { m2 = a.mvm[e]; v2 = a.vvm[e]; }
-    }
-    C z = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], W, Kp, k);
-    if (i == of) {
-      cfms(z, yff, wi);
-      cfms(z, yft, W[(size_t)ot * Kp + k]);
-    } else if (i == ot) {
-      cfms(z, yft, W[(size_t)of * Kp + k]);
-      cfms(z, ytt, wi);
-    }
-    const C g0 = conj_c_s(wi, vi, ty, ps, qs, qp, a.m_half);
-    const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
-    const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
-    const R g_th = -hi;
-    const R g_vm = (ty == BUS_PQ) ? div_step(hr, mwork(vm)) : R(0);
-    if (grad_only) {
-      a.gva[e] = g_th;
-      a.gvm[e] = g_vm;
-      continue;
-    }
-    // Adam on theta (pv and pq buses)
-    m1 = b1 * m1 + (R(1) - b1) * g_th;
-    v1 = b2 * v1 + (R(1) - b2) * g_th * g_th;
-    a.mth[e] = m1;
-    a.vth[e] = v1;
-    th = msub(th, div_step(step * m1, sqrt_step(v1) * isb + eps));
-    a.th[e] = th;
-    if (ty == BUS_PQ) {  // Adam on |V| (pq buses)
-      m2 = b1 * m2 + (R(1) - b1) * g_vm;
-      v2 = b2 * v2 + (R(1) - b2) * g_vm * g_vm;
-      a.mvm[e] = m2;
-      a.vvm[e] = v2;
-      vm = msub(vm, div_step(step * m2, sqrt_step(v2) * isb + eps));
-      a.vm[e] = vm;
-    }
-    a.V[e] = volt(th, vm);
+  // DPF_ADJ_ROWS rows per warp per step: their loads and gathers are all
+  // issued before any of them is consumed (more memory requests in flight)
+  constexpr int NR = DPF_ADJ_ROWS;
+  for (int i0 = mp.i0; i0 < mp.r1; i0 += NR * mp.istride) {
+    AdjRow<R> rw[NR];
+#pragma unroll
+    for (int u = 0; u < NR; ++u) adj_load(a, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
+#pragma unroll
+    for (int u = 0; u < NR; ++u)
+      if (rw[u].live) adj_gather(a, ys, rw[u], k, Kp, of, ot, yff, yft, ytt);
+#pragma unroll
+    for (int u = 0; u < NR; ++u)
+      if (rw[u].live) adj_finish(a, rw[u], grad_only, step, isb, b1, b2, eps);
   }
 }
 
@@ -641,11 +708,13 @@ __device__ __forceinline__ void fwd_epilogue(float2 vi, float2 I, int ty, float 
 
 __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (a.n_active && *a.n_active == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int r0 = blockIdx.y * a.rpb, r1 = min(a.N, r0 + a.rpb);
   YSmem<float> ys;
   ys.stage(a.rp, a.Y, r0, r1, smem);
+  pdl_wait();
+  pdl_release();
+  if (a.n_active && *a.n_active == 0) return;
   const int k0 = 2 * (blockIdx.x * 32 + lane);
   const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
   // this block's window of V (the rows its nonzeros reference), one
@@ -716,11 +785,13 @@ __device__ __forceinline__ float2 adam_step(float2 x, float g, float& m, float& 
 
 __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (a.n_active && *a.n_active == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int r0 = blockIdx.y * a.rpb, r1 = min(a.N, r0 + a.rpb);
   YSmem<float> ys;
   ys.stage(a.rp, a.Y, r0, r1, smem);
+  pdl_wait();
+  pdl_release();
+  if (a.n_active && *a.n_active == 0) return;
   const int k0 = 2 * (blockIdx.x * 32 + lane);
   const Pair q = load_pair(a, k0);
   if (!(q.on0 || q.on1)) return;
@@ -823,6 +894,8 @@ template <class R> struct SchedArgs {
 
 template <class R>
 __global__ void k_sched(SchedArgs<R> a) {
+  pdl_wait();
+  pdl_release();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.Kp || !a.active[k]) return;
   const double L = (double)a.loss_acc[k] * a.inv_m;  // MSE of the iterate the step came from
@@ -904,6 +977,8 @@ template <class M> struct Check64Args {
 // V64 = |V| e^{j theta} from the master state (FP64 sincos).
 template <class M>
 __global__ void __launch_bounds__(1024) k_volt64(Check64Args<M> a) {
+  pdl_wait();
+  pdl_release();
   if (!a.all_cases && *a.n_active == 0) return;
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
@@ -916,6 +991,8 @@ __global__ void __launch_bounds__(1024) k_volt64(Check64Args<M> a) {
 
 template <class M>
 __global__ void __launch_bounds__(1024) k_check64(Check64Args<M> a) {
+  pdl_wait();
+  pdl_release();
   if (!a.all_cases && *a.n_active == 0) return;
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
@@ -979,6 +1056,8 @@ struct ApplyArgs {
 
 __global__ void k_apply(ApplyArgs a) {
   __shared__ int cnt[32];
+  pdl_wait();
+  pdl_release();
   int c = 0;
   for (int k = threadIdx.x; k < a.Kp; k += blockDim.x) {
     if (k < a.K) {

@@ -173,6 +173,7 @@ class SolveOpts:
     row_blocks: int | None = None
     use_graph: int | None = None
     pair_cases: int | None = None
+    pdl: int | None = None
     stage_v: int | None = None
     plain: int | None = None
 
