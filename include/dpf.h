@@ -60,6 +60,7 @@ enum {
 enum { DPF_PQ = 0, DPF_PV = 1, DPF_SLACK = 2 };            /* bus types (Sec. 2.1) */
 enum { DPF_FP32 = 0, DPF_FP64 = 1 };                        /* iteration precision */
 enum { DPF_SCHED_CONST = 0, DPF_SCHED_PLATEAU = 1, DPF_SCHED_STEP = 2 };
+enum { DPF_OPT_ADAM = 0, DPF_OPT_SGD = 1, DPF_OPT_RMSPROP = 2 };    /* Sec. 5.3's optimisers */
 
 /* ---- grid description (host arrays, caller-owned, read-only) -------------
  * The problem statement of Sec. 2.1 / Alg. 1 inputs: bus types with exactly
@@ -143,7 +144,11 @@ typedef struct {
  * patience 41, threshold 0.0673 (relative), cooldown 97, max_iter 1000 --
  * with lr 1e-2, tol 1e-6 p.u., check_every 25, gate 1e-3, FP32 iterations. */
 typedef struct {
-  double lr, beta1, beta2, eps;
+  double lr, beta1, beta2, eps;   /* Adam (eps also RMSprop's)                 */
+  int32_t optimizer;         /* DPF_OPT_* (PyTorch semantics: SGD without
+                                dampening/Nesterov, RMSprop not centred)      */
+  double momentum;           /* SGD momentum (0 = plain SGD)                   */
+  double alpha;              /* RMSprop smoothing constant                     */
   int32_t sched;             /* DPF_SCHED_*                                    */
   double factor, threshold, min_lr;
   int32_t patience, cooldown;

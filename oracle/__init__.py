@@ -31,13 +31,13 @@ from .ybus import build_ybus, branch_blocks
 from .power import s_calc, mismatch, loss, learnable_sets
 from .jacobian import dS_dVm_dVa, jacobian_f
 from .gradient import loss_grad, param_grad
-from .optim import Adam, ReduceLROnPlateau, StepLR
+from .optim import SGD, Adam, ReduceLROnPlateau, RMSprop, StepLR
 from .dpf import DPFOptions, dpf_solve, flat_start
 from .nr import nr_solve
 
 __all__ = [
     "build_ybus", "branch_blocks", "s_calc", "mismatch", "loss", "learnable_sets",
-    "dS_dVm_dVa", "jacobian_f", "loss_grad", "param_grad", "Adam",
+    "dS_dVm_dVa", "jacobian_f", "loss_grad", "param_grad", "Adam", "SGD", "RMSprop",
     "ReduceLROnPlateau", "StepLR", "DPFOptions", "dpf_solve", "flat_start",
     "nr_solve",
 ]

@@ -22,7 +22,7 @@ import dataclasses
 import numpy as np
 
 from .gradient import loss_grad
-from .optim import Adam, ConstantLR, ReduceLROnPlateau, StepLR
+from .optim import SGD, Adam, ConstantLR, ReduceLROnPlateau, RMSprop, StepLR
 from .power import PQ, PV, SLACK, learnable_sets, mismatch
 
 CONVERGED, MAX_ITER, DIVERGED = 0, 1, 2
@@ -31,6 +31,9 @@ CONVERGED, MAX_ITER, DIVERGED = 0, 1, 2
 @dataclasses.dataclass
 class DPFOptions:
     lr: float = 1e-2
+    optimizer: str = "adam"  # "adam" | "sgd" | "rmsprop" (the optimisers of Sec. 5.3)
+    momentum: float = 0.0  # SGD
+    alpha: float = 0.99  # RMSprop
     beta1: float = 0.979  # Table 2
     beta2: float = 0.963
     eps: float = 1e-8
@@ -72,7 +75,13 @@ def dpf_solve(Y, p_spec, q_spec, bus_type, vm_set, opts: DPFOptions,
     va[bus_type == SLACK] = va_slack
     pvpq, pq = learnable_sets(bus_type)
     npv = pvpq.size
-    opt = Adam(npv + pq.size, opts.lr, (opts.beta1, opts.beta2), opts.eps)
+    nx = npv + pq.size
+    if opts.optimizer == "sgd":
+        opt = SGD(nx, opts.lr, opts.momentum)
+    elif opts.optimizer == "rmsprop":
+        opt = RMSprop(nx, opts.lr, opts.alpha, opts.eps)
+    else:
+        opt = Adam(nx, opts.lr, (opts.beta1, opts.beta2), opts.eps)
     if opts.sched == "plateau":
         sched = ReduceLROnPlateau(opt, opts.factor, opts.patience, opts.threshold,
                                   opts.cooldown, opts.min_lr)

@@ -1,7 +1,8 @@
 """Optimiser and learning-rate schedulers (oracle; test infrastructure).
 
 Sec. 5.3 selects Adam with ReduceLROnPlateau (Table 2) and, for the first step
-of a time series, StepLR (Table 3).  The paper ran them through torch.optim in
+of a time series, StepLR (Table 3); SGD and RMSprop, the other optimisers of
+its search, are provided as well.  The paper ran them through torch.optim in
 PyTorch 2.6 (Sec. 5.2), so their defaults apply where the tables are silent:
 epsilon 1e-8, bias correction on, no weight decay, no amsgrad; plateau mode
 'min' with a relative threshold, min_lr 0, and a reduction applied only when it
@@ -41,6 +42,40 @@ class Adam:
         v_hat = self.v / (1.0 - b2 ** self.t)
         lr = self.lr if lr_scale is None else self.lr * lr_scale
         return x - lr * m_hat / (np.sqrt(v_hat) + self.eps)
+
+
+class SGD:
+    """Sec. 5.3's SGD (PyTorch semantics, dampening 0, no Nesterov):
+    buf <- momentum * buf + g;  x <- x - lr * buf  (buf = g without momentum)."""
+
+    def __init__(self, n, lr, momentum=0.0):
+        self.lr = float(lr)
+        self.momentum = float(momentum)
+        self.buf = np.zeros(n)
+        self.t = 0
+
+    def step(self, x, g, lr_scale=None):
+        self.t += 1
+        self.buf = self.momentum * self.buf + g if self.momentum != 0.0 else np.asarray(g, np.float64)
+        lr = self.lr if lr_scale is None else self.lr * lr_scale
+        return x - lr * self.buf
+
+
+class RMSprop:
+    """Sec. 5.3's RMSprop (Hinton; PyTorch semantics, not centred, no momentum):
+    v <- alpha v + (1 - alpha) g^2;  x <- x - lr * g / (sqrt(v) + eps)."""
+
+    def __init__(self, n, lr, alpha=0.99, eps=1e-8):
+        self.lr = float(lr)
+        self.alpha, self.eps = float(alpha), float(eps)
+        self.v = np.zeros(n)
+        self.t = 0
+
+    def step(self, x, g, lr_scale=None):
+        self.t += 1
+        self.v = self.alpha * self.v + (1.0 - self.alpha) * g * g
+        lr = self.lr if lr_scale is None else self.lr * lr_scale
+        return x - lr * g / (np.sqrt(self.v) + self.eps)
 
 
 class ReduceLROnPlateau:

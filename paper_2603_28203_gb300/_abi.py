@@ -9,6 +9,7 @@ CASE_CONVERGED, CASE_MAX_ITER, CASE_DIVERGED = 0, 1, 2
 PQ, PV, SLACK = 0, 1, 2
 FP32, FP64 = 0, 1
 SCHED_CONST, SCHED_PLATEAU, SCHED_STEP = 0, 1, 2
+OPT_ADAM, OPT_SGD, OPT_RMSPROP = 0, 1, 2
 NOALLOC_MAX_ELEMS = 1 << 18
 
 p_i32 = C.POINTER(C.c_int32)
@@ -40,6 +41,7 @@ class DpfBatch(C.Structure):
 class DpfSolveOpts(C.Structure):
     _fields_ = [
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+        ("optimizer", C.c_int32), ("momentum", C.c_double), ("alpha", C.c_double),
         ("sched", C.c_int32),
         ("factor", C.c_double), ("threshold", C.c_double), ("min_lr", C.c_double),
         ("patience", C.c_int32), ("cooldown", C.c_int32),

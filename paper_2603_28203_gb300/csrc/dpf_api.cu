@@ -482,6 +482,9 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.beta2 = (R)w->opts.beta2;
   a.eps = (R)w->opts.eps;
   a.inv_m2 = (R)(y->m_loss > 0 ? 2.0 / y->m_loss : 0.0);
+  a.opt = w->opts.optimizer;
+  a.mom = (R)w->opts.momentum;
+  a.alpha = (R)w->opts.alpha;
   a.m_half = (R)(0.5 * y->m_loss);
   a.n_active = w->n_active;
 
@@ -515,6 +518,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   s.patience = w->opts.patience;
   s.cooldown = w->opts.cooldown;
   s.step_every = std::max(1, w->opts.step_size);
+  s.opt = w->opts.optimizer;
 
   Check64Args<M>& c = P.ck;
   c.N = y->n;
@@ -968,6 +972,7 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   ca.lr0 = w->opts.lr;
   ca.beta1 = w->opts.beta1;
   ca.beta2 = w->opts.beta2;
+  ca.opt = w->opts.optimizer;
   k_case_init<R><<<(w->Kp + 255) / 256, 256, 0, s>>>(ca);
   CKLAUNCH();
   CK(cudaMemcpyAsync(w->n_active, &w->K, 4, cudaMemcpyHostToDevice, s));
@@ -979,6 +984,9 @@ static int validate_opts(const dpf_solve_opts* o) {
   if (!(o->lr > 0) || !(o->beta1 >= 0 && o->beta1 < 1) || !(o->beta2 >= 0 && o->beta2 < 1) || !(o->eps >= 0))
     return fail(DPF_E_INVALID, "invalid Adam parameters");
   if (o->sched < DPF_SCHED_CONST || o->sched > DPF_SCHED_STEP) return fail(DPF_E_INVALID, "unknown scheduler");
+  if (o->optimizer < DPF_OPT_ADAM || o->optimizer > DPF_OPT_RMSPROP) return fail(DPF_E_INVALID, "unknown optimizer");
+  if (!(o->momentum >= 0 && o->momentum < 1) || !(o->alpha >= 0 && o->alpha < 1))
+    return fail(DPF_E_INVALID, "momentum and alpha must be in [0, 1)");
   if (o->sched == DPF_SCHED_PLATEAU && (!(o->factor > 0 && o->factor < 1) || o->patience < 0 || o->cooldown < 0))
     return fail(DPF_E_INVALID, "invalid plateau parameters");
   if (o->sched == DPF_SCHED_STEP && (o->step_size < 1 || !(o->gamma > 0)))

@@ -342,6 +342,9 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->beta1 = 0.979;
   o->beta2 = 0.963;
   o->eps = 1e-8;
+  o->optimizer = DPF_OPT_ADAM;
+  o->momentum = 0.0;
+  o->alpha = 0.99;
   o->sched = DPF_SCHED_PLATEAU;
   o->factor = 0.547;
   o->threshold = 0.0673;

@@ -31,6 +31,7 @@ namespace dpf {
 enum { BUS_PQ = 0, BUS_PV = 1, BUS_SLACK = 2 };
 enum { CASE_CONVERGED = 0, CASE_MAX_ITER = 1, CASE_DIVERGED = 2 };
 enum { SCHED_CONST = 0, SCHED_PLATEAU = 1, SCHED_STEP = 2 };
+enum { OPT_ADAM = 0, OPT_SGD = 1, OPT_RMSPROP = 2 };
 
 template <class R> struct Prec;
 template <> struct Prec<float> { using C = float2; using M = float2; };   // M: (hi, lo) master
@@ -330,6 +331,8 @@ template <class R> struct IterArgs {
   const R* step_size;
   const R* isbc2;
   R beta1, beta2, eps, inv_m2, m_half;
+  int opt;     // OPT_ADAM / OPT_SGD / OPT_RMSPROP
+  R mom, alpha;  // SGD momentum, RMSprop smoothing
   const int32_t* n_active;
   // optional outputs (evaluation entry points); NULL in the solve loop
   C* sbuf;   // S_calc
@@ -464,6 +467,25 @@ __device__ __forceinline__ C conj_c_s(C w, C v, int ty, R ps, R qs, R qpv, R m_h
 }
 
 // ---- adjoint SpMV + gradient + Adam ----------------------------------------
+// One optimiser step on a master value (Sec. 5.3's optimisers, PyTorch
+// semantics).  step = lr (bias-corrected lr / (1 - beta1^t) for Adam), isb =
+// 1 / sqrt(1 - beta2^t) (Adam); m, v are the per-element optimiser state.
+template <class R, class M>
+__device__ __forceinline__ M opt_update(int opt, M x, R g, R& m, R& v, R b1, R b2, R step, R isb, R eps, R mom,
+                                        R alpha) {
+  if (opt == OPT_SGD) {
+    m = (mom != R(0)) ? mom * m + g : g;
+    return msub(x, step * m);
+  }
+  if (opt == OPT_RMSPROP) {
+    v = alpha * v + (R(1) - alpha) * g * g;
+    return msub(x, div_step(step * g, sqrt_step(v) + eps));
+  }
+  m = b1 * m + (R(1) - b1) * g;
+  v = b2 * v + (R(1) - b2) * g * g;
+  return msub(x, div_step(step * m, sqrt_step(v) * isb + eps));
+}
+
 #ifndef DPF_ADJ_ROWS
 #define DPF_ADJ_ROWS 1
 #endif
@@ -541,19 +563,15 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
     a.gvm[e] = g_vm;
     return;
   }
-  // Adam on theta (pv and pq buses)
-  r.m1 = b1 * r.m1 + (R(1) - b1) * g_th;
-  r.v1 = b2 * r.v1 + (R(1) - b2) * g_th * g_th;
+  // optimiser step on theta (pv and pq buses)
+  r.th = opt_update(a.opt, r.th, g_th, r.m1, r.v1, b1, b2, step, isb, eps, a.mom, a.alpha);
   a.mth[e] = r.m1;
   a.vth[e] = r.v1;
-  r.th = msub(r.th, div_step(step * r.m1, sqrt_step(r.v1) * isb + eps));
   a.th[e] = r.th;
-  if (r.ty == BUS_PQ) {  // Adam on |V| (pq buses)
-    r.m2 = b1 * r.m2 + (R(1) - b1) * g_vm;
-    r.v2 = b2 * r.v2 + (R(1) - b2) * g_vm * g_vm;
+  if (r.ty == BUS_PQ) {  // and on |V| (pq buses)
+    r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha);
     a.mvm[e] = r.m2;
     a.vvm[e] = r.v2;
-    r.vm = msub(r.vm, div_step(step * r.m2, sqrt_step(r.v2) * isb + eps));
     a.vm[e] = r.vm;
   }
   a.V[e] = volt(r.th, r.vm);
@@ -775,13 +793,6 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
   pair_sum_max_atomic(acc0, acc1, mx0, mx1, a.loss_acc, a.mx32, a.Kp);
 }
 
-// Adam update of one double-float master value.
-__device__ __forceinline__ float2 adam_step(float2 x, float g, float& m, float& v, float b1, float b2, float step,
-                                           float isb, float eps) {
-  m = b1 * m + (1.f - b1) * g;
-  v = b2 * v + (1.f - b2) * g * g;
-  return msub(x, div_step(step * m, sqrt_step(v) * isb + eps));
-}
 
 __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -851,15 +862,17 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     const float2 g1 = conj_c_s(make_float2(wi.z, wi.w), v1, ty, ps1, qs1, qp.y, a.m_half);
     const float hr0 = g0.x + (v0.x * z0.x - v0.y * z0.y), hi0 = g0.y + (v0.x * z0.y + v0.y * z0.x);
     const float hr1 = g1.x + (v1.x * z1.x - v1.y * z1.y), hi1 = g1.y + (v1.x * z1.y + v1.y * z1.x);
-    // Adam on theta (pv and pq buses); an inactive case keeps its state
-    if (q.on0) th0 = adam_step(th0, -hi0, mt.x, vt.x, b1, b2, st0, ib0, eps);
-    if (q.on1) th1 = adam_step(th1, -hi1, mt.y, vt.y, b1, b2, st1, ib1, eps);
+    // optimiser step on theta (pv and pq buses); an inactive case keeps its state
+    if (q.on0) th0 = opt_update(a.opt, th0, -hi0, mt.x, vt.x, b1, b2, st0, ib0, eps, a.mom, a.alpha);
+    if (q.on1) th1 = opt_update(a.opt, th1, -hi1, mt.y, vt.y, b1, b2, st1, ib1, eps, a.mom, a.alpha);
     ((float2*)a.mth)[e] = mt;
     ((float2*)a.vth)[e] = vt;
     ((float4*)a.th)[e] = make_float4(th0.x, th0.y, th1.x, th1.y);
-    if (ty == BUS_PQ) {  // Adam on |V| (pq buses)
-      if (q.on0) vm0 = adam_step(vm0, div_step(hr0, mwork(vm0)), mv.x, vv.x, b1, b2, st0, ib0, eps);
-      if (q.on1) vm1 = adam_step(vm1, div_step(hr1, mwork(vm1)), mv.y, vv.y, b1, b2, st1, ib1, eps);
+    if (ty == BUS_PQ) {  // and on |V| (pq buses)
+      if (q.on0) vm0 = opt_update(a.opt, vm0, div_step(hr0, mwork(vm0)), mv.x, vv.x, b1, b2, st0, ib0, eps, a.mom,
+                                  a.alpha);
+      if (q.on1) vm1 = opt_update(a.opt, vm1, div_step(hr1, mwork(vm1)), mv.y, vv.y, b1, b2, st1, ib1, eps, a.mom,
+                                  a.alpha);
       ((float2*)a.mvm)[e] = mv;
       ((float2*)a.vvm)[e] = vv;
       ((float4*)a.vm)[e] = make_float4(vm0.x, vm0.y, vm1.x, vm1.y);
@@ -889,7 +902,7 @@ template <class R> struct SchedArgs {
   R* isbc2;
   int32_t* n_active;
   double inv_m, beta1, beta2, factor, threshold, min_lr, gamma, lr0;
-  int sched, patience, cooldown, step_every;
+  int sched, patience, cooldown, step_every, opt;
 };
 
 template <class R>
@@ -944,8 +957,13 @@ __global__ void k_sched(SchedArgs<R> a) {
   a.b2t[k] = b2t;
   // bias-corrected step terms in working precision (FP64 division and square
   // root are slow on this GPU; FP32 runs only consume them in FP32)
-  a.step_size[k] = (R)lr / (R(1) - (R)b1t);
-  a.isbc2[k] = R(1) / sqrtT(R(1) - (R)b2t);
+  if (a.opt == OPT_ADAM) {
+    a.step_size[k] = (R)lr / (R(1) - (R)b1t);
+    a.isbc2[k] = R(1) / sqrtT(R(1) - (R)b2t);
+  } else {
+    a.step_size[k] = (R)lr;
+    a.isbc2[k] = R(1);
+  }
 }
 
 // ---- FP64 convergence test --------------------------------------------------
@@ -1217,6 +1235,7 @@ template <class R> struct CaseInitArgs {
   unsigned long long* maxmis;
   double* loss64;
   double lr0, beta1, beta2;
+  int opt;
 };
 
 template <class R>
@@ -1232,8 +1251,8 @@ __global__ void k_case_init(CaseInitArgs<R> a) {
   a.bad[k] = 0;
   a.cool[k] = 0;
   a.loss_acc[k] = R(0);
-  a.step_size[k] = (R)(a.lr0 / (1.0 - a.beta1));
-  a.isbc2[k] = (R)(1.0 / sqrt(1.0 - a.beta2));
+  a.step_size[k] = (R)(a.opt == OPT_ADAM ? a.lr0 / (1.0 - a.beta1) : a.lr0);
+  a.isbc2[k] = (R)(a.opt == OPT_ADAM ? 1.0 / sqrt(1.0 - a.beta2) : 1.0);
   a.b1t[k] = a.beta1;  // beta^1: bias correction of the first step
   a.b2t[k] = a.beta2;
   a.cand[k] = 1;

@@ -151,6 +151,9 @@ def dpf_ybus_bridges(y: Ybus) -> np.ndarray:
 class SolveOpts:
     """Mirror of dpf_solve_opts; None keeps the library default (Table 2 etc.)."""
     lr: float | None = None
+    optimizer: int | None = None
+    momentum: float | None = None
+    alpha: float | None = None
     beta1: float | None = None
     beta2: float | None = None
     eps: float | None = None

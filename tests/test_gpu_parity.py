@@ -203,6 +203,28 @@ def test_solve_trajectory_fp64(sched, lanes):
         assert abs(r["loss"][k] - ref["loss"]) <= 1e-9 * max(ref["loss"], 1e-12)
 
 
+@pytest.mark.parametrize("opt", ["sgd", "rmsprop"])
+def test_other_optimisers_trajectory_fp64(opt):
+    """SGD (momentum) and RMSprop, the other optimisers of Sec. 5.3, step for step vs the oracle."""
+    g = GRIDS["c1"]()
+    Y = grid_ybus(g)
+    K = 3
+    code = dict(sgd=dpf.OPT_SGD, rmsprop=dpf.OPT_RMSPROP)[opt]
+    lr = 1e-3 if opt == "sgd" else 5e-3
+    kw = dict(lr=lr, momentum=0.9, alpha=0.95, sched=dpf.SCHED_PLATEAU, factor=0.5, patience=3, threshold=1e-3,
+              cooldown=2)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    r = _solve(y, ws, K, dpf.SolveOpts(precision=dpf.FP64, max_iter=120, check_every=1, optimizer=code, **kw))
+    ref = oracle.dpf_solve(Y, g.p_spec, g.q_spec, g.bus_type, g.vm_set,
+                           oracle.DPFOptions(optimizer=opt, lr=lr, momentum=0.9, alpha=0.95, sched="plateau",
+                                             factor=0.5, patience=3, threshold=1e-3, cooldown=2, max_iter=120))
+    for k in range(K):
+        assert np.abs(r["va"][k] - ref["va"]).max() < 1e-9
+        assert np.abs(r["vm"][k] - ref["vm"]).max() < 1e-9
+        assert r["iters"][k] == ref["iters"]
+
+
 def test_c1_converges_to_nr_fp64():
     """30-bus workload: FP64 DPF (lr 1e-2, Table 2 betas/plateau) to 1e-6 p.u., matches NR."""
     g = GRIDS["c1"]()

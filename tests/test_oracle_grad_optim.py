@@ -124,6 +124,28 @@ def test_adam_matches_torch():
         np.testing.assert_allclose(x, p.detach().numpy(), rtol=1e-12, atol=1e-14)
 
 
+def test_sgd_rmsprop_match_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    n = 11
+    x0 = rng.standard_normal(n)
+    grads = rng.standard_normal((200, n)) * np.logspace(0, -4, 200)[:, None]
+    for make, tmake in [
+        (lambda: oracle.SGD(n, 1e-2, 0.9), lambda p: torch.optim.SGD([p], lr=1e-2, momentum=0.9)),
+        (lambda: oracle.SGD(n, 1e-2, 0.0), lambda p: torch.optim.SGD([p], lr=1e-2)),
+        (lambda: oracle.RMSprop(n, 1e-3, 0.99), lambda p: torch.optim.RMSprop([p], lr=1e-3, alpha=0.99, eps=1e-8)),
+    ]:
+        opt = make()
+        x = x0.copy()
+        p = torch.tensor(x0.copy(), dtype=torch.float64, requires_grad=True)
+        topt = tmake(p)
+        for gk in grads:
+            x = opt.step(x, gk)
+            p.grad = torch.tensor(gk, dtype=torch.float64)
+            topt.step()
+        np.testing.assert_allclose(x, p.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
 def test_schedulers_match_torch():
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(1)
