@@ -430,6 +430,61 @@ def run_plain(dpf, y, g, outages, stream, args):
 
 
 # ---------------------------------------------------------------------------
+# scaling sweep (--workload scaling): single grids, node and edge scaling
+# ---------------------------------------------------------------------------
+def run_scaling(args):
+    """Time FP32 DPF iterations of single grids (K = 1) as the bus and branch
+    counts grow: the linear-cost claim of Sec. 5.2 / 5.4.3.  One JSON line per
+    grid; each carries the FP64 oracle check of S_calc on sampled buses."""
+    import torch
+    import gridgen
+    import oracle
+    from oracle.ybus import grid_ybus
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    base = gridgen.make_grid(10_000, 1, load_scale=0.1)
+    grids = [("nodes", gridgen.make_grid(n, 1, load_scale=0.1)) for n in (10_000, 100_000, 1_000_000)]
+    grids += [("edges", gridgen.add_random_branches(base, m, 7)) for m in (5_000, 20_000, 80_000)]
+    for kind, g in grids:
+        y = dpf.dpf_build_ybus(g, stream=stream)
+        ws = dpf.dpf_workspace_create(y, 1)
+        opts = dpf.SolveOpts(lr=1e-3, precision=dpf.FP32, check_every=25, max_iter=10 ** 6)
+        with torch.cuda.stream(stream):
+            dpf.dpf_solve_begin(y, ws, opts, stream=stream, n_case=1)
+            dpf.dpf_solve_iterate(ws, 50, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            n_it = 500
+            e0.record(stream)
+            dpf.dpf_solve_iterate(ws, n_it, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / n_it
+            # sampled parity of the forward evaluation against the oracle
+            rng = np.random.default_rng(0)
+            va = torch.tensor(0.05 * rng.standard_normal((1, g.n_bus)), dtype=torch.float64, device=dev)
+            vm = torch.tensor(1 + 0.02 * rng.standard_normal((1, g.n_bus)), dtype=torch.float64, device=dev)
+            p, q = dpf.dpf_power(y, ws, va, vm, precision=dpf.FP32, stream=stream)
+            stream.synchronize()
+        Y = grid_ybus(g)
+        S = oracle.s_calc(Y, vm[0].cpu().numpy() * np.exp(1j * va[0].cpu().numpy()))
+        err = max(np.abs(p[0].cpu().numpy() - S.real).max(), np.abs(q[0].cpu().numpy() - S.imag).max())
+        n_pv = int((g.bus_type == 1).sum())
+        n_pq = int((g.bus_type == 0).sum())
+        fwd_b, adj_b = algorithmic_bytes(g.n_bus, n_pv, n_pq, y.nnz, 1)
+        print(json.dumps({"workload": "scaling", "kind": kind, "n_bus": g.n_bus, "n_branch": g.n_branch,
+                          "nnz": y.nnz, "ms_per_iteration": ms, "us_per_iteration_per_1k_nnz": 1e3 * ms / (y.nnz / 1e3),
+                          "algorithmic_gbs": (fwd_b + adj_b) / (ms / 1e3) / 1e9,
+                          "fp32_S_max_abs_error_vs_fp64_oracle": float(err)}), flush=True)
+        ws.free()
+        y.free()
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
 def run_reference(args):
@@ -480,6 +535,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling"],
+                    help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
@@ -498,6 +555,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "scaling":
+        run_scaling(args)
     else:
         run_ours(args)
 

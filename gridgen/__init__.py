@@ -306,6 +306,35 @@ def perturb_branches(grid: Grid, seed: int, rel: float = 0.10) -> Grid:
     return g
 
 
+def add_random_branches(grid: Grid, n_extra: int, seed: int) -> Grid:
+    """Copy of `grid` with `n_extra` branches between random bus pairs (no
+    duplicates, no self-loops), drawn from the same r / x / b_ch
+    distributions; the edge-scaling experiment (Sec. 5.4.3) adds random
+    connections the same way."""
+    rng = np.random.default_rng(seed)
+    g = grid.copy()
+    have = set(zip(np.minimum(g.f_bus, g.t_bus).tolist(), np.maximum(g.f_bus, g.t_bus).tolist()))
+    f, t = [], []
+    while len(f) < n_extra:
+        a, b = (int(v) for v in rng.integers(0, g.n_bus, 2))
+        key = (min(a, b), max(a, b))
+        if a == b or key in have:
+            continue
+        have.add(key)
+        f.append(a)
+        t.append(b)
+    r = rng.uniform(0.002, 0.02, n_extra)
+    x = r * rng.uniform(5.0, 15.0, n_extra)
+    g.f_bus = np.concatenate([g.f_bus, np.array(f, np.int32)])
+    g.t_bus = np.concatenate([g.t_bus, np.array(t, np.int32)])
+    g.r = np.concatenate([g.r, r])
+    g.x = np.concatenate([g.x, x])
+    g.b_ch = np.concatenate([g.b_ch, rng.uniform(0.0, 0.05, n_extra)])
+    g.tap = np.concatenate([g.tap, np.ones(n_extra)])
+    g.shift = np.concatenate([g.shift, np.zeros(n_extra)])
+    return g
+
+
 def concat_grids(grids) -> Grid:
     """Block-diagonal batch of grids (one island each), bus indices offset."""
     off = np.cumsum([0] + [g.n_bus for g in grids])
