@@ -233,6 +233,8 @@ struct dpf_workspace {
   int32_t* outage_dev = nullptr;
   int32_t* n_active = nullptr;
   int32_t* h_n_active = nullptr;  // pinned
+  unsigned int* tile_cnt = nullptr;  // per case tile, for the forward pass's scheduler
+  int cap_tiles = 0;
   // user-layout staging for host_io
   double *st_a = nullptr, *st_b = nullptr, *st_c = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -277,6 +279,8 @@ static void ws_free_buffers(dpf_workspace* w) {
   dfree(w->st_a); dfree(w->st_b); dfree(w->st_c);
   dfree(w->d_wlo); dfree(w->d_whi);
   w->cap_wblocks = 0;
+  dfree(w->tile_cnt);
+  w->cap_tiles = 0;
   w->cap_elems = 0;
   w->cap_cases = 0;
   w->cap_stage = 0;
@@ -402,7 +406,6 @@ struct Plan {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
   IterArgs<R> it;
-  SchedArgs<R> sc;
   Check64Args<M> ck;
   ApplyArgs ap;
   dim3 grid, block;   // one case per thread
@@ -412,7 +415,6 @@ struct Plan {
   dim3 gridb, pgridb;
   int smem;
   int ysmem;
-  int sched_blocks;
   bool need_volt64;
 };
 
@@ -424,7 +426,6 @@ static Plan<R> make_plan(dpf_workspace* w) {
   const DeviceYbus& d = y->dev;
   Plan<R> P;
   memset(&P.it, 0, sizeof(P.it));
-  memset(&P.sc, 0, sizeof(P.sc));
   memset(&P.ck, 0, sizeof(P.ck));
   memset(&P.ap, 0, sizeof(P.ap));
   IterArgs<R>& a = P.it;
@@ -488,7 +489,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.m_half = (R)(0.5 * y->m_loss);
   a.n_active = w->n_active;
 
-  SchedArgs<R>& s = P.sc;
+  SchedArgs<R>& s = a.sc;
   s.Kp = w->Kp;
   s.active = w->active;
   s.iters = w->iters;
@@ -520,6 +521,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   s.step_every = std::max(1, w->opts.step_size);
   s.opt = w->opts.optimizer;
 
+  a.tile_cnt = w->tile_cnt;  // NULL in the evaluation entry points: no scheduler there
   Check64Args<M>& c = P.ck;
   c.N = y->n;
   c.Kp = w->Kp;
@@ -553,7 +555,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   p.Kp = w->Kp;
   p.final_pass = 0;
   p.tol = w->opts.tol;
-  p.inv_m = s.inv_m;
+  p.inv_m = y->m_loss > 0 ? 1.0 / y->m_loss : 0.0;
   p.active = w->active;
   p.cand = gated ? w->cand : nullptr;
   p.status = w->status;
@@ -575,7 +577,6 @@ static Plan<R> make_plan(dpf_workspace* w) {
   P.block = dim3(w->warps * 32);
   P.smem = w->smem;      // forward pass: Y rows + (optional) V window
   P.ysmem = w->ysmem_b;  // adjoint pass: its Y rows only
-  P.sched_blocks = (w->Kp + 63) / 64;
   return P;
 }
 
@@ -628,8 +629,7 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
     w->ev_fwd.push_back({i2 - 2, i2 - 1});
     w->ev_adj.push_back({i2 - 1, i2});
   }
-  CK(launch(k_sched<R>, dim3(P.sched_blocks), dim3(64), 0, s, pdl, P.sc));
-  w->launches += 3;
+  w->launches += 2;
   return DPF_OK;
 }
 
@@ -795,8 +795,17 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   }
 }
 
-// Device copies of the row-block windows (after choose_shape).
+// Device copies of the row-block windows (after choose_shape), and zeroed
+// per-tile counters for the forward pass's scheduler.
 static int upload_windows(dpf_workspace* w, cudaStream_t s) {
+  const int tiles = std::max(w->Kp / std::max(1, w->lanes), w->Kp / 64 + 1);
+  if (tiles > w->cap_tiles) {
+    dfree(w->tile_cnt);
+    w->cap_tiles = 0;
+    TRY(dalloc(&w->tile_cnt, tiles));
+    w->cap_tiles = tiles;
+  }
+  CK(cudaMemsetAsync(w->tile_cnt, 0, (size_t)w->cap_tiles * sizeof(unsigned int), s));
   if (w->gy > w->cap_wblocks) {
     dfree(w->d_wlo);
     dfree(w->d_whi);
@@ -1396,6 +1405,7 @@ static int power_impl(dpf_workspace* w, double* p_calc, double* q_calc, cudaStre
   P.it.sbuf = (typename Prec<R>::C*)w->sbuf;
   P.it.loss_acc = nullptr;
   P.it.n_active = nullptr;
+  P.it.tile_cnt = nullptr;
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
   const size_t E = (size_t)w->y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
@@ -1424,6 +1434,7 @@ static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, doub
   Plan<R> P = make_plan<R>(w);
   P.it.cbuf = (C*)w->cbuf;
   P.it.n_active = nullptr;
+  P.it.tile_cnt = nullptr;
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
   P.it.gva = (R*)w->tmp_c;  // reuse as gradient scratch: [N][Kp] R each
   P.it.gvm = (R*)w->sbuf;

@@ -8,12 +8,14 @@
 // neighbour's voltage is one coalesced 256-byte (FP32) access.  For a single
 // case (lanes = 1) the same code is a thread-per-row CSR SpMV.
 //
-// One DPF iteration (Alg. 1) is three launches:
+// One DPF iteration (Alg. 1) is two launches:
 //   k_fwd   I = Y V (+ N-1 correction), S = V conj(I), dP/dQ, loss partials,
-//           w = c conj(V), g0 = conj(c) S      (Eq. powerbalance, Alg. 1)
-//   k_adj   z = Y w (+ N-1 correction), h = g0 + V z,
-//           dL/dtheta = -Im h, dL/d|V| = Re h / |V|, Adam update, new V
-//   k_sched per-case loss, scheduler (ReduceLROnPlateau / StepLR), bias terms
+//           w = c conj(V); the last CTA of each case tile then runs the
+//           per-case scheduler (loss, ReduceLROnPlateau / StepLR, the step's
+//           bias-corrected terms)            (Eq. powerbalance, Alg. 1)
+//   k_adj   z = Y w (+ N-1 correction), h = conj(c) S + V z (conj(c) S
+//           rebuilt from w), dL/dtheta = -Im h, dL/d|V| = Re h / |V|,
+//           optimiser update, new V
 // and every `check_every` iterations the FP64 test k_volt64 + k_check64 +
 // k_apply (max |f| per case <= tol -> the case stops).
 //
@@ -296,6 +298,135 @@ __device__ __forceinline__ typename Prec<R>::C row_spmv(const YS& ys, int p0, in
   return mkc(a0.x + a1.x, a0.y + a1.y);
 }
 
+// ---- scheduler (one case) -------------------------------------------------
+template <class R> struct SchedArgs {
+  int Kp;
+  int32_t* active;
+  int32_t* iters;
+  int32_t* status;
+  R* loss_acc;
+  unsigned int* mx32;  // FP32 max mismatch of the forward pass (or NULL)
+  int32_t* cand;       // 1: the next FP64 test examines the case
+  double gate;         // FP32 max mismatch below which the FP64 test runs (<= 0: always)
+  double* lr;
+  double* best;
+  int32_t* bad;
+  int32_t* cool;
+  double* b1t;         // beta1^t, beta2^t of the last Adam step (running products)
+  double* b2t;
+  R* step_size;
+  R* isbc2;
+  int32_t* n_active;
+  double inv_m, beta1, beta2, factor, threshold, min_lr, gamma, lr0;
+  int sched, patience, cooldown, step_every, opt;
+};
+
+// Run once per active case per iteration, after the forward pass's loss and
+// mismatch partials of that case are complete and before the adjoint pass:
+//   1. the step terms of this iteration's update (step t + 1) from the current
+//      rate (Adam: lr / (1 - beta1^(t+1)) and 1 / sqrt(1 - beta2^(t+1)));
+//   2. the scheduler fed this iteration's loss (the loss of the iterate the
+//      step is taken from), giving the rate of the next step.
+// A non-finite loss stops the case as diverged before it steps.
+template <class R>
+__device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k) {
+  // every load is issued before the first store (one memory round trip: this
+  // runs in the forward pass's tail, on its critical path)
+  const int act = a.active[k];
+  const R lsum = __ldcg(a.loss_acc + k);
+  const unsigned mxu = a.mx32 ? __ldcg(a.mx32 + k) : 0u;
+  const int it0 = a.iters[k];
+  double lr = a.lr[k];
+  const double b1p = a.b1t[k], b2p = a.b2t[k];
+  const bool plateau = a.sched == SCHED_PLATEAU;
+  double best = plateau ? a.best[k] : 0.0;
+  int bad = plateau ? a.bad[k] : 0, cool = plateau ? a.cool[k] : 0;
+  if (!act) return;
+  const double L = (double)lsum * a.inv_m;
+  a.loss_acc[k] = R(0);
+  if (a.mx32) {
+    a.mx32[k] = 0u;
+    a.cand[k] = (a.gate <= 0.0 || (double)__uint_as_float(mxu) <= a.gate) ? 1 : 0;
+  }
+  if (!isfinite(L)) {
+    a.status[k] = CASE_DIVERGED;
+    a.active[k] = 0;
+    atomicSub(a.n_active, 1);
+    return;
+  }
+  const int it = it0 + 1;  // number of the step about to be taken
+  a.iters[k] = it;
+  const double b1t = b1p * a.beta1, b2t = b2p * a.beta2;
+  a.b1t[k] = b1t;
+  a.b2t[k] = b2t;
+  // (FP64 division and square root are slow on this GPU; FP32 runs only use
+  // the step terms in FP32)
+  if (a.opt == OPT_ADAM) {
+    a.step_size[k] = (R)lr / (R(1) - (R)b1t);
+    a.isbc2[k] = R(1) / sqrtT(R(1) - (R)b2t);
+  } else {
+    a.step_size[k] = (R)lr;
+    a.isbc2[k] = R(1);
+  }
+  if (plateau) {
+    if (L < best * (1.0 - a.threshold)) { best = L; bad = 0; }
+    else bad += 1;
+    if (cool > 0) { cool -= 1; bad = 0; }
+    if (bad > a.patience) {
+      const double nl = fmax(lr * a.factor, a.min_lr);
+      if (lr - nl > 1e-8) lr = nl;
+      cool = a.cooldown;
+      bad = 0;
+    }
+    a.best[k] = best;
+    a.bad[k] = bad;
+    a.cool[k] = cool;
+  } else if (a.sched == SCHED_STEP) {
+    double gk = 1.0;  // gamma^(it / step_every) by repeated squaring (no pow: FP64 is slow here)
+    double base = a.gamma;
+    for (int e = it / a.step_every; e > 0; e >>= 1) {
+      if (e & 1) gk *= base;
+      base *= base;
+    }
+    lr = a.lr0 * gk;
+  }
+  a.lr[k] = lr;
+}
+
+// After a forward CTA's loss/mismatch atomics: the last CTA of its case tile
+// (every CTA of the tile has counted itself after fencing its atomics) runs
+// sched_case for the tile's cases and resets the tile counter.  Every thread
+// of the CTA must call it.
+template <class R>
+__device__ __forceinline__ void tile_sched(const SchedArgs<R>& a, unsigned int* tile_cnt, int tile) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(tile_cnt + blockIdx.x, 1u);
+    last = (prev == gridDim.y - 1);
+    if (last) tile_cnt[blockIdx.x] = 0u;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+      const int k = blockIdx.x * tile + c;
+      if (k < a.Kp) sched_case(a, k);
+    }
+  }
+}
+
+// n_active drops to 0 inside a forward pass when its scheduler stops the last
+// running case as diverged: read it once per CTA so that all of a CTA's threads
+// take the same branch (the caller's barriers follow).
+__device__ __forceinline__ bool cta_idle(const int32_t* n_active) {
+  __shared__ int idle;
+  if (threadIdx.x == 0) idle = (n_active != nullptr && __ldcg(n_active) == 0);
+  __syncthreads();
+  return idle != 0;
+}
+
 // ---- arguments -------------------------------------------------------------
 template <class R> struct IterArgs {
   using C = typename Prec<R>::C;
@@ -334,6 +465,9 @@ template <class R> struct IterArgs {
   int opt;     // OPT_ADAM / OPT_SGD / OPT_RMSPROP
   R mom, alpha;  // SGD momentum, RMSprop smoothing
   const int32_t* n_active;
+  // the per-case scheduler, run by the forward pass (solve loop only)
+  SchedArgs<R> sc;
+  unsigned int* tile_cnt;  // [case tiles] completion counters, NULL: no scheduler
   // optional outputs (evaluation entry points); NULL in the solve loop
   C* sbuf;   // S_calc
   C* cbuf;   // c = (2/m)(dP + j dQ)
@@ -396,7 +530,10 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
   pdl_wait();
   pdl_release();
-  if (a.n_active && *a.n_active == 0) return;
+  if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
+    if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
+    return;
+  }
   const int k = mp.k;
   // window of V in shared memory (lanes = 32: one 32-case line per row)
   const bool staged = a.wlo && a.lanes == 32 && mp.r0 < mp.r1;
@@ -451,6 +588,7 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
     }
   }
   if (a.loss_acc || a.mx32) case_sum_max_atomic(acc, mx, a.lanes, a.loss_acc, a.mx32, a.Kp);
+  if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
 }
 
 // conj(c_i) S_i rebuilt from w_i = c_i conj(V_i):  c = w V / |V|^2;
@@ -590,7 +728,10 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
   pdl_wait();
   pdl_release();
-  if (a.n_active && *a.n_active == 0) return;
+  if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
+    if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
+    return;
+  }
   const int k = mp.k;
   if (k >= a.Kp || !a.active[k]) return;
   int of = -1, ot = -1;
@@ -732,7 +873,10 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
   ys.stage(a.rp, a.Y, r0, r1, smem);
   pdl_wait();
   pdl_release();
-  if (a.n_active && *a.n_active == 0) return;
+  if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
+    if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, 64);
+    return;
+  }
   const int k0 = 2 * (blockIdx.x * 32 + lane);
   const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
   // this block's window of V (the rows its nonzeros reference), one
@@ -791,6 +935,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
     if (!q.on1) { acc1 = 0.f; mx1 = 0.f; }
   }
   pair_sum_max_atomic(acc0, acc1, mx0, mx1, a.loss_acc, a.mx32, a.Kp);
+  if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, 64);
 }
 
 
@@ -879,90 +1024,6 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     }
     const float2 n0 = q.on0 ? volt(th0, vm0) : v0, n1 = q.on1 ? volt(th1, vm1) : v1;
     ((float4*)a.V)[e] = make_float4(n0.x, n0.y, n1.x, n1.y);
-  }
-}
-
-// ---- scheduler (one thread per case) ---------------------------------------
-template <class R> struct SchedArgs {
-  int Kp;
-  int32_t* active;
-  int32_t* iters;
-  int32_t* status;
-  R* loss_acc;
-  unsigned int* mx32;  // FP32 max mismatch of the last forward pass (or NULL)
-  int32_t* cand;       // 1: the next FP64 test examines the case
-  double gate;         // FP32 max mismatch below which the FP64 test runs (<= 0: always)
-  double* lr;
-  double* best;
-  int32_t* bad;
-  int32_t* cool;
-  double* b1t;         // beta1^t, beta2^t of the next Adam step (running products)
-  double* b2t;
-  R* step_size;
-  R* isbc2;
-  int32_t* n_active;
-  double inv_m, beta1, beta2, factor, threshold, min_lr, gamma, lr0;
-  int sched, patience, cooldown, step_every, opt;
-};
-
-template <class R>
-__global__ void k_sched(SchedArgs<R> a) {
-  pdl_wait();
-  pdl_release();
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.Kp || !a.active[k]) return;
-  const double L = (double)a.loss_acc[k] * a.inv_m;  // MSE of the iterate the step came from
-  a.loss_acc[k] = R(0);
-  if (a.mx32) {
-    const float mxf = __uint_as_float(a.mx32[k]);
-    a.mx32[k] = 0u;
-    a.cand[k] = (a.gate <= 0.0 || (double)mxf <= a.gate) ? 1 : 0;
-  }
-  const int it = a.iters[k] + 1;
-  a.iters[k] = it;
-  if (!isfinite(L)) {
-    a.status[k] = CASE_DIVERGED;
-    a.active[k] = 0;
-    atomicSub(a.n_active, 1);
-    return;
-  }
-  double lr = a.lr[k];
-  if (a.sched == SCHED_PLATEAU) {
-    double best = a.best[k];
-    int bad = a.bad[k], cool = a.cool[k];
-    if (L < best * (1.0 - a.threshold)) { best = L; bad = 0; }
-    else bad += 1;
-    if (cool > 0) { cool -= 1; bad = 0; }
-    if (bad > a.patience) {
-      const double nl = fmax(lr * a.factor, a.min_lr);
-      if (lr - nl > 1e-8) lr = nl;
-      cool = a.cooldown;
-      bad = 0;
-    }
-    a.best[k] = best;
-    a.bad[k] = bad;
-    a.cool[k] = cool;
-  } else if (a.sched == SCHED_STEP) {
-    double gk = 1.0;  // gamma^(it / step_every) by repeated squaring (no pow: FP64 is slow here)
-    double base = a.gamma;
-    for (int e = it / a.step_every; e > 0; e >>= 1) {
-      if (e & 1) gk *= base;
-      base *= base;
-    }
-    lr = a.lr0 * gk;
-  }
-  a.lr[k] = lr;
-  const double b1t = a.b1t[k] * a.beta1, b2t = a.b2t[k] * a.beta2;  // beta^(it+1)
-  a.b1t[k] = b1t;
-  a.b2t[k] = b2t;
-  // bias-corrected step terms in working precision (FP64 division and square
-  // root are slow on this GPU; FP32 runs only consume them in FP32)
-  if (a.opt == OPT_ADAM) {
-    a.step_size[k] = (R)lr / (R(1) - (R)b1t);
-    a.isbc2[k] = R(1) / sqrtT(R(1) - (R)b2t);
-  } else {
-    a.step_size[k] = (R)lr;
-    a.isbc2[k] = R(1);
   }
 }
 
@@ -1253,8 +1314,8 @@ __global__ void k_case_init(CaseInitArgs<R> a) {
   a.loss_acc[k] = R(0);
   a.step_size[k] = (R)(a.opt == OPT_ADAM ? a.lr0 / (1.0 - a.beta1) : a.lr0);
   a.isbc2[k] = (R)(a.opt == OPT_ADAM ? 1.0 / sqrt(1.0 - a.beta2) : 1.0);
-  a.b1t[k] = a.beta1;  // beta^1: bias correction of the first step
-  a.b2t[k] = a.beta2;
+  a.b1t[k] = 1.0;  // beta^0: the forward pass multiplies in beta before each step
+  a.b2t[k] = 1.0;
   a.cand[k] = 1;
   a.mx32[k] = 0u;
   a.maxmis[k] = 0ULL;

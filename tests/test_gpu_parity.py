@@ -371,8 +371,22 @@ def test_diverged_case_is_flagged():
     ws = dpf.dpf_workspace_create(y, K)
     r = _solve(y, ws, K, dpf.SolveOpts(precision=dpf.FP64, max_iter=30, check_every=1), p_spec=_t(P), q_spec=_t(Q))
     assert r["status"][1] == dpf.CASE_DIVERGED
+    ref = oracle.dpf_solve(grid_ybus(g), P[1], Q[1], g.bus_type, g.vm_set,
+                           oracle.DPFOptions(max_iter=30), va_slack=g.va_slack)
+    assert ref["status"] == oracle.dpf.DIVERGED and r["iters"][1] == ref["iters"]
     assert r["status"][0] == dpf.CASE_MAX_ITER and r["status"][2] == dpf.CASE_MAX_ITER
     assert r["iters"][0] == 30 and np.isfinite(r["va"][0]).all()
+    # the same workspace, reused after a case diverged (and every case of a
+    # batch stopped), solves a clean batch exactly as a fresh one does
+    r_all = _solve(y, ws, K, dpf.SolveOpts(max_iter=40, check_every=5), p_spec=_t(np.full_like(P, np.nan)),
+                   q_spec=_t(Q))
+    assert (r_all["status"] == dpf.CASE_DIVERGED).all()
+    opts = dpf.SolveOpts(max_iter=60, check_every=5)
+    r1 = _solve(y, ws, K, opts, p_spec=_t(np.tile(g.p_spec, (K, 1))), q_spec=_t(Q))
+    ws2 = dpf.dpf_workspace_create(y, K)
+    r2 = _solve(y, ws2, K, opts, p_spec=_t(np.tile(g.p_spec, (K, 1))), q_spec=_t(Q))
+    for key in ("va", "vm", "iters", "status"):
+        assert np.array_equal(r1[key], r2[key]), key
 
 
 def test_autograd_function():
