@@ -243,7 +243,7 @@ def run_ours(args):
                          max_iter=args.warmup + args.steps + args.profile_steps + 8 * CHECK_EVERY,
                          lanes=args.lanes or None, warps=args.warps or None, row_blocks=args.row_blocks or None,
                          pdl=0 if args.no_pdl else None)
-    if not (args or args.warps or args.row_blocks or args.no_autotune):
+    if not (args.lanes or args.warps or args.row_blocks or args.no_autotune):
         with torch.cuda.stream(stream):
             opts = dpf.dpf_autotune(y, ws, opts, iters=50, stream=stream, n_case=K, outage=out_dev)
     res = dict(va=torch.empty((K, N), dtype=torch.float64, device=dev),
@@ -340,9 +340,9 @@ def run_ours(args):
                 "l2": "per-iteration working set ~0.5 GB >> 129 MB L2 (no flush needed)",
                 "parallelism": f"replicas x{world} (independent cases, no data-path collective)",
                 "launch_shape": {"lanes": opts.lanes, "warps": opts.warps, "row_blocks": opts.row_blocks,
-                                 "pair_cases": opts.pair_cases, "stage_v": opts.stage_v, "chosen_by": "dpf_autotune"
-                                 if not (args.lanes or args.warps or args.row_blocks or args.no_autotune)
-                                 else "command line"},
+                                 "pair_cases": opts.pair_cases, "stage_v": opts.stage_v, "chosen_by": "command line"
+                                 if (args.lanes or args.warps or args.row_blocks)
+                                 else "library default" if args.no_autotune else "dpf_autotune"},
             },
             "case_iterations_per_s": case_iters / (t_max / 1e3),
             "converged_frac": float((st == 0).mean()),

@@ -104,7 +104,7 @@ int pow2ceil(int v) {
 // Y_bus upload
 // ---------------------------------------------------------------------------
 static void free_device(DeviceYbus& d) {
-  dfree(d.ent32); dfree(d.row_ptr); dfree(d.col); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
+  dfree(d.ent32); dfree(d.row_ptr); dfree(d.prow_ptr); dfree(d.ppos); dfree(d.col); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
   dfree(d.type); dfree(d.p64); dfree(d.q64); dfree(d.vmset); dfree(d.p32); dfree(d.q32);
   dfree(d.perm); dfree(d.iperm); dfree(d.br_f); dfree(d.br_t); dfree(d.br_r); dfree(d.br_x);
   dfree(d.br_bch); dfree(d.br_tap); dfree(d.bridge);
@@ -151,6 +151,8 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
   do {
     if ((rc = upload(&d.ent32, ent, s))) break;
     if ((rc = upload(&d.row_ptr, y->irow_ptr, s))) break;
+    if ((rc = upload(&d.prow_ptr, y->iprow_ptr, s))) break;
+    if ((rc = upload(&d.ppos, y->ippos, s))) break;
     if ((rc = upload(&d.col, y->icol, s))) break;
     if ((rc = upload(&d.val64, v64, s))) break;
     if ((rc = upload(&d.ebr, y->iebr, s))) break;
@@ -438,7 +440,8 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.ysmem = w->ysmem;
   // FP32 iterations gate the FP64 test with the forward pass's FP32 mismatch
   const bool gated = (sizeof(R) == 4) && w->opts.gate > 0.0;
-  a.rp = d.row_ptr;
+  a.prp = d.prow_ptr;
+  a.ppos = d.ppos;
   const int4* ent = w->use_local_y ? w->ent_loc : d.ent32;
   const double2* v64 = w->use_local_y ? w->val_loc : d.val64;
   if constexpr (sizeof(R) == 4) {
@@ -569,6 +572,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   P.grid = P.cgrid;
   P.pgrid = dim3(w->Kp / 64, w->gy);
   P.itb = P.it;
+  P.itb.tile_cnt = nullptr;  // the scheduler runs in the forward pass only
   P.itb.rpb = w->rpb_b;
   P.itb.wlo = nullptr;
   P.itb.whi = nullptr;
@@ -716,6 +720,7 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   gy = std::max(1, std::min(std::min(gy, gy_max), 65535));
   const int n = w->y->n;
   const std::vector<int32_t>& rp = w->y->irow_ptr;
+  const std::vector<int32_t>& prp = w->y->iprow_ptr;  // padded rows: the staged entries
   const std::vector<int32_t>& col = w->y->icol;
   const bool fp64 = (o ? o->precision : w->precision) == DPF_FP64;
   // bytes of one staged window row: the case tile's line of V
@@ -727,7 +732,7 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
     int mx = 0, wmax = 0;
     for (int r0 = 0; r0 < n; r0 += rpb) {
       const int r1 = std::min(n, r0 + rpb);
-      mx = std::max(mx, rp[r1] - rp[r0]);
+      mx = std::max(mx, prp[r1] - prp[r0]);
       int lo = r0, hi = r1 - 1;
       for (int q = rp[r0]; q < rp[r1]; ++q) { lo = std::min(lo, col[q]); hi = std::max(hi, col[q]); }
       wmax = std::max(wmax, hi - lo + 1);
@@ -749,7 +754,7 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   // of resident CTAs (a partial last wave leaves SMs idle at the tail).
   auto seg_nnz = [&](int rpb_) {
     int mx = 0;
-    for (int r0 = 0; r0 < n; r0 += rpb_) mx = std::max(mx, rp[std::min(n, r0 + rpb_)] - rp[r0]);
+    for (int r0 = 0; r0 < n; r0 += rpb_) mx = std::max(mx, prp[std::min(n, r0 + rpb_)] - prp[r0]);
     return mx;
   };
   auto aligned = [&](int gx_k, int slots, int gy0) {
@@ -1015,6 +1020,9 @@ static int common_checks(const dpf_ybus* y, dpf_workspace* w, int K) {
   if (w->y != y) return fail(DPF_E_INVALID, "workspace was created for another Y_bus");
   if (!y->dev.ready) return fail(DPF_E_STATE, "Y_bus is not on the device");
   if (K < 1) return fail(DPF_E_INVALID, "n_case must be >= 1");
+  // the staged SpMV addresses a gathered element by a 32-bit offset bus * Kp
+  if ((uint64_t)y->n * (uint64_t)(K + 64) >= (1ull << 32))
+    return fail(DPF_E_UNSUPPORTED, "n_bus * n_case must stay below 2^32 (split the batch)");
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != y->dev.device) return fail(DPF_E_STATE, "current device %d differs from the Y_bus device %d", dev, y->dev.device);

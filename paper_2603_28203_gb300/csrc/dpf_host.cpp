@@ -293,6 +293,19 @@ extern "C" int dpf_build_ybus_host(const dpf_grid* g, dpf_ybus** out) {
       if (row[k].first == ni) y->idpos[ni] = q;
     }
   }
+  // Padded rows for the shared-memory SpMV: each row's entries rounded up to
+  // a multiple of 4 by zero-weight entries on the row's own bus, so the
+  // device loop runs whole groups of four with no per-entry predicate.
+  // ippos maps a padded slot to its CSR position, or holds -(row + 1).
+  y->iprow_ptr.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i)
+    y->iprow_ptr[i + 1] = y->iprow_ptr[i] + ((y->irow_ptr[i + 1] - y->irow_ptr[i] + 3) & ~3);
+  y->ippos.assign(y->iprow_ptr[n], 0);
+  for (int i = 0; i < n; ++i) {
+    int q = y->iprow_ptr[i];
+    for (int p = y->irow_ptr[i]; p < y->irow_ptr[i + 1]; ++p) y->ippos[q++] = p;
+    for (; q < y->iprow_ptr[i + 1]; ++q) y->ippos[q] = -(i + 1);
+  }
   *out = y;
   return DPF_OK;
 }

@@ -21,6 +21,8 @@ struct DeviceYbus {
   int device = -1;
   int4* ent32 = nullptr;        // [nnz] {col, re bits, im bits, 0}: one 16-byte load per nonzero
   int32_t* row_ptr = nullptr;   // [n+1]
+  int32_t* prow_ptr = nullptr;  // [n+1] rows padded to multiples of 4 entries
+  int32_t* ppos = nullptr;      // [prow_ptr[n]] CSR position of a padded slot, -(row+1) for a pad
   int32_t* col = nullptr;       // [nnz]
   double2* val64 = nullptr;     // [nnz]
   int32_t* ebr = nullptr;       // [nnz] branch of an off-diagonal entry, -1 on the diagonal
@@ -60,6 +62,7 @@ struct dpf_ybus {
   // internal order: perm[new] = old, iperm[old] = new; CSR in the new order
   std::vector<int32_t> perm, iperm;
   std::vector<int32_t> irow_ptr, icol, idpos, iebr;
+  std::vector<int32_t> iprow_ptr, ippos;     // padded rows (see DeviceYbus)
   std::vector<double> ival_re, ival_im;
   dpf::DeviceYbus dev;
 };

@@ -53,6 +53,11 @@ __device__ __forceinline__ float sqrt_step(float v) { return v > 0.f ? v * rsqrt
 __device__ __forceinline__ double sqrt_step(double v) { return sqrt(v); }
 __device__ __forceinline__ float div_step(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double div_step(double a, double b) { return a / b; }
+// a*b + c in an optimiser's moment update: fused in FP32; in FP64 a rounded
+// product and a rounded sum, as the textbook update the FP64 path is checked
+// against writes it.
+__device__ __forceinline__ float madd_step(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double madd_step(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
 
 // acc += y * v (complex)
 template <class C> __device__ __forceinline__ void cfma(C& acc, const C y, const C v) {
@@ -63,6 +68,22 @@ template <class C> __device__ __forceinline__ void cfma(C& acc, const C y, const
 template <class C> __device__ __forceinline__ void cfms(C& acc, const C y, const C v) {
   acc.x = fmaT(-y.x, v.x, fmaT(y.y, v.y, acc.x));
   acc.y = fmaT(-y.x, v.y, fmaT(-y.y, v.x, acc.y));
+}
+
+// The per-element arithmetic of the forward epilogue and of the adjoint is
+// written with explicit FMAs (no a*b + c left for the compiler to contract
+// at its choice), so every kernel variant rounds it identically.
+//   S = V conj(I):  P = Re V Re I + Im V Im I,  Q = Im V Re I - Re V Im I
+template <class C> __device__ __forceinline__ C power_of(C v, C I) {
+  return mkc(fmaT(v.x, I.x, v.y * I.y), fmaT(v.y, I.x, -(v.x * I.y)));
+}
+//   w = c conj(V) for c = ca + j cb
+template <class C, class R> __device__ __forceinline__ C w_of(R ca, R cb, C v) {
+  return mkc(fmaT(ca, v.x, cb * v.y), fmaT(cb, v.x, -(ca * v.y)));
+}
+//   h = conj(c) S + V z
+template <class C> __device__ __forceinline__ C adj_h(C g0, C v, C z) {
+  return mkc(g0.x + fmaT(v.x, z.x, -(v.y * z.y)), g0.y + fmaT(v.x, z.y, v.y * z.x));
 }
 
 // ---- programmatic dependent launch -------------------------------------------
@@ -210,86 +231,119 @@ __device__ __forceinline__ BMap block_map(int lanes, int N, int rpb) {
 }
 
 // Bytes of dynamic shared memory for a row block of `rows` rows and `nnz`
-// nonzeros (same formula on host and device).
-__host__ __device__ __forceinline__ int ysmem_bytes(int rows, int nnz, bool fp64) {
+// padded entries, with the rows' bus types at the end (same formula on host
+// and device).
+__host__ __device__ __forceinline__ int ysmem_entries_end(int rows, int nnz, bool fp64) {
   const int rp = ((rows + 1) * 4 + 15) & ~15;
   return fp64 ? rp + ((nnz * 4 + 15) & ~15) + nnz * 16 : rp + nnz * 16;
 }
+__host__ __device__ __forceinline__ int ysmem_bytes(int rows, int nnz, bool fp64) {
+  return ysmem_entries_end(rows, nnz, fp64) + ((rows + 15) & ~15);
+}
+
+// The row block's Y_bus rows and bus types in shared memory (a bus type
+// decides which operands a row loads: read from here it costs no global
+// round trip ahead of them).  Rows are padded to groups of four
+// entries (a pad has weight 0 and points at the row's own bus, whose value
+// the row's diagonal term reads anyway).  Each entry keeps its column as the
+// element offset col * stride of the operand it gathers (stride: the case
+// stride of the operand array, or of a shared-memory window), so a gather is
+// one address computation from a per-thread base.  Offsets are 32-bit: the
+// host keeps N * Kp below 2^32.
+__device__ __forceinline__ int ysmem_pad_row(int pos) { return -pos - 1; }
 
 template <class R> struct YSmem;
 template <> struct YSmem<float> {
   const int* rp;
-  const int4* ent;
-  __device__ __forceinline__ void stage(const int32_t* __restrict__ grp, const YView<float>& Y, int r0, int r1,
-                                        unsigned char* sm) {
+  const int4* ent;  // {offset, re bits, im bits, 0}
+  const uint8_t* ty;
+  __device__ __forceinline__ void stage(const int32_t* __restrict__ prp, const int32_t* __restrict__ ppos,
+                                        const YView<float>& Y, const uint8_t* __restrict__ type, int r0, int r1,
+                                        unsigned stride, unsigned char* sm) {
     const int nrow = max(0, r1 - r0);
     int* srp = (int*)sm;
     int4* sent = (int4*)(sm + (((nrow + 1) * 4 + 15) & ~15));
-    const int base = nrow ? __ldg(grp + r0) : 0;
-    const int cnt = nrow ? __ldg(grp + r1) - base : 0;
-    for (int t = threadIdx.x; t <= nrow; t += blockDim.x) srp[t] = (nrow ? __ldg(grp + r0 + t) : 0) - base;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) sent[t] = __ldg(Y.ent + base + t);
+    const int base = nrow ? __ldg(prp + r0) : 0;
+    const int cnt = nrow ? __ldg(prp + r1) - base : 0;
+    for (int t = threadIdx.x; t <= nrow; t += blockDim.x) srp[t] = (nrow ? __ldg(prp + r0 + t) : 0) - base;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int pos = __ldg(ppos + base + t);
+      int4 e;
+      if (pos >= 0) {
+        e = __ldg(Y.ent + pos);
+        e.x = (int)((unsigned)e.x * stride);
+      } else {
+        e = make_int4((int)((unsigned)ysmem_pad_row(pos) * stride), 0, 0, 0);
+      }
+      sent[t] = e;
+    }
+    uint8_t* sty = sm + ysmem_entries_end(nrow, cnt, false);
+    for (int t = threadIdx.x; t < nrow; t += blockDim.x) sty[t] = __ldg(type + r0 + t);
     __syncthreads();
     rp = srp - r0;  // index by global row
     ent = sent;
+    ty = sty - r0;
   }
-  __device__ __forceinline__ void get(int p, int& j, float2& y) const {
+  __device__ __forceinline__ void get(int p, unsigned& o, float2& y) const {
     const int4 e = ent[p];
-    j = e.x;
+    o = (unsigned)e.x;
     y = make_float2(__int_as_float(e.y), __int_as_float(e.z));
   }
 };
 template <> struct YSmem<double> {
   const int* rp;
-  const int* col;
+  const unsigned* off;
   const double2* val;
-  __device__ __forceinline__ void stage(const int32_t* __restrict__ grp, const YView<double>& Y, int r0, int r1,
-                                        unsigned char* sm) {
+  const uint8_t* ty;
+  __device__ __forceinline__ void stage(const int32_t* __restrict__ prp, const int32_t* __restrict__ ppos,
+                                        const YView<double>& Y, const uint8_t* __restrict__ type, int r0, int r1,
+                                        unsigned stride, unsigned char* sm) {
     const int nrow = max(0, r1 - r0);
     int* srp = (int*)sm;
-    const int base = nrow ? __ldg(grp + r0) : 0;
-    const int cnt = nrow ? __ldg(grp + r1) - base : 0;
-    int* scol = (int*)(sm + (((nrow + 1) * 4 + 15) & ~15));
-    double2* sval = (double2*)((unsigned char*)scol + ((cnt * 4 + 15) & ~15));
-    for (int t = threadIdx.x; t <= nrow; t += blockDim.x) srp[t] = (nrow ? __ldg(grp + r0 + t) : 0) - base;
+    const int base = nrow ? __ldg(prp + r0) : 0;
+    const int cnt = nrow ? __ldg(prp + r1) - base : 0;
+    unsigned* soff = (unsigned*)(sm + (((nrow + 1) * 4 + 15) & ~15));
+    double2* sval = (double2*)((unsigned char*)soff + ((cnt * 4 + 15) & ~15));
+    for (int t = threadIdx.x; t <= nrow; t += blockDim.x) srp[t] = (nrow ? __ldg(prp + r0 + t) : 0) - base;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      scol[t] = __ldg(Y.col + base + t);
-      sval[t] = __ldg(Y.val + base + t);
+      const int pos = __ldg(ppos + base + t);
+      if (pos >= 0) {
+        soff[t] = (unsigned)__ldg(Y.col + pos) * stride;
+        sval[t] = __ldg(Y.val + pos);
+      } else {
+        soff[t] = (unsigned)ysmem_pad_row(pos) * stride;
+        sval[t] = make_double2(0.0, 0.0);
+      }
     }
+    uint8_t* sty = sm + ysmem_entries_end(nrow, cnt, true);
+    for (int t = threadIdx.x; t < nrow; t += blockDim.x) sty[t] = __ldg(type + r0 + t);
     __syncthreads();
     rp = srp - r0;
-    col = scol;
+    off = soff;
     val = sval;
+    ty = sty - r0;
   }
-  __device__ __forceinline__ void get(int p, int& j, double2& y) const {
-    j = col[p];
+  __device__ __forceinline__ void get(int p, unsigned& o, double2& y) const {
+    o = off[p];
     y = val[p];
   }
 };
 
-// acc_row = sum_p Y[p] * X[col(p)*Kp + k] over the row's nonzeros [p0, p1).
-// Four nonzeros per step with predicated loads, so up to four independent
-// gathers are in flight per thread.
+// acc_row = sum_p Y[p] * X[offset(p)] over the row's padded entries [p0, p1)
+// (X already points at this thread's case).  Four entries per step, so four
+// independent gathers are in flight per thread; a pad adds an exact zero.
 template <class R, class YS>
 __device__ __forceinline__ typename Prec<R>::C row_spmv(const YS& ys, int p0, int p1,
-                                                        const typename Prec<R>::C* __restrict__ X, size_t Kp,
-                                                        int k) {
+                                                        const typename Prec<R>::C* __restrict__ X) {
   using C = typename Prec<R>::C;
   C a0 = mkc(R(0), R(0)), a1 = a0;
   for (int p = p0; p < p1; p += 4) {
-    int j[4];
+    unsigned o[4];
     C y[4], x[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (p + u < p1) {
-        ys.get(p + u, j[u], y[u]);
-      } else {
-        j[u] = -1;
-        y[u] = mkc(R(0), R(0));
-      }
-    }
+    for (int u = 0; u < 4; ++u) ys.get(p + u, o[u], y[u]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = (j[u] >= 0) ? X[(size_t)j[u] * Kp + k] : mkc(R(0), R(0));
+    for (int u = 0; u < 4; ++u) x[u] = X[o[u]];
     cfma(a0, y[0], x[0]);
     cfma(a1, y[1], x[1]);
     cfma(a0, y[2], x[2]);
@@ -432,7 +486,8 @@ template <class R> struct IterArgs {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
   int N, Kp, lanes, rpb;
-  const int32_t* __restrict__ rp;
+  const int32_t* __restrict__ prp;   // padded row pointers (rows of 4k entries)
+  const int32_t* __restrict__ ppos;  // padded slot -> CSR position, -(row+1) for a pad
   YView<R> Y;
   const int32_t* wlo;  // per row block: first and last row its nonzeros reference
   const int32_t* whi;  //   (NULL: neighbour gathers read global memory)
@@ -526,17 +581,30 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   extern __shared__ __align__(16) unsigned char smem[];
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
+  // window of V in shared memory (lanes = 32: one 32-case line per row)
+  const bool staged = a.wlo && a.lanes == 32 && mp.r0 < mp.r1;
   YSmem<R> ys;
-  ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
+  ys.stage(a.prp, a.ppos, a.Y, a.type, mp.r0, mp.r1, staged ? 32u : (unsigned)a.Kp, smem);
   pdl_wait();
   pdl_release();
+  // the case's data in one round of independent loads, in flight during the
+  // idle test (the outage arrays span Kp; an unused entry never matches a row)
+  const int k = mp.k;
+  const bool inb = k < a.Kp;
+  const int act = inb ? a.active[k] : 0;
+  int of = -1, ot = -1;
+  C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
+  if (inb && a.has_outage) {
+    of = a.of[k];
+    ot = a.ot[k];
+    yff = a.yff[k];
+    yft = a.yft[k];
+    ytt = a.ytt[k];
+  }
   if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
     if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
     return;
   }
-  const int k = mp.k;
-  // window of V in shared memory (lanes = 32: one 32-case line per row)
-  const bool staged = a.wlo && a.lanes == 32 && mp.r0 < mp.r1;
   const int wlo = staged ? a.wlo[blockIdx.y] : 0;
   C* vt = (C*)(smem + a.ysmem);
   if (staged) {
@@ -545,27 +613,19 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
                  a.whi[blockIdx.y], per_row, (float4*)vt);
   }
   const C* __restrict__ Vsh = vt - (size_t)wlo * 32 + (k & 31);
-  const bool on = (k < a.Kp) && a.active[k];
+  const bool on = act != 0;
   R acc = 0;
   float mx = 0.f;
   if (on) {
-    int of = -1, ot = -1;
-    C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
-    if (a.has_outage) {
-      of = a.of[k];
-      ot = a.ot[k];
-      if (of >= 0) { yff = a.yff[k]; yft = a.yft[k]; ytt = a.ytt[k]; }
-    }
     const size_t Kp = (size_t)a.Kp;
     const C* __restrict__ V = a.V;
     for (int i = mp.i0; i < mp.r1; i += mp.istride) {
       const size_t e = (size_t)i * Kp + k;
-      const int ty = __ldg(a.type + i);
+      const int ty = ys.ty[i];
       const size_t si = a.spec_per_case ? e : (size_t)i;
       const C vi = staged ? Vsh[(size_t)i * 32] : V[e];
       const R ps = a.pspec[si], qs = a.qspec[si];
-      C I = staged ? row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], Vsh, 32, 0)
-                   : row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], V, Kp, k);
+      C I = staged ? row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], Vsh) : row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], V + k);
       if (i == of) {
         cfms(I, yff, vi);
         cfms(I, yft, V[(size_t)ot * Kp + k]);
@@ -573,16 +633,16 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
         cfms(I, yft, V[(size_t)of * Kp + k]);
         cfms(I, ytt, vi);
       }
-      const R P = vi.x * I.x + vi.y * I.y;
-      const R Q = vi.y * I.x - vi.x * I.y;
+      const C S = power_of(vi, I);
+      const R P = S.x, Q = S.y;
       const R dP = (ty != BUS_SLACK) ? P - ps : R(0);
       const R dQ = (ty == BUS_PQ) ? Q - qs : R(0);
       const R ca = a.inv_m2 * dP, cb = a.inv_m2 * dQ;
-      a.W[e] = mkc(ca * vi.x + cb * vi.y, cb * vi.x - ca * vi.y);
+      a.W[e] = w_of(ca, cb, vi);
       if (ty == BUS_PV) a.qpv[e] = Q;
       if (a.sbuf) a.sbuf[e] = mkc(P, Q);
       if (a.cbuf) a.cbuf[e] = mkc(ca, cb);
-      acc += dP * dP + dQ * dQ;
+      acc = fmaT(dP, dP, fmaT(dQ, dQ, acc));
       const float am = fmaxf(fabsf((float)dP), fabsf((float)dQ));
       mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);  // NaN -> +inf
     }
@@ -596,12 +656,12 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
 // forward pass's Q_calc at pv buses (c is real there).
 template <class C, class R>
 __device__ __forceinline__ C conj_c_s(C w, C v, int ty, R ps, R qs, R qpv, R m_half) {
-  const R inv = div_step(R(1), v.x * v.x + v.y * v.y);
-  const R ca = (w.x * v.x - w.y * v.y) * inv;
-  const R cb = (ty == BUS_PQ) ? (w.x * v.y + w.y * v.x) * inv : R(0);
-  const R P = ps + m_half * ca;
-  const R Q = (ty == BUS_PQ) ? qs + m_half * cb : qpv;
-  return mkc(ca * P + cb * Q, ca * Q - cb * P);
+  const R inv = div_step(R(1), fmaT(v.x, v.x, v.y * v.y));
+  const R ca = fmaT(w.x, v.x, -(w.y * v.y)) * inv;
+  const R cb = (ty == BUS_PQ) ? fmaT(w.x, v.y, w.y * v.x) * inv : R(0);
+  const R P = fmaT(m_half, ca, ps);
+  const R Q = (ty == BUS_PQ) ? fmaT(m_half, cb, qs) : qpv;
+  return mkc(fmaT(ca, P, cb * Q), fmaT(ca, Q, -(cb * P)));
 }
 
 // ---- adjoint SpMV + gradient + Adam ----------------------------------------
@@ -612,16 +672,16 @@ template <class R, class M>
 __device__ __forceinline__ M opt_update(int opt, M x, R g, R& m, R& v, R b1, R b2, R step, R isb, R eps, R mom,
                                         R alpha) {
   if (opt == OPT_SGD) {
-    m = (mom != R(0)) ? mom * m + g : g;
+    m = (mom != R(0)) ? madd_step(mom, m, g) : g;
     return msub(x, step * m);
   }
   if (opt == OPT_RMSPROP) {
-    v = alpha * v + (R(1) - alpha) * g * g;
+    v = madd_step(alpha, v, ((R(1) - alpha) * g) * g);
     return msub(x, div_step(step * g, sqrt_step(v) + eps));
   }
-  m = b1 * m + (R(1) - b1) * g;
-  v = b2 * v + (R(1) - b2) * g * g;
-  return msub(x, div_step(step * m, sqrt_step(v) * isb + eps));
+  m = madd_step(b1, m, (R(1) - b1) * g);
+  v = madd_step(b2, v, ((R(1) - b2) * g) * g);
+  return msub(x, div_step(step * m, madd_step(sqrt_step(v), isb, eps)));
 }
 
 #ifndef DPF_ADJ_ROWS
@@ -640,14 +700,14 @@ template <class R> struct AdjRow {
   M th, vm;
 };
 
-template <class R>
-__device__ __forceinline__ void adj_load(const IterArgs<R>& a, AdjRow<R>& r, int i, int r1, int k, size_t Kp,
-                                         bool grad_only) {
+template <class R, class YS>
+__device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, AdjRow<R>& r, int i, int r1, int k,
+                                         size_t Kp, bool grad_only) {
   r.live = false;
   if (i >= r1) return;
   r.i = i;
   r.e = (size_t)i * Kp + k;
-  r.ty = __ldg(a.type + i);
+  r.ty = ys.ty[i];
   if (r.ty == BUS_SLACK) {
     if (grad_only) { a.gva[r.e] = R(0); a.gvm[r.e] = R(0); }
     return;
@@ -675,7 +735,7 @@ __device__ __forceinline__ void adj_gather(const IterArgs<R>& a, const YS& ys, A
                                            int of, int ot, typename Prec<R>::C yff, typename Prec<R>::C yft,
                                            typename Prec<R>::C ytt) {
   const int i = r.i;
-  r.z = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], a.W, Kp, k);
+  r.z = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], a.W + k);
   if (i == of) {
     cfms(r.z, yff, r.wi);
     cfms(r.z, yft, a.W[(size_t)ot * Kp + k]);
@@ -692,8 +752,8 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
   const size_t e = r.e;
   const C vi = r.vi, z = r.z;
   const C g0 = conj_c_s(r.wi, vi, r.ty, r.ps, r.qs, r.qp, a.m_half);
-  const R hr = g0.x + (vi.x * z.x - vi.y * z.y);
-  const R hi = g0.y + (vi.x * z.y + vi.y * z.x);
+  const C h = adj_h(g0, vi, z);
+  const R hr = h.x, hi = h.y;
   const R g_th = -hi;
   const R g_vm = (r.ty == BUS_PQ) ? div_step(hr, mwork(r.vm)) : R(0);
   if (grad_only) {
@@ -716,7 +776,7 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
 }
 
 #ifndef DPF_ADJ_MINB
-#define DPF_ADJ_MINB 5
+#define DPF_ADJ_MINB 4
 #endif
 template <class R>
 __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
@@ -725,25 +785,27 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
   YSmem<R> ys;
-  ys.stage(a.rp, a.Y, mp.r0, mp.r1, smem);
+  ys.stage(a.prp, a.ppos, a.Y, a.type, mp.r0, mp.r1, (unsigned)a.Kp, smem);
   pdl_wait();
   pdl_release();
-  if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
-    if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
-    return;
-  }
+  // the case's data in one round of independent loads, in flight during the
+  // idle test (the outage arrays span Kp; an unused entry never matches a row)
   const int k = mp.k;
-  if (k >= a.Kp || !a.active[k]) return;
+  const bool inb = k < a.Kp;
+  const bool grad_only = (a.gva != nullptr);
+  const int act = inb ? a.active[k] : 0;
   int of = -1, ot = -1;
   C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
-  if (a.has_outage) {
+  if (inb && a.has_outage) {
     of = a.of[k];
     ot = a.ot[k];
-    if (of >= 0) { yff = a.yff[k]; yft = a.yft[k]; ytt = a.ytt[k]; }
+    yff = a.yff[k];
+    yft = a.yft[k];
+    ytt = a.ytt[k];
   }
-  const bool grad_only = (a.gva != nullptr);
   R step = 0, isb = 1;
-  if (!grad_only) { step = a.step_size[k]; isb = a.isbc2[k]; }
+  if (inb && !grad_only) { step = a.step_size[k]; isb = a.isbc2[k]; }
+  if (cta_idle(a.n_active) || !act) return;
   const R b1 = a.beta1, b2 = a.beta2, eps = a.eps;
   const size_t Kp = (size_t)a.Kp;
   const C* __restrict__ W = a.W;
@@ -753,7 +815,7 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   for (int i0 = mp.i0; i0 < mp.r1; i0 += NR * mp.istride) {
     AdjRow<R> rw[NR];
 #pragma unroll
-    for (int u = 0; u < NR; ++u) adj_load(a, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
+    for (int u = 0; u < NR; ++u) adj_load(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
       if (rw[u].live) adj_gather(a, ys, rw[u], k, Kp, of, ot, yff, yft, ytt);
@@ -774,44 +836,45 @@ struct Pair {
   float2 yff0, yft0, ytt0, yff1, yft1, ytt1;
 };
 
+// One round of independent loads: k0 is even and k0 + 1 < Kp (Kp is a
+// multiple of 64 here), so each two-case access is one aligned 8- or 16-byte
+// load.  The outage data is read whether or not a case has an outage (the
+// arrays span Kp; an unused entry never matches a row).
 __device__ __forceinline__ Pair load_pair(const IterArgs<float>& a, int k0) {
   Pair q;
   q.k0 = k0;
-  q.on0 = (k0 < a.Kp) && a.active[k0];
-  q.on1 = (k0 + 1 < a.Kp) && a.active[k0 + 1];
+  const int2 act = *(const int2*)(a.active + k0);
   q.of0 = q.ot0 = q.of1 = q.ot1 = -1;
   q.yff0 = q.yft0 = q.ytt0 = q.yff1 = q.yft1 = q.ytt1 = make_float2(0.f, 0.f);
-  if (a.has_outage && (q.on0 || q.on1)) {
-    q.of0 = a.of[k0];
-    q.ot0 = a.ot[k0];
-    q.of1 = a.of[k0 + 1];
-    q.ot1 = a.ot[k0 + 1];
-    if (q.of0 >= 0) { q.yff0 = a.yff[k0]; q.yft0 = a.yft[k0]; q.ytt0 = a.ytt[k0]; }
-    if (q.of1 >= 0) { q.yff1 = a.yff[k0 + 1]; q.yft1 = a.yft[k0 + 1]; q.ytt1 = a.ytt[k0 + 1]; }
+  if (a.has_outage) {
+    const int2 of = *(const int2*)(a.of + k0), ot = *(const int2*)(a.ot + k0);
+    const float4 ff = *(const float4*)(a.yff + k0), ft = *(const float4*)(a.yft + k0),
+                 tt = *(const float4*)(a.ytt + k0);
+    q.of0 = of.x; q.of1 = of.y;
+    q.ot0 = ot.x; q.ot1 = ot.y;
+    q.yff0 = make_float2(ff.x, ff.y); q.yff1 = make_float2(ff.z, ff.w);
+    q.yft0 = make_float2(ft.x, ft.y); q.yft1 = make_float2(ft.z, ft.w);
+    q.ytt0 = make_float2(tt.x, tt.y); q.ytt1 = make_float2(tt.z, tt.w);
   }
+  q.on0 = act.x != 0;
+  q.on1 = act.y != 0;
   return q;
 }
 
-// sum_p Y[p] X[col(p)] for two adjacent cases (X as float4 pairs).
+// sum_p Y[p] X[offset(p)] for two adjacent cases (X as float4 pairs, already
+// pointing at this thread's pair); padded rows as in row_spmv.
 __device__ __forceinline__ void row_spmv2(const YSmem<float>& ys, int p0, int p1, const float4* __restrict__ X,
-                                          unsigned hKp, unsigned h0, float2& r0, float2& r1) {
+                                          float2& r0, float2& r1) {
   // two accumulators per case, alternating like row_spmv: the same sums
   float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
   for (int p = p0; p < p1; p += 4) {
-    int j[4];
+    unsigned o[4];
     float2 y[4];
     float4 x[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (p + u < p1) {
-        ys.get(p + u, j[u], y[u]);
-      } else {
-        j[u] = -1;
-        y[u] = make_float2(0.f, 0.f);
-      }
-    }
+    for (int u = 0; u < 4; ++u) ys.get(p + u, o[u], y[u]);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = (j[u] >= 0) ? X[(unsigned)j[u] * hKp + h0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < 4; ++u) x[u] = X[o[u]];
     cfma(a0, y[0], make_float2(x[0].x, x[0].y));
     cfma(b0, y[0], make_float2(x[0].z, x[0].w));
     cfma(a1, y[1], make_float2(x[1].x, x[1].y));
@@ -853,14 +916,14 @@ __device__ __forceinline__ void pair_sum_max_atomic(float s0, float s1, float m0
 // Forward epilogue of one case (the same arithmetic as k_fwd).
 __device__ __forceinline__ void fwd_epilogue(float2 vi, float2 I, int ty, float ps, float qs, float inv_m2,
                                              float2& w, float& q, float& acc, float& mx) {
-  const float P = vi.x * I.x + vi.y * I.y;
-  const float Q = vi.y * I.x - vi.x * I.y;
+  const float2 S = power_of(vi, I);
+  const float P = S.x, Q = S.y;
   const float dP = (ty != BUS_SLACK) ? P - ps : 0.f;
   const float dQ = (ty == BUS_PQ) ? Q - qs : 0.f;
   const float ca = inv_m2 * dP, cb = inv_m2 * dQ;
-  w = make_float2(ca * vi.x + cb * vi.y, cb * vi.x - ca * vi.y);
+  w = w_of(ca, cb, vi);
   q = Q;
-  acc += dP * dP + dQ * dQ;
+  acc = fmaf(dP, dP, fmaf(dQ, dQ, acc));
   const float am = fmaxf(fabsf(dP), fabsf(dQ));
   mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);
 }
@@ -869,30 +932,31 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int r0 = blockIdx.y * a.rpb, r1 = min(a.N, r0 + a.rpb);
+  const unsigned hKp = (unsigned)a.Kp >> 1;
   YSmem<float> ys;
-  ys.stage(a.rp, a.Y, r0, r1, smem);
+  ys.stage(a.prp, a.ppos, a.Y, a.type, r0, r1, (a.wlo && r0 < r1) ? 32u : hKp, smem);
   pdl_wait();
   pdl_release();
+  const int k0 = 2 * (blockIdx.x * 32 + lane);
+  const Pair q = load_pair(a, k0);  // in flight during the idle test
   if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
     if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, 64);
     return;
   }
-  const int k0 = 2 * (blockIdx.x * 32 + lane);
-  const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
+  const unsigned h0 = (unsigned)k0 >> 1;
   // this block's window of V (the rows its nonzeros reference), one
   // 512-byte line of 64 cases per row
   const int wlo = (a.wlo && r0 < r1) ? a.wlo[blockIdx.y] : 0;
   float4* vt = (float4*)(smem + a.ysmem);
   if (a.wlo && r0 < r1) stage_window((const float4*)a.V, hKp, blockIdx.x * 32, wlo, a.whi[blockIdx.y], 32, vt);
   const float4* __restrict__ Vs = vt - (size_t)wlo * 32 + lane;  // Vs[j * 32]: row j, this thread's pair
-  const Pair q = load_pair(a, k0);
   float acc0 = 0.f, acc1 = 0.f, mx0 = 0.f, mx1 = 0.f;
   if (q.on0 || q.on1) {
     const float4* __restrict__ V = (const float4*)a.V;
     float4* W = (float4*)a.W;
     for (int i = r0 + warp; i < r1; i += wpb) {
       const unsigned e = (unsigned)i * hKp + h0;  // pair index
-      const int ty = __ldg(a.type + i);
+      const int ty = ys.ty[i];
       const float4 v = a.wlo ? Vs[(size_t)i * 32] : V[e];
       float ps0, ps1, qs0, qs1;
       if (a.spec_per_case) {
@@ -903,8 +967,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
         qs0 = qs1 = a.qspec[i];
       }
       float2 I0, I1;
-      if (a.wlo) row_spmv2(ys, ys.rp[i], ys.rp[i + 1], Vs, 32u, 0u, I0, I1);
-      else row_spmv2(ys, ys.rp[i], ys.rp[i + 1], V, hKp, h0, I0, I1);
+      row_spmv2(ys, ys.rp[i], ys.rp[i + 1], a.wlo ? Vs : V + h0, I0, I1);
       const float2 vi0 = make_float2(v.x, v.y), vi1 = make_float2(v.z, v.w);
       if (i == q.of0) {
         cfms(I0, q.yff0, vi0);
@@ -944,20 +1007,19 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int r0 = blockIdx.y * a.rpb, r1 = min(a.N, r0 + a.rpb);
   YSmem<float> ys;
-  ys.stage(a.rp, a.Y, r0, r1, smem);
+  ys.stage(a.prp, a.ppos, a.Y, a.type, r0, r1, (unsigned)a.Kp >> 1, smem);
   pdl_wait();
   pdl_release();
-  if (a.n_active && *a.n_active == 0) return;
   const int k0 = 2 * (blockIdx.x * 32 + lane);
   const Pair q = load_pair(a, k0);
-  if (!(q.on0 || q.on1)) return;
-  const float st0 = a.step_size[k0], st1 = a.step_size[k0 + 1];
-  const float ib0 = a.isbc2[k0], ib1 = a.isbc2[k0 + 1];
+  const float2 st = *(const float2*)(a.step_size + k0), ib = *(const float2*)(a.isbc2 + k0);
+  if (cta_idle(a.n_active) || !(q.on0 || q.on1)) return;
+  const float st0 = st.x, st1 = st.y, ib0 = ib.x, ib1 = ib.y;
   const float b1 = a.beta1, b2 = a.beta2, eps = a.eps;
   const unsigned hKp = (unsigned)a.Kp >> 1, h0 = (unsigned)k0 >> 1;
   const float4* __restrict__ W = (const float4*)a.W;
   for (int i = r0 + warp; i < r1; i += wpb) {
-    const int ty = __ldg(a.type + i);
+    const int ty = ys.ty[i];
     if (ty == BUS_SLACK) continue;
     const unsigned e = (unsigned)i * hKp + h0;
     // this element's operands first: they do not depend on the gather chain
@@ -981,7 +1043,7 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
       vv = ((const float2*)a.vvm)[e];
     }
     float2 z0, z1;
-    row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W, hKp, h0, z0, z1);
+    row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W + h0, z0, z1);
     if (i == q.of0) {
       cfms(z0, q.yff0, make_float2(wi.x, wi.y));
       const float4 t = W[(unsigned)q.ot0 * hKp + h0];
@@ -1005,8 +1067,8 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     const float2 v0 = make_float2(vv4.x, vv4.y), v1 = make_float2(vv4.z, vv4.w);
     const float2 g0 = conj_c_s(make_float2(wi.x, wi.y), v0, ty, ps0, qs0, qp.x, a.m_half);
     const float2 g1 = conj_c_s(make_float2(wi.z, wi.w), v1, ty, ps1, qs1, qp.y, a.m_half);
-    const float hr0 = g0.x + (v0.x * z0.x - v0.y * z0.y), hi0 = g0.y + (v0.x * z0.y + v0.y * z0.x);
-    const float hr1 = g1.x + (v1.x * z1.x - v1.y * z1.y), hi1 = g1.y + (v1.x * z1.y + v1.y * z1.x);
+    const float2 h0 = adj_h(g0, v0, z0), h1 = adj_h(g1, v1, z1);
+    const float hr0 = h0.x, hi0 = h0.y, hr1 = h1.x, hi1 = h1.y;
     // optimiser step on theta (pv and pq buses); an inactive case keeps its state
     if (q.on0) th0 = opt_update(a.opt, th0, -hi0, mt.x, vt.x, b1, b2, st0, ib0, eps, a.mom, a.alpha);
     if (q.on1) th1 = opt_update(a.opt, th1, -hi1, mt.y, vt.y, b1, b2, st1, ib1, eps, a.mom, a.alpha);
