@@ -86,6 +86,30 @@ template <class C> __device__ __forceinline__ C adj_h(C g0, C v, C z) {
   return mkc(g0.x + fmaT(v.x, z.x, -(v.y * z.y)), g0.y + fmaT(v.x, z.y, v.y * z.x));
 }
 
+// ---- cache policy of the optimiser state -------------------------------------
+// Per iteration the adjoint pass streams the optimiser state (master theta,
+// |V|, the moments, Q_calc at pv buses) through once, several times the L2's
+// 129 MB at large batches.  It is read and written with the evict-first
+// (streaming) policy, so that V and w, which the next pass gathers from, keep
+// their L2 lines at normal priority.
+#ifndef DPF_STREAM_HINTS
+#define DPF_STREAM_HINTS 1
+#endif
+template <class T> __device__ __forceinline__ T ld_stream(const T* p) {
+#if DPF_STREAM_HINTS
+  return __ldcs(p);
+#else
+  return *p;
+#endif
+}
+template <class T> __device__ __forceinline__ void st_stream(T* p, T v) {
+#if DPF_STREAM_HINTS
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
+
 // ---- programmatic dependent launch -------------------------------------------
 // A kernel launched with programmatic stream serialisation may start while its
 // predecessor drains.  pdl_wait() blocks until the predecessor grid has
@@ -639,7 +663,7 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
       const R dQ = (ty == BUS_PQ) ? Q - qs : R(0);
       const R ca = a.inv_m2 * dP, cb = a.inv_m2 * dQ;
       a.W[e] = w_of(ca, cb, vi);
-      if (ty == BUS_PV) a.qpv[e] = Q;
+      if (ty == BUS_PV) st_stream(a.qpv + e, Q);
       if (a.sbuf) a.sbuf[e] = mkc(P, Q);
       if (a.cbuf) a.cbuf[e] = mkc(ca, cb);
       acc = fmaT(dP, dP, fmaT(dQ, dQ, acc));
@@ -718,15 +742,15 @@ __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, Adj
   const size_t si = a.spec_per_case ? e : (size_t)i;
   r.ps = a.pspec[si];
   r.qs = a.qspec[si];
-  r.qp = (r.ty == BUS_PV) ? a.qpv[e] : R(0);
-  r.th = a.th[e];
-  r.vm = a.vm[e];
+  r.qp = (r.ty == BUS_PV) ? ld_stream(a.qpv + e) : R(0);
+  r.th = ld_stream(a.th + e);
+  r.vm = ld_stream(a.vm + e);
   r.vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
   r.m1 = r.v1 = r.m2 = r.v2 = R(0);
   if (!grad_only) {
-    r.m1 = a.mth[e];
-    r.v1 = a.vth[e];
-    if (r.ty == BUS_PQ) { r.m2 = a.mvm[e]; r.v2 = a.vvm[e]; }
+    r.m1 = ld_stream(a.mth + e);
+    r.v1 = ld_stream(a.vth + e);
+    if (r.ty == BUS_PQ) { r.m2 = ld_stream(a.mvm + e); r.v2 = ld_stream(a.vvm + e); }
   }
 }
 
@@ -763,14 +787,14 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
   }
   // optimiser step on theta (pv and pq buses)
   r.th = opt_update(a.opt, r.th, g_th, r.m1, r.v1, b1, b2, step, isb, eps, a.mom, a.alpha);
-  a.mth[e] = r.m1;
-  a.vth[e] = r.v1;
-  a.th[e] = r.th;
+  st_stream(a.mth + e, r.m1);
+  st_stream(a.vth + e, r.v1);
+  st_stream(a.th + e, r.th);
   if (r.ty == BUS_PQ) {  // and on |V| (pq buses)
     r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha);
-    a.mvm[e] = r.m2;
-    a.vvm[e] = r.v2;
-    a.vm[e] = r.vm;
+    st_stream(a.mvm + e, r.m2);
+    st_stream(a.vvm + e, r.v2);
+    st_stream(a.vm + e, r.vm);
   }
   a.V[e] = volt(r.th, r.vm);
 }
@@ -992,7 +1016,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
       fwd_epilogue(vi0, I0, ty, ps0, qs0, a.inv_m2, w0, q0, acc0, mx0);
       fwd_epilogue(vi1, I1, ty, ps1, qs1, a.inv_m2, w1, q1, acc1, mx1);
       W[e] = make_float4(w0.x, w0.y, w1.x, w1.y);
-      if (ty == BUS_PV) ((float2*)a.qpv)[e] = make_float2(q0, q1);
+      if (ty == BUS_PV) st_stream((float2*)a.qpv + e, make_float2(q0, q1));
     }
     if (!q.on0) { acc0 = 0.f; mx0 = 0.f; }
     if (!q.on1) { acc1 = 0.f; mx1 = 0.f; }
@@ -1032,15 +1056,15 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
       ps0 = ps1 = a.pspec[i];
       qs0 = qs1 = a.qspec[i];
     }
-    const float2 qp = (ty == BUS_PV) ? ((const float2*)a.qpv)[e] : make_float2(0.f, 0.f);
-    float4 th = ((const float4*)a.th)[e];  // (hi, lo) of case k0, then of k0 + 1
-    float4 vm = ((const float4*)a.vm)[e];
+    const float2 qp = (ty == BUS_PV) ? ld_stream((const float2*)a.qpv + e) : make_float2(0.f, 0.f);
+    float4 th = ld_stream((const float4*)a.th + e);  // (hi, lo) of case k0, then of k0 + 1
+    float4 vm = ld_stream((const float4*)a.vm + e);
     const float4 vv4 = ((const float4*)a.V)[e];  // current V of both cases (no second sincos)
-    float2 mt = ((const float2*)a.mth)[e], vt = ((const float2*)a.vth)[e];
+    float2 mt = ld_stream((const float2*)a.mth + e), vt = ld_stream((const float2*)a.vth + e);
     float2 mv = make_float2(0.f, 0.f), vv = mv;
     if (ty == BUS_PQ) {
-      mv = ((const float2*)a.mvm)[e];
-      vv = ((const float2*)a.vvm)[e];
+      mv = ld_stream((const float2*)a.mvm + e);
+      vv = ld_stream((const float2*)a.vvm + e);
     }
     float2 z0, z1;
     row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W + h0, z0, z1);
@@ -1072,17 +1096,17 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     // optimiser step on theta (pv and pq buses); an inactive case keeps its state
     if (q.on0) th0 = opt_update(a.opt, th0, -hi0, mt.x, vt.x, b1, b2, st0, ib0, eps, a.mom, a.alpha);
     if (q.on1) th1 = opt_update(a.opt, th1, -hi1, mt.y, vt.y, b1, b2, st1, ib1, eps, a.mom, a.alpha);
-    ((float2*)a.mth)[e] = mt;
-    ((float2*)a.vth)[e] = vt;
-    ((float4*)a.th)[e] = make_float4(th0.x, th0.y, th1.x, th1.y);
+    st_stream((float2*)a.mth + e, mt);
+    st_stream((float2*)a.vth + e, vt);
+    st_stream((float4*)a.th + e, make_float4(th0.x, th0.y, th1.x, th1.y));
     if (ty == BUS_PQ) {  // and on |V| (pq buses)
       if (q.on0) vm0 = opt_update(a.opt, vm0, div_step(hr0, mwork(vm0)), mv.x, vv.x, b1, b2, st0, ib0, eps, a.mom,
                                   a.alpha);
       if (q.on1) vm1 = opt_update(a.opt, vm1, div_step(hr1, mwork(vm1)), mv.y, vv.y, b1, b2, st1, ib1, eps, a.mom,
                                   a.alpha);
-      ((float2*)a.mvm)[e] = mv;
-      ((float2*)a.vvm)[e] = vv;
-      ((float4*)a.vm)[e] = make_float4(vm0.x, vm0.y, vm1.x, vm1.y);
+      st_stream((float2*)a.mvm + e, mv);
+      st_stream((float2*)a.vvm + e, vv);
+      st_stream((float4*)a.vm + e, make_float4(vm0.x, vm0.y, vm1.x, vm1.y));
     }
     const float2 n0 = q.on0 ? volt(th0, vm0) : v0, n1 = q.on1 ? volt(th1, vm1) : v1;
     ((float4*)a.V)[e] = make_float4(n0.x, n0.y, n1.x, n1.y);
