@@ -541,7 +541,7 @@ def main():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--row-blocks", type=int, default=0)
-    ap.add_argument("--cpu-iters", type=int, default=2000)
+    ap.add_argument("--cpu-iters", type=int, default=5000)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")

@@ -952,7 +952,10 @@ __device__ __forceinline__ void fwd_epilogue(float2 vi, float2 I, int ty, float 
   mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);
 }
 
-__global__ void __launch_bounds__(256, 4) k_fwd2(IterArgs<float> a) {
+#ifndef DPF_FWD2_MINB
+#define DPF_FWD2_MINB 4
+#endif
+__global__ void __launch_bounds__(256, DPF_FWD2_MINB) k_fwd2(IterArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int r0 = blockIdx.y * a.rpb, r1 = min(a.N, r0 + a.rpb);
