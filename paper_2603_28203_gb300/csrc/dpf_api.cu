@@ -214,8 +214,10 @@ struct dpf_workspace {
   int cap_cases = 0;      // Kp capacity
   size_t cap_stage = 0;   // K * N capacity of the user-layout staging buffers
   // element buffers (sized for FP64; FP32 mode uses the front half)
-  void *V = nullptr, *W = nullptr, *G0 = nullptr, *th = nullptr, *vm = nullptr;
-  void *mth = nullptr, *vth = nullptr, *mvm = nullptr, *vvm = nullptr, *p = nullptr, *q = nullptr;
+  void *V = nullptr, *W = nullptr, *G0 = nullptr;
+  void* ms = nullptr;  // master (theta, |V|) pairs, 16 bytes per element
+  void* os = nullptr;  // optimiser moments, 4 values per element
+  void *p = nullptr, *q = nullptr;
   double *p64 = nullptr, *q64 = nullptr, *tmp_a = nullptr, *tmp_b = nullptr, *tmp_c = nullptr;
   double2* V64 = nullptr;
   void *sbuf = nullptr, *cbuf = nullptr;
@@ -269,7 +271,7 @@ struct dpf_workspace {
 };
 
 static void ws_free_buffers(dpf_workspace* w) {
-  void** ptrs[] = {&w->V, &w->W, &w->G0, &w->th, &w->vm, &w->mth, &w->vth, &w->mvm, &w->vvm, &w->p, &w->q,
+  void** ptrs[] = {&w->V, &w->W, &w->G0, &w->ms, &w->os, &w->p, &w->q,
                    &w->sbuf, &w->cbuf, &w->loss_acc, &w->step_size, &w->isbc2, &w->yff, &w->yft, &w->ytt};
   for (void** p : ptrs) dfree(*p);
   dfree(w->p64); dfree(w->q64); dfree(w->tmp_a); dfree(w->tmp_b); dfree(w->tmp_c); dfree(w->V64);
@@ -310,8 +312,8 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
   const size_t E = (size_t)y->n * Kp;
   if (E > w->cap_elems || Kp > w->cap_cases) {
     ws_drop_graph(w);
-    dfree(w->V); dfree(w->W); dfree(w->G0); dfree(w->th); dfree(w->vm); dfree(w->mth); dfree(w->vth);
-    dfree(w->mvm); dfree(w->vvm); dfree(w->p); dfree(w->q); dfree(w->sbuf); dfree(w->cbuf);
+    dfree(w->V); dfree(w->W); dfree(w->G0); dfree(w->ms); dfree(w->os);
+    dfree(w->p); dfree(w->q); dfree(w->sbuf); dfree(w->cbuf);
     dfree(w->p64); dfree(w->q64); dfree(w->tmp_a); dfree(w->tmp_b); dfree(w->tmp_c); dfree(w->V64);
     dfree(w->loss_acc); dfree(w->step_size); dfree(w->isbc2); dfree(w->yff); dfree(w->yft); dfree(w->ytt);
     dfree(w->active); dfree(w->iters); dfree(w->status); dfree(w->of); dfree(w->ot); dfree(w->bad);
@@ -321,10 +323,10 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     w->cap_elems = 0;
     w->cap_cases = 0;
     char** bufs16[] = {(char**)&w->V, (char**)&w->W, (char**)&w->G0, (char**)&w->V64, (char**)&w->sbuf,
-                       (char**)&w->cbuf};
+                       (char**)&w->cbuf, (char**)&w->ms};
     for (char** b : bufs16) TRY(dalloc(b, E * 16));
-    char** bufs8[] = {(char**)&w->th, (char**)&w->vm, (char**)&w->mth, (char**)&w->vth, (char**)&w->mvm,
-                      (char**)&w->vvm, (char**)&w->p, (char**)&w->q, (char**)&w->p64, (char**)&w->q64,
+    TRY(dalloc((char**)&w->os, E * 32));
+    char** bufs8[] = {(char**)&w->p, (char**)&w->q, (char**)&w->p64, (char**)&w->q64,
                       (char**)&w->tmp_a, (char**)&w->tmp_b, (char**)&w->tmp_c};
     for (char** b : bufs8) TRY(dalloc(b, E * 8));
     TRY(dalloc((char**)&w->loss_acc, (size_t)Kp * 8));
@@ -454,12 +456,8 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.V = (C*)w->V;
   a.W = (C*)w->W;
   a.qpv = (R*)w->G0;  // the buffer holds Q_calc at pv buses
-  a.th = (M*)w->th;
-  a.vm = (M*)w->vm;
-  a.mth = (R*)w->mth;
-  a.vth = (R*)w->vth;
-  a.mvm = (R*)w->mvm;
-  a.vvm = (R*)w->vvm;
+  a.ms = (typename Prec<R>::MS*)w->ms;
+  a.os = (Mom<R>*)w->os;
   a.spec_per_case = w->spec_per_case ? 1 : 0;
   if (w->spec_per_case) {
     a.pspec = (const R*)w->p;
@@ -534,8 +532,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   c.col = d.col;
   c.val = v64;
   c.type = d.type;
-  c.th = (const M*)w->th;
-  c.vm = (const M*)w->vm;
+  c.ms = (const typename Prec<R>::MS*)w->ms;
   P.need_volt64 = (sizeof(R) == 4);
   c.V64 = P.need_volt64 ? w->V64 : (double2*)w->V;
   c.pspec = w->spec_per_case ? w->p64 : d.p64;
@@ -924,13 +921,9 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   ia.q64 = w->spec_per_case ? w->q64 : nullptr;
   ia.p = (R*)w->p;
   ia.q = (R*)w->q;
-  ia.th = (typename Prec<R>::M*)w->th;
-  ia.vm = (typename Prec<R>::M*)w->vm;
+  ia.ms = (typename Prec<R>::MS*)w->ms;
   ia.V = (typename Prec<R>::C*)w->V;
-  ia.mth = (R*)w->mth;
-  ia.vth = (R*)w->vth;
-  ia.mvm = (R*)w->mvm;
-  ia.vvm = (R*)w->vvm;
+  ia.os = (Mom<R>*)w->os;
   const size_t E = (size_t)y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
   k_init<R><<<std::max(nb, 1), 256, 0, s>>>(ia);
@@ -1157,11 +1150,9 @@ extern "C" int dpf_solve_end(dpf_workspace* w, const dpf_batch* b, void* stream)
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
   if (b->va || b->vm) {
     if (w->precision == DPF_FP64) {
-      k_master64<double><<<nb, 256, 0, s>>>((const double*)w->th, w->tmp_a, E);
-      k_master64<double><<<nb, 256, 0, s>>>((const double*)w->vm, w->tmp_b, E);
+      k_master64<double2><<<nb, 256, 0, s>>>((const double2*)w->ms, w->tmp_a, w->tmp_b, E);
     } else {
-      k_master64<float2><<<nb, 256, 0, s>>>((const float2*)w->th, w->tmp_a, E);
-      k_master64<float2><<<nb, 256, 0, s>>>((const float2*)w->vm, w->tmp_b, E);
+      k_master64<float4><<<nb, 256, 0, s>>>((const float4*)w->ms, w->tmp_a, w->tmp_b, E);
     }
     CKLAUNCH();
     if (b->va) TRY(to_user(w, w->tmp_a, hio, w->st_a, b->va, s));

@@ -28,6 +28,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dpf {
 
 enum { BUS_PQ = 0, BUS_PV = 1, BUS_SLACK = 2 };
@@ -36,8 +38,14 @@ enum { SCHED_CONST = 0, SCHED_PLATEAU = 1, SCHED_STEP = 2 };
 enum { OPT_ADAM = 0, OPT_SGD = 1, OPT_RMSPROP = 2 };
 
 template <class R> struct Prec;
-template <> struct Prec<float> { using C = float2; using M = float2; };   // M: (hi, lo) master
-template <> struct Prec<double> { using C = double2; using M = double; };
+// C: complex working value; M: master value (FP32 mode: (hi, lo) double-float);
+// MS: one element's master pair (theta, |V|) in one 16-byte word
+template <> struct Prec<float> { using C = float2; using M = float2; using MS = float4; };
+template <> struct Prec<double> { using C = double2; using M = double; using MS = double2; };
+
+// One element's optimiser moments: (m, v) of theta, then of |V| (pq buses).
+// Stored interleaved so that an element's state is one aligned access.
+template <class R> struct __align__(4 * sizeof(R) >= 16 ? 16 : 4 * sizeof(R)) Mom { R m1, v1, m2, v2; };
 
 __device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
@@ -110,6 +118,22 @@ template <class T> __device__ __forceinline__ void st_stream(T* p, T v) {
 #endif
 }
 
+__device__ __forceinline__ Mom<float> mom_load(const Mom<float>* p) {
+  const float4 t = ld_stream((const float4*)p);
+  return Mom<float>{t.x, t.y, t.z, t.w};
+}
+__device__ __forceinline__ void mom_store(Mom<float>* p, const Mom<float>& m) {
+  st_stream((float4*)p, make_float4(m.m1, m.v1, m.m2, m.v2));
+}
+__device__ __forceinline__ Mom<double> mom_load(const Mom<double>* p) {
+  const double2 a = ld_stream((const double2*)p), b = ld_stream((const double2*)p + 1);
+  return Mom<double>{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void mom_store(Mom<double>* p, const Mom<double>& m) {
+  st_stream((double2*)p, make_double2(m.m1, m.v1));
+  st_stream((double2*)p + 1, make_double2(m.m2, m.v2));
+}
+
 // ---- programmatic dependent launch -------------------------------------------
 // A kernel launched with programmatic stream serialisation may start while its
 // predecessor drains.  pdl_wait() blocks until the predecessor grid has
@@ -146,6 +170,14 @@ template <> __device__ __forceinline__ float2 mfrom<float2>(double v) {
   return make_float2(hi, (float)(v - (double)hi));
 }
 template <> __device__ __forceinline__ double mfrom<double>(double v) { return v; }
+
+// (theta, |V|) master pair of one element
+__device__ __forceinline__ float2 ms_th(float4 s) { return make_float2(s.x, s.y); }
+__device__ __forceinline__ float2 ms_vm(float4 s) { return make_float2(s.z, s.w); }
+__device__ __forceinline__ float4 ms_make(float2 th, float2 vm) { return make_float4(th.x, th.y, vm.x, vm.y); }
+__device__ __forceinline__ double ms_th(double2 s) { return s.x; }
+__device__ __forceinline__ double ms_vm(double2 s) { return s.y; }
+__device__ __forceinline__ double2 ms_make(double th, double vm) { return make_double2(th, vm); }
 
 // V = |V| e^{j theta} in working precision.  FP32: sincos of the high word,
 // first-order correction for the low word (|lo| <= 2^-24 |hi|).
@@ -520,12 +552,8 @@ template <class R> struct IterArgs {
   C* V;
   C* W;
   R* qpv;    // Q_calc at pv buses (the rows k_adj cannot rebuild from w)
-  M* th;
-  M* vm;
-  R* mth;
-  R* vth;
-  R* mvm;
-  R* vvm;
+  typename Prec<R>::MS* ms;  // [N][Kp] master (theta, |V|)
+  Mom<R>* os;                // [N][Kp] optimiser moments
   const R* pspec;
   const R* qspec;
   int spec_per_case;
@@ -743,14 +771,19 @@ __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, Adj
   r.ps = a.pspec[si];
   r.qs = a.qspec[si];
   r.qp = (r.ty == BUS_PV) ? ld_stream(a.qpv + e) : R(0);
-  r.th = ld_stream(a.th + e);
-  r.vm = ld_stream(a.vm + e);
+  const typename Prec<R>::MS s = ld_stream(a.ms + e);
+  r.th = ms_th(s);
+  r.vm = ms_vm(s);
   r.vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
   r.m1 = r.v1 = r.m2 = r.v2 = R(0);
   if (!grad_only) {
-    r.m1 = ld_stream(a.mth + e);
-    r.v1 = ld_stream(a.vth + e);
-    if (r.ty == BUS_PQ) { r.m2 = ld_stream(a.mvm + e); r.v2 = ld_stream(a.vvm + e); }
+    // full 16-byte accesses at pv buses too (their |V| halves pass through
+    // unchanged): a half-written sector would cost a read-modify-write
+    const Mom<R> o = mom_load(a.os + e);
+    r.m1 = o.m1;
+    r.v1 = o.v1;
+    r.m2 = o.m2;
+    r.v2 = o.v2;
   }
 }
 
@@ -785,17 +818,11 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
     a.gvm[e] = g_vm;
     return;
   }
-  // optimiser step on theta (pv and pq buses)
+  // optimiser step on theta (pv and pq buses) and on |V| (pq buses)
   r.th = opt_update(a.opt, r.th, g_th, r.m1, r.v1, b1, b2, step, isb, eps, a.mom, a.alpha);
-  st_stream(a.mth + e, r.m1);
-  st_stream(a.vth + e, r.v1);
-  st_stream(a.th + e, r.th);
-  if (r.ty == BUS_PQ) {  // and on |V| (pq buses)
-    r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha);
-    st_stream(a.mvm + e, r.m2);
-    st_stream(a.vvm + e, r.v2);
-    st_stream(a.vm + e, r.vm);
-  }
+  if (r.ty == BUS_PQ) r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha);
+  st_stream(a.ms + e, ms_make(r.th, r.vm));
+  mom_store(a.os + e, Mom<R>{r.m1, r.v1, r.m2, r.v2});
   a.V[e] = volt(r.th, r.vm);
 }
 
@@ -1060,15 +1087,9 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
       qs0 = qs1 = a.qspec[i];
     }
     const float2 qp = (ty == BUS_PV) ? ld_stream((const float2*)a.qpv + e) : make_float2(0.f, 0.f);
-    float4 th = ld_stream((const float4*)a.th + e);  // (hi, lo) of case k0, then of k0 + 1
-    float4 vm = ld_stream((const float4*)a.vm + e);
+    const float4 s0 = ld_stream(a.ms + 2 * (size_t)e), s1 = ld_stream(a.ms + 2 * (size_t)e + 1);
     const float4 vv4 = ((const float4*)a.V)[e];  // current V of both cases (no second sincos)
-    float2 mt = ld_stream((const float2*)a.mth + e), vt = ld_stream((const float2*)a.vth + e);
-    float2 mv = make_float2(0.f, 0.f), vv = mv;
-    if (ty == BUS_PQ) {
-      mv = ld_stream((const float2*)a.mvm + e);
-      vv = ld_stream((const float2*)a.vvm + e);
-    }
+    Mom<float> o0 = mom_load(a.os + 2 * (size_t)e), o1 = mom_load(a.os + 2 * (size_t)e + 1);
     float2 z0, z1;
     row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W + h0, z0, z1);
     if (i == q.of0) {
@@ -1089,28 +1110,26 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
       cfms(z1, q.yft1, make_float2(t.z, t.w));
       cfms(z1, q.ytt1, make_float2(wi.z, wi.w));
     }
-    float2 th0 = make_float2(th.x, th.y), th1 = make_float2(th.z, th.w);
-    float2 vm0 = make_float2(vm.x, vm.y), vm1 = make_float2(vm.z, vm.w);
+    float2 th0 = ms_th(s0), th1 = ms_th(s1);
+    float2 vm0 = ms_vm(s0), vm1 = ms_vm(s1);
     const float2 v0 = make_float2(vv4.x, vv4.y), v1 = make_float2(vv4.z, vv4.w);
     const float2 g0 = conj_c_s(make_float2(wi.x, wi.y), v0, ty, ps0, qs0, qp.x, a.m_half);
     const float2 g1 = conj_c_s(make_float2(wi.z, wi.w), v1, ty, ps1, qs1, qp.y, a.m_half);
     const float2 h0 = adj_h(g0, v0, z0), h1 = adj_h(g1, v1, z1);
     const float hr0 = h0.x, hi0 = h0.y, hr1 = h1.x, hi1 = h1.y;
     // optimiser step on theta (pv and pq buses); an inactive case keeps its state
-    if (q.on0) th0 = opt_update(a.opt, th0, -hi0, mt.x, vt.x, b1, b2, st0, ib0, eps, a.mom, a.alpha);
-    if (q.on1) th1 = opt_update(a.opt, th1, -hi1, mt.y, vt.y, b1, b2, st1, ib1, eps, a.mom, a.alpha);
-    st_stream((float2*)a.mth + e, mt);
-    st_stream((float2*)a.vth + e, vt);
-    st_stream((float4*)a.th + e, make_float4(th0.x, th0.y, th1.x, th1.y));
+    if (q.on0) th0 = opt_update(a.opt, th0, -hi0, o0.m1, o0.v1, b1, b2, st0, ib0, eps, a.mom, a.alpha);
+    if (q.on1) th1 = opt_update(a.opt, th1, -hi1, o1.m1, o1.v1, b1, b2, st1, ib1, eps, a.mom, a.alpha);
     if (ty == BUS_PQ) {  // and on |V| (pq buses)
-      if (q.on0) vm0 = opt_update(a.opt, vm0, div_step(hr0, mwork(vm0)), mv.x, vv.x, b1, b2, st0, ib0, eps, a.mom,
+      if (q.on0) vm0 = opt_update(a.opt, vm0, div_step(hr0, mwork(vm0)), o0.m2, o0.v2, b1, b2, st0, ib0, eps, a.mom,
                                   a.alpha);
-      if (q.on1) vm1 = opt_update(a.opt, vm1, div_step(hr1, mwork(vm1)), mv.y, vv.y, b1, b2, st1, ib1, eps, a.mom,
+      if (q.on1) vm1 = opt_update(a.opt, vm1, div_step(hr1, mwork(vm1)), o1.m2, o1.v2, b1, b2, st1, ib1, eps, a.mom,
                                   a.alpha);
-      st_stream((float2*)a.mvm + e, mv);
-      st_stream((float2*)a.vvm + e, vv);
-      st_stream((float4*)a.vm + e, make_float4(vm0.x, vm0.y, vm1.x, vm1.y));
     }
+    st_stream(a.ms + 2 * (size_t)e, ms_make(th0, vm0));
+    st_stream(a.ms + 2 * (size_t)e + 1, ms_make(th1, vm1));
+    mom_store(a.os + 2 * (size_t)e, o0);
+    mom_store(a.os + 2 * (size_t)e + 1, o1);
     const float2 n0 = q.on0 ? volt(th0, vm0) : v0, n1 = q.on1 ? volt(th1, vm1) : v1;
     ((float4*)a.V)[e] = make_float4(n0.x, n0.y, n1.x, n1.y);
   }
@@ -1123,8 +1142,7 @@ template <class M> struct Check64Args {
   const int32_t* __restrict__ col;
   const double2* __restrict__ val;
   const uint8_t* __restrict__ type;
-  const M* th;
-  const M* vm;
+  const typename std::conditional<std::is_same<M, float2>::value, float4, double2>::type* ms;  // master pairs
   double2* V64;
   const double* pspec;
   const double* qspec;
@@ -1153,7 +1171,8 @@ __global__ void __launch_bounds__(1024) k_volt64(Check64Args<M> a) {
   if (k >= a.Kp || !(a.all_cases || (a.active[k] && (!a.cand || a.cand[k])))) return;
   for (int i = mp.row0; i < a.N; i += mp.rstride) {
     const size_t e = (size_t)i * a.Kp + k;
-    a.V64[e] = volt64(a.th[e], a.vm[e]);
+    const auto s = a.ms[e];
+    a.V64[e] = volt64(ms_th(s), ms_vm(s));
   }
 }
 
@@ -1308,13 +1327,9 @@ template <class R> struct InitArgs {
   const double* q64;
   R* p;                      // per-case working-precision copies
   R* q;
-  M* th;
-  M* vm;
+  typename Prec<R>::MS* ms;
   C* V;
-  R* mth;
-  R* vth;
-  R* mvm;
-  R* vvm;
+  Mom<R>* os;
 };
 
 template <class R>
@@ -1334,13 +1349,9 @@ __global__ void k_init(InitArgs<R> a) {
       }
     }
     const M mth = mfrom<M>(th), mvm = mfrom<M>(vm);
-    a.th[e] = mth;
-    a.vm[e] = mvm;
+    a.ms[e] = ms_make(mth, mvm);
     a.V[e] = volt(mth, mvm);
-    a.mth[e] = R(0);
-    a.vth[e] = R(0);
-    a.mvm[e] = R(0);
-    a.vvm[e] = R(0);
+    a.os[e] = Mom<R>{R(0), R(0), R(0), R(0)};
     if (a.p64) {
       a.p[e] = (R)a.p64[e];
       a.q[e] = (R)a.q64[e];
@@ -1432,11 +1443,14 @@ __global__ void k_case_init(CaseInitArgs<R> a) {
   a.ytt[k] = mkc((R)tt.x, (R)tt.y);
 }
 
-// master -> FP64 (for the solution output)
-template <class M>
-__global__ void k_master64(const M* __restrict__ src, double* __restrict__ dst, size_t n) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    dst[e] = mval(src[e]);
+// master (theta, |V|) -> FP64 (for the solution output)
+template <class MS>
+__global__ void k_master64(const MS* __restrict__ src, double* __restrict__ th, double* __restrict__ vm, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const MS s = src[e];
+    th[e] = mval(ms_th(s));
+    vm[e] = mval(ms_vm(s));
+  }
 }
 
 // working precision -> FP64, optional scale (outputs of the evaluation calls)
