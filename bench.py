@@ -160,7 +160,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # roofline helpers
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(n_bus, n_pv, n_pq, nnz, n_case):
+def algorithmic_bytes(n_bus, n_pv, n_pq, nnz, n_case, spec_per_case=False):
     """Bytes each kernel must move per launch (every array element once).
 
     k_fwd, per case: read V (8 B/bus), write w (8 B/bus), write Q_calc at pv
@@ -170,11 +170,14 @@ def algorithmic_bytes(n_bus, n_pv, n_pq, nnz, n_case):
       V (16), read+write the two Adam moments of theta (16); at pq buses also
       write |V| (8) and read+write its moments (16).
     Shared per launch: Y in CSR (16 B per nonzero + 4 B row pointers + bus
-    types) and the shared specified P, Q (8 B/bus).
+    types) and the shared specified P, Q (8 B/bus) -- or, with a specification
+    per case, P and Q per element (8 B, FP32) read by both passes.
     """
-    shared = 16 * nnz + 4 * (n_bus + 1) + n_bus + 8 * n_bus
-    fwd = n_case * (16 * n_bus + 4 * n_pv) + shared
-    adj = n_case * (8 * n_bus + 60 * n_pv + 80 * n_pq) + shared
+    shared = 16 * nnz + 4 * (n_bus + 1) + n_bus
+    spec_f = n_case * 8 * n_bus if spec_per_case else 8 * n_bus
+    spec_a = n_case * 8 * (n_pv + n_pq) if spec_per_case else 8 * n_bus
+    fwd = n_case * (16 * n_bus + 4 * n_pv) + shared + spec_f
+    adj = n_case * (8 * n_bus + 60 * n_pv + 80 * n_pq) + shared + spec_a
     return fwd, adj
 
 
@@ -484,6 +487,117 @@ def run_scaling(args):
         y.free()
 
 
+def run_uneven(args):
+    """The uneven batch of the parameter-identification workload: 64 synthetic
+    grids of log-uniform sizes (300 to 80,000 buses; seeded) in one
+    block-diagonal system with one slack per island, and 16 hourly operating
+    points (the time-series load model) as the cases.  Times (a) FP32 DPF
+    iterations over the whole batch and (b) one parameter-identification step
+    (the loss and its branch adjoint w.r.t. the series g, b of every branch,
+    then the two Adam updates) at the iterate the solve reached (timing input
+    only: the identification tests use the oracle's Newton-Raphson points).  One JSON
+    line, with the FP64 oracle check of S_calc on one operating point."""
+    import torch
+    import gridgen
+    import oracle
+    from oracle.ybus import grid_ybus
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    from paper_2603_28203_gb300.paramid import identify_branches
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    t0 = time.time()
+    sizes = gridgen.uneven_sizes(64, 100)
+    grids = [gridgen.make_grid(int(n), 1000 + i, load_scale=0.1) for i, n in enumerate(sizes)]
+    cat = gridgen.concat_grids(grids)
+    K = 16
+    P, Q = gridgen.time_series(cat, K, seed=5)
+    t_gen = time.time() - t0
+    n_pv = int((cat.bus_type == 1).sum())
+    n_pq = int((cat.bus_type == 0).sum())
+    y = dpf.dpf_build_ybus(cat, stream=stream)
+    ws = dpf.dpf_workspace_create(y, K)
+    p_t = torch.tensor(P, dtype=torch.float64, device=dev)
+    q_t = torch.tensor(Q, dtype=torch.float64, device=dev)
+    opts = dpf.SolveOpts(lr=1e-3, precision=dpf.FP32, check_every=25, max_iter=10 ** 6,
+                         lanes=args.lanes or None, warps=args.warps or None, row_blocks=args.row_blocks or None)
+    fixed_shape = bool(args.lanes or args.warps or args.row_blocks)
+    n_it = args.uneven_iters
+    with torch.cuda.stream(stream):
+        if not (args.no_autotune or fixed_shape):
+            opts = dpf.dpf_autotune(y, ws, opts, iters=20, stream=stream, n_case=K, p_spec=p_t, q_spec=q_t)
+        dpf.dpf_solve_begin(y, ws, opts, stream=stream, n_case=K, p_spec=p_t, q_spec=q_t)
+        dpf.dpf_solve_iterate(ws, 50, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        dpf.dpf_solve_iterate(ws, n_it, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms_it = e0.elapsed_time(e1) / n_it
+        dpf.dpf_profile_enable(ws, True)
+        dpf.dpf_solve_iterate(ws, 50, stream=stream)
+        f_ms, a_ms, nf, na = dpf.dpf_kernel_times(ws, stream=stream)
+        dpf.dpf_profile_enable(ws, False)
+        out = {k: torch.empty((K, cat.n_bus), dtype=torch.float64, device=dev) for k in ("va", "vm")}
+        st = torch.empty(K, dtype=torch.int32, device=dev)
+        mm = torch.empty(K, dtype=torch.float64, device=dev)
+        dpf.dpf_solve_end(ws, stream=stream, n_case=K, va=out["va"], vm=out["vm"], status=st, max_mismatch=mm)
+        stream.synchronize()
+        # one parameter-identification step at that iterate (timed over several)
+        pert = gridgen.perturb_branches(cat, 5)
+        y0 = 1.0 / (pert.r + 1j * pert.x)
+        g0 = torch.tensor(y0.real, dtype=torch.float64, device=dev)
+        b0 = torch.tensor(y0.imag, dtype=torch.float64, device=dev)
+        identify_branches(y, ws, out["va"], out["vm"], p_t, q_t, g0, b0, iters=2, stream=stream)
+        stream.synchronize()
+        n_pid = args.uneven_pid_steps
+        e0.record(stream)
+        identify_branches(y, ws, out["va"], out["vm"], p_t, q_t, g0, b0, iters=n_pid, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms_pid = e0.elapsed_time(e1) / n_pid
+        # FP64 oracle check of the forward evaluation on operating point 0
+        pc, qc = dpf.dpf_power(y, ws, out["va"][:1].contiguous(), out["vm"][:1].contiguous(), precision=dpf.FP32,
+                               stream=stream)
+        stream.synchronize()
+    S = oracle.s_calc(grid_ybus(cat), out["vm"][0].cpu().numpy() * np.exp(1j * out["va"][0].cpu().numpy()))
+    err = max(np.abs(pc[0].cpu().numpy() - S.real).max(), np.abs(qc[0].cpu().numpy() - S.imag).max())
+    fwd_b, adj_b = algorithmic_bytes(cat.n_bus, n_pv, n_pq, y.nnz, K, spec_per_case=True)
+    peak, src = _peaks()
+    stc = st.cpu().numpy()
+    print(json.dumps({
+        "workload": "uneven",
+        "config": {"grids": int(len(sizes)), "bus_sizes": "log-uniform 300-80,000 (seed 100)",
+                   "n_bus": int(cat.n_bus), "n_branch": int(cat.n_branch), "nnz": int(y.nnz),
+                   "operating_points": K, "largest_grid": int(sizes.max()), "smallest_grid": int(sizes.min()),
+                   "precision": "fp32 iterations, FP64 master and test", "generation_s": round(t_gen, 1),
+                   "launch_shape": {"lanes": opts.lanes, "warps": opts.warps, "row_blocks": opts.row_blocks,
+                                    "chosen_by": "command line" if fixed_shape else
+                                    "library default" if args.no_autotune else "dpf_autotune"}},
+        "ms_per_iteration": ms_it,
+        "case_iterations_per_s": K / (ms_it / 1e3),
+        "bus_iterations_per_s": K * cat.n_bus / (ms_it / 1e3),
+        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src,
+                     "achieved": (fwd_b + adj_b) / (ms_it / 1e3) / 1e9,
+                     "frac": (fwd_b + adj_b) / (ms_it / 1e3) / 1e9 / peak,
+                     "algorithmic_bytes_per_iteration": fwd_b + adj_b,
+                     "fwd_us": 1e3 * f_ms / max(nf, 1), "adj_us": 1e3 * a_ms / max(na, 1),
+                     "adj_frac": adj_b / (a_ms / max(na, 1) / 1e3) / 1e9 / peak},
+        "paramid_step_ms": ms_pid,
+        "paramid_step": "Y values from (g, b) + forward pass + branch adjoint (g, b of every branch) over all "
+                        "operating points + 2 Adam updates (dpf_paramid_step, operating points staged once)",
+        "status_counts": {str(k): int((stc == k).sum()) for k in (0, 1, 2)},
+        "max_mismatch_p50": float(np.median(mm.cpu().numpy())),
+        "fp32_S_max_abs_error_vs_fp64_oracle": float(err),
+    }), flush=True)
+    ws.free()
+    y.free()
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -535,9 +649,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling"],
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven"],
                     help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep")
     ap.add_argument("--profile-steps", type=int, default=100)
+    ap.add_argument("--uneven-iters", type=int, default=300)
+    ap.add_argument("--uneven-pid-steps", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--row-blocks", type=int, default=0)
@@ -557,6 +673,8 @@ def main():
         run_reference(args)
     elif args.workload == "scaling":
         run_scaling(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -298,6 +298,31 @@ int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
                       double* d_p, double* d_q,
                       double* d_g, double* d_b, double* d_bch, void* stream);
 
+/* ---- parameter identification over measured operating points -------------
+ * The gradient of the loss to the branch parameters (Sec. 1 / abstract:
+ * gradients to the simulation parameters, which lets them be identified)
+ * for an iterative identification loop.
+ * dpf_paramid_begin stages n_case measured operating points in the
+ * workspace once: va, vm, p_spec, q_spec are [n_case][n_bus] FP64 device
+ * arrays (caller-owned; p_spec/q_spec NULL = the grid's); precision as in
+ * dpf_loss_backward.  dpf_paramid_step then evaluates, at those points and
+ * for the series admittances g_series + j b_series ([n_branch] FP64 device,
+ * required; charging and taps as built): the Y values, the forward pass and
+ * the branch adjoint -- the same quantities as dpf_loss_backward with these
+ * inputs and d_va = d_vm = d_p = d_q = NULL, without restaging the points.
+ * d_g, d_b, d_bch [n_branch] (summed over the points) and loss [n_case]
+ * (FP64; an extra FP64 pass) are device outputs, each may be NULL.
+ * Any other call on the workspace (a solve, an evaluation) discards the
+ * staged points: a later step returns DPF_E_STATE.  Errors as elsewhere. */
+int dpf_paramid_begin(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
+                      const double* va, const double* vm,
+                      const double* p_spec, const double* q_spec,
+                      int32_t precision, void* stream);
+int dpf_paramid_step(const dpf_ybus* y, dpf_workspace* ws,
+                     const double* g_series, const double* b_series,
+                     double* d_g, double* d_b, double* d_bch, double* loss,
+                     void* stream);
+
 /* ---- Adam on a parameter vector -------------------------------------------
  * One Adam step (the optimiser of Sec. 5.3, Kingma & Ba with bias correction)
  * on n FP64 parameters, e.g. the branch admittances g, b of parameter

@@ -80,6 +80,8 @@ SIGNATURES = {
     "dpf_loss_backward": (C.c_int, [VP, VP, I32, VP, VP, VP, VP, VP, VP, VP, I32,
                                     VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "dpf_power_noalloc": (C.c_int, [VP, I32, VP, VP, VP, VP, VP]),
+    "dpf_paramid_begin": (C.c_int, [VP, VP, I32, VP, VP, VP, VP, I32, VP]),
+    "dpf_paramid_step": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "dpf_profile_enable": (C.c_int, [VP, I32]),
     "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),
     "dpf_kernel_launches": (C.c_int, [VP, C.POINTER(C.c_int64)]),

@@ -107,7 +107,7 @@ static void free_device(DeviceYbus& d) {
   dfree(d.ent32); dfree(d.row_ptr); dfree(d.prow_ptr); dfree(d.ppos); dfree(d.col); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
   dfree(d.type); dfree(d.p64); dfree(d.q64); dfree(d.vmset); dfree(d.p32); dfree(d.q32);
   dfree(d.perm); dfree(d.iperm); dfree(d.br_f); dfree(d.br_t); dfree(d.br_r); dfree(d.br_x);
-  dfree(d.br_bch); dfree(d.br_tap); dfree(d.bridge);
+  dfree(d.br_bch); dfree(d.br_tap); dfree(d.br_itap); dfree(d.bridge);
   d.ready = false;
 }
 
@@ -143,9 +143,11 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
     q32[i] = (float)q64[i];
   }
   std::vector<int32_t> bf(m), bt(m);
+  std::vector<double> itap(m);
   for (int e = 0; e < m; ++e) {
     bf[e] = y->iperm[y->f_bus[e]];
     bt[e] = y->iperm[y->t_bus[e]];
+    itap[e] = 1.0 / (y->tap[e] == 0.0 ? 1.0 : y->tap[e]);
   }
   int rc = DPF_OK;
   do {
@@ -171,6 +173,7 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
     if ((rc = upload(&d.br_x, y->x, s))) break;
     if ((rc = upload(&d.br_bch, y->b_ch, s))) break;
     if ((rc = upload(&d.br_tap, y->tap, s))) break;
+    if ((rc = upload(&d.br_itap, itap, s))) break;
     if ((rc = upload(&d.bridge, y->bridge, s))) break;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { rc = fail(DPF_E_CUDA, "upload sync: %s", cudaGetErrorString(e)); break; }
@@ -255,6 +258,7 @@ struct dpf_workspace {
   bool staged = false;
   int ysmem = 0;
   bool pair_fwd = false, pair_adj = false;
+  bool pid_ready = false;  // operating points staged by dpf_paramid_begin
   std::vector<std::pair<std::vector<long long>, std::vector<int>>> tune_cache;  // key -> (lanes, warps, rb, pairs)
   bool spec_per_case = false, has_outage = false;
   dpf_solve_opts opts;
@@ -737,7 +741,8 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
     const int ybytes = ysmem_bytes(rpb, mx, fp64);
     const int wbytes = line * wmax;
     const bool fits = ybytes + wbytes <= 150 * 1024;
-    if ((fits && line > 0) || (line == 0 && ybytes <= 96 * 1024) || gy >= 65535 || rpb <= 1 || tries >= 6) {
+    // (staged Y rows above ~32 KB would cap the resident CTAs per SM)
+    if ((fits && line > 0) || (line == 0 && ybytes <= 32 * 1024) || gy >= 65535 || rpb <= 1 || tries >= 6) {
       w->gy = (n + rpb - 1) / rpb;
       w->rpb = rpb;
       w->ysmem = ybytes;
@@ -1034,6 +1039,7 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   if (!o->flat_start && (!b->va || !b->vm)) return fail(DPF_E_INVALID, "warm start needs va and vm");
   cudaStream_t s = (cudaStream_t)stream;
   w->begun = false;
+  w->pid_ready = false;
   ws_drop_graph(w);
   w->opts = *o;
   w->K = b->n_case;
@@ -1377,6 +1383,7 @@ static int eval_setup(const dpf_ybus* y, dpf_workspace* w, int K, int precision,
   if (precision != DPF_FP32 && precision != DPF_FP64) return fail(DPF_E_INVALID, "unknown precision");
   if (!va || !vm) return fail(DPF_E_INVALID, "va and vm are required");
   w->begun = false;
+  w->pid_ready = false;
   ws_drop_graph(w);
   dpf_default_opts(&w->opts);
   w->opts.precision = precision;
@@ -1425,24 +1432,59 @@ extern "C" int dpf_power(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, co
   return precision == DPF_FP64 ? power_impl<double>(w, p_calc, q_calc, s) : power_impl<float>(w, p_calc, q_calc, s);
 }
 
+// dL/d(series g, b, b_ch) of every branch, summed over the cases, from w and V
+// (branch adjoint; written into zeroed outputs).
+template <class R>
+static int launch_edge_grad(dpf_workspace* w, double* d_g, double* d_b, double* d_bch, cudaStream_t s) {
+  using C = typename Prec<R>::C;
+  const dpf_ybus* y = w->y;
+  if (d_g) CK(cudaMemsetAsync(d_g, 0, (size_t)y->m * 8, s));
+  if (d_b) CK(cudaMemsetAsync(d_b, 0, (size_t)y->m * 8, s));
+  if (d_bch) CK(cudaMemsetAsync(d_bch, 0, (size_t)y->m * 8, s));
+  EdgeArgs<R> ea;
+  memset(&ea, 0, sizeof ea);
+  ea.M = y->m;
+  ea.K = w->K;
+  ea.Kp = w->Kp;
+  ea.lanes = w->lanes;
+  ea.br_f = y->dev.br_f;
+  ea.br_t = y->dev.br_t;
+  ea.itap = y->dev.br_itap;
+  ea.V = (const C*)w->V;
+  ea.W = (const C*)w->W;
+  ea.d_g = d_g;
+  ea.d_b = d_b;
+  ea.d_bch = d_bch;
+  const int rpw = 32 / w->lanes;
+  const int gy = std::max(1, std::min((y->m + w->warps * rpw - 1) / (w->warps * rpw), 65535));
+  k_edge_grad<R><<<dim3(w->gx, gy), dim3(w->warps * 32), 0, s>>>(ea);
+  CKLAUNCH();
+  return DPF_OK;
+}
+
 template <class R>
 static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, double* d_vm, double* d_p,
                               double* d_q, double* d_g, double* d_b, double* d_bch, cudaStream_t s) {
   using C = typename Prec<R>::C;
   const dpf_ybus* y = w->y;
   Plan<R> P = make_plan<R>(w);
-  P.it.cbuf = (C*)w->cbuf;
+  P.it.cbuf = (d_p || d_q) ? (C*)w->cbuf : nullptr;
+  P.it.loss_acc = nullptr;  // (the loss is the FP64 pass's)
+  P.it.mx32 = nullptr;
   P.it.n_active = nullptr;
   P.it.tile_cnt = nullptr;
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
-  P.it.gva = (R*)w->tmp_c;  // reuse as gradient scratch: [N][Kp] R each
-  P.it.gvm = (R*)w->sbuf;
-  P.itb = P.it;
-  P.itb.rpb = w->rpb_b;
-  k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
   CKLAUNCH();
   const size_t E = (size_t)y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+  if (d_va || d_vm) {  // the voltage adjoint (the branch adjoint needs only w and V)
+    P.it.gva = (R*)w->tmp_c;  // gradient scratch: [N][Kp] R each
+    P.it.gvm = (R*)w->sbuf;
+    P.itb = P.it;
+    P.itb.rpb = w->rpb_b;
+    k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
+    CKLAUNCH();
+  }
   if (d_va) {
     k_widen<R><<<nb, 256, 0, s>>>((const R*)w->tmp_c, w->tmp_a, E, 1, 1.0);
     CKLAUNCH();
@@ -1463,34 +1505,31 @@ static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, doub
     CKLAUNCH();
     TRY(to_user(w, w->tmp_a, false, nullptr, d_q, s));
   }
-  if (d_g || d_b || d_bch) {
-    if (d_g) CK(cudaMemsetAsync(d_g, 0, (size_t)y->m * 8, s));
-    if (d_b) CK(cudaMemsetAsync(d_b, 0, (size_t)y->m * 8, s));
-    if (d_bch) CK(cudaMemsetAsync(d_bch, 0, (size_t)y->m * 8, s));
-    EdgeArgs<R> ea;
-    memset(&ea, 0, sizeof ea);
-    ea.M = y->m;
-    ea.K = w->K;
-    ea.Kp = w->Kp;
-    ea.lanes = w->lanes;
-    ea.br_f = y->dev.br_f;
-    ea.br_t = y->dev.br_t;
-    ea.tap = y->dev.br_tap;
-    ea.V = (const C*)w->V;
-    ea.W = (const C*)w->W;
-    ea.d_g = d_g;
-    ea.d_b = d_b;
-    ea.d_bch = d_bch;
-    const int rpw = 32 / w->lanes;
-    const int gy = std::max(1, std::min((y->m + w->warps * rpw - 1) / (w->warps * rpw), 65535));
-    k_edge_grad<R><<<dim3(w->gx, gy), P.block, 0, s>>>(ea);
-    CKLAUNCH();
-  }
+  if (d_g || d_b || d_bch) TRY(launch_edge_grad<R>(w, d_g, d_b, d_bch, s));
   if (loss) {
     TRY(launch_check<R>(w, s, true));
     CK(cudaMemcpyAsync(loss, w->out_loss, (size_t)w->K * 8, cudaMemcpyDeviceToDevice, s));
   }
   return DPF_OK;
+}
+
+// Y_bus values from caller series admittances (the workspace's local copy).
+static void rebuild_local_y(const dpf_ybus* y, dpf_workspace* w, const double* g_series, const double* b_series,
+                            cudaStream_t s) {
+  YValArgs ya;
+  ya.N = y->n;
+  ya.rp = y->dev.row_ptr;
+  ya.col = y->dev.col;
+  ya.ebr = y->dev.ebr;
+  ya.br_f = y->dev.br_f;
+  ya.g = g_series;
+  ya.b = b_series;
+  ya.bch = y->dev.br_bch;
+  ya.itap = y->dev.br_itap;
+  ya.ent32 = w->ent_loc;
+  ya.val64 = w->val_loc;
+  k_ybus_values<<<(y->n + 127) / 128, 128, 0, s>>>(ya);
+  w->use_local_y = true;
 }
 
 extern "C" int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* va,
@@ -1504,25 +1543,62 @@ extern "C" int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* w, int32_t n_
     return fail(DPF_E_INVALID, "g_series and b_series must be given together");
   TRY(eval_setup(y, w, n_case, precision, va, vm, p_spec, q_spec, outage, s));
   if (g_series) {
-    YValArgs ya;
-    ya.N = y->n;
-    ya.rp = y->dev.row_ptr;
-    ya.col = y->dev.col;
-    ya.ebr = y->dev.ebr;
-    ya.br_f = y->dev.br_f;
-    ya.g = g_series;
-    ya.b = b_series;
-    ya.bch = y->dev.br_bch;
-    ya.tap = y->dev.br_tap;
-    ya.ent32 = w->ent_loc;
-    ya.val64 = w->val_loc;
-    k_ybus_values<<<(y->n + 127) / 128, 128, 0, s>>>(ya);
+    rebuild_local_y(y, w, g_series, b_series, s);
     CKLAUNCH();
-    w->use_local_y = true;
   }
   const int rc = precision == DPF_FP64
                      ? loss_backward_impl<double>(w, loss, d_va, d_vm, d_p, d_q, d_g, d_b, d_bch, s)
                      : loss_backward_impl<float>(w, loss, d_va, d_vm, d_p, d_q, d_g, d_b, d_bch, s);
+  w->use_local_y = false;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Parameter identification: operating points staged once, then per step the
+// Y values from (g, b), the forward pass and the branch adjoint.
+// ---------------------------------------------------------------------------
+extern "C" int dpf_paramid_begin(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* va,
+                                 const double* vm, const double* p_spec, const double* q_spec, int32_t precision,
+                                 void* stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(eval_setup(y, w, n_case, precision, va, vm, p_spec, q_spec, nullptr, s));
+  w->pid_ready = true;
+  return DPF_OK;
+}
+
+template <class R>
+static int paramid_impl(dpf_workspace* w, double* d_g, double* d_b, double* d_bch, double* loss, cudaStream_t s) {
+  k_activate<<<(w->Kp + 255) / 256, 256, 0, s>>>(w->active, w->K, w->Kp);
+  Plan<R> P = make_plan<R>(w);
+  P.it.cbuf = nullptr;
+  P.it.loss_acc = nullptr;
+  P.it.mx32 = nullptr;
+  P.it.n_active = nullptr;
+  P.it.tile_cnt = nullptr;
+  k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);  // w = c conj(V) at the staged points (V unchanged)
+  CKLAUNCH();
+  if (d_g || d_b || d_bch) TRY(launch_edge_grad<R>(w, d_g, d_b, d_bch, s));
+  if (loss) {
+    TRY(launch_check<R>(w, s, true));
+    CK(cudaMemcpyAsync(loss, w->out_loss, (size_t)w->K * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  return DPF_OK;
+}
+
+extern "C" int dpf_paramid_step(const dpf_ybus* y, dpf_workspace* w, const double* g_series,
+                                const double* b_series, double* d_g, double* d_b, double* d_bch, double* loss,
+                                void* stream) {
+  clear_error();
+  if (!y || !w) return fail(DPF_E_INVALID, "dpf_paramid_step: NULL handle");
+  if (w->y != y) return fail(DPF_E_INVALID, "workspace was created for another Y_bus");
+  if (!w->pid_ready) return fail(DPF_E_STATE, "dpf_paramid_step: no operating points staged (dpf_paramid_begin)");
+  if (!g_series || !b_series) return fail(DPF_E_INVALID, "dpf_paramid_step: g_series and b_series are required");
+  cudaStream_t s = (cudaStream_t)stream;
+  rebuild_local_y(y, w, g_series, b_series, s);
+  CKLAUNCH();
+  const int rc = w->precision == DPF_FP64 ? paramid_impl<double>(w, d_g, d_b, d_bch, loss, s)
+                                          : paramid_impl<float>(w, d_g, d_b, d_bch, loss, s);
   w->use_local_y = false;
   return rc;
 }

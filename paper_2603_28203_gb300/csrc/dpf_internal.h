@@ -41,6 +41,7 @@ struct DeviceYbus {
   double* br_x = nullptr;
   double* br_bch = nullptr;
   double* br_tap = nullptr;
+  double* br_itap = nullptr;    // [m] 1 / tap (tap 0 read as 1): no division on the device
   uint8_t* bridge = nullptr;    // [m]
 };
 

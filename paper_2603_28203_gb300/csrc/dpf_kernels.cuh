@@ -1276,6 +1276,12 @@ __global__ void k_apply(ApplyArgs a) {
   }
 }
 
+// Re-activate the first K of Kp cases (a final convergence pass deactivates all).
+__global__ void k_activate(int32_t* __restrict__ active, int K, int Kp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < Kp) active[k] = (k < K) ? 1 : 0;
+}
+
 // ---- set-up / tear-down ----------------------------------------------------
 // Tiled transpose of a case-major [K][N] user-order FP64 array into the
 // case-minor internal layout [N][Kp] (row iperm[u] for user bus u).
@@ -1472,7 +1478,7 @@ struct YValArgs {
   const double* g;      // [M] user branch order
   const double* b;
   const double* bch;
-  const double* tap;
+  const double* itap;   // 1 / tap per branch
   int4* ent32;
   double2* val64;
 };
@@ -1485,12 +1491,12 @@ __global__ void k_ybus_values(YValArgs a) {
   for (int p = a.rp[i]; p < a.rp[i + 1]; ++p) {
     const int ell = a.ebr[p];
     if (ell < 0) { pd = p; continue; }
-    const double tau = (a.tap[ell] == 0.0) ? 1.0 : a.tap[ell];
+    const double it = a.itap[ell], it2 = it * it;
     const double gs = a.g[ell], bs = a.b[ell], sh = 0.5 * a.bch[ell];
-    const double vr = -gs / tau, vi = -bs / tau;
+    const double vr = -gs * it, vi = -bs * it;
     a.val64[p] = make_double2(vr, vi);
     a.ent32[p] = make_int4(a.col[p], __float_as_int((float)vr), __float_as_int((float)vi), 0);
-    if (a.br_f[ell] == i) { dr += gs / (tau * tau); di += (bs + sh) / (tau * tau); }
+    if (a.br_f[ell] == i) { dr += gs * it2; di += (bs + sh) * it2; }
     else { dr += gs; di += bs + sh; }
   }
   if (pd >= 0) {
@@ -1508,7 +1514,7 @@ template <class R> struct EdgeArgs {
   int M, K, Kp, lanes;
   const int32_t* br_f;
   const int32_t* br_t;
-  const double* tap;
+  const double* itap;  // 1 / tap per branch
   const C* V;
   const C* W;
   double* d_g;
@@ -1526,8 +1532,7 @@ __global__ void __launch_bounds__(1024) k_edge_grad(EdgeArgs<R> a) {
     R eg = 0, eb = 0, ec = 0;
     if (ell < a.M && k < a.K) {
       const int f = a.br_f[ell], t = a.br_t[ell];
-      const double tau = (a.tap[ell] == 0.0) ? 1.0 : a.tap[ell];
-      const R it = (R)(1.0 / tau), it2 = (R)(1.0 / (tau * tau));
+      const R it = (R)a.itap[ell], it2 = it * it;
       const size_t Kp = (size_t)a.Kp;
       const C wf = a.W[(size_t)f * Kp + k], wt = a.W[(size_t)t * Kp + k];
       const C vf = a.V[(size_t)f * Kp + k], vt = a.V[(size_t)t * Kp + k];

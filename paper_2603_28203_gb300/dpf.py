@@ -342,6 +342,32 @@ def dpf_loss_backward(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, 
     return out
 
 
+def dpf_paramid_begin(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, precision=_abi.FP32, stream=None):
+    """Stage K measured operating points ([K][N] float64 CUDA tensors) for dpf_paramid_step."""
+    _check(lib().dpf_paramid_begin(y.handle, ws.handle, int(va.shape[0]), _ptr(va), _ptr(vm), _ptr(p_spec),
+                                   _ptr(q_spec), int(precision), _stream(stream)))
+    ws.pid_cases = int(va.shape[0])
+
+
+def dpf_paramid_step(y: Ybus, ws: Workspace, g_series, b_series, want=("d_g", "d_b"), out=None, stream=None):
+    """Branch gradients (and optionally the loss) at the staged operating points.
+
+    `out` may hold preallocated float64 CUDA tensors by name (reused across
+    steps); missing ones are allocated.  Returns the dict of requested outputs.
+    """
+    import torch
+    M = y.n_branch
+    out = dict(out or {})
+    for name in want:
+        if name not in out:
+            n = getattr(ws, "pid_cases", 0) if name == "loss" else M
+            out[name] = torch.empty(n, dtype=torch.float64, device=g_series.device)
+    g = [out.get(n) if n in want else None for n in ("d_g", "d_b", "d_bch", "loss")]
+    _check(lib().dpf_paramid_step(y.handle, ws.handle, _ptr(g_series), _ptr(b_series),
+                                  *[_ptr(t) for t in g], _stream(stream)))
+    return {k: out[k] for k in want}
+
+
 def dpf_adam_update(x, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, lr_scale=None, stream=None):
     """One Adam step on device float64 vectors (in place on x, m, v)."""
     _check(lib().dpf_adam_update(int(x.numel()), _ptr(x), _ptr(grad), _ptr(m), _ptr(v), _ptr(lr_scale), int(t),

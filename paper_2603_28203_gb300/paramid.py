@@ -6,9 +6,10 @@ the simulation parameters, which "allows these parameters to be identified"
 points (V = |V| e^{j theta} and the injections P, Q at every bus), the series
 admittances g + jb of every branch are adjusted by Adam to minimise the sum
 over operating points of the DPF loss of Alg. 1 at those fixed voltages.
-The gradient comes from dpf_loss_backward's branch adjoint (k_edge_grad, Y
-values rebuilt by k_ybus_values) and the step from dpf_adam_update; the
-learning rate of each parameter is scaled by its starting magnitude, so a
+The operating points are staged once (dpf_paramid_begin); each step takes
+the branch gradient from dpf_paramid_step (Y values rebuilt by k_ybus_values,
+forward pass, branch adjoint k_edge_grad) and the step from dpf_adam_update;
+the learning rate of each parameter is scaled by its starting magnitude, so a
 step is a relative change of about `lr`.
 """
 from __future__ import annotations
@@ -16,7 +17,7 @@ from __future__ import annotations
 import torch
 
 from . import _abi
-from .dpf import Workspace, Ybus, dpf_adam_update, dpf_loss_backward
+from .dpf import Workspace, Ybus, dpf_adam_update, dpf_paramid_begin, dpf_paramid_step
 
 
 def identify_branches(y: Ybus, ws: Workspace, va, vm, p, q, g0, b0, iters: int, lr: float = 3e-3,
@@ -27,10 +28,12 @@ def identify_branches(y: Ybus, ws: Workspace, va, vm, p, q, g0, b0, iters: int, 
     mg, vg, mb, vb = (torch.zeros_like(g0) for _ in range(4))
     sg, sb = g0.abs(), b0.abs()
     hist = []
+    dpf_paramid_begin(y, ws, va, vm, p, q, precision=precision, stream=stream)
+    bufs = {}
     for t in range(1, iters + 1):
         want = ("d_g", "d_b", "loss") if (record_every and t % record_every == 0) else ("d_g", "d_b")
-        out = dpf_loss_backward(y, ws, va, vm, p, q, g_series=g, b_series=b, precision=precision, want=want,
-                                stream=stream)
+        out = dpf_paramid_step(y, ws, g, b, want=want, out=bufs, stream=stream)
+        bufs.update(out)
         if "loss" in out:
             hist.append((t, float(out["loss"].sum().item())))
         dpf_adam_update(g, out["d_g"], mg, vg, t, lr, betas[0], betas[1], lr_scale=sg, stream=stream)

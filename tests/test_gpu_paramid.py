@@ -94,3 +94,39 @@ def test_paramid_fp32_reduces_error(case):
     e1 = np.median(np.abs(b.cpu().numpy() - ys_true.imag) / np.abs(ys_true.imag))
     assert hist[-1][1] < 0.05 * hist[0][1] or hist[-1][1] < 1e-6
     assert e1 < 0.5 * e0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_paramid_step_matches_loss_backward(case, precision):
+    """The staged step gives dpf_loss_backward's branch gradients and loss for the
+    same inputs, on every step (the loss pass does not disturb the staged points)."""
+    cat, va, vm, P, Q, ys_true, ys0 = case
+    prec = dict(fp64=dpf.FP64, fp32=dpf.FP32)[precision]
+    y = dpf.dpf_build_ybus(cat)
+    ws = dpf.dpf_workspace_create(y, va.shape[0])
+    g, b = _t(ys0.real), _t(ys0.imag)
+    ref = dpf.dpf_loss_backward(y, ws, _t(va), _t(vm), _t(P), _t(Q), g_series=g, b_series=b, precision=prec,
+                                want=("loss", "d_g", "d_b"))
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    dpf.dpf_paramid_begin(y, ws, _t(va), _t(vm), _t(P), _t(Q), precision=prec)
+    for _ in range(3):
+        out = dpf.dpf_paramid_step(y, ws, g, b, want=("d_g", "d_b", "loss"))
+        out = {k: v.cpu().numpy() for k, v in out.items()}
+        for k in ("d_g", "d_b", "loss"):
+            assert np.allclose(out[k], ref[k], rtol=1e-12, atol=1e-14 * np.abs(ref[k]).max()), k
+
+
+def test_paramid_step_needs_staged_points(case):
+    cat, va, vm, P, Q, ys_true, ys0 = case
+    y = dpf.dpf_build_ybus(cat)
+    ws = dpf.dpf_workspace_create(y, va.shape[0])
+    g, b = _t(ys0.real), _t(ys0.imag)
+    with pytest.raises(dpf.DPFError) as e:
+        dpf.dpf_paramid_step(y, ws, g, b)
+    assert e.value.code == -6  # DPF_E_STATE
+    dpf.dpf_paramid_begin(y, ws, _t(va), _t(vm), _t(P), _t(Q))
+    dpf.dpf_paramid_step(y, ws, g, b)
+    dpf.dpf_power(y, ws, _t(va), _t(vm))  # another use of the workspace drops the staged points
+    with pytest.raises(dpf.DPFError) as e:
+        dpf.dpf_paramid_step(y, ws, g, b)
+    assert e.value.code == -6
