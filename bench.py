@@ -598,6 +598,66 @@ def run_uneven(args):
     y.free()
 
 
+def run_timeseries(args):
+    """The time-series workload: the 10,000-bus grid over `--ts-hours` hourly
+    snapshots (default the year, 8,760) of the load model, solved in windows
+    of 96 by the library's warm-start driver with Table 3's settings (the
+    first window flat, each later one from the previous window's solutions),
+    FP32 iterations with the FP64 test.  Times the whole series (injections
+    in, solutions out).  The FP64 oracle recomputes the mismatch of sampled
+    snapshots from the returned voltages and compares it with the reported
+    one.  One JSON line."""
+    import torch
+    import gridgen
+    import oracle
+    from oracle.ybus import grid_ybus
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    from paper_2603_28203_gb300.timeseries import solve_time_series
+    g = gridgen.config_grid("c4_timeseries_10kbus")
+    T = args.ts_hours
+    P, Q = gridgen.time_series(g, T, seed=4)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    y = dpf.dpf_build_ybus(g, stream=stream)
+    ws = dpf.dpf_workspace_create(y, 96)
+    with torch.cuda.stream(stream):
+        solve_time_series(y, ws, P[:96], Q[:96], window=96, stream=stream)  # warm-up (first window)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = solve_time_series(y, ws, P, Q, window=96, stream=stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    Y = grid_ybus(g)
+    rng = np.random.default_rng(0)
+    sample = sorted(set([0, 95, 96, T - 1] + [int(t) for t in rng.choice(T, 4, replace=False)]))
+    err = 0.0
+    for t in sample:
+        f, _ = oracle.mismatch(Y, out["va"][t], out["vm"][t], P[t], Q[t], g.bus_type)
+        err = max(err, abs(float(np.max(np.abs(f))) - float(out["max_mismatch"][t])))
+    st = out["status"]
+    it = out["iters"]
+    print(json.dumps({
+        "workload": "timeseries",
+        "config": {"grid": "c4_timeseries_10kbus", "n_bus": int(g.n_bus), "n_branch": int(g.n_branch),
+                   "snapshots": int(T), "window": 96, "settings": "Table 3 (first window flat, later warm)",
+                   "precision": "fp32 iterations, FP64 master and test", "tol_pu": 1e-6},
+        "wall_s": wall,
+        "snapshots_per_s": T / wall,
+        "iterations_total": int(it.sum()),
+        "iterations_p50": float(np.median(it)), "iterations_first_window_p50": float(np.median(it[:96])),
+        "status_counts": {str(k): int((st == k).sum()) for k in (0, 1, 2)},
+        "max_mismatch_p50": float(np.median(out["max_mismatch"])),
+        "max_mismatch_p99": float(np.percentile(out["max_mismatch"], 99)),
+        "sampled_snapshots": sample,
+        "reported_vs_fp64_oracle_mismatch_max_abs_diff": err,
+    }), flush=True)
+    ws.free()
+    y.free()
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -649,10 +709,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven"],
-                    help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep")
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries"],
+                    help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep; "
+                         "uneven: 64-grid block-diagonal batch + parameter identification; "
+                         "timeseries: the 10k-bus grid over a year of hourly snapshots")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--uneven-iters", type=int, default=300)
+    ap.add_argument("--ts-hours", type=int, default=8760)
     ap.add_argument("--uneven-pid-steps", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
@@ -675,6 +738,8 @@ def main():
         run_scaling(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "timeseries":
+        run_timeseries(args)
     else:
         run_ours(args)
 
