@@ -658,6 +658,103 @@ def run_timeseries(args):
     y.free()
 
 
+def _nr_point_worker(item):
+    """FP64 oracle Newton-Raphson of one grid at one operating point."""
+    import oracle
+    from oracle.ybus import grid_ybus
+    g, p, q = item
+    r = oracle.nr_solve(grid_ybus(g), p, q, g.bus_type, g.vm_set)
+    return r["va"], r["vm"], bool(r["converged"])
+
+
+def run_paramid(args):
+    """Parameter identification against the ground truth (the uneven-batch
+    experiment at a size the FP64 oracle can measure): `--pid-grids` synthetic
+    grids of log-uniform 300-3,000 buses in one block-diagonal batch, 16 hourly
+    operating points measured by the oracle's Newton-Raphson at the true branch
+    parameters, branch r and x perturbed by U(-10%, +10%), then Adam on the
+    series g, b of every branch from the branch adjoint (dpf_paramid_step).
+    Reports the relative errors of r and x before and after, the loss, and the
+    time per step.  One JSON line."""
+    import multiprocessing as mp
+    import gridgen
+    sizes = gridgen.uneven_sizes(args.pid_grids, 200, lo=300, hi=3000)
+    grids = [gridgen.make_grid(int(n), 2000 + i, load_scale=0.1) for i, n in enumerate(sizes)]
+    cat = gridgen.concat_grids(grids)
+    K, H = 16, 48  # 16 operating points: the first hours at which every grid has a power-flow solution
+    P, Q = gridgen.time_series(cat, H, seed=5)
+    off = np.cumsum([0] + [g.n_bus for g in grids])
+    items = []
+    for gi, g in enumerate(grids):
+        sl = slice(off[gi], off[gi + 1])
+        for k in range(H):
+            items.append((g, P[k, sl], Q[k, sl]))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(len(os.sched_getaffinity(0))) as pool:  # before any CUDA call
+        res = pool.map(_nr_point_worker, items)
+    t_nr = time.perf_counter() - t0
+    va = np.zeros((H, cat.n_bus))
+    vm = np.zeros((H, cat.n_bus))
+    ok = np.ones(H, bool)
+    for j, (a, m, conv) in enumerate(res):
+        gi, k = divmod(j, H)
+        va[k, off[gi]:off[gi + 1]] = a
+        vm[k, off[gi]:off[gi + 1]] = m
+        ok[k] &= conv
+    import torch
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    from paper_2603_28203_gb300.paramid import identify_branches
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    kk = np.where(ok)[0][:K]
+    t = lambda a: torch.tensor(np.ascontiguousarray(a[kk]), dtype=torch.float64, device=dev)
+    y = dpf.dpf_build_ybus(cat, stream=stream)
+    ws = dpf.dpf_workspace_create(y, len(kk))
+    z_true = cat.r + 1j * cat.x
+    pert = gridgen.perturb_branches(cat, 5)
+    ys0 = 1.0 / (pert.r + 1j * pert.x)
+    g0 = torch.tensor(ys0.real, dtype=torch.float64, device=dev)
+    b0 = torch.tensor(ys0.imag, dtype=torch.float64, device=dev)
+    n = args.pid_steps
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g, b, hist = identify_branches(y, ws, t(va), t(vm), t(P), t(Q), g0, b0, n, lr=args.pid_lr,
+                                       precision=dpf.FP32, record_every=max(1, n // 4), stream=stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out0 = dpf.dpf_loss_backward(y, ws, t(va), t(vm), t(P), t(Q), g_series=g0, b_series=b0,
+                                     precision=dpf.FP64, want=("loss",), stream=stream)
+        out1 = dpf.dpf_loss_backward(y, ws, t(va), t(vm), t(P), t(Q), g_series=g, b_series=b,
+                                     precision=dpf.FP64, want=("loss",), stream=stream)
+        stream.synchronize()
+    z1 = 1.0 / (g.cpu().numpy() + 1j * b.cpu().numpy())
+    z0 = pert.r + 1j * pert.x
+    rel = lambda a, b_: np.abs(a - b_) / np.abs(b_)
+    def stats(z):
+        er, ex = rel(z.real, z_true.real), rel(z.imag, z_true.imag)
+        return {"r_median": float(np.median(er)), "r_max": float(er.max()),
+                "x_median": float(np.median(ex)), "x_max": float(ex.max())}
+    print(json.dumps({
+        "workload": "paramid",
+        "config": {"grids": int(len(sizes)), "bus_sizes": "log-uniform 300-3,000 (seed 200)",
+                   "n_bus": int(cat.n_bus), "n_branch": int(cat.n_branch), "operating_points": int(len(kk)),
+                   "hours_with_a_solution": f"{int(ok.sum())} of the first {H}",
+                   "measurements": "FP64 oracle Newton-Raphson at the true parameters",
+                   "perturbation": "r, x x U(0.9, 1.1) per branch (seed 5)",
+                   "steps": n, "lr": args.pid_lr, "precision": "fp32 adjoint, FP64 loss"},
+        "oracle_nr_s": t_nr,
+        "error_before": stats(z0), "error_after": stats(z1),
+        "loss_fp64_before": float(out0["loss"].sum()), "loss_fp64_after": float(out1["loss"].sum()),
+        "ms_per_step": 1e3 * wall / n,
+    }), flush=True)
+    ws.free()
+    y.free()
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -709,13 +806,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries"],
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid"],
                     help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep; "
                          "uneven: 64-grid block-diagonal batch + parameter identification; "
-                         "timeseries: the 10k-bus grid over a year of hourly snapshots")
+                         "timeseries: the 10k-bus grid over a year of hourly snapshots; "
+                         "paramid: branch identification against the oracle's operating points")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--uneven-iters", type=int, default=300)
     ap.add_argument("--ts-hours", type=int, default=8760)
+    ap.add_argument("--pid-grids", type=int, default=16)
+    ap.add_argument("--pid-steps", type=int, default=4000)
+    ap.add_argument("--pid-lr", type=float, default=3e-3)
     ap.add_argument("--uneven-pid-steps", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
@@ -740,6 +841,8 @@ def main():
         run_uneven(args)
     elif args.workload == "timeseries":
         run_timeseries(args)
+    elif args.workload == "paramid":
+        run_paramid(args)
     else:
         run_ours(args)
 
