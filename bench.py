@@ -755,6 +755,86 @@ def run_paramid(args):
     y.free()
 
 
+def dc_bytes_per_iteration(n_bus, nnz, n_case):
+    """Bytes one CG iteration of dpf_dc_solve must move (FP64): per element,
+    k_dc_spmv reads p and writes q (16), k_dc_update reads p, q, x, r and
+    writes x, r, z (56), k_dc_dir reads z, p and writes p (24); B in CSR
+    (8 B value + 4 B column per nonzero, row pointers, diagonal positions)
+    and the bus types once per launch of the row kernels."""
+    shared = 12 * nnz + 8 * (n_bus + 1) + n_bus
+    return n_case * n_bus * (16 + 56 + 24) + 3 * shared
+
+
+def run_dc(args):
+    """The DC approximation (Sec. 2's comparison model, Alg. 2's optional
+    initialisation) on the N-1 batch: dpf_dc_solve's batched CG for all
+    2,379 cases (relative residual 1e-10), sampled cases against the oracle,
+    and Alg. 1 from the DC angles vs from the flat start after the same
+    number of iterations.  One JSON line."""
+    import torch
+    import oracle
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    g, outages = _workload()
+    K = outages.size
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    y = dpf.dpf_build_ybus(g, stream=stream)
+    ws = dpf.dpf_workspace_create(y, K)
+    od = torch.tensor(outages, dtype=torch.int32, device=dev)
+    with torch.cuda.stream(stream):
+        dpf.dpf_dc_solve(y, ws, K, outage=od, tol=1e-10, stream=stream)  # warm-up
+        stream.synchronize()
+        t0 = time.perf_counter()
+        out = dpf.dpf_dc_solve(y, ws, K, outage=od, tol=1e-10, stream=stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+    it = out["iters"].cpu().numpy()
+    th = out["va"].cpu().numpy()
+    rng = np.random.default_rng(0)
+    err = 0.0
+    for k in sorted(set([0, K - 1] + [int(v) for v in rng.choice(K, 4, replace=False)])):
+        ref = oracle.dc_solve(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, g.p_spec, va_slack=g.va_slack,
+                              outage=int(outages[k]))
+        err = max(err, float(np.abs(th[k] - ref).max() / np.abs(ref).max()))
+    # Alg. 1 from the DC angles vs flat, same iteration budget
+    mm = {}
+    for start in ("flat", "dc"):
+        res = dict(va=torch.empty((K, g.n_bus), dtype=torch.float64, device=dev),
+                   vm=torch.empty((K, g.n_bus), dtype=torch.float64, device=dev),
+                   status=torch.empty(K, dtype=torch.int32, device=dev),
+                   max_mismatch=torch.empty(K, dtype=torch.float64, device=dev))
+        opts = dpf.SolveOpts(lr=LR, tol=TOL, check_every=CHECK_EVERY, max_iter=ITERS_PER_SOLVE,
+                             dc_start=1 if start == "dc" else 0)
+        with torch.cuda.stream(stream):
+            dpf.dpf_solve_batch(y, ws, opts, stream=stream, n_case=K, outage=od, **res)
+            stream.synchronize()
+        m = res["max_mismatch"].cpu().numpy()
+        mm[start] = {"p50": float(np.median(m)), "max": float(m.max()),
+                     "converged": int((res["status"].cpu().numpy() == 0).sum())}
+    iters_max = int(it.max())
+    b = dc_bytes_per_iteration(g.n_bus, y.nnz, K)
+    peak, src = _peaks()
+    print(json.dumps({
+        "workload": "dc",
+        "config": {"grid": "c3_n1_2kbus", "n_bus": int(g.n_bus), "cases": int(K), "tol_rel_residual": 1e-10,
+                   "solver": "Jacobi-preconditioned CG, FP64, all cases batched"},
+        "wall_ms": 1e3 * wall,
+        "cg_iterations_max": iters_max, "cg_iterations_p50": float(np.median(it)),
+        "us_per_cg_iteration": 1e6 * wall / max(iters_max, 1),
+        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src,
+                     "achieved": b * iters_max / wall / 1e9, "frac": b * iters_max / wall / 1e9 / peak,
+                     "algorithmic_bytes_per_iteration": b,
+                     "note": "all cases run until the slowest converges (host polls every 16 iterations)"},
+        "max_rel_error_vs_oracle_sampled": err,
+        "alg1_after_1000_iterations": mm,
+    }), flush=True)
+    ws.free()
+    y.free()
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -806,11 +886,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid"],
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc"],
                     help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep; "
                          "uneven: 64-grid block-diagonal batch + parameter identification; "
                          "timeseries: the 10k-bus grid over a year of hourly snapshots; "
-                         "paramid: branch identification against the oracle's operating points")
+                         "paramid: branch identification against the oracle's operating points; "
+                         "dc: the DC approximation of the N-1 batch (and Alg. 1 started from it)")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--uneven-iters", type=int, default=300)
     ap.add_argument("--ts-hours", type=int, default=8760)
@@ -843,6 +924,8 @@ def main():
         run_timeseries(args)
     elif args.workload == "paramid":
         run_paramid(args)
+    elif args.workload == "dc":
+        run_dc(args)
     else:
         run_ours(args)
 

@@ -184,6 +184,9 @@ typedef struct {
                                 host stop test (FP64 check + device-to-host
                                 read) after every iteration; check_every is
                                 taken as 1.  Used as the unbatched baseline. */
+  int32_t dc_start;          /* 1 (with flat_start): the angles start from the
+                                DC approximation (dpf_dc_solve, relative
+                                residual 1e-10), |V| from the flat start    */
 } dpf_solve_opts;
 
 void dpf_default_opts(dpf_solve_opts* o);
@@ -297,6 +300,24 @@ int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
                       double* loss, double* d_va, double* d_vm,
                       double* d_p, double* d_q,
                       double* d_g, double* d_b, double* d_bch, void* stream);
+
+/* ---- DC approximation ------------------------------------------------------
+ * The linearised comparison model and optional initialisation (Sec. 2,
+ * Alg. 2): angles solving B theta = P over the pv and pq buses, with
+ * B = sum_l b_l (e_f - e_t)(e_f - e_t)^T, b_l = 1 / (x_l tau_l) (resistance,
+ * charging and |V| ignored), slack angles fixed at the grid's va_slack (one
+ * slack per island).  For n_case cases: p_spec [n_case][n_bus] FP64 device
+ * (NULL = the grid's), outage [n_case] device (-1 = none; NULL = none; a
+ * bridge is DPF_E_ISLANDED) as for dpf_solve_batch.  Conjugate gradients
+ * with the Jacobi preconditioner in FP64 on the GPU, per case until
+ * |r| <= tol |r0| or max_iter iterations.  Outputs (caller-owned device
+ * arrays): va [n_case][n_bus] (required), iters [n_case] and rel_residual
+ * [n_case] (|r| / |r0| at the stop; either may be NULL).  Uses (and
+ * resets) the workspace like the other calls. */
+int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
+                 const double* p_spec, const int32_t* outage, double tol,
+                 int32_t max_iter, double* va, int32_t* iters,
+                 double* rel_residual, void* stream);
 
 /* ---- parameter identification over measured operating points -------------
  * The gradient of the loss to the branch parameters (Sec. 1 / abstract:

@@ -51,6 +51,7 @@ class DpfSolveOpts(C.Structure):
         ("lanes", C.c_int32), ("warps", C.c_int32), ("row_blocks", C.c_int32),
         ("use_graph", C.c_int32), ("pair_cases", C.c_int32), ("pdl", C.c_int32), ("stage_v", C.c_int32),
         ("plain", C.c_int32),
+        ("dc_start", C.c_int32),
     ]
 
 
@@ -81,6 +82,7 @@ SIGNATURES = {
                                     VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "dpf_power_noalloc": (C.c_int, [VP, I32, VP, VP, VP, VP, VP]),
     "dpf_paramid_begin": (C.c_int, [VP, VP, I32, VP, VP, VP, VP, I32, VP]),
+    "dpf_dc_solve": (C.c_int, [VP, VP, I32, VP, VP, C.c_double, I32, VP, VP, VP, VP]),
     "dpf_paramid_step": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "dpf_profile_enable": (C.c_int, [VP, I32]),
     "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),

@@ -10,6 +10,7 @@
 
 #include "dpf_internal.h"
 #include "dpf_kernels.cuh"
+#include "dpf_dc.cuh"
 
 using namespace dpf;
 
@@ -104,7 +105,7 @@ int pow2ceil(int v) {
 // Y_bus upload
 // ---------------------------------------------------------------------------
 static void free_device(DeviceYbus& d) {
-  dfree(d.ent32); dfree(d.row_ptr); dfree(d.prow_ptr); dfree(d.ppos); dfree(d.col); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
+  dfree(d.ent32); dfree(d.row_ptr); dfree(d.prow_ptr); dfree(d.ppos); dfree(d.col); dfree(d.dcval); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
   dfree(d.type); dfree(d.p64); dfree(d.q64); dfree(d.vmset); dfree(d.p32); dfree(d.q32);
   dfree(d.perm); dfree(d.iperm); dfree(d.br_f); dfree(d.br_t); dfree(d.br_r); dfree(d.br_x);
   dfree(d.br_bch); dfree(d.br_tap); dfree(d.br_itap); dfree(d.bridge);
@@ -143,12 +144,22 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
     q32[i] = (float)q64[i];
   }
   std::vector<int32_t> bf(m), bt(m);
-  std::vector<double> itap(m);
+  std::vector<double> itap(m), bdc(m);
   for (int e = 0; e < m; ++e) {
     bf[e] = y->iperm[y->f_bus[e]];
     bt[e] = y->iperm[y->t_bus[e]];
     itap[e] = 1.0 / (y->tap[e] == 0.0 ? 1.0 : y->tap[e]);
+    bdc[e] = itap[e] / y->x[e];  // DC susceptance 1 / (x tau)
   }
+  // DC matrix B in the internal CSR: -b_l off the diagonal, sum of b_l on it
+  std::vector<double> dcval(nnz, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int p = y->irow_ptr[i]; p < y->irow_ptr[i + 1]; ++p) {
+      const int l = y->iebr[p];
+      if (l < 0) continue;
+      dcval[p] = -bdc[l];
+      dcval[y->idpos[i]] += bdc[l];
+    }
   int rc = DPF_OK;
   do {
     if ((rc = upload(&d.ent32, ent, s))) break;
@@ -157,6 +168,7 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
     if ((rc = upload(&d.ppos, y->ippos, s))) break;
     if ((rc = upload(&d.col, y->icol, s))) break;
     if ((rc = upload(&d.val64, v64, s))) break;
+    if ((rc = upload(&d.dcval, dcval, s))) break;
     if ((rc = upload(&d.ebr, y->iebr, s))) break;
     if ((rc = upload(&d.dpos, y->idpos, s))) break;
     if ((rc = upload(&d.type, type, s))) break;
@@ -241,6 +253,9 @@ struct dpf_workspace {
   int32_t* n_active = nullptr;
   int32_t* h_n_active = nullptr;  // pinned
   unsigned int* tile_cnt = nullptr;  // per case tile, for the forward pass's scheduler
+  double* dcs = nullptr;     // DC solver, per case: rz, rz', pq, rr, rr0, beta, res, b_out ([8][Kp])
+  int32_t* dci = nullptr;    // DC solver, per case: active, iters ([2][Kp]), then its active count
+  int32_t* h_dc_nact = nullptr;  // pinned
   int cap_tiles = 0;
   // user-layout staging for host_io
   double *st_a = nullptr, *st_b = nullptr, *st_c = nullptr;
@@ -284,6 +299,7 @@ static void ws_free_buffers(dpf_workspace* w) {
   dfree(w->lr); dfree(w->best); dfree(w->out_max); dfree(w->out_loss); dfree(w->loss64);
   dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
   dfree(w->b1t); dfree(w->b2t); dfree(w->cand); dfree(w->mx32);
+  dfree(w->dcs); dfree(w->dci);
   dfree(w->st_a); dfree(w->st_b); dfree(w->st_c);
   dfree(w->d_wlo); dfree(w->d_whi);
   w->cap_wblocks = 0;
@@ -324,6 +340,7 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     dfree(w->cool); dfree(w->lr); dfree(w->best); dfree(w->out_max); dfree(w->out_loss); dfree(w->loss64);
     dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
     dfree(w->b1t); dfree(w->b2t); dfree(w->cand); dfree(w->mx32);
+    dfree(w->dcs); dfree(w->dci);
     w->cap_elems = 0;
     w->cap_cases = 0;
     char** bufs16[] = {(char**)&w->V, (char**)&w->W, (char**)&w->G0, (char**)&w->V64, (char**)&w->sbuf,
@@ -346,6 +363,7 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     TRY(dalloc(&w->yff64, Kp)); TRY(dalloc(&w->yft64, Kp)); TRY(dalloc(&w->ytt64, Kp));
     TRY(dalloc(&w->maxmis, Kp)); TRY(dalloc(&w->outage_dev, Kp));
     TRY(dalloc(&w->b1t, Kp)); TRY(dalloc(&w->b2t, Kp)); TRY(dalloc(&w->cand, Kp)); TRY(dalloc(&w->mx32, Kp));
+    TRY(dalloc(&w->dcs, (size_t)8 * Kp)); TRY(dalloc(&w->dci, (size_t)2 * Kp + 1));
     CK(cudaMemset(w->p64, 0, E * 8));
     CK(cudaMemset(w->q64, 0, E * 8));
     w->cap_elems = E;
@@ -380,6 +398,8 @@ extern "C" int dpf_workspace_create(const dpf_ybus* y, int32_t max_case, dpf_wor
     if ((rc = dalloc(&w->n_active, 1))) break;
     cudaError_t e = cudaMallocHost((void**)&w->h_n_active, sizeof(int32_t));
     if (e != cudaSuccess) { rc = fail(DPF_E_OOM, "cudaMallocHost: %s", cudaGetErrorString(e)); break; }
+    e = cudaMallocHost((void**)&w->h_dc_nact, sizeof(int32_t));
+    if (e != cudaSuccess) { rc = fail(DPF_E_OOM, "cudaMallocHost: %s", cudaGetErrorString(e)); break; }
     e = cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { rc = fail(DPF_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)); break; }
     const int Kp = max_case <= 16 ? pow2ceil(max_case) : (max_case + 31) / 32 * 32;
@@ -401,6 +421,7 @@ extern "C" int dpf_workspace_free(dpf_workspace* w) {
   ws_free_buffers(w);
   dfree(w->n_active);
   if (w->h_n_active) cudaFreeHost(w->h_n_active);
+  if (w->h_dc_nact) cudaFreeHost(w->h_dc_nact);
   if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
   delete w;
   return DPF_OK;
@@ -1008,6 +1029,7 @@ static int validate_opts(const dpf_solve_opts* o) {
   if (o->precision != DPF_FP32 && o->precision != DPF_FP64) return fail(DPF_E_INVALID, "unknown precision");
   if (!(o->gate >= 0.0)) return fail(DPF_E_INVALID, "gate must be >= 0");
   if (o->pdl != 0 && o->pdl != 1) return fail(DPF_E_INVALID, "pdl must be 0 or 1");
+  if (o->dc_start != 0 && o->dc_start != 1) return fail(DPF_E_INVALID, "dc_start must be 0 or 1");
   if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 8 || o->row_blocks < 0)
     return fail(DPF_E_INVALID, "invalid launch shape (lanes 0..32, warps 0..8, row_blocks >= 0)");
   return DPF_OK;
@@ -1024,6 +1046,109 @@ static int common_checks(const dpf_ybus* y, dpf_workspace* w, int K) {
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != y->dev.device) return fail(DPF_E_STATE, "current device %d differs from the Y_bus device %d", dev, y->dev.device);
+  return DPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DC approximation (batched Jacobi-preconditioned CG, FP64); the solution x
+// is left in w->tmp_a ([N][Kp]); needs the specification and outages staged by
+// init_state.
+// ---------------------------------------------------------------------------
+__global__ void k_dc_set_count(int32_t* n, int K) { *n = K; }
+
+static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int max_iter, cudaStream_t s) {
+  const dpf_ybus* y = w->y;
+  const DeviceYbus& d = y->dev;
+  const int Kp = w->Kp;
+  DCArgs a;
+  memset(&a, 0, sizeof a);
+  a.N = y->n;
+  a.Kp = Kp;
+  a.lanes = w->lanes;
+  a.K = w->K;
+  a.rp = d.row_ptr;
+  a.col = d.col;
+  a.bval = d.dcval;
+  a.dpos = d.dpos;
+  a.type = d.type;
+  a.spec_per_case = w->spec_per_case ? 1 : 0;
+  a.pspec = w->spec_per_case ? w->p64 : d.p64;
+  a.va_slack = y->va_slack;
+  a.of = w->has_outage ? w->of : nullptr;
+  a.ot = w->has_outage ? w->ot : nullptr;
+  a.x = w->tmp_a;
+  a.r = w->tmp_b;
+  a.z = w->tmp_c;
+  a.p = (double*)w->V64;
+  a.q = (double*)w->sbuf;
+  double* c = w->dcs;
+  a.rz = c;
+  a.rzn = c + Kp;
+  a.pq = c + 2 * (size_t)Kp;
+  a.rr = c + 3 * (size_t)Kp;
+  a.rr0 = c + 4 * (size_t)Kp;
+  a.beta = c + 5 * (size_t)Kp;
+  a.res = c + 6 * (size_t)Kp;
+  a.ob = c + 7 * (size_t)Kp;
+  a.active = w->dci;
+  a.iters = w->dci + Kp;
+  a.n_active = w->dci + 2 * (size_t)Kp;
+  a.tol2 = tol * tol;
+  const dim3 grid(Kp / w->lanes, w->gy), block(w->warps * 32);
+  const int cb = (Kp + 255) / 256;
+  const size_t E = (size_t)y->n * Kp;
+  const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+  k_dc_case_init<<<cb, 256, 0, s>>>(a, outage_dev, d.br_x, d.br_tap);
+  k_dc_set_count<<<1, 1, 0, s>>>(a.n_active, w->K);
+  k_dc_x0<<<std::max(nb, 1), 256, 0, s>>>(a);
+  k_dc_start<<<grid, block, 0, s>>>(a);
+  CKLAUNCH();
+  for (int it = 0; it < max_iter; ++it) {
+    k_dc_spmv<<<grid, block, 0, s>>>(a);
+    k_dc_update<<<grid, block, 0, s>>>(a);
+    k_dc_case<<<cb, 256, 0, s>>>(a);
+    k_dc_dir<<<grid, block, 0, s>>>(a);
+    CKLAUNCH();
+    if ((it & 15) == 15 || it == max_iter - 1) {
+      CK(cudaMemcpyAsync(w->h_dc_nact, a.n_active, 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*w->h_dc_nact == 0) break;
+    }
+  }
+  return DPF_OK;
+}
+
+extern "C" int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* p_spec,
+                            const int32_t* outage, double tol, int32_t max_iter, double* va, int32_t* iters,
+                            double* rel_residual, void* stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(common_checks(y, w, n_case));
+  if (!va) return fail(DPF_E_INVALID, "dpf_dc_solve: va is required");
+  if (!(tol > 0) || max_iter < 1) return fail(DPF_E_INVALID, "dpf_dc_solve: tol > 0 and max_iter >= 1 required");
+  w->begun = false;
+  w->pid_ready = false;
+  ws_drop_graph(w);
+  dpf_default_opts(&w->opts);
+  w->opts.precision = DPF_FP64;
+  w->precision = DPF_FP64;
+  w->K = n_case;
+  choose_shape(w, nullptr, n_case);
+  TRY(upload_windows(w, s));
+  TRY(ws_reserve(w, w->Kp, 0));
+  StateIn in;
+  memset(&in, 0, sizeof in);
+  in.K = n_case;
+  in.enforce_fixed = true;
+  in.p = p_spec;
+  in.q = p_spec;  // (the DC model reads only P)
+  in.outage = outage;
+  TRY(init_state<double>(w, in, s));
+  TRY(dc_run(w, outage, tol, max_iter, s));
+  TRY(to_user(w, w->tmp_a, false, nullptr, va, s));
+  if (iters) CK(cudaMemcpyAsync(iters, w->dci + w->Kp, (size_t)n_case * 4, cudaMemcpyDeviceToDevice, s));
+  if (rel_residual)
+    CK(cudaMemcpyAsync(rel_residual, w->dcs + 6 * (size_t)w->Kp, (size_t)n_case * 8, cudaMemcpyDeviceToDevice, s));
   return DPF_OK;
 }
 
@@ -1064,6 +1189,17 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   in.q = b->q_spec;
   in.outage = b->outage;
   TRY(w->precision == DPF_FP64 ? init_state<double>(w, in, s) : init_state<float>(w, in, s));
+  if (o->flat_start && o->dc_start) {  // angles from the DC approximation, |V| as initialised
+    const int32_t* od = b->outage ? (b->host_io ? w->outage_dev : b->outage) : nullptr;
+    TRY(dc_run(w, od, 1e-10, 10000, s));
+    const size_t E = (size_t)y->n * w->Kp;
+    const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+    if (w->precision == DPF_FP64)
+      k_dc_apply<double><<<nb, 256, 0, s>>>(w->tmp_a, (double2*)w->ms, (double2*)w->V, y->dev.type, y->n, w->K, w->Kp);
+    else
+      k_dc_apply<float><<<nb, 256, 0, s>>>(w->tmp_a, (float4*)w->ms, (float2*)w->V, y->dev.type, y->n, w->K, w->Kp);
+    CKLAUNCH();
+  }
   w->t_done = 0;
   w->begun = true;
   return DPF_OK;

@@ -380,4 +380,5 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->stage_v = 0;
   o->pdl = 1;
   o->plain = 0;
+  o->dc_start = 0;
 }

@@ -25,6 +25,7 @@ struct DeviceYbus {
   int32_t* ppos = nullptr;      // [prow_ptr[n]] CSR position of a padded slot, -(row+1) for a pad
   int32_t* col = nullptr;       // [nnz]
   double2* val64 = nullptr;     // [nnz]
+  double* dcval = nullptr;      // [nnz] DC matrix B (susceptances 1/(x tau)) in the same CSR
   int32_t* ebr = nullptr;       // [nnz] branch of an off-diagonal entry, -1 on the diagonal
   int32_t* dpos = nullptr;      // [n] position of the diagonal entry in its row
   uint8_t* type = nullptr;      // [n]

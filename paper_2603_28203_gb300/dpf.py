@@ -179,6 +179,7 @@ class SolveOpts:
     pdl: int | None = None
     stage_v: int | None = None
     plain: int | None = None
+    dc_start: int | None = None
 
     def to_c(self) -> _abi.DpfSolveOpts:
         o = _abi.DpfSolveOpts()
@@ -340,6 +341,19 @@ def dpf_loss_backward(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, 
                                    _ptr(outage), _ptr(g_series), _ptr(b_series), int(precision),
                                    *[_ptr(t) for t in g], _stream(stream)))
     return out
+
+
+def dpf_dc_solve(y: Ybus, ws: Workspace, n_case: int, p_spec=None, outage=None, tol: float = 1e-10,
+                 max_iter: int = 10000, stream=None):
+    """DC angles [n_case][N] (float64 CUDA), CG iterations and relative residual per case."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    va = torch.empty((n_case, y.n_bus), dtype=torch.float64, device=dev)
+    it = torch.empty(n_case, dtype=torch.int32, device=dev)
+    res = torch.empty(n_case, dtype=torch.float64, device=dev)
+    _check(lib().dpf_dc_solve(y.handle, ws.handle, int(n_case), _ptr(p_spec), _ptr(outage), float(tol), int(max_iter),
+                              _ptr(va), _ptr(it), _ptr(res), _stream(stream)))
+    return dict(va=va, iters=it, rel_residual=res)
 
 
 def dpf_paramid_begin(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, precision=_abi.FP32, stream=None):

@@ -1,0 +1,118 @@
+"""GPU DC approximation (dpf_dc_solve, batched CG) against the oracle's
+dc_solve: N-1 cases and per-case injections on the 2,000-bus grid, islands,
+a single small case, the residual of the 10,000-bus grid computed by the
+oracle, bridge outages rejected, and the DC start of the DPF solve."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from oracle.power import SLACK
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_28203_gb300 as dpf  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import os
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    dpf.lib()
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def _oracle_dc(g, p, ell=-1):
+    return oracle.dc_solve(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, p, va_slack=g.va_slack, outage=ell)
+
+
+def test_dc_n1_and_per_case_injections_match_oracle():
+    g = gridgen.config_grid("c3_n1_2kbus")
+    K = 40
+    ells = np.concatenate([[-1], np.random.default_rng(3).choice(gridgen.n1_outages(g), K - 1, replace=False)])
+    P, _ = gridgen.time_series(g, K, seed=9)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    out = dpf.dpf_dc_solve(y, ws, K, p_spec=_t(P), outage=_t(ells.astype(np.int32), torch.int32), tol=1e-12)
+    th = out["va"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    assert (it > 0).all() and (out["rel_residual"].cpu().numpy() <= 1e-12).all()
+    for k in range(K):
+        ref = _oracle_dc(g, P[k], int(ells[k]))
+        assert np.abs(th[k] - ref).max() <= 1e-7 * np.abs(ref).max(), k
+        assert th[k][g.bus_type == SLACK][0] == g.va_slack
+
+
+def test_dc_islands_and_single_case():
+    grids = [gridgen.make_grid(n, 40 + i, load_scale=0.2) for i, n in enumerate([30, 55, 80])]
+    cat = gridgen.concat_grids(grids)
+    cat.va_slack = 0.07
+    y = dpf.dpf_build_ybus(cat)
+    ws = dpf.dpf_workspace_create(y, 3)
+    out = dpf.dpf_dc_solve(y, ws, 3, tol=1e-13)  # the grid's injections for every case
+    ref = _oracle_dc(cat, cat.p_spec)
+    for k in range(3):
+        assert np.abs(out["va"][k].cpu().numpy() - ref).max() <= 1e-9
+    g = gridgen.config_grid("c1_30bus_fp64")
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, 1)
+    out = dpf.dpf_dc_solve(y, ws, 1, tol=1e-14)
+    assert np.abs(out["va"][0].cpu().numpy() - _oracle_dc(g, g.p_spec)).max() <= 1e-12
+
+
+def test_dc_residual_at_10k_buses():
+    g = gridgen.config_grid("c2_10kbus")
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, 4)
+    P = np.stack([g.p_spec * s for s in (1.0, 0.5, 1.5, 0.9)])
+    out = dpf.dpf_dc_solve(y, ws, 4, p_spec=_t(P), tol=1e-11, max_iter=20000)
+    B = oracle.dc_matrix(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap)
+    u = g.bus_type != SLACK
+    for k in range(4):
+        th = out["va"][k].cpu().numpy()
+        r = (B @ th - P[k])[u]
+        assert np.abs(r).max() <= 1e-8 * np.abs(P[k][u]).max(), k
+
+
+def test_dc_rejects_bridge_outage():
+    g = gridgen.config_grid("c3_n1_2kbus")
+    bridge = int(np.where(gridgen.bridges(g.n_bus, g.f_bus, g.t_bus))[0][0])
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, 1)
+    with pytest.raises(dpf.DPFError) as e:
+        dpf.dpf_dc_solve(y, ws, 1, outage=_t(np.array([bridge], np.int32), torch.int32))
+    assert e.value.code == -2  # DPF_E_ISLANDED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dpf_dc_start_begins_at_the_dc_angles(precision):
+    g = gridgen.config_grid("c3_n1_2kbus")
+    K = 8
+    ells = np.concatenate([[-1], gridgen.n1_outages(g)[:K - 1]]).astype(np.int32)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    prec = dict(fp64=dpf.FP64, fp32=dpf.FP32)[precision]
+    res = dict(va=torch.zeros((K, g.n_bus), dtype=torch.float64, device=DEV),
+               vm=torch.zeros((K, g.n_bus), dtype=torch.float64, device=DEV),
+               iters=torch.zeros(K, dtype=torch.int32, device=DEV))
+    dpf.dpf_solve_batch(y, ws, dpf.SolveOpts(precision=prec, max_iter=0, dc_start=1), n_case=K,
+                        outage=_t(ells, torch.int32), **res)
+    va = res["va"].cpu().numpy()
+    vm = res["vm"].cpu().numpy()
+    fva, fvm = oracle.flat_start(g.bus_type, g.vm_set, g.va_slack)
+    for k in range(K):
+        ref = _oracle_dc(g, g.p_spec, int(ells[k]))
+        assert np.abs(va[k] - ref).max() <= 1e-8 * np.abs(ref).max()
+        # |V| as flat-started (FP32 mode keeps it as a double-float, ~48 bits)
+        assert np.abs(vm[k] - fvm).max() <= (0.0 if precision == "fp64" else 1e-14)
