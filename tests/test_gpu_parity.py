@@ -359,6 +359,11 @@ def test_invalid_inputs_raise():
         dpf.dpf_solve_batch(y, ws, None, n_case=0, va=va, vm=va.clone())
     with pytest.raises(dpf.DPFError):
         dpf.dpf_solve_iterate(ws, 1)  # no begin
+    # element offsets are 32-bit: n_bus * n_case >= 2^32 is rejected before any work
+    big = 2 ** 32 // g.n_bus + 1
+    with pytest.raises(dpf.DPFError) as e:
+        dpf.dpf_solve_batch(y, ws, None, n_case=big, va=va, vm=va.clone())
+    assert e.value.code == -5
 
 
 def test_diverged_case_is_flagged():
