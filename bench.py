@@ -835,6 +835,61 @@ def run_dc(args):
     y.free()
 
 
+def run_warmstart(args):
+    """Iterations to 1e-6 p.u. from a flat start and from the solution of a
+    neighbouring operating point (the paper's warm-start claim, Sec. 5.4.2),
+    on the 30-bus grid, the one where Alg. 1 reaches 1e-6 (FP64, one case):
+    the base loads solved flat, then loads x 1.01 / 1.02 / 1.05 solved flat
+    and warm with Table 2's settings at several rates and with Table 3's
+    settings for t > 0.  One JSON line."""
+    import torch
+    import gridgen
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    from paper_2603_28203_gb300.timeseries import TABLE3_T1
+    g = gridgen.config_grid("c1_30bus_fp64")
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, 1)
+    dev = torch.device("cuda", 0)
+    cap = args.warm_max_iter
+
+    def solve(p, q, opts, start=None):
+        r = {k: torch.zeros((1, g.n_bus), dtype=torch.float64, device=dev) for k in ("va", "vm")}
+        r.update(iters=torch.zeros(1, dtype=torch.int32, device=dev),
+                 status=torch.zeros(1, dtype=torch.int32, device=dev))
+        if start is not None:
+            r["va"].copy_(start["va"])
+            r["vm"].copy_(start["vm"])
+        dpf.dpf_solve_batch(y, ws, opts, n_case=1, p_spec=torch.tensor(p[None], dtype=torch.float64, device=dev),
+                            q_spec=torch.tensor(q[None], dtype=torch.float64, device=dev), **r)
+        torch.cuda.synchronize()
+        return r
+
+    def iters(r):
+        return int(r["iters"][0]) if int(r["status"][0]) == 0 else None  # None: not converged within the cap
+
+    t2 = dpf.SolveOpts(precision=dpf.FP64, lr=1e-2, max_iter=cap, check_every=1)
+    base = solve(g.p_spec, g.q_spec, t2)
+    rows = []
+    t3 = {k: v for k, v in TABLE3_T1.items() if k != "max_iter"}
+    for scale in (1.01, 1.02, 1.05):
+        p, q = g.p_spec * scale, g.q_spec * scale
+        row = {"load_scale": scale, "flat_table2_lr1e-2": iters(solve(p, q, t2))}
+        for lr in (1e-2, 1e-3, 2.7e-4):
+            o = dpf.SolveOpts(precision=dpf.FP64, lr=lr, max_iter=cap, check_every=1, flat_start=0)
+            row[f"warm_table2_lr{lr:g}"] = iters(solve(p, q, o, base))
+        o = dpf.SolveOpts(precision=dpf.FP64, max_iter=cap, check_every=1, flat_start=0, **t3)
+        row["warm_table3_t>0"] = iters(solve(p, q, o, base))
+        rows.append(row)
+    print(json.dumps({"workload": "warmstart", "grid": "c1_30bus_fp64", "tol_pu": 1e-6, "precision": "fp64",
+                      "iteration_cap": cap, "base_flat_iterations": iters(base), "rows": rows,
+                      "note": "None = not converged within the cap"}), flush=True)
+    ws.free()
+    y.free()
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -886,15 +941,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc"],
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc", "warmstart"],
                     help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep; "
                          "uneven: 64-grid block-diagonal batch + parameter identification; "
                          "timeseries: the 10k-bus grid over a year of hourly snapshots; "
                          "paramid: branch identification against the oracle's operating points; "
-                         "dc: the DC approximation of the N-1 batch (and Alg. 1 started from it)")
+                         "dc: the DC approximation of the N-1 batch (and Alg. 1 started from it); "
+                         "warmstart: iterations from flat vs warm starts on the 30-bus grid")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--uneven-iters", type=int, default=300)
     ap.add_argument("--ts-hours", type=int, default=8760)
+    ap.add_argument("--warm-max-iter", type=int, default=50000)
     ap.add_argument("--pid-grids", type=int, default=16)
     ap.add_argument("--pid-steps", type=int, default=4000)
     ap.add_argument("--pid-lr", type=float, default=3e-3)
@@ -926,6 +983,8 @@ def main():
         run_paramid(args)
     elif args.workload == "dc":
         run_dc(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 
