@@ -243,7 +243,7 @@ struct dpf_workspace {
   int32_t *active = nullptr, *iters = nullptr, *status = nullptr, *of = nullptr, *ot = nullptr;
   int32_t *bad = nullptr, *cool = nullptr;
   double *lr = nullptr, *best = nullptr, *out_max = nullptr, *out_loss = nullptr, *loss64 = nullptr;
-  void *loss_acc = nullptr, *step_size = nullptr, *isbc2 = nullptr, *yff = nullptr, *yft = nullptr, *ytt = nullptr;
+  void *step_size = nullptr, *isbc2 = nullptr, *yff = nullptr, *yft = nullptr, *ytt = nullptr;
   double2 *yff64 = nullptr, *yft64 = nullptr, *ytt64 = nullptr;
   double *b1t = nullptr, *b2t = nullptr;
   int32_t* cand = nullptr;
@@ -253,6 +253,8 @@ struct dpf_workspace {
   int32_t* n_active = nullptr;
   int32_t* h_n_active = nullptr;  // pinned
   unsigned int* tile_cnt = nullptr;  // per case tile, for the forward pass's scheduler
+  void* loss_part = nullptr;         // [row blocks][Kp] the forward pass's loss partials (8 B each)
+  size_t cap_part = 0;
   double* dcs = nullptr;     // DC solver, per case: rz, rz', pq, rr, rr0, beta, res, b_out ([8][Kp])
   int32_t* dci = nullptr;    // DC solver, per case: active, iters ([2][Kp]), then its active count
   int32_t* h_dc_nact = nullptr;  // pinned
@@ -291,7 +293,7 @@ struct dpf_workspace {
 
 static void ws_free_buffers(dpf_workspace* w) {
   void** ptrs[] = {&w->V, &w->W, &w->G0, &w->ms, &w->os, &w->p, &w->q,
-                   &w->sbuf, &w->cbuf, &w->loss_acc, &w->step_size, &w->isbc2, &w->yff, &w->yft, &w->ytt};
+                   &w->sbuf, &w->cbuf, &w->step_size, &w->isbc2, &w->yff, &w->yft, &w->ytt};
   for (void** p : ptrs) dfree(*p);
   dfree(w->p64); dfree(w->q64); dfree(w->tmp_a); dfree(w->tmp_b); dfree(w->tmp_c); dfree(w->V64);
   dfree(w->ent_loc); dfree(w->val_loc);
@@ -305,6 +307,8 @@ static void ws_free_buffers(dpf_workspace* w) {
   w->cap_wblocks = 0;
   dfree(w->tile_cnt);
   w->cap_tiles = 0;
+  dfree(w->loss_part);
+  w->cap_part = 0;
   w->cap_elems = 0;
   w->cap_cases = 0;
   w->cap_stage = 0;
@@ -335,7 +339,7 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     dfree(w->V); dfree(w->W); dfree(w->G0); dfree(w->ms); dfree(w->os);
     dfree(w->p); dfree(w->q); dfree(w->sbuf); dfree(w->cbuf);
     dfree(w->p64); dfree(w->q64); dfree(w->tmp_a); dfree(w->tmp_b); dfree(w->tmp_c); dfree(w->V64);
-    dfree(w->loss_acc); dfree(w->step_size); dfree(w->isbc2); dfree(w->yff); dfree(w->yft); dfree(w->ytt);
+    dfree(w->step_size); dfree(w->isbc2); dfree(w->yff); dfree(w->yft); dfree(w->ytt);
     dfree(w->active); dfree(w->iters); dfree(w->status); dfree(w->of); dfree(w->ot); dfree(w->bad);
     dfree(w->cool); dfree(w->lr); dfree(w->best); dfree(w->out_max); dfree(w->out_loss); dfree(w->loss64);
     dfree(w->yff64); dfree(w->yft64); dfree(w->ytt64); dfree(w->maxmis); dfree(w->outage_dev);
@@ -350,7 +354,6 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     char** bufs8[] = {(char**)&w->p, (char**)&w->q, (char**)&w->p64, (char**)&w->q64,
                       (char**)&w->tmp_a, (char**)&w->tmp_b, (char**)&w->tmp_c};
     for (char** b : bufs8) TRY(dalloc(b, E * 8));
-    TRY(dalloc((char**)&w->loss_acc, (size_t)Kp * 8));
     TRY(dalloc((char**)&w->step_size, (size_t)Kp * 8));
     TRY(dalloc((char**)&w->isbc2, (size_t)Kp * 8));
     TRY(dalloc((char**)&w->yff, (size_t)Kp * 16));
@@ -501,7 +504,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.yft = (const C*)w->yft;
   a.ytt = (const C*)w->ytt;
   a.has_outage = w->has_outage ? 1 : 0;
-  a.loss_acc = (R*)w->loss_acc;
+  a.loss_part = (R*)w->loss_part;
   a.mx32 = gated ? w->mx32 : nullptr;
   a.step_size = (const R*)w->step_size;
   a.isbc2 = (const R*)w->isbc2;
@@ -520,7 +523,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   s.active = w->active;
   s.iters = w->iters;
   s.status = w->status;
-  s.loss_acc = (R*)w->loss_acc;
+  s.loss_part = (const R*)w->loss_part;
   s.mx32 = gated ? w->mx32 : nullptr;
   s.cand = w->cand;
   s.gate = w->opts.gate;
@@ -834,6 +837,13 @@ static int upload_windows(dpf_workspace* w, cudaStream_t s) {
     w->cap_tiles = tiles;
   }
   CK(cudaMemsetAsync(w->tile_cnt, 0, (size_t)w->cap_tiles * sizeof(unsigned int), s));
+  const size_t part = (size_t)w->gy * w->Kp;
+  if (part > w->cap_part) {
+    dfree(w->loss_part);
+    w->cap_part = 0;
+    TRY(dalloc((char**)&w->loss_part, part * 8));
+    w->cap_part = part;
+  }
   if (w->gy > w->cap_wblocks) {
     dfree(w->d_wlo);
     dfree(w->d_whi);
@@ -993,7 +1003,6 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   ca.best = w->best;
   ca.bad = w->bad;
   ca.cool = w->cool;
-  ca.loss_acc = (R*)w->loss_acc;
   ca.step_size = (R*)w->step_size;
   ca.isbc2 = (R*)w->isbc2;
   ca.b1t = w->b1t;
@@ -1545,7 +1554,7 @@ template <class R>
 static int power_impl(dpf_workspace* w, double* p_calc, double* q_calc, cudaStream_t s) {
   Plan<R> P = make_plan<R>(w);
   P.it.sbuf = (typename Prec<R>::C*)w->sbuf;
-  P.it.loss_acc = nullptr;
+  P.it.loss_part = nullptr;
   P.it.n_active = nullptr;
   P.it.tile_cnt = nullptr;
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
@@ -1605,7 +1614,7 @@ static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, doub
   const dpf_ybus* y = w->y;
   Plan<R> P = make_plan<R>(w);
   P.it.cbuf = (d_p || d_q) ? (C*)w->cbuf : nullptr;
-  P.it.loss_acc = nullptr;  // (the loss is the FP64 pass's)
+  P.it.loss_part = nullptr;  // (the loss is the FP64 pass's)
   P.it.mx32 = nullptr;
   P.it.n_active = nullptr;
   P.it.tile_cnt = nullptr;
@@ -1708,7 +1717,7 @@ static int paramid_impl(dpf_workspace* w, double* d_g, double* d_b, double* d_bc
   k_activate<<<(w->Kp + 255) / 256, 256, 0, s>>>(w->active, w->K, w->Kp);
   Plan<R> P = make_plan<R>(w);
   P.it.cbuf = nullptr;
-  P.it.loss_acc = nullptr;
+  P.it.loss_part = nullptr;
   P.it.mx32 = nullptr;
   P.it.n_active = nullptr;
   P.it.tile_cnt = nullptr;

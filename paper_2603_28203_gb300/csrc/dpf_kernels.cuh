@@ -414,7 +414,7 @@ template <class R> struct SchedArgs {
   int32_t* active;
   int32_t* iters;
   int32_t* status;
-  R* loss_acc;
+  const R* loss_part;  // [row blocks][Kp] the forward pass's loss partials
   unsigned int* mx32;  // FP32 max mismatch of the forward pass (or NULL)
   int32_t* cand;       // 1: the next FP64 test examines the case
   double gate;         // FP32 max mismatch below which the FP64 test runs (<= 0: always)
@@ -439,11 +439,14 @@ template <class R> struct SchedArgs {
 //      step is taken from), giving the rate of the next step.
 // A non-finite loss stops the case as diverged before it steps.
 template <class R>
-__device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k) {
+__device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k, int n_part) {
   // every load is issued before the first store (one memory round trip: this
   // runs in the forward pass's tail, on its critical path)
   const int act = a.active[k];
-  const R lsum = __ldcg(a.loss_acc + k);
+  // the loss: the row blocks' partials summed in a fixed order, so that a
+  // solve repeats bit for bit (an atomic sum's order varies between runs)
+  R lsum = R(0);
+  for (int yb = 0; yb < n_part; ++yb) lsum += __ldcg(a.loss_part + (size_t)yb * a.Kp + k);
   const unsigned mxu = a.mx32 ? __ldcg(a.mx32 + k) : 0u;
   const int it0 = a.iters[k];
   double lr = a.lr[k];
@@ -453,7 +456,6 @@ __device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k) {
   int bad = plateau ? a.bad[k] : 0, cool = plateau ? a.cool[k] : 0;
   if (!act) return;
   const double L = (double)lsum * a.inv_m;
-  a.loss_acc[k] = R(0);
   if (a.mx32) {
     a.mx32[k] = 0u;
     a.cand[k] = (a.gate <= 0.0 || (double)__uint_as_float(mxu) <= a.gate) ? 1 : 0;
@@ -503,7 +505,7 @@ __device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k) {
   a.lr[k] = lr;
 }
 
-// After a forward CTA's loss/mismatch atomics: the last CTA of its case tile
+// After a forward CTA's loss partials and mismatch atomics: the last CTA of its case tile
 // (every CTA of the tile has counted itself after fencing its atomics) runs
 // sched_case for the tile's cases and resets the tile counter.  Every thread
 // of the CTA must call it.
@@ -522,7 +524,7 @@ __device__ __forceinline__ void tile_sched(const SchedArgs<R>& a, unsigned int* 
     __threadfence();
     for (int c = threadIdx.x; c < tile; c += blockDim.x) {
       const int k = blockIdx.x * tile + c;
-      if (k < a.Kp) sched_case(a, k);
+      if (k < a.Kp) sched_case(a, k, gridDim.y);
     }
   }
 }
@@ -564,7 +566,7 @@ template <class R> struct IterArgs {
   const C* yft;
   const C* ytt;
   int has_outage;
-  R* loss_acc;
+  R* loss_part;        // [row blocks][Kp] per-CTA loss partials (solve loop; NULL: none)
   unsigned int* mx32;  // per-case max |dP|,|dQ| (float bits) or NULL
   const R* step_size;
   const R* isbc2;
@@ -582,10 +584,11 @@ template <class R> struct IterArgs {
   R* gvm;
 };
 
-// Per-case sum and max over the CTA, one atomic each per case.  Every thread
-// of the CTA must call it.
+// Per-case sum and max over the CTA: the sum stored in this row block's slot
+// of part_out ([row blocks][Kp]), the max by one atomic per case.  Every
+// thread of the CTA must call it.
 template <class R>
-__device__ __forceinline__ void case_sum_max_atomic(R v, float mx, int lanes, R* sum_out, unsigned int* max_out,
+__device__ __forceinline__ void case_sum_max_atomic(R v, float mx, int lanes, R* part_out, unsigned int* max_out,
                                                     int Kp) {
   __shared__ R red[32][32];
   __shared__ float redm[32][32];
@@ -608,7 +611,7 @@ __device__ __forceinline__ void case_sum_max_atomic(R v, float mx, int lanes, R*
     }
     const int k = blockIdx.x * lanes + threadIdx.x;
     if (k < Kp) {
-      if (sum_out && s != R(0)) atomicAdd(sum_out + k, s);
+      if (part_out) part_out[(size_t)blockIdx.y * Kp + k] = s;
       if (max_out && m > 0.f) atomicMax(max_out + k, __float_as_uint(m));
     }
   }
@@ -699,7 +702,7 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
       mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);  // NaN -> +inf
     }
   }
-  if (a.loss_acc || a.mx32) case_sum_max_atomic(acc, mx, a.lanes, a.loss_acc, a.mx32, a.Kp);
+  if (a.loss_part || a.mx32) case_sum_max_atomic(acc, mx, a.lanes, a.loss_part, a.mx32, a.Kp);
   if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
 }
 
@@ -939,8 +942,9 @@ __device__ __forceinline__ void row_spmv2(const YSmem<float>& ys, int p0, int p1
   r1 = make_float2(b0.x + b1.x, b0.y + b1.y);
 }
 
-// Per-case sum and max for two cases per thread, one atomic each per case.
-__device__ __forceinline__ void pair_sum_max_atomic(float s0, float s1, float m0, float m1, float* sum_out,
+// Per-case sum (into this row block's slot of part_out) and max (one atomic)
+// for two cases per thread.
+__device__ __forceinline__ void pair_sum_max_atomic(float s0, float s1, float m0, float m1, float* part_out,
                                                     unsigned int* max_out, int Kp) {
   __shared__ float rs[8][64];
   __shared__ float rm[8][64];
@@ -958,7 +962,7 @@ __device__ __forceinline__ void pair_sum_max_atomic(float s0, float s1, float m0
     }
     const int k = blockIdx.x * 64 + threadIdx.x;
     if (k < Kp) {
-      if (sum_out && s != 0.f) atomicAdd(sum_out + k, s);
+      if (part_out) part_out[(size_t)blockIdx.y * Kp + k] = s;
       if (max_out && m > 0.f) atomicMax(max_out + k, __float_as_uint(m));
     }
   }
@@ -1051,7 +1055,7 @@ __global__ void __launch_bounds__(256, DPF_FWD2_MINB) k_fwd2(IterArgs<float> a) 
     if (!q.on0) { acc0 = 0.f; mx0 = 0.f; }
     if (!q.on1) { acc1 = 0.f; mx1 = 0.f; }
   }
-  pair_sum_max_atomic(acc0, acc1, mx0, mx1, a.loss_acc, a.mx32, a.Kp);
+  pair_sum_max_atomic(acc0, acc1, mx0, mx1, a.loss_part, a.mx32, a.Kp);
   if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, 64);
 }
 
@@ -1392,7 +1396,6 @@ template <class R> struct CaseInitArgs {
   double* best;
   int32_t* bad;
   int32_t* cool;
-  R* loss_acc;
   R* step_size;
   R* isbc2;
   double* b1t;
@@ -1417,7 +1420,6 @@ __global__ void k_case_init(CaseInitArgs<R> a) {
   a.best[k] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
   a.bad[k] = 0;
   a.cool[k] = 0;
-  a.loss_acc[k] = R(0);
   a.step_size[k] = (R)(a.opt == OPT_ADAM ? a.lr0 / (1.0 - a.beta1) : a.lr0);
   a.isbc2[k] = (R)(a.opt == OPT_ADAM ? 1.0 / sqrt(1.0 - a.beta2) : 1.0);
   a.b1t[k] = 1.0;  // beta^0: the forward pass multiplies in beta before each step

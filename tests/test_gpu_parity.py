@@ -410,3 +410,23 @@ def test_autograd_function():
     for k in range(K):
         Lk, d_va, d_vm = oracle.loss_grad(Y, va[k], vm[k], g.p_spec, g.q_spec, g.bus_type)
         assert np.abs(tva.grad[k].cpu().numpy() - 3 * d_va).max() <= 1e-10 * np.abs(d_va).max()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_solve_repeats_bit_for_bit(precision):
+    """Two identical batched solves give identical iterates, iteration counts,
+    statuses and FP64 mismatches: the per-case loss that drives the scheduler
+    is summed in a fixed order (no atomic sum), so no scheduling decision
+    depends on the order in which CTAs finish."""
+    g = GRIDS["c3"]()
+    K = 130
+    ells = np.concatenate([[-1], np.random.default_rng(12).choice(gridgen.n1_outages(g), K - 1, replace=False)])
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    prec = dict(fp32=dpf.FP32, fp64=dpf.FP64)[precision]
+    opts = dpf.SolveOpts(precision=prec, max_iter=300, check_every=10, lr=1e-3)
+    kw = dict(outage=_t(ells.astype(np.int32), torch.int32))
+    a = _solve(y, ws, K, opts, **kw)
+    b = _solve(y, ws, K, opts, **kw)
+    for key in ("va", "vm", "iters", "status", "max_mismatch"):
+        assert np.array_equal(a[key], b[key]), key
