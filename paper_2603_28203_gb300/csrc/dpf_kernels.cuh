@@ -439,14 +439,10 @@ template <class R> struct SchedArgs {
 //      step is taken from), giving the rate of the next step.
 // A non-finite loss stops the case as diverged before it steps.
 template <class R>
-__device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k, int n_part) {
+__device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k, R lsum) {
   // every load is issued before the first store (one memory round trip: this
   // runs in the forward pass's tail, on its critical path)
   const int act = a.active[k];
-  // the loss: the row blocks' partials summed in a fixed order, so that a
-  // solve repeats bit for bit (an atomic sum's order varies between runs)
-  R lsum = R(0);
-  for (int yb = 0; yb < n_part; ++yb) lsum += __ldcg(a.loss_part + (size_t)yb * a.Kp + k);
   const unsigned mxu = a.mx32 ? __ldcg(a.mx32 + k) : 0u;
   const int it0 = a.iters[k];
   double lr = a.lr[k];
@@ -522,9 +518,40 @@ __device__ __forceinline__ void tile_sched(const SchedArgs<R>& a, unsigned int* 
   __syncthreads();
   if (last) {
     __threadfence();
-    for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+    // Each case's loss: its row blocks' partials summed in a fixed order, so
+    // that a solve repeats bit for bit (an atomic sum's order varies between
+    // runs): one thread per case for a few row blocks; for many (a single
+    // case over ~1,000 row blocks) a group of tpc threads per case takes
+    // strided slices, then a fixed tree.  blockDim.x <= 256 (launch bounds).
+    if (gridDim.y <= 64) {
+      for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+        const int k = blockIdx.x * tile + c;
+        if (k >= a.Kp) continue;
+        R s = R(0);
+        for (int yb = 0; yb < (int)gridDim.y; ++yb) s += __ldcg(a.loss_part + (size_t)yb * a.Kp + k);
+        sched_case(a, k, s);
+      }
+      return;
+    }
+    __shared__ R part[256];
+    int tpc = 1;  // threads per case: a power of two with tile * tpc <= blockDim.x
+    while (2 * tpc * tile <= (int)blockDim.x) tpc *= 2;
+    const int cases_per_pass = max(1, (int)blockDim.x / tpc);
+    for (int c0 = 0; c0 < tile; c0 += cases_per_pass) {
+      const int c = c0 + (int)threadIdx.x / tpc, j = (int)threadIdx.x % tpc;
       const int k = blockIdx.x * tile + c;
-      if (k < a.Kp) sched_case(a, k, gridDim.y);
+      const bool mine = (int)threadIdx.x < cases_per_pass * tpc && c < tile && k < a.Kp;
+      R s = R(0);
+      if (mine)
+        for (int yb = j; yb < (int)gridDim.y; yb += tpc) s += __ldcg(a.loss_part + (size_t)yb * a.Kp + k);
+      part[threadIdx.x] = s;
+      __syncthreads();
+      for (int step = tpc >> 1; step > 0; step >>= 1) {
+        if (j < step) part[threadIdx.x] += part[threadIdx.x + step];
+        __syncthreads();
+      }
+      if (mine && j == 0) sched_case(a, k, part[threadIdx.x]);
+      __syncthreads();
     }
   }
 }
