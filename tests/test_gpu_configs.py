@@ -13,7 +13,10 @@
   an lr-sized (2.7e-4) difference in that coordinate, and each window
   inherits the previous window's differences.  There the bar is 1e-4 rad /
   p.u. on the iterates and 1e-6 relative on the FP64 mismatch, with equal
-  iteration counts and statuses.
+  iteration counts and statuses;
+* the full N-1 batch in the launch shape the benchmark times: the reported
+  FP64 mismatch of every case against the oracle's recomputation, and
+  sampled cases against the oracle's trajectory.
 """
 import numpy as np
 import pytest
@@ -134,3 +137,44 @@ def test_c4_time_series_fp32_close_to_fp64():
     assert np.abs(a["va"] - b["va"]).max() < 5e-3
     assert np.abs(a["vm"] - b["vm"]).max() < 5e-3
     assert np.abs(a["max_mismatch"] - b["max_mismatch"]).max() <= 0.05 * a["max_mismatch"].max()
+
+
+def test_c3_full_batch_in_the_benchmark_shape():
+    """The whole N-1 batch (2,000 buses, every non-bridge outage) in the launch
+    shape the autotuner picks (what bench.py times), FP32, 50 iterations.
+    Exact at any size: the FP64 max mismatch reported for every case equals
+    the oracle's mismatch recomputed from the returned voltages (1e-9).
+    Sampled cases: the oracle's FP64 Alg. 1 loop on Y_bus rebuilt without the
+    outaged branch follows the same trajectory within the FP32 bar (5e-3 on
+    the iterates, 5% on the mismatch -- FP32 rounding against FP64 under a
+    nearly sign-like Adam step)."""
+    g = gridgen.config_grid("c3_n1_2kbus")
+    outs = gridgen.n1_outages(g)
+    K = outs.size
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    od = torch.tensor(outs, dtype=torch.int32, device=DEV)
+    opts = dpf.SolveOpts(precision=dpf.FP32, lr=1e-3, check_every=25, max_iter=50)
+    opts = dpf.dpf_autotune(y, ws, opts, iters=10, n_case=K, outage=od)
+    res = dict(va=torch.empty((K, g.n_bus), dtype=torch.float64, device=DEV),
+               vm=torch.empty((K, g.n_bus), dtype=torch.float64, device=DEV),
+               iters=torch.empty(K, dtype=torch.int32, device=DEV),
+               status=torch.empty(K, dtype=torch.int32, device=DEV),
+               max_mismatch=torch.empty(K, dtype=torch.float64, device=DEV))
+    dpf.dpf_solve_batch(y, ws, opts, n_case=K, outage=od, **res)
+    torch.cuda.synchronize()
+    r = {k: v.cpu().numpy() for k, v in res.items()}
+    assert (r["iters"] == 50).all() and (r["status"] == dpf.CASE_MAX_ITER).all()
+    rng = np.random.default_rng(21)
+    sample = sorted(set([0, K // 2, K - 1] + [int(k) for k in rng.choice(K, 3, replace=False)]))
+    for k in sample:
+        keep = np.arange(g.n_branch) != outs[k]
+        Yk = oracle.build_ybus(g.n_bus, g.f_bus[keep], g.t_bus[keep], g.r[keep], g.x[keep], g.b_ch[keep],
+                               g.tap[keep])
+        f, _ = oracle.mismatch(Yk, r["va"][k], r["vm"][k], g.p_spec, g.q_spec, g.bus_type)
+        assert abs(np.abs(f).max() - r["max_mismatch"][k]) <= 1e-9, k
+        ref = oracle.dpf_solve(Yk, g.p_spec, g.q_spec, g.bus_type, g.vm_set,
+                               oracle.DPFOptions(lr=1e-3, max_iter=50, check_every=25), va_slack=g.va_slack)
+        assert np.abs(r["va"][k] - ref["va"]).max() <= 5e-3, k
+        assert np.abs(r["vm"][k] - ref["vm"]).max() <= 5e-3, k
+        assert abs(r["max_mismatch"][k] - ref["max_mismatch"]) <= 0.05 * ref["max_mismatch"], k
