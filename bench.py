@@ -890,6 +890,63 @@ def run_warmstart(args):
     y.free()
 
 
+def run_c1batch(args):
+    """Solves/s to 1e-6 p.u. where Alg. 1 reaches it: `--c1-cases` load
+    variants (x U(0.95, 1.05), seeded) of the 30-bus grid in one batch, Table 2
+    settings with lr 1e-2, up to 20,000 iterations, FP64 and FP32 iterations
+    (FP64 test in both).  Counts only the cases the FP64 test declares
+    converged; the oracle recomputes the mismatch of sampled returned states.
+    One JSON line."""
+    import torch
+    import gridgen
+    import oracle
+    from oracle.ybus import grid_ybus
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    g = gridgen.config_grid("c1_30bus_fp64")
+    K = args.c1_cases
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(0)
+    sc = 1 + 0.05 * rng.uniform(-1, 1, (K, 1))
+    P, Q = g.p_spec[None] * sc, g.q_spec[None] * sc
+    Pt = torch.tensor(P, device=dev)
+    Qt = torch.tensor(Q, device=dev)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    Y = grid_ybus(g)
+    out = {}
+    for prec, name in ((dpf.FP64, "fp64"), (dpf.FP32, "fp32")):
+        r = dict(va=torch.empty((K, g.n_bus), dtype=torch.float64, device=dev),
+                 vm=torch.empty((K, g.n_bus), dtype=torch.float64, device=dev),
+                 iters=torch.empty(K, dtype=torch.int32, device=dev),
+                 status=torch.empty(K, dtype=torch.int32, device=dev),
+                 max_mismatch=torch.empty(K, dtype=torch.float64, device=dev))
+        o = dpf.SolveOpts(precision=prec, lr=1e-2, max_iter=20000, check_every=25)
+        dpf.dpf_solve_batch(y, ws, o, n_case=K, p_spec=Pt, q_spec=Qt, **r)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dpf.dpf_solve_batch(y, ws, o, n_case=K, p_spec=Pt, q_spec=Qt, **r)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st, it, mm = (r[k].cpu().numpy() for k in ("status", "iters", "max_mismatch"))
+        va, vm = r["va"].cpu().numpy(), r["vm"].cpu().numpy()
+        err = 0.0
+        for k in [0, K // 2, K - 1]:
+            f, _ = oracle.mismatch(Y, va[k], vm[k], P[k], Q[k], g.bus_type)
+            err = max(err, abs(float(np.abs(f).max()) - float(mm[k])))
+        conv = int((st == 0).sum())
+        out[name] = {"wall_s": wall, "converged": conv, "solves_to_1e-6_per_s": conv / wall,
+                     "iterations_p50": float(np.median(it)), "iterations_max": int(it.max()),
+                     "max_mismatch_max": float(mm.max()), "reported_vs_oracle_mismatch_max_abs_diff": err}
+    print(json.dumps({"workload": "c1batch", "grid": "c1_30bus_fp64", "cases": K, "tol_pu": 1e-6,
+                      "loads": "x U(0.95, 1.05) per case (seed 0)",
+                      "settings": "Table 2, lr 1e-2, <= 20,000 iterations, FP64 test every 25", **out}), flush=True)
+    ws.free()
+    y.free()
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -941,17 +998,19 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc", "warmstart"],
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc", "warmstart", "c1batch"],
                     help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep; "
                          "uneven: 64-grid block-diagonal batch + parameter identification; "
                          "timeseries: the 10k-bus grid over a year of hourly snapshots; "
                          "paramid: branch identification against the oracle's operating points; "
                          "dc: the DC approximation of the N-1 batch (and Alg. 1 started from it); "
-                         "warmstart: iterations from flat vs warm starts on the 30-bus grid")
+                         "warmstart: iterations from flat vs warm starts on the 30-bus grid; "
+                         "c1batch: solves/s to 1e-6 on a batch of 30-bus load variants")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--uneven-iters", type=int, default=300)
     ap.add_argument("--ts-hours", type=int, default=8760)
     ap.add_argument("--warm-max-iter", type=int, default=50000)
+    ap.add_argument("--c1-cases", type=int, default=8192)
     ap.add_argument("--pid-grids", type=int, default=16)
     ap.add_argument("--pid-steps", type=int, default=4000)
     ap.add_argument("--pid-lr", type=float, default=3e-3)
@@ -985,6 +1044,8 @@ def main():
         run_dc(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "c1batch":
+        run_c1batch(args)
     else:
         run_ours(args)
 
