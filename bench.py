@@ -893,8 +893,8 @@ def run_warmstart(args):
 def run_c1batch(args):
     """Solves/s to 1e-6 p.u. where Alg. 1 reaches it: `--c1-cases` load
     variants (x U(0.95, 1.05), seeded) of the 30-bus grid in one batch, Table 2
-    settings with lr 1e-2, up to 20,000 iterations, FP64 and FP32 iterations
-    (FP64 test in both).  Counts only the cases the FP64 test declares
+    settings with lr 1e-2, up to 20,000 iterations, FP64, mixed (FP64 forward,
+    FP32 adjoint) and FP32 iterations (FP64 test in all).  Counts only the cases the FP64 test declares
     converged; the oracle recomputes the mismatch of sampled returned states.
     One JSON line."""
     import torch
@@ -917,7 +917,7 @@ def run_c1batch(args):
     ws = dpf.dpf_workspace_create(y, K)
     Y = grid_ybus(g)
     out = {}
-    for prec, name in ((dpf.FP64, "fp64"), (dpf.FP32, "fp32")):
+    for prec, name in ((dpf.FP64, "fp64"), (dpf.MIXED, "mixed"), (dpf.FP32, "fp32")):
         r = dict(va=torch.empty((K, g.n_bus), dtype=torch.float64, device=dev),
                  vm=torch.empty((K, g.n_bus), dtype=torch.float64, device=dev),
                  iters=torch.empty(K, dtype=torch.int32, device=dev),

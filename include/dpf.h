@@ -58,7 +58,14 @@ enum {
 };
 
 enum { DPF_PQ = 0, DPF_PV = 1, DPF_SLACK = 2 };            /* bus types (Sec. 2.1) */
-enum { DPF_FP32 = 0, DPF_FP64 = 1 };                        /* iteration precision */
+/* iteration precision: DPF_FP32 -- FP32 iterations on an FP64-accurate
+ * (double-float) master with the FP64 convergence test; DPF_FP64 -- FP64
+ * throughout; DPF_MIXED (solves only) -- the forward pass (currents, S, the
+ * mismatch and its weights) in FP64 over FP64 voltages, the adjoint and the
+ * optimiser in FP32 on the double-float master: it resolves mismatches below
+ * the FP32 current's error of a few |Y_ii| 2^-24 (~1e-5 p.u. with short
+ * lines) at about the FP32 cost of the adjoint. */
+enum { DPF_FP32 = 0, DPF_FP64 = 1, DPF_MIXED = 2 };
 enum { DPF_SCHED_CONST = 0, DPF_SCHED_PLATEAU = 1, DPF_SCHED_STEP = 2 };
 enum { DPF_OPT_ADAM = 0, DPF_OPT_SGD = 1, DPF_OPT_RMSPROP = 2 };    /* Sec. 5.3's optimisers */
 
@@ -163,7 +170,7 @@ typedef struct {
                                 tests that cannot pass; a case is marked
                                 converged by the FP64 test alone.             */
   int32_t flat_start;        /* 1: ignore va/vm inputs, start flat             */
-  int32_t precision;         /* DPF_FP32 (FP64 master + FP64 test) / DPF_FP64  */
+  int32_t precision;         /* DPF_FP32 / DPF_FP64 / DPF_MIXED (see above)    */
   int32_t lanes;             /* cases per row group 1..32 (power of 2); 0=auto */
   int32_t warps;             /* warps per CTA (1..8); 0 = auto                 */
   int32_t row_blocks;        /* CTAs along the bus dimension; 0 = auto         */

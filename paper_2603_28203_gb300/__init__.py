@@ -9,7 +9,7 @@ per-case correction of one shared Y_bus, and an FP64 convergence test.
 torch.autograd.Function over the adjoint.
 """
 from . import _abi
-from ._abi import (CASE_CONVERGED, CASE_DIVERGED, CASE_MAX_ITER, FP32, FP64, OPT_ADAM, OPT_RMSPROP, OPT_SGD,
+from ._abi import (CASE_CONVERGED, CASE_DIVERGED, CASE_MAX_ITER, FP32, FP64, MIXED, OPT_ADAM, OPT_RMSPROP, OPT_SGD,
                    PQ, PV, SCHED_CONST,
                    SCHED_PLATEAU, SCHED_STEP, SLACK)
 from .dpf import (DPFError, SolveOpts, Workspace, Ybus, dpf_active_count, dpf_adam_update, dpf_autotune, dpf_build_ybus,

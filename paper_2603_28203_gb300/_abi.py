@@ -7,7 +7,7 @@ DPF_OK = 0
 DPF_E_INVALID, DPF_E_ISLANDED, DPF_E_CUDA, DPF_E_OOM, DPF_E_UNSUPPORTED, DPF_E_STATE = -1, -2, -3, -4, -5, -6
 CASE_CONVERGED, CASE_MAX_ITER, CASE_DIVERGED = 0, 1, 2
 PQ, PV, SLACK = 0, 1, 2
-FP32, FP64 = 0, 1
+FP32, FP64, MIXED = 0, 1, 2
 SCHED_CONST, SCHED_PLATEAU, SCHED_STEP = 0, 1, 2
 OPT_ADAM, OPT_SGD, OPT_RMSPROP = 0, 1, 2
 NOALLOC_MAX_ELEMS = 1 << 18

@@ -517,6 +517,18 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.alpha = (R)w->opts.alpha;
   a.m_half = (R)(0.5 * y->m_loss);
   a.n_active = w->n_active;
+  if constexpr (sizeof(R) == 4) {
+    if (w->precision == DPF_MIXED) {
+      a.V64m = (double2*)w->V;
+      a.Y64.col = d.col;
+      a.Y64.val = v64;
+      a.pspec64 = w->spec_per_case ? w->p64 : d.p64;
+      a.qspec64 = w->spec_per_case ? w->q64 : d.q64;
+      a.yff64 = w->yff64;
+      a.yft64 = w->yft64;
+      a.ytt64 = w->ytt64;
+    }
+  }
 
   SchedArgs<R>& s = a.sc;
   s.Kp = w->Kp;
@@ -640,14 +652,16 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
     CK(cudaEventRecord(e0, s));
   }
   if constexpr (sizeof(R) == 4) {
-    if (w->pair_fwd) CK(launch(k_fwd2, P.pgrid, P.block, P.smem, s, pdl, P.it));
+    if (w->precision == DPF_MIXED) CK(launch(k_fwd_mixed, P.grid, P.block, P.smem, s, pdl, P.it));
+    else if (w->pair_fwd) CK(launch(k_fwd2, P.pgrid, P.block, P.smem, s, pdl, P.it));
     else CK(launch(k_fwd<R>, P.grid, P.block, P.smem, s, pdl, P.it));
   } else {
     CK(launch(k_fwd<R>, P.grid, P.block, P.smem, s, pdl, P.it));
   }
   if (w->profile) CK(cudaEventRecord(e1, s));
   if constexpr (sizeof(R) == 4) {
-    if (w->pair_adj) CK(launch(k_adj2, P.pgridb, P.block, P.ysmem, s, pdl, P.itb));
+    if (w->precision == DPF_MIXED) CK(launch(k_adj<float, true>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
+    else if (w->pair_adj) CK(launch(k_adj2, P.pgridb, P.block, P.ysmem, s, pdl, P.itb));
     else CK(launch(k_adj<R>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
   } else {
     CK(launch(k_adj<R>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
@@ -747,9 +761,12 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   const std::vector<int32_t>& rp = w->y->irow_ptr;
   const std::vector<int32_t>& prp = w->y->iprow_ptr;  // padded rows: the staged entries
   const std::vector<int32_t>& col = w->y->icol;
-  const bool fp64 = (o ? o->precision : w->precision) == DPF_FP64;
-  // bytes of one staged window row: the case tile's line of V
-  const bool stage_v = o && o->stage_v;
+  const int prec = o ? o->precision : w->precision;
+  const bool fp64 = prec == DPF_FP64;        // FP64 adjoint (and forward)
+  const bool mixed = prec == DPF_MIXED;      // FP64 forward, FP32 adjoint
+  const bool fp64_fwd = fp64 || mixed;       // the forward pass stages FP64 Y rows
+  // bytes of one staged window row: the case tile's line of V (not in mixed mode)
+  const bool stage_v = o && o->stage_v && !mixed;
   const int line = !stage_v ? 0 : w->pair_fwd ? 512 : (lanes == 32 ? 32 * (fp64 ? 16 : 8) : 0);
   // shrink row blocks until the staged Y rows (and the V window) fit
   for (int tries = 0;; ++tries) {
@@ -762,7 +779,7 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
       for (int q = rp[r0]; q < rp[r1]; ++q) { lo = std::min(lo, col[q]); hi = std::max(hi, col[q]); }
       wmax = std::max(wmax, hi - lo + 1);
     }
-    const int ybytes = ysmem_bytes(rpb, mx, fp64);
+    const int ybytes = ysmem_bytes(rpb, mx, fp64_fwd);
     const int wbytes = line * wmax;
     const bool fits = ybytes + wbytes <= 150 * 1024;
     // (staged Y rows above ~32 KB would cap the resident CTAs per SM)
@@ -796,8 +813,14 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   w->gy_b = w->gy;
   if (auto_rb && !w->staged) {
     int occ_f = 0, occ_b = 0;
-    const void* kf = fp64 ? (const void*)k_fwd<double> : w->pair_fwd ? (const void*)k_fwd2 : (const void*)k_fwd<float>;
-    const void* kb = fp64 ? (const void*)k_adj<double> : w->pair_adj ? (const void*)k_adj2 : (const void*)k_adj<float>;
+    const void* kf = fp64          ? (const void*)k_fwd<double>
+                     : mixed       ? (const void*)k_fwd_mixed
+                     : w->pair_fwd ? (const void*)k_fwd2
+                                   : (const void*)k_fwd<float>;
+    const void* kb = fp64          ? (const void*)k_adj<double>
+                     : mixed       ? (const void*)k_adj<float, true>
+                     : w->pair_adj ? (const void*)k_adj2
+                                   : (const void*)k_adj<float>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, block, w->smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, kb, block, w->smem);
     cudaGetLastError();  // a failed query only disables the alignment
@@ -808,13 +831,13 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
     if (gyf != w->gy) {
       w->rpb = (n + gyf - 1) / gyf;
       w->gy = (n + w->rpb - 1) / w->rpb;
-      w->ysmem = ysmem_bytes(w->rpb, seg_nnz(w->rpb), fp64);
+      w->ysmem = ysmem_bytes(w->rpb, seg_nnz(w->rpb), fp64_fwd);
       w->smem = w->ysmem;
     }
   }
   w->rpb_b = (n + w->gy_b - 1) / w->gy_b;
   w->gy_b = (n + w->rpb_b - 1) / w->rpb_b;
-  w->ysmem_b = ysmem_bytes(w->rpb_b, seg_nnz(w->rpb_b), fp64);
+  w->ysmem_b = ysmem_bytes(w->rpb_b, seg_nnz(w->rpb_b), fp64);  // the adjoint's own precision
   w->h_wlo.assign(w->gy, 0);
   w->h_whi.assign(w->gy, 0);
   for (int b = 0; b < w->gy; ++b) {
@@ -866,6 +889,8 @@ static int set_smem_attr(int bytes) {
     if constexpr (sizeof(R) == 4) {
       CK(cudaFuncSetAttribute(k_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
       CK(cudaFuncSetAttribute(k_adj2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_fwd_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_adj<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     }
   }
   return DPF_OK;
@@ -964,6 +989,12 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
   k_init<R><<<std::max(nb, 1), 256, 0, s>>>(ia);
   CKLAUNCH();
+  if constexpr (sizeof(R) == 4) {
+    if (w->precision == DPF_MIXED) {  // FP64 voltages for the mixed forward pass
+      k_mixed_v64<<<std::max(nb, 1), 256, 0, s>>>((const float4*)w->ms, (double2*)w->V, E);
+      CKLAUNCH();
+    }
+  }
 
   // per-case state and N-1 corrections
   w->has_outage = (in.outage != nullptr);
@@ -1035,7 +1066,8 @@ static int validate_opts(const dpf_solve_opts* o) {
     return fail(DPF_E_INVALID, "invalid StepLR parameters");
   if (o->max_iter < 0 || o->check_every < 1 || !(o->tol >= 0))
     return fail(DPF_E_INVALID, "invalid max_iter / check_every / tol");
-  if (o->precision != DPF_FP32 && o->precision != DPF_FP64) return fail(DPF_E_INVALID, "unknown precision");
+  if (o->precision != DPF_FP32 && o->precision != DPF_FP64 && o->precision != DPF_MIXED)
+    return fail(DPF_E_INVALID, "unknown precision");
   if (!(o->gate >= 0.0)) return fail(DPF_E_INVALID, "gate must be >= 0");
   if (o->pdl != 0 && o->pdl != 1) return fail(DPF_E_INVALID, "pdl must be 0 or 1");
   if (o->dc_start != 0 && o->dc_start != 1) return fail(DPF_E_INVALID, "dc_start must be 0 or 1");
@@ -1207,6 +1239,7 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
       k_dc_apply<double><<<nb, 256, 0, s>>>(w->tmp_a, (double2*)w->ms, (double2*)w->V, y->dev.type, y->n, w->K, w->Kp);
     else
       k_dc_apply<float><<<nb, 256, 0, s>>>(w->tmp_a, (float4*)w->ms, (float2*)w->V, y->dev.type, y->n, w->K, w->Kp);
+    if (w->precision == DPF_MIXED) k_mixed_v64<<<nb, 256, 0, s>>>((const float4*)w->ms, (double2*)w->V, E);
     CKLAUNCH();
   }
   w->t_done = 0;

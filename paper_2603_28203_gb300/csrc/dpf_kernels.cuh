@@ -604,6 +604,15 @@ template <class R> struct IterArgs {
   // the per-case scheduler, run by the forward pass (solve loop only)
   SchedArgs<R> sc;
   unsigned int* tile_cnt;  // [case tiles] completion counters, NULL: no scheduler
+  // mixed precision (DPF_MIXED): FP64 forward pass over FP64 voltages, FP32
+  // adjoint and optimiser on the double-float master
+  double2* V64m;           // [N][Kp] FP64 voltages (NULL: not mixed)
+  YView<double> Y64;       // FP64 Y_bus values
+  const double* pspec64;   // FP64 specified injections ([N][Kp] per case, or [N])
+  const double* qspec64;
+  const double2* yff64;    // FP64 N-1 blocks per case
+  const double2* yft64;
+  const double2* ytt64;
   // optional outputs (evaluation entry points); NULL in the solve loop
   C* sbuf;   // S_calc
   C* cbuf;   // c = (2/m)(dP + j dQ)
@@ -782,7 +791,7 @@ template <class R> struct AdjRow {
   M th, vm;
 };
 
-template <class R, class YS>
+template <class R, class YS, bool MIXED = false>
 __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, AdjRow<R>& r, int i, int r1, int k,
                                          size_t Kp, bool grad_only) {
   r.live = false;
@@ -804,7 +813,12 @@ __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, Adj
   const typename Prec<R>::MS s = ld_stream(a.ms + e);
   r.th = ms_th(s);
   r.vm = ms_vm(s);
-  r.vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
+  if constexpr (MIXED) {  // the FP64 voltage, rounded for the FP32 adjoint
+    const double2 v = a.V64m[e];
+    r.vi = mkc((R)v.x, (R)v.y);
+  } else {
+    r.vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
+  }
   r.m1 = r.v1 = r.m2 = r.v2 = R(0);
   if (!grad_only) {
     // full 16-byte accesses at pv buses too (their |V| halves pass through
@@ -832,7 +846,7 @@ __device__ __forceinline__ void adj_gather(const IterArgs<R>& a, const YS& ys, A
   }
 }
 
-template <class R>
+template <class R, bool MIXED = false>
 __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, bool grad_only, R step, R isb, R b1,
                                            R b2, R eps) {
   using C = typename Prec<R>::C;
@@ -853,13 +867,14 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
   if (r.ty == BUS_PQ) r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha);
   st_stream(a.ms + e, ms_make(r.th, r.vm));
   mom_store(a.os + e, Mom<R>{r.m1, r.v1, r.m2, r.v2});
-  a.V[e] = volt(r.th, r.vm);
+  if constexpr (MIXED) a.V64m[e] = volt64(r.th, r.vm);  // FP64 voltage from the master
+  else a.V[e] = volt(r.th, r.vm);
 }
 
 #ifndef DPF_ADJ_MINB
 #define DPF_ADJ_MINB 4
 #endif
-template <class R>
+template <class R, bool MIXED = false>
 __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
@@ -896,13 +911,89 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   for (int i0 = mp.i0; i0 < mp.r1; i0 += NR * mp.istride) {
     AdjRow<R> rw[NR];
 #pragma unroll
-    for (int u = 0; u < NR; ++u) adj_load(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
+    for (int u = 0; u < NR; ++u)
+      adj_load<R, YSmem<R>, MIXED>(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
       if (rw[u].live) adj_gather(a, ys, rw[u], k, Kp, of, ot, yff, yft, ytt);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
-      if (rw[u].live) adj_finish(a, rw[u], grad_only, step, isb, b1, b2, eps);
+      if (rw[u].live) adj_finish<R, MIXED>(a, rw[u], grad_only, step, isb, b1, b2, eps);
+  }
+}
+
+// ---- mixed precision forward pass (DPF_MIXED) -------------------------------
+// The mismatch of a current I_i = sum_j Y_ij V_j that cancels terms of size
+// |Y_ii| to a result of order 1 has an FP32 error of a few |Y_ii| 2^-24 --
+// about 1e-5 p.u. on grids with short lines, above a 1e-6 p.u. target.  This
+// pass reads FP64 voltages and FP64 Y_bus values and forms S, dP, dQ, the
+// weights c and w = c conj(V) in FP64; it hands the FP32 adjoint w, Q_calc at
+// pv buses and the loss partials in FP32 (the gradient needs no more: near
+// convergence its error is relative to the small mismatch it is built from).
+__global__ void __launch_bounds__(256, 4) k_fwd_mixed(IterArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BMap mp = block_map(a.lanes, a.N, a.rpb);
+  YSmem<double> ys;
+  ys.stage(a.prp, a.ppos, a.Y64, a.type, mp.r0, mp.r1, (unsigned)a.Kp, smem);
+  pdl_wait();
+  pdl_release();
+  const int k = mp.k;
+  const bool inb = k < a.Kp;
+  const int act = inb ? a.active[k] : 0;
+  int of = -1, ot = -1;
+  double2 yff = make_double2(0.0, 0.0), yft = yff, ytt = yff;
+  if (inb && a.has_outage) {
+    of = a.of[k];
+    ot = a.ot[k];
+    yff = a.yff64[k];
+    yft = a.yft64[k];
+    ytt = a.ytt64[k];
+  }
+  if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
+    if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
+    return;
+  }
+  const double inv_m2 = 1.0 / (double)a.m_half;  // 2 / m (m_half is exact in FP32)
+  double acc = 0.0;
+  float mx = 0.f;
+  if (act) {
+    const size_t Kp = (size_t)a.Kp;
+    const double2* __restrict__ V = a.V64m;
+    for (int i = mp.i0; i < mp.r1; i += mp.istride) {
+      const size_t e = (size_t)i * Kp + k;
+      const int ty = ys.ty[i];
+      const size_t si = a.spec_per_case ? e : (size_t)i;
+      const double2 vi = V[e];
+      const double ps = a.pspec64[si], qs = a.qspec64[si];
+      double2 I = row_spmv<double>(ys, ys.rp[i], ys.rp[i + 1], V + k);
+      if (i == of) {
+        cfms(I, yff, vi);
+        cfms(I, yft, V[(size_t)ot * Kp + k]);
+      } else if (i == ot) {
+        cfms(I, yft, V[(size_t)of * Kp + k]);
+        cfms(I, ytt, vi);
+      }
+      const double2 S = power_of(vi, I);
+      const double dP = (ty != BUS_SLACK) ? S.x - ps : 0.0;
+      const double dQ = (ty == BUS_PQ) ? S.y - qs : 0.0;
+      const double ca = inv_m2 * dP, cb = inv_m2 * dQ;
+      const double2 w = w_of(ca, cb, vi);
+      a.W[e] = make_float2((float)w.x, (float)w.y);
+      if (ty == BUS_PV) st_stream(a.qpv + e, (float)S.y);
+      acc = fma(dP, dP, fma(dQ, dQ, acc));
+      const float am = (float)fmax(fabs(dP), fabs(dQ));
+      mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);  // NaN -> +inf
+    }
+  }
+  if (a.loss_part || a.mx32) case_sum_max_atomic((float)acc, mx, a.lanes, a.loss_part, a.mx32, a.Kp);
+  if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
+}
+
+// FP64 voltages from the double-float master (mixed precision set-up).
+__global__ void k_mixed_v64(const float4* __restrict__ ms, double2* __restrict__ v, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float4 s = ms[e];
+    v[e] = volt64(ms_th(s), ms_vm(s));
   }
 }
 

@@ -430,3 +430,53 @@ def test_solve_repeats_bit_for_bit(precision):
     b = _solve(y, ws, K, opts, **kw)
     for key in ("va", "vm", "iters", "status", "max_mismatch"):
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_c1_converges_to_nr_mixed():
+    """DPF_MIXED (FP64 forward pass and voltages, FP32 adjoint and optimiser)
+    reaches 1e-6 p.u. on the 30-bus grid, which FP32 iterations cannot (their
+    current's cancellation error is ~1e-5 p.u. here), and lands on the NR
+    solution; FP32 iterations of the same batch stall above 1e-6."""
+    g = GRIDS["c1"]()
+    Y = grid_ybus(g)
+    K = 64
+    rng = np.random.default_rng(5)
+    sc = 1 + 0.05 * rng.uniform(-1, 1, (K, 1))
+    P, Q = g.p_spec[None, :] * sc, g.q_spec[None, :] * sc
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    base = dict(max_iter=20000, check_every=25, lr=1e-2)
+    r = _solve(y, ws, K, dpf.SolveOpts(precision=dpf.MIXED, **base), p_spec=_t(P), q_spec=_t(Q))
+    assert (r["status"] == dpf.CASE_CONVERGED).all() and (r["max_mismatch"] <= 1e-6).all()
+    for k in (0, K // 2, K - 1):
+        f, _ = oracle.mismatch(Y, r["va"][k], r["vm"][k], P[k], Q[k], g.bus_type)
+        assert abs(np.abs(f).max() - r["max_mismatch"][k]) <= 1e-12
+        nr = oracle.nr_solve(Y, P[k], Q[k], g.bus_type, g.vm_set)
+        assert np.abs(r["vm"][k] - nr["vm"]).max() < 1e-5
+        assert np.abs(r["va"][k] - nr["va"]).max() < 1e-5
+    f32 = _solve(y, ws, K, dpf.SolveOpts(precision=dpf.FP32, **base), p_spec=_t(P), q_spec=_t(Q))
+    assert (f32["status"] != dpf.CASE_CONVERGED).all()
+
+
+def test_mixed_n1_batch_against_oracle():
+    """DPF_MIXED on N-1 cases of the 2,000-bus grid: the FP64 mismatch
+    reported for each case equals the oracle's recomputation from the returned
+    voltages, and the iterates stay within the FP32 bar of the oracle's FP64
+    trajectory (the adjoint and the optimiser run in FP32)."""
+    g = GRIDS["c3"]()
+    K = 70
+    outs = np.random.default_rng(13).choice(gridgen.n1_outages(g), K, replace=False).astype(np.int32)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    r = _solve(y, ws, K, dpf.SolveOpts(precision=dpf.MIXED, max_iter=60, check_every=10, lr=1e-3),
+               outage=_t(outs, torch.int32))
+    for k in (0, K // 2, K - 1):
+        keep = np.arange(g.n_branch) != outs[k]
+        Yk = oracle.build_ybus(g.n_bus, g.f_bus[keep], g.t_bus[keep], g.r[keep], g.x[keep], g.b_ch[keep],
+                               g.tap[keep])
+        f, _ = oracle.mismatch(Yk, r["va"][k], r["vm"][k], g.p_spec, g.q_spec, g.bus_type)
+        assert abs(np.abs(f).max() - r["max_mismatch"][k]) <= 1e-9
+        ref = oracle.dpf_solve(Yk, g.p_spec, g.q_spec, g.bus_type, g.vm_set,
+                               oracle.DPFOptions(lr=1e-3, max_iter=60, check_every=10), va_slack=g.va_slack)
+        assert np.abs(r["va"][k] - ref["va"]).max() <= 5e-3
+        assert np.abs(r["vm"][k] - ref["vm"]).max() <= 5e-3
