@@ -527,6 +527,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
       a.yff64 = w->yff64;
       a.yft64 = w->yft64;
       a.ytt64 = w->ytt64;
+      a.inv_m2_64 = y->m_loss > 0 ? 2.0 / y->m_loss : 0.0;
     }
   }
 

@@ -201,6 +201,8 @@ template <class M> __device__ __forceinline__ double2 volt64(M th, M vm) {
   return make_double2(m * c, m * s);
 }
 
+
+
 // ---- Y_bus views -----------------------------------------------------------
 template <class R> struct YView;
 template <> struct YView<float> {
@@ -613,6 +615,7 @@ template <class R> struct IterArgs {
   const double2* yff64;    // FP64 N-1 blocks per case
   const double2* yft64;
   const double2* ytt64;
+  double inv_m2_64;        // 2 / m in FP64
   // optional outputs (evaluation entry points); NULL in the solve loop
   C* sbuf;   // S_calc
   C* cbuf;   // c = (2/m)(dP + j dQ)
@@ -867,7 +870,7 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
   if (r.ty == BUS_PQ) r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha);
   st_stream(a.ms + e, ms_make(r.th, r.vm));
   mom_store(a.os + e, Mom<R>{r.m1, r.v1, r.m2, r.v2});
-  if constexpr (MIXED) a.V64m[e] = volt64(r.th, r.vm);  // FP64 voltage from the master
+  if constexpr (MIXED) a.V64m[e] = volt64(r.th, r.vm);  // FP64 voltage from the master (FP64 sincos)
   else a.V[e] = volt(r.th, r.vm);
 }
 
@@ -953,7 +956,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd_mixed(IterArgs<float> a) {
     if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
     return;
   }
-  const double inv_m2 = 1.0 / (double)a.m_half;  // 2 / m (m_half is exact in FP32)
+  const double inv_m2 = a.inv_m2_64;
   double acc = 0.0;
   float mx = 0.f;
   if (act) {
