@@ -105,7 +105,7 @@ int pow2ceil(int v) {
 // Y_bus upload
 // ---------------------------------------------------------------------------
 static void free_device(DeviceYbus& d) {
-  dfree(d.ent32); dfree(d.row_ptr); dfree(d.prow_ptr); dfree(d.ppos); dfree(d.col); dfree(d.dcval); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
+  dfree(d.ent32); dfree(d.row_ptr); dfree(d.prow_ptr); dfree(d.ppos); dfree(d.col); dfree(d.dcval); dfree(d.dcinv); dfree(d.val64); dfree(d.ebr); dfree(d.dpos);
   dfree(d.type); dfree(d.p64); dfree(d.q64); dfree(d.vmset); dfree(d.p32); dfree(d.q32);
   dfree(d.perm); dfree(d.iperm); dfree(d.br_f); dfree(d.br_t); dfree(d.br_r); dfree(d.br_x);
   dfree(d.br_bch); dfree(d.br_tap); dfree(d.br_itap); dfree(d.bridge);
@@ -160,6 +160,11 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
       dcval[p] = -bdc[l];
       dcval[y->idpos[i]] += bdc[l];
     }
+  std::vector<double> dcinv(n);
+  for (int i = 0; i < n; ++i) {
+    const double dii = dcval[y->idpos[i]];
+    dcinv[i] = dii != 0.0 ? 1.0 / dii : 0.0;
+  }
   int rc = DPF_OK;
   do {
     if ((rc = upload(&d.ent32, ent, s))) break;
@@ -169,6 +174,7 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
     if ((rc = upload(&d.col, y->icol, s))) break;
     if ((rc = upload(&d.val64, v64, s))) break;
     if ((rc = upload(&d.dcval, dcval, s))) break;
+    if ((rc = upload(&d.dcinv, dcinv, s))) break;
     if ((rc = upload(&d.ebr, y->iebr, s))) break;
     if ((rc = upload(&d.dpos, y->idpos, s))) break;
     if ((rc = upload(&d.type, type, s))) break;
@@ -1112,6 +1118,7 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   a.col = d.col;
   a.bval = d.dcval;
   a.dpos = d.dpos;
+  a.dinv = d.dcinv;
   a.type = d.type;
   a.spec_per_case = w->spec_per_case ? 1 : 0;
   a.pspec = w->spec_per_case ? w->p64 : d.p64;
@@ -1121,8 +1128,12 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   a.x = w->tmp_a;
   a.r = w->tmp_b;
   a.z = w->tmp_c;
-  a.p = (double*)w->V64;
+  const size_t E0 = (size_t)y->n * Kp;
+  a.p = (double*)w->V64;            // the two direction buffers share V64's 16 B/element
+  a.p_new = (double*)w->V64 + E0;
   a.q = (double*)w->sbuf;
+  a.rpb = w->rpb;
+  a.tile_cnt = w->tile_cnt;
   double* c = w->dcs;
   a.rz = c;
   a.rzn = c + Kp;
@@ -1146,11 +1157,10 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   k_dc_start<<<grid, block, 0, s>>>(a);
   CKLAUNCH();
   for (int it = 0; it < max_iter; ++it) {
-    k_dc_spmv<<<grid, block, 0, s>>>(a);
-    k_dc_update<<<grid, block, 0, s>>>(a);
-    k_dc_case<<<cb, 256, 0, s>>>(a);
-    k_dc_dir<<<grid, block, 0, s>>>(a);
+    k_dc_spmv_dir<<<grid, block, 0, s>>>(a);
+    k_dc_update_case<<<grid, block, 0, s>>>(a);
     CKLAUNCH();
+    std::swap(a.p, a.p_new);
     if ((it & 15) == 15 || it == max_iter - 1) {
       CK(cudaMemcpyAsync(w->h_dc_nact, a.n_active, 4, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));

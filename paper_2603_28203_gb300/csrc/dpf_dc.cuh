@@ -9,15 +9,22 @@
 // B' = B - b_l (e_f - e_t)(e_f - e_t)^T of the shared B, as for the N-1 Y_bus.
 //
 // Solver: conjugate gradients with the Jacobi preconditioner, in FP64, all
-// cases at once in the case-minor layout (element (i, k) at i*Kp + k).  One
-// iteration is four launches:
-//   k_dc_spmv    q = B' p and the per-case partial sums of p.q
-//   k_dc_update  alpha = rz / pq; x += alpha p; r -= alpha q; z = r / diag(B');
-//                partial sums of r.z and r.r
-//   k_dc_case    per case: stop when |r| <= tol |r0|, else beta = rz' / rz
-//   k_dc_dir     p = z + beta p
-// Slack rows are not unknowns: their r, z, p stay 0 and their x holds the
-// slack angle.
+// cases at once in the case-minor layout (element (i, k) at i*Kp + k), each
+// CTA on a contiguous block of rows.  One iteration is two launches:
+//   k_dc_spmv_dir     the new direction p' = z + beta p and q' = B' p', formed
+//                     as B' z + beta q from the previous q = B' p (so no CTA
+//                     waits for another's p' and p is never gathered), and the
+//                     per-case partial sums of p'.q'
+//   k_dc_update_case  alpha = rz / pq; x += alpha p'; r -= alpha q';
+//                     z = r / diag(B'); partial sums of r.z and r.r; the last
+//                     CTA of each case tile then takes the per-case step:
+//                     stop when |r| <= tol |r0|, else beta = rz' / rz
+// The recurrence for q' is the same arithmetic as B' p' up to rounding.  On
+// this GPU the loop is bound by FP64 issue (a few FP64 FMA per clock per SM),
+// so the Jacobi step multiplies by the inverse diagonal uploaded with B rather
+// than dividing, except at the two rows an outage changes.  The two direction
+// buffers alternate.  Slack rows are not unknowns: their
+// r, z, p stay 0 and their x holds the slack angle.
 #pragma once
 
 #include "dpf_kernels.cuh"
@@ -30,6 +37,7 @@ struct DCArgs {
   const int32_t* __restrict__ col;
   const double* __restrict__ bval;  // B values in CSR order
   const int32_t* __restrict__ dpos;  // position of each row's diagonal entry
+  const double* __restrict__ dinv;  // [N] 1 / B_ii
   const uint8_t* __restrict__ type;
   const double* pspec;  // [N][Kp] per case or [N]
   int spec_per_case;
@@ -40,8 +48,11 @@ struct DCArgs {
   double* x;
   double* r;
   double* z;
-  double* p;
-  double* q;
+  double* p;       // direction of the previous iteration
+  double* p_new;   // direction of this iteration
+  double* q;       // B' p of the previous iteration, then of this one
+  int rpb;                  // rows per CTA
+  unsigned int* tile_cnt;   // per case tile: CTAs done with the update (reset by the last)
   // per case
   double* rz;
   double* rzn;
@@ -100,6 +111,11 @@ __device__ __forceinline__ double dc_diag(const DCArgs& a, int i, int of, int ot
   return (i == of || i == ot) ? d - ob : d;
 }
 
+// Jacobi step z_i = r_i / B'_ii.
+__device__ __forceinline__ double dc_jacobi(const DCArgs& a, double r, int i, int of, int ot, double ob) {
+  return (i == of || i == ot) ? r / dc_diag(a, i, of, ot, ob) : r * __ldg(a.dinv + i);
+}
+
 // Per case: the outaged branch's susceptance, the solver state reset.
 __global__ void k_dc_case_init(DCArgs a, const int32_t* __restrict__ outage, const double* __restrict__ br_x,
                                const double* __restrict__ br_tap) {
@@ -114,13 +130,15 @@ __global__ void k_dc_case_init(DCArgs a, const int32_t* __restrict__ outage, con
   a.res[k] = 0.0;
 }
 
-// x0 (slack angle at slack buses, 0 elsewhere) for every element.
+// x0 (slack angle at slack buses, 0 elsewhere) for every element; p, q zeroed.
 __global__ void k_dc_x0(DCArgs a) {
   const size_t n = (size_t)a.N * a.Kp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / a.Kp);
     a.x[e] = (__ldg(a.type + i) == BUS_SLACK) ? a.va_slack : 0.0;
     a.p[e] = 0.0;
+    a.p_new[e] = 0.0;
+    a.q[e] = 0.0;  // q' = B' z + beta q reads it with beta = 0 first
   }
 }
 
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(1024) k_dc_start(DCArgs a) {
       if (__ldg(a.type + i) != BUS_SLACK) {
         const double P = a.spec_per_case ? a.pspec[e] : a.pspec[i];
         r = P - dc_row(a, a.x, i, k, Kp, of, ot, ob);
-        z = r / dc_diag(a, i, of, ot, ob);
+        z = dc_jacobi(a, r, i, of, ot, ob);
       }
       a.r[e] = r;
       a.z[e] = z;
@@ -151,62 +169,40 @@ __global__ void __launch_bounds__(1024) k_dc_start(DCArgs a) {
   case_sum2_atomic(rz, rr, a.lanes, a.rz, a.rr0, a.Kp);
 }
 
-__global__ void __launch_bounds__(1024) k_dc_spmv(DCArgs a) {
-  const Map mp = thread_map(a.lanes);
+__global__ void __launch_bounds__(256) k_dc_spmv_dir(DCArgs a) {
+  const BMap mp = block_map(a.lanes, a.N, a.rpb);
   const int k = mp.k;
   const size_t Kp = (size_t)a.Kp;
   double pq = 0.0;
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const double ob = a.ob[k];
-    for (int i = mp.row0; i < a.N; i += mp.rstride) {
+    const double ob = a.ob[k], beta = a.beta[k];
+    for (int i = mp.i0; i < mp.r1; i += mp.istride) {
+      if (__ldg(a.type + i) == BUS_SLACK) continue;  // p, q stay 0 there
       const size_t e = (size_t)i * Kp + k;
-      const double q = (__ldg(a.type + i) != BUS_SLACK) ? dc_row(a, a.p, i, k, Kp, of, ot, ob) : 0.0;
+      const double pn = fma(beta, a.p[e], a.z[e]);
+      const double q = fma(beta, a.q[e], dc_row(a, a.z, i, k, Kp, of, ot, ob));
+      a.p_new[e] = pn;
       a.q[e] = q;
-      pq = fma(a.p[e], q, pq);
+      pq = fma(pn, q, pq);
     }
   }
   case_sum2_atomic(pq, 0.0, a.lanes, a.pq, nullptr, a.Kp);
 }
 
-__global__ void __launch_bounds__(1024) k_dc_update(DCArgs a) {
-  const Map mp = thread_map(a.lanes);
-  const int k = mp.k;
-  const size_t Kp = (size_t)a.Kp;
-  double rz = 0.0, rr = 0.0;
-  if (k < a.Kp && a.active[k]) {
-    const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const double ob = a.ob[k];
-    const double alpha = a.pq[k] != 0.0 ? a.rz[k] / a.pq[k] : 0.0;
-    for (int i = mp.row0; i < a.N; i += mp.rstride) {
-      if (__ldg(a.type + i) == BUS_SLACK) continue;
-      const size_t e = (size_t)i * Kp + k;
-      a.x[e] = fma(alpha, a.p[e], a.x[e]);
-      const double r = fma(-alpha, a.q[e], a.r[e]);
-      const double z = r / dc_diag(a, i, of, ot, ob);
-      a.r[e] = r;
-      a.z[e] = z;
-      rz = fma(r, z, rz);
-      rr = fma(r, r, rr);
-    }
-  }
-  case_sum2_atomic(rz, rr, a.lanes, a.rzn, a.rr, a.Kp);
-}
-
-// One thread per case: convergence test and the next direction's beta.
-__global__ void k_dc_case(DCArgs a) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.Kp) return;
+// Per case, after all row blocks' sums: convergence test and the next beta.
+__device__ __forceinline__ void dc_case_step(const DCArgs& a, int k) {
   if (a.active[k]) {
     a.iters[k] += 1;
-    const double rr = a.rr[k], rr0 = a.rr0[k];
+    const double rr = __ldcg(a.rr + k), rr0 = __ldcg(a.rr0 + k), rzn = __ldcg(a.rzn + k);
     a.res[k] = rr0 > 0.0 ? sqrt(rr / rr0) : 0.0;
     if (rr <= a.tol2 * rr0 || !(rr == rr)) {  // converged (or broken down: NaN)
       a.active[k] = 0;
       atomicSub(a.n_active, 1);
     } else {
-      a.beta[k] = a.rz[k] != 0.0 ? a.rzn[k] / a.rz[k] : 0.0;
-      a.rz[k] = a.rzn[k];
+      const double rz = __ldcg(a.rz + k);
+      a.beta[k] = rz != 0.0 ? rzn / rz : 0.0;
+      a.rz[k] = rzn;
     }
   }
   a.rzn[k] = 0.0;
@@ -214,15 +210,46 @@ __global__ void k_dc_case(DCArgs a) {
   a.rr[k] = 0.0;
 }
 
-__global__ void __launch_bounds__(1024) k_dc_dir(DCArgs a) {
-  const Map mp = thread_map(a.lanes);
+__global__ void __launch_bounds__(256) k_dc_update_case(DCArgs a) {
+  const BMap mp = block_map(a.lanes, a.N, a.rpb);
   const int k = mp.k;
-  if (k >= a.Kp || !a.active[k]) return;
   const size_t Kp = (size_t)a.Kp;
-  const double beta = a.beta[k];
-  for (int i = mp.row0; i < a.N; i += mp.rstride) {
-    const size_t e = (size_t)i * Kp + k;
-    a.p[e] = fma(beta, a.p[e], a.z[e]);
+  double rz = 0.0, rr = 0.0;
+  if (k < a.Kp && a.active[k]) {
+    const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
+    const double ob = a.ob[k];
+    const double pq = __ldcg(a.pq + k);
+    const double alpha = pq != 0.0 ? __ldcg(a.rz + k) / pq : 0.0;
+    for (int i = mp.i0; i < mp.r1; i += mp.istride) {
+      if (__ldg(a.type + i) == BUS_SLACK) continue;
+      const size_t e = (size_t)i * Kp + k;
+      a.x[e] = fma(alpha, a.p_new[e], a.x[e]);
+      const double r = fma(-alpha, a.q[e], a.r[e]);
+      const double z = dc_jacobi(a, r, i, of, ot, ob);
+      a.r[e] = r;
+      a.z[e] = z;
+      rz = fma(r, z, rz);
+      rr = fma(r, r, rr);
+    }
+  }
+  case_sum2_atomic(rz, rr, a.lanes, a.rzn, a.rr, a.Kp);
+  // the last CTA of the case tile (every CTA counts itself after fencing its
+  // atomics) takes the per-case step for the tile's cases
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(a.tile_cnt + blockIdx.x, 1u);
+    last = (prev == gridDim.y - 1);
+    if (last) a.tile_cnt[blockIdx.x] = 0u;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int c = threadIdx.x; c < a.lanes; c += blockDim.x) {
+      const int kk = blockIdx.x * a.lanes + c;
+      if (kk < a.Kp) dc_case_step(a, kk);
+    }
   }
 }
 
