@@ -326,6 +326,52 @@ int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
                  int32_t max_iter, double* va, int32_t* iters,
                  double* rel_residual, void* stream);
 
+/* ---- Newton-Raphson (Alg. 2) on the GPU ------------------------------------
+ * The ground-truth solver of the paper (Alg. 2) for the same batches as
+ * dpf_solve_batch, and the second stage of a hybrid in which Alg. 1 supplies
+ * the start (its solution passed as va/vm with flat_start = 0).  Each Newton
+ * step solves J_f dx = -f with J_f the Jacobian of Alg. 2 (rows P at pv and
+ * pq buses, Q at pq buses; unknowns theta at pv and pq, |V| at pq), written
+ * per bus as 2x2 blocks on the pattern of Y_bus (left-out rows and columns
+ * become identity rows and columns), factorised by block LU without pivoting
+ * outside the 2x2 diagonal blocks in a minimum-degree order found on the host.
+ *
+ * dpf_nr_create: host analysis of Y_bus (order, filled pattern, elimination
+ * tree, update lists) and the device buffers for up to max_case cases (the
+ * factor takes n_pos * 32 bytes per case).  y must be uploaded
+ * (DPF_E_STATE otherwise) and outlive the handle.  Synchronous.
+ * Errors: DPF_E_INVALID, DPF_E_OOM, DPF_E_UNSUPPORTED (update lists above
+ * 2^28 block products or factor storage above 2^40 bytes).
+ *
+ * dpf_nr_solve: every case of the batch (device pointers only: host_io must
+ * be 0; p_spec/q_spec/vm_set/outage as for dpf_solve_batch) from the flat
+ * start (flat_start = 1) or from va/vm (fixed |V| and the slack angle
+ * enforced), Newton steps until FP64 max |f| <= tol or max_iter steps.
+ * precision: DPF_FP64 factorises and solves in FP64; DPF_FP32 in FP32 (the
+ * mismatch, the stop test and the state stay FP64; convergence turns linear
+ * at about cond(J) 2^-24 per step near the solution).  Outputs: va, vm
+ * (solution), iters (Newton steps), status (DPF_CASE_CONVERGED, _MAX_ITER,
+ * or _DIVERGED: a non-finite mismatch or a singular diagonal block),
+ * max_mismatch and loss of the returned state (any of the last four may be
+ * NULL).  Reads the number of unconverged cases from the device after every
+ * step (synchronises `stream`).  Errors: DPF_E_INVALID (sizes, pointers,
+ * outage index), DPF_E_ISLANDED (an outage of a bridge).
+ *
+ * dpf_nr_stats: positions of the filled pattern, block products of one
+ * factorisation, tree levels, kernels enqueued so far (any output may be NULL).
+ * dpf_nr_analyze / dpf_nr_pattern: the host analysis alone, no CUDA call:
+ * sizes, and the elimination order (user bus indices, [n_bus]), the filled
+ * pattern in that order (row_ptr [n_bus + 1], col [n_pos]) and the tree
+ * level of every step ([n_bus]); any array may be NULL. */
+typedef struct dpf_nr dpf_nr;
+int dpf_nr_create(const dpf_ybus* y, int32_t max_case, dpf_nr** out);
+int dpf_nr_free(dpf_nr* h);
+int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, double tol, int32_t max_iter,
+                 int32_t flat_start, void* stream);
+int dpf_nr_stats(const dpf_nr* h, int64_t* n_pos, int64_t* n_pairs, int32_t* n_levels, int64_t* launches);
+int dpf_nr_analyze(const dpf_ybus* y, int64_t* n_pos, int64_t* n_pairs, int32_t* n_levels);
+int dpf_nr_pattern(const dpf_ybus* y, int32_t* order, int32_t* row_ptr, int32_t* col, int32_t* level);
+
 /* ---- parameter identification over measured operating points -------------
  * The gradient of the loss to the branch parameters (Sec. 1 / abstract:
  * gradients to the simulation parameters, which lets them be identified)

@@ -83,6 +83,12 @@ SIGNATURES = {
     "dpf_power_noalloc": (C.c_int, [VP, I32, VP, VP, VP, VP, VP]),
     "dpf_paramid_begin": (C.c_int, [VP, VP, I32, VP, VP, VP, VP, I32, VP]),
     "dpf_dc_solve": (C.c_int, [VP, VP, I32, VP, VP, C.c_double, I32, VP, VP, VP, VP]),
+    "dpf_nr_create": (C.c_int, [VP, I32, C.POINTER(VP)]),
+    "dpf_nr_free": (C.c_int, [VP]),
+    "dpf_nr_solve": (C.c_int, [VP, C.POINTER(DpfBatch), I32, C.c_double, I32, I32, VP]),
+    "dpf_nr_stats": (C.c_int, [VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64), p_i32, C.POINTER(C.c_int64)]),
+    "dpf_nr_analyze": (C.c_int, [VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64), p_i32]),
+    "dpf_nr_pattern": (C.c_int, [VP, VP, VP, VP, VP]),
     "dpf_paramid_step": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "dpf_profile_enable": (C.c_int, [VP, I32]),
     "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),

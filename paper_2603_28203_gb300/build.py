@@ -34,7 +34,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     objs, cmds = [], []
-    for src in ("dpf_api.cu", "dpf_noalloc.cu"):
+    for src in ("dpf_api.cu", "dpf_noalloc.cu", "dpf_nr.cu"):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         cu = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I" + INCLUDE, *os.environ.get("DPF_NVCC_FLAGS", "").split(), "-c", os.path.join(CSRC, src),
@@ -43,10 +43,11 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
             cu.insert(1, "-Xptxas=-v")
         objs.append(obj)
         cmds.append(cu)
-    host_o = os.path.join(OUT_DIR, "dpf_host.o")
-    cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE,
-                 "-I" + os.path.join(cuda, "include"), "-c", os.path.join(CSRC, "dpf_host.cpp"), "-o", host_o])
-    objs.append(host_o)
+    for src in ("dpf_host.cpp", "dpf_nr_symbolic.cpp"):
+        host_o = os.path.join(OUT_DIR, src.replace(".cpp", ".o"))
+        cmds.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE,
+                     "-I" + os.path.join(cuda, "include"), "-c", os.path.join(CSRC, src), "-o", host_o])
+        objs.append(host_o)
     with ThreadPoolExecutor(len(cmds)) as ex:
         outs = list(ex.map(_run, cmds))
     tmp = LIB + ".tmp"

@@ -1,0 +1,770 @@
+// Batched Newton-Raphson power flow (Alg. 2) on the GPU, for the same batches
+// dpf_solve_batch takes (one Y_bus, per-case injections and one outage each):
+// the comparison solver of the paper and the second half of a hybrid in which
+// Alg. 1 supplies the starting point (Sec. 5.4, Sec. 6).
+//
+// Per Newton iteration, for every case still iterating:
+//   k_nr_volt      V = |V| e^{j theta} (FP64)
+//   k_nr_eval      I = Y' V, S = V conj(I), f, right-hand side -f (FP64)
+//   k_nr_check     per case max |f|, loss, stop test (the host reads the
+//                  number of cases left)
+//   k_nr_assemble  the 2x2 Jacobian blocks of Alg. 2 on the filled pattern
+//   k_nr_factor    block LU, left-looking, level by level of the elimination
+//                  tree; one CTA per tile of cases, which syncs only its own
+//                  threads: the cases are independent, so no CTA waits for
+//                  another
+//   k_nr_solve     L y = -f, U dx = y, level by level
+//   k_nr_update    theta += dx_theta (pv, pq), |V| += dx_|V| (pq)
+// The factor and the triangular solves run in the factor precision (FP64, or
+// FP32: GB300 issues FP32 FMA at many times its FP64 rate, and a Newton step
+// solved to FP32 accuracy still converges, linearly at a rate of about
+// cond(J) 2^-24 once quadratic convergence has run out); the mismatch, the
+// stop test and the state are FP64 in both.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "dpf_internal.h"
+#include "dpf_nr.h"
+
+using namespace dpf;
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(e_ == cudaErrorMemoryAllocation ? DPF_E_OOM : DPF_E_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+  } while (0)
+
+#define CKLAUNCH()                                                                            \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(DPF_E_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                  \
+  } while (0)
+
+#define TRY(x)                   \
+  do {                           \
+    int s_ = (x);                \
+    if (s_ != DPF_OK) return s_; \
+  } while (0)
+
+namespace {
+
+constexpr uint8_t NR_PQ = 0, NR_SLACK = 2;  // bus types (pv = 1)
+constexpr int NR_THREADS = 256;
+
+// 2x2 block: rows (P, Q), columns (theta, |V|), row-major.
+template <class T>
+struct alignas(4 * sizeof(T)) Blk {
+  T a, b, c, d;
+};
+
+template <class T>
+__device__ __forceinline__ Blk<T> ldb(const Blk<T>* p) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ Blk<double> ldb(const Blk<double>* p) {
+  const double2 u = reinterpret_cast<const double2*>(p)[0], v = reinterpret_cast<const double2*>(p)[1];
+  return Blk<double>{u.x, u.y, v.x, v.y};
+}
+template <class T>
+__device__ __forceinline__ void stb(Blk<T>* p, const Blk<T>& v) {
+  *p = v;
+}
+template <>
+__device__ __forceinline__ void stb(Blk<double>* p, const Blk<double>& v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.a, v.b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.c, v.d);
+}
+
+// acc -= x y
+template <class T>
+__device__ __forceinline__ void msub(Blk<T>& acc, const Blk<T>& x, const Blk<T>& y) {
+  acc.a = fma(-x.a, y.a, fma(-x.b, y.c, acc.a));
+  acc.b = fma(-x.a, y.b, fma(-x.b, y.d, acc.b));
+  acc.c = fma(-x.c, y.a, fma(-x.d, y.c, acc.c));
+  acc.d = fma(-x.c, y.b, fma(-x.d, y.d, acc.d));
+}
+template <class T>
+__device__ __forceinline__ Blk<T> mul(const Blk<T>& x, const Blk<T>& y) {
+  return Blk<T>{fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d), fma(x.c, y.a, x.d * y.c),
+                fma(x.c, y.b, x.d * y.d)};
+}
+// inverse of a 2x2 block; false if it is singular (or not finite)
+template <class T>
+__device__ __forceinline__ bool inv2(const Blk<T>& m, Blk<T>& r) {
+  const T det = fma(m.a, m.d, -m.b * m.c);
+  const T id = T(1) / det;
+  r = Blk<T>{m.d * id, -m.b * id, -m.c * id, m.a * id};
+  return det != T(0) && isfinite(id);
+}
+
+__device__ __forceinline__ double2 cmul(double2 x, double2 y) {
+  return make_double2(fma(x.x, y.x, -x.y * y.y), fma(x.x, y.y, x.y * y.x));
+}
+__device__ __forceinline__ double2 cconj(double2 x) { return make_double2(x.x, -x.y); }
+__device__ __forceinline__ double2 csub(double2 x, double2 y) { return make_double2(x.x - y.x, x.y - y.y); }
+
+struct NrArgs {
+  int N, K, Kp, C;
+  double va_slack, tol, inv_m;
+  int max_iter;
+  // grid (device, internal order)
+  const int32_t* rp;
+  const int32_t* ycol;
+  const double2* yval;
+  const uint8_t* type;
+  const double* p64;
+  const double* q64;
+  const double* vmset;
+  const int32_t* perm;
+  // schedule
+  const int32_t* order;
+  const int32_t* rank;
+  const int32_t* frp;
+  const int32_t* fcol;
+  const int32_t* fdiag;
+  const int32_t* prow;
+  const int32_t* ymap;
+  int n_levels;
+  const int32_t* lvl_ptr;
+  const int4* targets;
+  const int2* pairs;
+  const int32_t* rlvl_ptr;
+  const int32_t* rows;
+  int64_t npos;
+  // state [N][Kp]
+  double* th;
+  double* vm;
+  double2* V;
+  double2* I;
+  double2* X;    // right-hand side / solution, by elimination step
+  double* Ps;    // per-case specification or NULL
+  double* Qs;
+  void* F;       // [npos][Kp] blocks
+  void* Dinv;    // [N][Kp] blocks
+  // per case
+  int32_t* of;
+  int32_t* ot;
+  double2* yff;
+  double2* yft;
+  double2* ytt;
+  int32_t* active;
+  int32_t* status;
+  int32_t* iters;
+  int32_t* bad;
+  double* maxmis;
+  double* loss;
+  int32_t* n_active;
+};
+
+// Per case: outage data (pi-model block of the removed branch), state flags.
+__global__ void k_nr_init(NrArgs a, const int32_t* __restrict__ outage, const int32_t* __restrict__ br_f,
+                          const int32_t* __restrict__ br_t, const double* __restrict__ br_r,
+                          const double* __restrict__ br_x, const double* __restrict__ br_bch,
+                          const double* __restrict__ br_tap) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.Kp) return;
+  a.active[k] = k < a.K ? 1 : 0;
+  a.status[k] = DPF_CASE_MAX_ITER;
+  a.iters[k] = 0;
+  a.bad[k] = 0;
+  a.maxmis[k] = 0.0;
+  a.loss[k] = 0.0;
+  const int ell = (k < a.K && outage) ? outage[k] : -1;
+  if (ell < 0) {
+    a.of[k] = -1;
+    a.ot[k] = -1;
+    return;
+  }
+  const double r = br_r[ell], x = br_x[ell], bch = br_bch[ell];
+  const double tau = br_tap[ell] == 0.0 ? 1.0 : br_tap[ell];
+  const double d = r * r + x * x, gs = r / d, bs = -x / d, t2 = tau * tau;
+  a.of[k] = br_f[ell];
+  a.ot[k] = br_t[ell];
+  a.yff[k] = make_double2(gs / t2, (bs + 0.5 * bch) / t2);
+  a.yft[k] = make_double2(-gs / tau, -bs / tau);
+  a.ytt[k] = make_double2(gs, bs + 0.5 * bch);
+}
+
+// Inputs to the internal layout: start (flat or given, set-points enforced)
+// and per-case specifications.
+__global__ void k_nr_in(NrArgs a, const double* __restrict__ va_in, const double* __restrict__ vm_in,
+                        const double* __restrict__ p_in, const double* __restrict__ q_in,
+                        const double* __restrict__ vs_in, int flat) {
+  const size_t n = (size_t)a.N * a.Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / a.Kp), k = (int)(e % a.Kp);
+    const uint8_t t = __ldg(a.type + i);
+    double th = 0.0, vm = 1.0;
+    if (k < a.K) {
+      const size_t u = (size_t)k * a.N + __ldg(a.perm + i);
+      const double vs = vs_in ? vs_in[u] : __ldg(a.vmset + i);
+      if (a.Ps) {
+        a.Ps[e] = p_in[u];
+        a.Qs[e] = q_in[u];
+      }
+      if (!flat) {
+        th = va_in[u];
+        vm = vm_in[u];
+      }
+      if (t == NR_SLACK) th = a.va_slack;
+      if (t != NR_PQ) vm = vs;
+    }
+    a.th[e] = th;
+    a.vm[e] = vm;
+  }
+}
+
+__global__ void k_nr_volt(NrArgs a) {
+  const size_t n = (size_t)a.N * a.Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    if (!a.active[e % a.Kp]) continue;
+    double s, c;
+    sincos(a.th[e], &s, &c);
+    a.V[e] = make_double2(a.vm[e] * c, a.vm[e] * s);
+  }
+}
+
+// Currents, power, mismatch f = [P_calc - P (pv, pq); Q_calc - Q (pq)] and
+// the right-hand side -f by elimination step (0 for the identity rows).
+__global__ void k_nr_eval(NrArgs a) {
+  const size_t n = (size_t)a.N * a.Kp, Kp = a.Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / Kp), k = (int)(e % Kp);
+    if (!a.active[k]) continue;
+    double2 cur = make_double2(0.0, 0.0);
+    const int p1 = __ldg(a.rp + i + 1);
+    for (int p = __ldg(a.rp + i); p < p1; ++p) {
+      const double2 y = __ldg(a.yval + p), v = a.V[(size_t)__ldg(a.ycol + p) * Kp + k];
+      cur.x = fma(y.x, v.x, fma(-y.y, v.y, cur.x));
+      cur.y = fma(y.x, v.y, fma(y.y, v.x, cur.y));
+    }
+    const int of = a.of[k], ot = a.ot[k];
+    if (i == of || i == ot) {  // the outaged branch's share leaves Y_bus
+      const double2 vf = a.V[(size_t)of * Kp + k], vt = a.V[(size_t)ot * Kp + k];
+      const double2 d = (i == of) ? cmul(a.yff[k], vf) : cmul(a.yft[k], vf);
+      const double2 d2 = (i == of) ? cmul(a.yft[k], vt) : cmul(a.ytt[k], vt);
+      cur = csub(csub(cur, d), d2);
+    }
+    const double2 v = a.V[e];
+    const double2 s = cmul(v, cconj(cur));
+    const uint8_t t = __ldg(a.type + i);
+    const double ps = a.Ps ? a.Ps[e] : __ldg(a.p64 + i), qs = a.Ps ? a.Qs[e] : __ldg(a.q64 + i);
+    const double fp = (t != NR_SLACK) ? s.x - ps : 0.0;
+    const double fq = (t == NR_PQ) ? s.y - qs : 0.0;
+    a.I[e] = cur;
+    a.X[(size_t)__ldg(a.rank + i) * Kp + k] = make_double2(-fp, -fq);
+  }
+}
+
+// Per case (32 cases x 8 row groups per CTA, fixed summation order): max |f|,
+// loss (1/m) ||f||^2 and the stop test of Alg. 2.  `it` is the number of
+// Newton steps taken so far.
+__global__ void __launch_bounds__(256) k_nr_check(NrArgs a) {
+  __shared__ double smax[8][32], ssum[8][32];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int k = blockIdx.x * 32 + lane;
+  const bool on = k < a.K && a.active[k];
+  double mx = 0.0, sm = 0.0;
+  if (on)
+    for (int r = g; r < a.N; r += 8) {
+      const double2 x = a.X[(size_t)r * a.Kp + k];
+      mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
+      if (!(x.x == x.x) || !(x.y == x.y)) mx = __longlong_as_double(0x7ff8000000000000LL);
+      sm = fma(x.x, x.x, fma(x.y, x.y, sm));
+    }
+  smax[g][lane] = mx;
+  ssum[g][lane] = sm;
+  __syncthreads();
+  if (g != 0 || !on) return;
+  bool nan = false;
+  for (int q = 0; q < 8; ++q) {
+    nan = nan || !(smax[q][lane] == smax[q][lane]);
+    mx = fmax(mx, smax[q][lane]);
+  }
+  sm = 0.0;
+  for (int q = 0; q < 8; ++q) sm += ssum[q][lane];
+  if (nan) mx = __longlong_as_double(0x7ff8000000000000LL);
+  a.maxmis[k] = mx;
+  a.loss[k] = sm * a.inv_m;
+  if (a.bad[k] || nan || isinf(mx)) {
+    a.status[k] = DPF_CASE_DIVERGED;
+    a.active[k] = 0;
+  } else if (mx <= a.tol) {
+    a.status[k] = DPF_CASE_CONVERGED;
+    a.active[k] = 0;
+  } else if (a.iters[k] >= a.max_iter) {
+    a.status[k] = DPF_CASE_MAX_ITER;
+    a.active[k] = 0;
+  } else {
+    a.iters[k] += 1;  // a Newton step follows
+    atomicAdd(a.n_active, 1);
+  }
+}
+
+// Jacobian blocks (Alg. 2) at every position of the filled pattern:
+//   i != j: T = V_i conj(Y'_ij V_j); dS_i/dtheta_j = -j T, dS_i/d|V|_j = T / |V|_j
+//   i == j: S_i = V_i conj(I_i);     dS_i/dtheta_i = j (S_i - T), dS_i/d|V|_i = (S_i + T) / |V|_i
+// rows P = Re, Q = Im; equations and unknowns Alg. 2 leaves out are zeroed,
+// with a 1 on the diagonal.  Fill positions start at 0.
+template <class T>
+__global__ void k_nr_assemble(NrArgs a) {
+  Blk<T>* F = static_cast<Blk<T>*>(a.F);
+  const size_t n = (size_t)a.npos * a.Kp, Kp = a.Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int64_t q = (int64_t)(e / Kp);
+    const int k = (int)(e % Kp);
+    if (!a.active[k]) continue;
+    const int i = __ldg(a.order + __ldg(a.prow + q)), j = __ldg(a.order + __ldg(a.fcol + q));
+    const int yp = __ldg(a.ymap + q);
+    double2 y = yp >= 0 ? __ldg(a.yval + yp) : make_double2(0.0, 0.0);
+    const int of = a.of[k], ot = a.ot[k];
+    if (of >= 0 && yp >= 0) {
+      if (i == of && j == of) y = csub(y, a.yff[k]);
+      else if (i == ot && j == ot) y = csub(y, a.ytt[k]);
+      else if ((i == of && j == ot) || (i == ot && j == of)) y = csub(y, a.yft[k]);
+    }
+    const double2 vi = a.V[(size_t)i * Kp + k], vj = a.V[(size_t)j * Kp + k];
+    const double2 tt = cmul(vi, cconj(cmul(y, vj)));
+    const double ivm = 1.0 / a.vm[(size_t)j * Kp + k];
+    double ba, bb, bc, bd;
+    if (i != j) {
+      ba = tt.y;
+      bc = -tt.x;
+      bb = tt.x * ivm;
+      bd = tt.y * ivm;
+    } else {
+      const double2 s = cmul(vi, cconj(a.I[(size_t)i * Kp + k]));
+      ba = -(s.y - tt.y);
+      bc = s.x - tt.x;
+      bb = (s.x + tt.x) * ivm;
+      bd = (s.y + tt.y) * ivm;
+    }
+    const uint8_t ti = __ldg(a.type + i), tj = __ldg(a.type + j);
+    const bool rp = ti != NR_SLACK, rq = ti == NR_PQ, ct = tj != NR_SLACK, cv = tj == NR_PQ;
+    Blk<T> b;
+    b.a = (rp && ct) ? (T)ba : T(0);
+    b.b = (rp && cv) ? (T)bb : T(0);
+    b.c = (rq && ct) ? (T)bc : T(0);
+    b.d = (rq && cv) ? (T)bd : T(0);
+    if (i == j) {
+      if (!rp) b.a = T(1);
+      if (!rq) b.d = T(1);
+    }
+    stb(F + e, b);
+  }
+}
+
+// Block LU of every case in the tile, level by level of the elimination
+// tree.  Pass 1: each target position receives its updates -L(i,k) U(k,j)
+// from earlier pivots (all final: they sit on lower levels).  Pass 2: the
+// diagonal blocks of the level's pivots are inverted and their L positions
+// scaled, L(i,p) = A(i,p) D_p^-1.  C cases per CTA are the lanes, the
+// remaining thread index is the slot a target goes to.
+template <class T>
+__global__ void __launch_bounds__(NR_THREADS) k_nr_factor(NrArgs a) {
+  Blk<T>* F = static_cast<Blk<T>*>(a.F);
+  Blk<T>* Dv = static_cast<Blk<T>*>(a.Dinv);
+  const int lane = threadIdx.x & (a.C - 1), slot = threadIdx.x / a.C, S = blockDim.x / a.C;
+  const int k = blockIdx.x * a.C + lane;
+  const bool on = k < a.K && a.active[k];
+  const size_t Kp = a.Kp;
+  for (int l = 0; l < a.n_levels; ++l) {
+    const int t0 = __ldg(a.lvl_ptr + l), t1 = __ldg(a.lvl_ptr + l + 1);
+    if (on)
+      for (int t = t0 + slot; t < t1; t += S) {
+        const int4 tg = __ldg(a.targets + t);
+        Blk<T> acc = ldb(F + (size_t)tg.x * Kp + k);
+        int p = tg.y;
+        for (; p + 1 < tg.z; p += 2) {
+          const int2 p0 = __ldg(a.pairs + p), p1 = __ldg(a.pairs + p + 1);
+          const Blk<T> l0 = ldb(F + (size_t)p0.x * Kp + k), u0 = ldb(F + (size_t)p0.y * Kp + k);
+          const Blk<T> l1 = ldb(F + (size_t)p1.x * Kp + k), u1 = ldb(F + (size_t)p1.y * Kp + k);
+          msub(acc, l0, u0);
+          msub(acc, l1, u1);
+        }
+        if (p < tg.z) {
+          const int2 p0 = __ldg(a.pairs + p);
+          msub(acc, ldb(F + (size_t)p0.x * Kp + k), ldb(F + (size_t)p0.y * Kp + k));
+        }
+        stb(F + (size_t)tg.x * Kp + k, acc);
+      }
+    __syncthreads();
+    if (on)
+      for (int t = t0 + slot; t < t1; t += S) {
+        const int4 tg = __ldg(a.targets + t);
+        if (tg.w == -1) continue;
+        Blk<T> di;
+        if (tg.w >= 0) {
+          inv2(ldb(F + (size_t)tg.w * Kp + k), di);
+          stb(F + (size_t)tg.x * Kp + k, mul(ldb(F + (size_t)tg.x * Kp + k), di));
+        } else {
+          if (!inv2(ldb(F + (size_t)tg.x * Kp + k), di)) a.bad[k] = 1;
+          stb(Dv + (size_t)(-2 - tg.w) * Kp + k, di);
+        }
+      }
+    __syncthreads();
+  }
+}
+
+// L y = b (unit block-lower), then U x = y with x_r = D_r^-1 (y_r - sum U x),
+// in place in X, level by level (forward: leaves first; backward: root first).
+template <class T>
+__global__ void __launch_bounds__(NR_THREADS) k_nr_solve(NrArgs a) {
+  const Blk<T>* F = static_cast<const Blk<T>*>(a.F);
+  const Blk<T>* Dv = static_cast<const Blk<T>*>(a.Dinv);
+  const int lane = threadIdx.x & (a.C - 1), slot = threadIdx.x / a.C, S = blockDim.x / a.C;
+  const int k = blockIdx.x * a.C + lane;
+  const bool on = k < a.K && a.active[k];
+  const size_t Kp = a.Kp;
+  for (int l = 0; l < a.n_levels; ++l) {
+    const int t0 = __ldg(a.rlvl_ptr + l), t1 = __ldg(a.rlvl_ptr + l + 1);
+    if (on)
+      for (int t = t0 + slot; t < t1; t += S) {
+        const int r = __ldg(a.rows + t);
+        const double2 b = a.X[(size_t)r * Kp + k];
+        T y0 = (T)b.x, y1 = (T)b.y;
+        const int q1 = __ldg(a.fdiag + r);
+        for (int q = __ldg(a.frp + r); q < q1; ++q) {
+          const Blk<T> m = ldb(F + (size_t)q * Kp + k);
+          const double2 x = a.X[(size_t)__ldg(a.fcol + q) * Kp + k];
+          y0 = fma(-m.a, (T)x.x, fma(-m.b, (T)x.y, y0));
+          y1 = fma(-m.c, (T)x.x, fma(-m.d, (T)x.y, y1));
+        }
+        a.X[(size_t)r * Kp + k] = make_double2((double)y0, (double)y1);
+      }
+    __syncthreads();
+  }
+  for (int l = a.n_levels - 1; l >= 0; --l) {
+    const int t0 = __ldg(a.rlvl_ptr + l), t1 = __ldg(a.rlvl_ptr + l + 1);
+    if (on)
+      for (int t = t0 + slot; t < t1; t += S) {
+        const int r = __ldg(a.rows + t);
+        const double2 b = a.X[(size_t)r * Kp + k];
+        T y0 = (T)b.x, y1 = (T)b.y;
+        const int q1 = __ldg(a.frp + r + 1);
+        for (int q = __ldg(a.fdiag + r) + 1; q < q1; ++q) {
+          const Blk<T> m = ldb(F + (size_t)q * Kp + k);
+          const double2 x = a.X[(size_t)__ldg(a.fcol + q) * Kp + k];
+          y0 = fma(-m.a, (T)x.x, fma(-m.b, (T)x.y, y0));
+          y1 = fma(-m.c, (T)x.x, fma(-m.d, (T)x.y, y1));
+        }
+        const Blk<T> di = ldb(Dv + (size_t)r * Kp + k);
+        a.X[(size_t)r * Kp + k] = make_double2((double)fma(di.a, y0, di.b * y1), (double)fma(di.c, y0, di.d * y1));
+      }
+    __syncthreads();
+  }
+}
+
+__global__ void k_nr_update(NrArgs a) {
+  const size_t n = (size_t)a.N * a.Kp, Kp = a.Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / Kp), k = (int)(e % Kp);
+    if (!a.active[k] || a.bad[k]) continue;
+    const int i = __ldg(a.order + r);
+    const uint8_t t = __ldg(a.type + i);
+    const double2 dx = a.X[e];
+    const size_t ei = (size_t)i * Kp + k;
+    if (t != NR_SLACK) a.th[ei] += dx.x;
+    if (t == NR_PQ) a.vm[ei] += dx.y;
+  }
+}
+
+// Solution and per-case results to the caller's arrays (case-major, user bus order).
+__global__ void k_nr_out(NrArgs a, double* __restrict__ va, double* __restrict__ vm) {
+  const size_t n = (size_t)a.N * a.Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / a.Kp), k = (int)(e % a.Kp);
+    if (k >= a.K) continue;
+    const size_t u = (size_t)k * a.N + __ldg(a.perm + i);
+    va[u] = a.th[e];
+    vm[u] = a.vm[e];
+  }
+}
+
+__global__ void k_nr_case_out(NrArgs a, int32_t* iters, int32_t* status, double* maxmis, double* loss) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.K) return;
+  if (iters) iters[k] = a.iters[k];
+  if (status) status[k] = a.status[k];
+  if (maxmis) maxmis[k] = a.maxmis[k];
+  if (loss) loss[k] = a.loss[k];
+}
+
+template <class T>
+int dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? DPF_E_OOM : DPF_E_CUDA, "cudaMalloc(%zu bytes): %s",
+                n * sizeof(T), cudaGetErrorString(e));
+  }
+  return DPF_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+template <class T>
+int upload(T** dst, const std::vector<T>& src) {
+  TRY(dalloc(dst, src.size()));
+  if (!src.empty()) CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return DPF_OK;
+}
+
+int num_sms_nr() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)num_sms_nr() * 8)); }
+
+}  // namespace
+
+struct dpf_nr {
+  const dpf_ybus* y = nullptr;
+  int max_case = 0, Kp = 0;
+  NrSymbolic sym;
+  int64_t launches = 0;
+  // schedule (device)
+  int32_t *order = nullptr, *rank = nullptr, *frp = nullptr, *fcol = nullptr, *fdiag = nullptr, *prow = nullptr,
+          *ymap = nullptr, *lvl_ptr = nullptr, *rlvl_ptr = nullptr, *rows = nullptr;
+  int4* targets = nullptr;
+  int2* pairs = nullptr;
+  // state
+  double *th = nullptr, *vm = nullptr, *Ps = nullptr, *Qs = nullptr;
+  double2 *V = nullptr, *I = nullptr, *X = nullptr;
+  char* F = nullptr;
+  char* Dinv = nullptr;
+  int32_t *of = nullptr, *ot = nullptr, *active = nullptr, *status = nullptr, *iters = nullptr, *bad = nullptr,
+          *n_active = nullptr;
+  double2 *yff = nullptr, *yft = nullptr, *ytt = nullptr;
+  double *maxmis = nullptr, *loss = nullptr;
+  int32_t* h_nact = nullptr;  // pinned
+};
+
+static void nr_release(dpf_nr* h) {
+  dfree(h->order); dfree(h->rank); dfree(h->frp); dfree(h->fcol); dfree(h->fdiag); dfree(h->prow);
+  dfree(h->ymap); dfree(h->lvl_ptr); dfree(h->rlvl_ptr); dfree(h->rows); dfree(h->targets); dfree(h->pairs);
+  dfree(h->th); dfree(h->vm); dfree(h->Ps); dfree(h->Qs); dfree(h->V); dfree(h->I); dfree(h->X);
+  dfree(h->F); dfree(h->Dinv);
+  dfree(h->of); dfree(h->ot); dfree(h->active); dfree(h->status); dfree(h->iters); dfree(h->bad);
+  dfree(h->n_active); dfree(h->yff); dfree(h->yft); dfree(h->ytt); dfree(h->maxmis); dfree(h->loss);
+  if (h->h_nact) cudaFreeHost(h->h_nact);
+  h->h_nact = nullptr;
+}
+
+static int nr_setup(dpf_nr* h) {
+  const NrSymbolic& s = h->sym;
+  const int n = s.n;
+  const size_t npos = (size_t)s.row_ptr[n];
+  TRY(upload(&h->order, s.order));
+  TRY(upload(&h->rank, s.rank));
+  TRY(upload(&h->frp, s.row_ptr));
+  TRY(upload(&h->fcol, s.col));
+  TRY(upload(&h->fdiag, s.diag));
+  TRY(upload(&h->prow, s.prow));
+  TRY(upload(&h->ymap, s.ymap));
+  TRY(upload(&h->lvl_ptr, s.lvl_ptr));
+  TRY(upload(&h->rlvl_ptr, s.rlvl_ptr));
+  TRY(upload(&h->rows, s.rows));
+  TRY(dalloc(&h->targets, s.targets.size() / 4));
+  CK(cudaMemcpy(h->targets, s.targets.data(), s.targets.size() * 4, cudaMemcpyHostToDevice));
+  TRY(dalloc(&h->pairs, s.pairs.size() / 2));
+  if (!s.pairs.empty()) CK(cudaMemcpy(h->pairs, s.pairs.data(), s.pairs.size() * 4, cudaMemcpyHostToDevice));
+  const int Kp = h->Kp;
+  const size_t E = (size_t)n * Kp;
+  TRY(dalloc(&h->th, E)); TRY(dalloc(&h->vm, E));
+  TRY(dalloc(&h->Ps, E)); TRY(dalloc(&h->Qs, E));
+  TRY(dalloc(&h->V, E)); TRY(dalloc(&h->I, E)); TRY(dalloc(&h->X, E));
+  TRY(dalloc(&h->F, npos * Kp * sizeof(Blk<double>)));
+  TRY(dalloc(&h->Dinv, E * sizeof(Blk<double>)));
+  TRY(dalloc(&h->of, Kp)); TRY(dalloc(&h->ot, Kp)); TRY(dalloc(&h->active, Kp)); TRY(dalloc(&h->status, Kp));
+  TRY(dalloc(&h->iters, Kp)); TRY(dalloc(&h->bad, Kp)); TRY(dalloc(&h->n_active, 1));
+  TRY(dalloc(&h->yff, Kp)); TRY(dalloc(&h->yft, Kp)); TRY(dalloc(&h->ytt, Kp));
+  TRY(dalloc(&h->maxmis, Kp)); TRY(dalloc(&h->loss, Kp));
+  CK(cudaMallocHost((void**)&h->h_nact, sizeof(int32_t)));
+  return DPF_OK;
+}
+
+extern "C" int dpf_nr_create(const dpf_ybus* y, int32_t max_case, dpf_nr** out) {
+  clear_error();
+  if (!y || !out || max_case <= 0) return fail(DPF_E_INVALID, "dpf_nr_create: NULL argument or max_case <= 0");
+  *out = nullptr;
+  if (!y->dev.ready) return fail(DPF_E_STATE, "dpf_nr_create: Y_bus not uploaded (dpf_ybus_upload)");
+  dpf_nr* h = new (std::nothrow) dpf_nr;
+  if (!h) return fail(DPF_E_OOM, "dpf_nr_create: host allocation");
+  h->y = y;
+  h->max_case = max_case;
+  h->Kp = (max_case + 31) / 32 * 32;
+  int rc = nr_symbolic(y, (int64_t)1 << 28, &h->sym);
+  if (rc == DPF_OK && (int64_t)h->sym.row_ptr[y->n] * h->Kp > ((int64_t)1 << 40) / 32)
+    rc = fail(DPF_E_UNSUPPORTED, "dpf_nr_create: factor storage too large");
+  if (rc == DPF_OK) rc = nr_setup(h);
+  if (rc != DPF_OK) {
+    nr_release(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return DPF_OK;
+}
+
+extern "C" int dpf_nr_free(dpf_nr* h) {
+  if (!h) return DPF_OK;
+  nr_release(h);
+  delete h;
+  return DPF_OK;
+}
+
+extern "C" int dpf_nr_stats(const dpf_nr* h, int64_t* n_pos, int64_t* n_pairs, int32_t* n_levels,
+                            int64_t* launches) {
+  clear_error();
+  if (!h) return fail(DPF_E_INVALID, "dpf_nr_stats: NULL handle");
+  if (n_pos) *n_pos = h->sym.row_ptr[h->sym.n];
+  if (n_pairs) *n_pairs = (int64_t)h->sym.pairs.size() / 2;
+  if (n_levels) *n_levels = h->sym.n_levels;
+  if (launches) *launches = h->launches;
+  return DPF_OK;
+}
+
+template <class T>
+static int nr_iterate_linear(dpf_nr* h, const NrArgs& a, cudaStream_t s) {
+  const size_t np = (size_t)a.npos * a.Kp;
+  k_nr_assemble<T><<<grid_for(np), 256, 0, s>>>(a);
+  const int ctas = a.Kp / a.C;
+  k_nr_factor<T><<<ctas, NR_THREADS, 0, s>>>(a);
+  k_nr_solve<T><<<ctas, NR_THREADS, 0, s>>>(a);
+  CKLAUNCH();
+  h->launches += 3;
+  return DPF_OK;
+}
+
+extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, double tol, int32_t max_iter,
+                            int32_t flat_start, void* stream) {
+  clear_error();
+  if (!h || !b) return fail(DPF_E_INVALID, "dpf_nr_solve: NULL argument");
+  const dpf_ybus* y = h->y;
+  const int K = b->n_case;
+  if (K <= 0 || K > h->max_case) return fail(DPF_E_INVALID, "dpf_nr_solve: n_case %d outside 1..%d", K, h->max_case);
+  if (b->host_io) return fail(DPF_E_INVALID, "dpf_nr_solve: device pointers only (host_io = 0)");
+  if (!b->va || !b->vm) return fail(DPF_E_INVALID, "dpf_nr_solve: va and vm are required");
+  if ((b->p_spec == nullptr) != (b->q_spec == nullptr))
+    return fail(DPF_E_INVALID, "dpf_nr_solve: p_spec and q_spec are given together");
+  if (precision != DPF_FP32 && precision != DPF_FP64)
+    return fail(DPF_E_INVALID, "dpf_nr_solve: precision must be DPF_FP32 or DPF_FP64");
+  if (!(tol >= 0.0) || max_iter < 0) return fail(DPF_E_INVALID, "dpf_nr_solve: tol >= 0 and max_iter >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (b->outage) {
+    std::vector<int32_t> ho(K);
+    CK(cudaMemcpyAsync(ho.data(), b->outage, (size_t)K * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < K; ++k) {
+      const int l = ho[k];
+      if (l < -1 || l >= y->m) return fail(DPF_E_INVALID, "case %d: outage index %d out of range", k, l);
+      if (l >= 0 && y->bridge[l]) return fail(DPF_E_ISLANDED, "case %d: removing branch %d islands the grid", k, l);
+    }
+  }
+  const DeviceYbus& d = y->dev;
+  const NrSymbolic& sym = h->sym;
+  NrArgs a;
+  memset(&a, 0, sizeof a);
+  a.N = y->n;
+  a.K = K;
+  a.Kp = (K + 31) / 32 * 32;
+  // cases per CTA: as many as keep every SM busy, at most 16
+  int C = 16;
+  const int sms = num_sms_nr();
+  while (C > 1 && (K + C - 1) / C < sms) C >>= 1;
+  a.C = C;
+  a.va_slack = y->va_slack;
+  a.tol = tol;
+  a.inv_m = y->m_loss > 0 ? 1.0 / y->m_loss : 0.0;
+  a.max_iter = max_iter;
+  a.rp = d.row_ptr;
+  a.ycol = d.col;
+  a.yval = d.val64;
+  a.type = d.type;
+  a.p64 = d.p64;
+  a.q64 = d.q64;
+  a.vmset = d.vmset;
+  a.perm = d.perm;
+  a.order = h->order;
+  a.rank = h->rank;
+  a.frp = h->frp;
+  a.fcol = h->fcol;
+  a.fdiag = h->fdiag;
+  a.prow = h->prow;
+  a.ymap = h->ymap;
+  a.n_levels = sym.n_levels;
+  a.lvl_ptr = h->lvl_ptr;
+  a.targets = h->targets;
+  a.pairs = h->pairs;
+  a.rlvl_ptr = h->rlvl_ptr;
+  a.rows = h->rows;
+  a.npos = sym.row_ptr[sym.n];
+  a.th = h->th;
+  a.vm = h->vm;
+  a.V = h->V;
+  a.I = h->I;
+  a.X = h->X;
+  a.Ps = b->p_spec ? h->Ps : nullptr;
+  a.Qs = b->p_spec ? h->Qs : nullptr;
+  a.F = h->F;
+  a.Dinv = h->Dinv;
+  a.of = h->of;
+  a.ot = h->ot;
+  a.yff = h->yff;
+  a.yft = h->yft;
+  a.ytt = h->ytt;
+  a.active = h->active;
+  a.status = h->status;
+  a.iters = h->iters;
+  a.bad = h->bad;
+  a.maxmis = h->maxmis;
+  a.loss = h->loss;
+  a.n_active = h->n_active;
+  const size_t E = (size_t)a.N * a.Kp;
+  const int cb = (a.Kp + 255) / 256;
+  k_nr_init<<<cb, 256, 0, s>>>(a, b->outage, d.br_f, d.br_t, d.br_r, d.br_x, d.br_bch, d.br_tap);
+  k_nr_in<<<grid_for(E), 256, 0, s>>>(a, b->va, b->vm, b->p_spec, b->q_spec, b->vm_set, flat_start ? 1 : 0);
+  CKLAUNCH();
+  h->launches += 2;
+  for (int it = 0;; ++it) {
+    k_nr_volt<<<grid_for(E), 256, 0, s>>>(a);
+    k_nr_eval<<<grid_for(E), 256, 0, s>>>(a);
+    CK(cudaMemsetAsync(a.n_active, 0, 4, s));
+    k_nr_check<<<a.Kp / 32, 256, 0, s>>>(a);
+    CKLAUNCH();
+    h->launches += 3;
+    CK(cudaMemcpyAsync(h->h_nact, a.n_active, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->h_nact == 0 || it > max_iter) break;
+    if (precision == DPF_FP64) TRY(nr_iterate_linear<double>(h, a, s));
+    else TRY(nr_iterate_linear<float>(h, a, s));
+    k_nr_update<<<grid_for(E), 256, 0, s>>>(a);
+    CKLAUNCH();
+    h->launches += 1;
+  }
+  k_nr_out<<<grid_for(E), 256, 0, s>>>(a, b->va, b->vm);
+  k_nr_case_out<<<cb, 256, 0, s>>>(a, b->iters, b->status, b->max_mismatch, b->loss);
+  CKLAUNCH();
+  h->launches += 2;
+  return DPF_OK;
+}

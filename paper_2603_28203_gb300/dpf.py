@@ -356,6 +356,66 @@ def dpf_dc_solve(y: Ybus, ws: Workspace, n_case: int, p_spec=None, outage=None, 
     return dict(va=va, iters=it, rel_residual=res)
 
 
+# ---- Newton-Raphson (Alg. 2) ---------------------------------------------------
+def dpf_nr_analyze(y: Ybus) -> dict:
+    """Sizes of the host analysis of the Newton solver (no CUDA call)."""
+    npos, npairs, nl = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(lib().dpf_nr_analyze(y.handle, C.byref(npos), C.byref(npairs), C.byref(nl)))
+    return dict(n_pos=npos.value, n_pairs=npairs.value, n_levels=nl.value)
+
+
+def dpf_nr_pattern(y: Ybus) -> dict:
+    """Elimination order (user bus indices), filled pattern in that order and
+    tree levels of the Newton solver's host analysis (no CUDA call)."""
+    sz = dpf_nr_analyze(y)
+    n = y.n_bus
+    order = np.empty(n, np.int32)
+    row_ptr = np.empty(n + 1, np.int32)
+    col = np.empty(sz["n_pos"], np.int32)
+    level = np.empty(n, np.int32)
+    _check(lib().dpf_nr_pattern(y.handle, order.ctypes.data, row_ptr.ctypes.data, col.ctypes.data,
+                                level.ctypes.data))
+    return dict(order=order, row_ptr=row_ptr, col=col, level=level, **sz)
+
+
+class NewtonSolver:
+    """dpf_nr handle: host analysis + device buffers for up to max_case cases."""
+
+    def __init__(self, y: Ybus, max_case: int):
+        self.ybus = y
+        h = C.c_void_p()
+        _check(lib().dpf_nr_create(y.handle, int(max_case), C.byref(h)))
+        self.handle = h
+
+    def free(self):
+        if self.handle:
+            lib().dpf_nr_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        npos, npairs, nl, nlaunch = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()
+        _check(lib().dpf_nr_stats(self.handle, C.byref(npos), C.byref(npairs), C.byref(nl), C.byref(nlaunch)))
+        return dict(n_pos=npos.value, n_pairs=npairs.value, n_levels=nl.value, launches=nlaunch.value)
+
+
+def dpf_nr_create(y: Ybus, max_case: int) -> NewtonSolver:
+    return NewtonSolver(y, max_case)
+
+
+def dpf_nr_solve(nr: NewtonSolver, precision=_abi.FP64, tol: float = 1e-10, max_iter: int = 20, flat_start=True,
+                 stream=None, **batch):
+    """Newton-Raphson for every case; `batch` holds the dpf_batch fields as CUDA tensors (va, vm required)."""
+    b = _batch_struct(**batch)
+    _check(lib().dpf_nr_solve(nr.handle, C.byref(b), int(precision), float(tol), int(max_iter),
+                              1 if flat_start else 0, _stream(stream)))
+
+
 def dpf_paramid_begin(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, precision=_abi.FP32, stream=None):
     """Stage K measured operating points ([K][N] float64 CUDA tensors) for dpf_paramid_step."""
     _check(lib().dpf_paramid_begin(y.handle, ws.handle, int(va.shape[0]), _ptr(va), _ptr(vm), _ptr(p_spec),
