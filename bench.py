@@ -968,6 +968,160 @@ def run_c1batch(args):
     y.free()
 
 
+def nr_bytes_per_step(n_bus, n_pos, n_pairs, n_case):
+    """Bytes one Newton step of dpf_nr_solve must move (FP64 state, factor of
+    `fb` bytes per block) for n_case active cases: k_nr_volt reads theta,
+    |V| and writes V (32 B per bus); k_nr_eval gathers V (each value once)
+    and writes I and the right-hand side (48); k_nr_check reads it (16);
+    k_nr_assemble reads V, I, |V| (40 per bus) and writes every block of the
+    filled pattern; k_nr_lu reads every block once as its own target and
+    twice per block product, writes every block but the diagonals and the
+    inverse diagonals, and reads/writes the right-hand side twice (64 per
+    bus) plus one right-hand-side read per off-diagonal block in the two
+    substitutions; k_nr_update reads dx, theta, |V| and writes theta, |V|
+    (48).  The schedule (shared by all cases) is left out; so is the
+    pivots' diagonal block that each L target re-forms (not needed by the
+    arithmetic)."""
+    def per_case(fb):
+        bus = 32 + 48 + 16 + 40 + 64 + 48
+        lu = fb * (n_pos + 2 * n_pairs) + fb * (n_pos - n_bus) + fb * n_bus + 16 * (n_pos - n_bus)
+        return n_bus * bus + fb * n_pos + lu
+    return {"fp64": n_case * per_case(32), "fp32": n_case * per_case(16)}
+
+
+def run_nr(args):
+    """Newton-Raphson (Alg. 2) on the GPU over the N-1 batch (dpf_nr_solve):
+    all 2,379 cases from the flat start to 1e-6 and 1e-10 p.u. with the FP64
+    and the FP32 factor, and the hybrid of Sec. 6 (Alg. 1 for a few hundred
+    iterations, then Newton from its state).  Solves/s count converged cases
+    only; cases the oracle's NR cannot solve either are listed.  The oracle's
+    NR (scipy sparse LU) on a bounded sample of cases, one per host core, is
+    the CPU baseline.  One JSON line."""
+    import torch
+    import oracle
+    from oracle.ybus import grid_ybus
+    from paper_2603_28203_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    import paper_2603_28203_gb300 as dpf
+    g, outages = _workload()
+    K = outages.size
+    cores = len(os.sched_getaffinity(0))
+    sample = [int(c) for c in np.random.default_rng(7).choice(outages, size=8 * cores, replace=False)]
+    cpu = _oracle_nr_sample(sample, cores)
+    dev = torch.device("cuda", 0)
+    y = dpf.dpf_build_ybus(g)
+    nr = dpf.dpf_nr_create(y, K)
+    st = nr.stats()
+    od = torch.tensor(outages.astype(np.int32), device=dev)
+    peak, src = _peaks()
+
+    def state():
+        return dict(va=torch.zeros((K, g.n_bus), dtype=torch.float64, device=dev),
+                    vm=torch.ones((K, g.n_bus), dtype=torch.float64, device=dev),
+                    iters=torch.empty(K, dtype=torch.int32, device=dev),
+                    status=torch.empty(K, dtype=torch.int32, device=dev),
+                    max_mismatch=torch.empty(K, dtype=torch.float64, device=dev))
+
+    def timed(fn, reps=3):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        return best
+
+    out = {}
+    steps_bytes = nr_bytes_per_step(g.n_bus, st["n_pos"], st["n_pairs"], 1)
+    for prec, pname in ((dpf.FP64, "fp64"), (dpf.FP32, "fp32")):
+        for tol in (1e-6, 1e-10):
+            r = state()
+            wall = timed(lambda: dpf.dpf_nr_solve(nr, precision=prec, tol=tol, max_iter=args.nr_max_iter,
+                                                  n_case=K, outage=od, **r))
+            it, stt, mm = (r[k].cpu().numpy() for k in ("iters", "status", "max_mismatch"))
+            conv = stt == 0
+            steps = int(it.sum())  # Newton steps taken over all cases
+            out[f"{pname}_tol{tol:g}"] = {
+                "wall_ms": 1e3 * wall, "converged": int(conv.sum()), "solves_per_s": float(conv.sum() / wall),
+                "newton_steps_p50": float(np.median(it)), "newton_steps_max": int(it.max()),
+                "not_converged_outages": [int(outages[k]) for k in np.flatnonzero(~conv)],
+                "max_mismatch_converged": float(mm[conv].max()),
+                "achieved_gbs_algorithmic": steps * steps_bytes[pname] / wall / 1e9,
+                "hbm_frac": steps * steps_bytes[pname] / wall / 1e9 / peak,
+            }
+    # Sec. 6 hybrid: Alg. 1 (FP32 iterations, Table 2, lr 1e-2) then Newton from its state
+    ws = dpf.dpf_workspace_create(y, K)
+    hyb = {}
+    for t_dpf in (100, 300):
+        r = state()
+        o = dpf.SolveOpts(lr=LR, max_iter=t_dpf, check_every=CHECK_EVERY, tol=TOL)
+
+        def both():
+            dpf.dpf_solve_batch(y, ws, o, n_case=K, outage=od, **r)
+            dpf.dpf_nr_solve(nr, precision=dpf.FP64, tol=1e-10, max_iter=args.nr_max_iter, flat_start=False,
+                             n_case=K, outage=od, **r)
+        wall = timed(both, reps=2)
+        it, stt = r["iters"].cpu().numpy(), r["status"].cpu().numpy()
+        conv = stt == 0
+        hyb[f"dpf{t_dpf}_then_nr"] = {"wall_ms": 1e3 * wall, "converged": int(conv.sum()),
+                                      "solves_per_s": float(conv.sum() / wall),
+                                      "newton_steps_p50": float(np.median(it)), "newton_steps_max": int(it.max())}
+    # reported mismatch against the oracle's recomputation (FP32 factor, 1e-10)
+    r = state()
+    dpf.dpf_nr_solve(nr, precision=dpf.FP32, tol=1e-10, max_iter=args.nr_max_iter, n_case=K, outage=od, **r)
+    va, vm, mm = (r[k].cpu().numpy() for k in ("va", "vm", "max_mismatch"))
+    err = 0.0
+    for k in (0, K // 2, K - 1):
+        Yk = grid_ybus(g.without_branch(int(outages[k])))
+        f, _ = oracle.mismatch(Yk, va[k], vm[k], g.p_spec, g.q_spec, g.bus_type)
+        err = max(err, abs(float(np.abs(f).max()) - float(mm[k])))
+    print(json.dumps({
+        "workload": "nr",
+        "config": {"grid": "c3_n1_2kbus", "n_bus": int(g.n_bus), "cases": int(K), "start": "flat",
+                   "max_newton_steps": args.nr_max_iter},
+        "pattern": st,
+        "newton": out,
+        "hybrid": hyb,
+        "reported_vs_oracle_mismatch_max_abs_diff": err,
+        "cpu_baseline": cpu,
+        "note": "Alg. 1 (DPF) converges none of these cases to 1e-6 within 1,000 iterations (workload n1)",
+    }), flush=True)
+    ws.free()
+    nr.free()
+    y.free()
+
+
+def _oracle_nr_worker(ell):
+    import gridgen
+    import oracle
+    from oracle.ybus import grid_ybus
+    g = gridgen.config_grid("c3_n1_2kbus")
+    Y = grid_ybus(g.without_branch(int(ell)))
+    t0 = time.perf_counter()
+    r = oracle.nr_solve(Y, g.p_spec, g.q_spec, g.bus_type, g.vm_set, tol=1e-10, max_iter=20)
+    return time.perf_counter() - t0, bool(r["converged"])
+
+
+def _oracle_nr_sample(sample, cores):
+    """The oracle's NR (Alg. 2 with scipy's sparse LU) on sampled N-1 cases,
+    one process per host core (spawn)."""
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_nr_worker, sample)
+    wall = time.perf_counter() - t0
+    conv = sum(c for _, c in res)
+    return {"value": conv / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sample)} N-1 cases, oracle NR to 1e-10 (one case per core, spawn pool, "
+                      f"{wall:.1f} s wall incl. pool start)",
+            "seconds_per_case_median": float(np.median([t for t, _ in res]))}
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -1019,19 +1173,21 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc", "warmstart", "c1batch"],
+    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc", "warmstart", "c1batch", "nr"],
                     help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep; "
                          "uneven: 64-grid block-diagonal batch + parameter identification; "
                          "timeseries: the 10k-bus grid over a year of hourly snapshots; "
                          "paramid: branch identification against the oracle's operating points; "
                          "dc: the DC approximation of the N-1 batch (and Alg. 1 started from it); "
                          "warmstart: iterations from flat vs warm starts on the 30-bus grid; "
-                         "c1batch: solves/s to 1e-6 on a batch of 30-bus load variants")
+                         "c1batch: solves/s to 1e-6 on a batch of 30-bus load variants; "
+                         "nr: Newton-Raphson on the GPU over the N-1 batch, and the DPF-then-Newton hybrid")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--uneven-iters", type=int, default=300)
     ap.add_argument("--ts-hours", type=int, default=8760)
     ap.add_argument("--warm-max-iter", type=int, default=50000)
     ap.add_argument("--c1-cases", type=int, default=8192)
+    ap.add_argument("--nr-max-iter", type=int, default=10)
     ap.add_argument("--pid-grids", type=int, default=16)
     ap.add_argument("--pid-steps", type=int, default=4000)
     ap.add_argument("--pid-lr", type=float, default=3e-3)
@@ -1067,6 +1223,8 @@ def main():
         run_warmstart(args)
     elif args.workload == "c1batch":
         run_c1batch(args)
+    elif args.workload == "nr":
+        run_nr(args)
     else:
         run_ours(args)
 

@@ -345,9 +345,9 @@ int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
  *
  * dpf_nr_solve: every case of the batch (device pointers only: host_io must
  * be 0; p_spec/q_spec/vm_set/outage as for dpf_solve_batch) from the flat
- * start (flat_start = 1) or from va/vm (fixed |V| and the slack angle
- * enforced), Newton steps until FP64 max |f| <= tol or max_iter steps.
- * precision: DPF_FP64 factorises and solves in FP64; DPF_FP32 in FP32 (the
+ * start (o->flat_start = 1) or from va/vm (fixed |V| and the slack angle
+ * enforced), Newton steps until FP64 max |f| <= o->tol or o->max_iter steps.
+ * o->precision: DPF_FP64 factorises and solves in FP64; DPF_FP32 in FP32 (the
  * mismatch, the stop test and the state stay FP64; convergence turns linear
  * at about cond(J) 2^-24 per step near the solution).  Outputs: va, vm
  * (solution), iters (Newton steps), status (DPF_CASE_CONVERGED, _MAX_ITER,
@@ -355,7 +355,7 @@ int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
  * max_mismatch and loss of the returned state (any of the last four may be
  * NULL).  Reads the number of unconverged cases from the device after every
  * step (synchronises `stream`).  Errors: DPF_E_INVALID (sizes, pointers,
- * outage index), DPF_E_ISLANDED (an outage of a bridge).
+ * outage index, options), DPF_E_ISLANDED (an outage of a bridge).
  *
  * dpf_nr_stats: positions of the filled pattern, block products of one
  * factorisation, tree levels, kernels enqueued so far (any output may be NULL).
@@ -364,10 +364,19 @@ int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
  * pattern in that order (row_ptr [n_bus + 1], col [n_pos]) and the tree
  * level of every step ([n_bus]); any array may be NULL. */
 typedef struct dpf_nr dpf_nr;
+typedef struct {
+  int32_t precision;         /* DPF_FP64 or DPF_FP32: the factor and the solves */
+  double tol;                /* stop when FP64 max |f| <= tol                   */
+  int32_t max_iter;          /* Newton steps per case                           */
+  int32_t flat_start;        /* 1: ignore va/vm inputs, start flat              */
+  int32_t lanes;             /* cases per CTA of the factor and solve kernels
+                                (power of 2 up to 32; 0 = auto)               */
+} dpf_nr_opts;
+/* Defaults: DPF_FP64, tol 1e-10, max_iter 20, flat start, lanes auto. */
+void dpf_nr_default_opts(dpf_nr_opts* o);
 int dpf_nr_create(const dpf_ybus* y, int32_t max_case, dpf_nr** out);
 int dpf_nr_free(dpf_nr* h);
-int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, double tol, int32_t max_iter,
-                 int32_t flat_start, void* stream);
+int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o, void* stream);
 int dpf_nr_stats(const dpf_nr* h, int64_t* n_pos, int64_t* n_pairs, int32_t* n_levels, int64_t* launches);
 int dpf_nr_analyze(const dpf_ybus* y, int64_t* n_pos, int64_t* n_pairs, int32_t* n_levels);
 int dpf_nr_pattern(const dpf_ybus* y, int32_t* order, int32_t* row_ptr, int32_t* col, int32_t* level);

@@ -55,6 +55,11 @@ class DpfSolveOpts(C.Structure):
     ]
 
 
+class DpfNrOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("flat_start", C.c_int32), ("lanes", C.c_int32)]
+
+
 VP = C.c_void_p
 I32 = C.c_int32
 
@@ -85,7 +90,8 @@ SIGNATURES = {
     "dpf_dc_solve": (C.c_int, [VP, VP, I32, VP, VP, C.c_double, I32, VP, VP, VP, VP]),
     "dpf_nr_create": (C.c_int, [VP, I32, C.POINTER(VP)]),
     "dpf_nr_free": (C.c_int, [VP]),
-    "dpf_nr_solve": (C.c_int, [VP, C.POINTER(DpfBatch), I32, C.c_double, I32, I32, VP]),
+    "dpf_nr_default_opts": (None, [C.POINTER(DpfNrOpts)]),
+    "dpf_nr_solve": (C.c_int, [VP, C.POINTER(DpfBatch), C.POINTER(DpfNrOpts), VP]),
     "dpf_nr_stats": (C.c_int, [VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64), p_i32, C.POINTER(C.c_int64)]),
     "dpf_nr_analyze": (C.c_int, [VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64), p_i32]),
     "dpf_nr_pattern": (C.c_int, [VP, VP, VP, VP, VP]),

@@ -9,11 +9,11 @@
 //   k_nr_check     per case max |f|, loss, stop test (the host reads the
 //                  number of cases left)
 //   k_nr_assemble  the 2x2 Jacobian blocks of Alg. 2 on the filled pattern
-//   k_nr_factor    block LU, left-looking, level by level of the elimination
-//                  tree; one CTA per tile of cases, which syncs only its own
-//                  threads: the cases are independent, so no CTA waits for
-//                  another
-//   k_nr_solve     L y = -f, U dx = y, level by level
+//   k_nr_lu        block LU, left-looking, level by level of the elimination
+//                  tree, with the forward substitution L y = -f folded into
+//                  the same level pass, then U dx = y back down the tree; one
+//                  CTA per tile of cases, which syncs only its own threads:
+//                  the cases are independent, so no CTA waits for another
 //   k_nr_update    theta += dx_theta (pv, pq), |V| += dx_|V| (pq)
 // The factor and the triangular solves run in the factor precision (FP64, or
 // FP32: GB300 issues FP32 FMA at many times its FP64 rate, and a Newton step
@@ -132,7 +132,6 @@ struct NrArgs {
   const int32_t* frp;
   const int32_t* fcol;
   const int32_t* fdiag;
-  const int32_t* prow;
   const int32_t* ymap;
   int n_levels;
   const int32_t* lvl_ptr;
@@ -145,6 +144,7 @@ struct NrArgs {
   double* th;
   double* vm;
   double2* V;
+  double2* U;    // e^{j theta}: V = |V| U
   double2* I;
   double2* X;    // right-hand side / solution, by elimination step
   double* Ps;    // per-case specification or NULL
@@ -230,6 +230,7 @@ __global__ void k_nr_volt(NrArgs a) {
     if (!a.active[e % a.Kp]) continue;
     double s, c;
     sincos(a.th[e], &s, &c);
+    a.U[e] = make_double2(c, s);
     a.V[e] = make_double2(a.vm[e] * c, a.vm[e] * s);
   }
 }
@@ -266,17 +267,17 @@ __global__ void k_nr_eval(NrArgs a) {
   }
 }
 
-// Per case (32 cases x 8 row groups per CTA, fixed summation order): max |f|,
+// Per case (32 cases x 32 row groups per CTA, fixed summation order): max |f|,
 // loss (1/m) ||f||^2 and the stop test of Alg. 2.  `it` is the number of
 // Newton steps taken so far.
-__global__ void __launch_bounds__(256) k_nr_check(NrArgs a) {
-  __shared__ double smax[8][32], ssum[8][32];
+__global__ void __launch_bounds__(1024) k_nr_check(NrArgs a) {
+  __shared__ double smax[32][32], ssum[32][32];
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int k = blockIdx.x * 32 + lane;
   const bool on = k < a.K && a.active[k];
   double mx = 0.0, sm = 0.0;
   if (on)
-    for (int r = g; r < a.N; r += 8) {
+    for (int r = g; r < a.N; r += 32) {
       const double2 x = a.X[(size_t)r * a.Kp + k];
       mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
       if (!(x.x == x.x) || !(x.y == x.y)) mx = __longlong_as_double(0x7ff8000000000000LL);
@@ -287,12 +288,12 @@ __global__ void __launch_bounds__(256) k_nr_check(NrArgs a) {
   __syncthreads();
   if (g != 0 || !on) return;
   bool nan = false;
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < 32; ++q) {
     nan = nan || !(smax[q][lane] == smax[q][lane]);
     mx = fmax(mx, smax[q][lane]);
   }
   sm = 0.0;
-  for (int q = 0; q < 8; ++q) sm += ssum[q][lane];
+  for (int q = 0; q < 32; ++q) sm += ssum[q][lane];
   if (nan) mx = __longlong_as_double(0x7ff8000000000000LL);
   a.maxmis[k] = mx;
   a.loss[k] = sm * a.inv_m;
@@ -311,129 +312,169 @@ __global__ void __launch_bounds__(256) k_nr_check(NrArgs a) {
   }
 }
 
-// Jacobian blocks (Alg. 2) at every position of the filled pattern:
-//   i != j: T = V_i conj(Y'_ij V_j); dS_i/dtheta_j = -j T, dS_i/d|V|_j = T / |V|_j
-//   i == j: S_i = V_i conj(I_i);     dS_i/dtheta_i = j (S_i - T), dS_i/d|V|_i = (S_i + T) / |V|_i
-// rows P = Re, Q = Im; equations and unknowns Alg. 2 leaves out are zeroed,
-// with a 1 on the diagonal.  Fill positions start at 0.
+// Jacobian blocks (Alg. 2) at every position of the filled pattern, with
+// u = e^{j theta} (so V = |V| u) and W = V_i conj(Y'_ij u_j):
+//   i != j: dS_i/dtheta_j = -j |V|_j W,        dS_i/d|V|_j = W
+//   i == j: dS_i/dtheta_i = j (S_i - |V|_i W), dS_i/d|V|_i = u_i conj(I_i) + W
+// (the element rules of Alg. 2 with T = V_i conj(Y'_ij V_j) = |V|_j W; the
+// division by |V|_j cancels, and none is left: an FP64 divide costs many
+// issue slots here).  Computed in the factor's precision T (the FP64 state
+// rounded once); rows P = Re, Q = Im; equations and unknowns Alg. 2 leaves
+// out are zeroed, with a 1 on the diagonal.  Fill positions start at 0.  One
+// thread per (block row, case) walks the row's positions.
+template <class T>
+struct Cx {
+  T x, y;
+};
+template <class T>
+__device__ __forceinline__ Cx<T> cx(double2 v) {
+  return Cx<T>{(T)v.x, (T)v.y};
+}
+template <class T>
+__device__ __forceinline__ Cx<T> mulc(Cx<T> a, Cx<T> b) {  // a conj(b)
+  return Cx<T>{fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y)};
+}
+template <class T>
+__device__ __forceinline__ Cx<T> mul(Cx<T> a, Cx<T> b) {
+  return Cx<T>{fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
+}
+
 template <class T>
 __global__ void k_nr_assemble(NrArgs a) {
-  Blk<T>* F = static_cast<Blk<T>*>(a.F);
-  const size_t n = (size_t)a.npos * a.Kp, Kp = a.Kp;
+  Blk<T>* __restrict__ F = static_cast<Blk<T>*>(a.F);
+  const double2* __restrict__ U = a.U;
+  const double* __restrict__ VM = a.vm;
+  const size_t n = (size_t)a.N * a.Kp, Kp = a.Kp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int64_t q = (int64_t)(e / Kp);
-    const int k = (int)(e % Kp);
+    const int r = (int)(e / Kp), k = (int)(e % Kp);
     if (!a.active[k]) continue;
-    const int i = __ldg(a.order + __ldg(a.prow + q)), j = __ldg(a.order + __ldg(a.fcol + q));
-    const int yp = __ldg(a.ymap + q);
-    double2 y = yp >= 0 ? __ldg(a.yval + yp) : make_double2(0.0, 0.0);
+    const int i = __ldg(a.order + r);
+    const size_t ei = (size_t)i * Kp + k;
+    const Cx<T> vi = cx<T>(a.V[ei]), ii = cx<T>(a.I[ei]);
+    const Cx<T> si = mulc(vi, ii);         // S_i
+    const Cx<T> sdi = mulc(cx<T>(U[ei]), ii);  // S_i / |V|_i
+    const uint8_t ti = __ldg(a.type + i);
+    const bool rp = ti != NR_SLACK, rq = ti == NR_PQ;
     const int of = a.of[k], ot = a.ot[k];
-    if (of >= 0 && yp >= 0) {
-      if (i == of && j == of) y = csub(y, a.yff[k]);
-      else if (i == ot && j == ot) y = csub(y, a.ytt[k]);
-      else if ((i == of && j == ot) || (i == ot && j == of)) y = csub(y, a.yft[k]);
+    const int q1 = __ldg(a.frp + r + 1);
+    for (int q = __ldg(a.frp + r); q < q1; ++q) {
+      const int j = __ldg(a.order + __ldg(a.fcol + q));
+      const int yp = __ldg(a.ymap + q);
+      Blk<T> b{T(0), T(0), T(0), T(0)};
+      if (yp >= 0) {
+        double2 y = __ldg(a.yval + yp);
+        if (of >= 0) {
+          if (i == of && j == of) y = csub(y, a.yff[k]);
+          else if (i == ot && j == ot) y = csub(y, a.ytt[k]);
+          else if ((i == of && j == ot) || (i == ot && j == of)) y = csub(y, a.yft[k]);
+        }
+        const size_t ej = (size_t)j * Kp + k;
+        const Cx<T> w = mulc(vi, mul(cx<T>(y), cx<T>(U[ej])));
+        const T vmj = (T)VM[ej];
+        T ba, bb, bc, bd;
+        if (i != j) {
+          ba = vmj * w.y;
+          bc = -vmj * w.x;
+          bb = w.x;
+          bd = w.y;
+        } else {
+          ba = fma(vmj, w.y, -si.y);
+          bc = fma(-vmj, w.x, si.x);
+          bb = sdi.x + w.x;
+          bd = sdi.y + w.y;
+        }
+        const uint8_t tj = __ldg(a.type + j);
+        const bool ct = tj != NR_SLACK, cv = tj == NR_PQ;
+        b.a = (rp && ct) ? ba : T(0);
+        b.b = (rp && cv) ? bb : T(0);
+        b.c = (rq && ct) ? bc : T(0);
+        b.d = (rq && cv) ? bd : T(0);
+        if (i == j) {
+          if (!rp) b.a = T(1);
+          if (!rq) b.d = T(1);
+        }
+      }
+      stb(F + (size_t)q * Kp + k, b);
     }
-    const double2 vi = a.V[(size_t)i * Kp + k], vj = a.V[(size_t)j * Kp + k];
-    const double2 tt = cmul(vi, cconj(cmul(y, vj)));
-    const double ivm = 1.0 / a.vm[(size_t)j * Kp + k];
-    double ba, bb, bc, bd;
-    if (i != j) {
-      ba = tt.y;
-      bc = -tt.x;
-      bb = tt.x * ivm;
-      bd = tt.y * ivm;
-    } else {
-      const double2 s = cmul(vi, cconj(a.I[(size_t)i * Kp + k]));
-      ba = -(s.y - tt.y);
-      bc = s.x - tt.x;
-      bb = (s.x + tt.x) * ivm;
-      bd = (s.y + tt.y) * ivm;
-    }
-    const uint8_t ti = __ldg(a.type + i), tj = __ldg(a.type + j);
-    const bool rp = ti != NR_SLACK, rq = ti == NR_PQ, ct = tj != NR_SLACK, cv = tj == NR_PQ;
-    Blk<T> b;
-    b.a = (rp && ct) ? (T)ba : T(0);
-    b.b = (rp && cv) ? (T)bb : T(0);
-    b.c = (rq && ct) ? (T)bc : T(0);
-    b.d = (rq && cv) ? (T)bd : T(0);
-    if (i == j) {
-      if (!rp) b.a = T(1);
-      if (!rq) b.d = T(1);
-    }
-    stb(F + e, b);
   }
 }
 
-// Block LU of every case in the tile, level by level of the elimination
-// tree.  Pass 1: each target position receives its updates -L(i,k) U(k,j)
-// from earlier pivots (all final: they sit on lower levels).  Pass 2: the
-// diagonal blocks of the level's pivots are inverted and their L positions
-// scaled, L(i,p) = A(i,p) D_p^-1.  C cases per CTA are the lanes, the
-// remaining thread index is the slot a target goes to.
+// acc minus the updates of one target: sum over its pairs of L(i,k) U(k,j)
 template <class T>
-__global__ void __launch_bounds__(NR_THREADS) k_nr_factor(NrArgs a) {
+__device__ __forceinline__ void apply_pairs(Blk<T>& acc, const Blk<T>* __restrict__ F, const int2* __restrict__ pairs,
+                                            int p, int p1, size_t Kp, int k) {
+  for (; p + 1 < p1; p += 2) {
+    const int2 q0 = __ldg(pairs + p), q1 = __ldg(pairs + p + 1);
+    const Blk<T> l0 = ldb(F + (size_t)q0.x * Kp + k), u0 = ldb(F + (size_t)q0.y * Kp + k);
+    const Blk<T> l1 = ldb(F + (size_t)q1.x * Kp + k), u1 = ldb(F + (size_t)q1.y * Kp + k);
+    msub(acc, l0, u0);
+    msub(acc, l1, u1);
+  }
+  if (p < p1) {
+    const int2 q0 = __ldg(pairs + p);
+    msub(acc, ldb(F + (size_t)q0.x * Kp + k), ldb(F + (size_t)q0.y * Kp + k));
+  }
+}
+
+// Block LU of every case in the tile and both triangular solves, in one
+// pass per level of the elimination tree (leaves first) and one back down.
+// At level l every target position (i, j) whose pivot p = min(i, j) sits on
+// level l takes its updates -L(i,k) U(k,j) from earlier pivots (all on lower
+// levels, final after the previous level's barrier); an L position also
+// forms its pivot's updated diagonal block D_p itself (a short list for this
+// kind of grid) and stores L(i,p) = A(i,p) D_p^-1, so one barrier per level
+// suffices; the diagonal target of row r stores D_r^-1 and the forward
+// substitution y_r = b_r - sum_c L(r,c) y_c (its L columns are descendants:
+// final).  The assembled diagonal blocks are only read.  Then, root first,
+// x_r = D_r^-1 (y_r - sum_c U(r,c) x_c), in place in X.  C cases per CTA
+// are the lanes, the remaining thread index is the slot a target goes to.
+template <class T>
+__global__ void __launch_bounds__(NR_THREADS) k_nr_lu(NrArgs a) {
   Blk<T>* F = static_cast<Blk<T>*>(a.F);
   Blk<T>* Dv = static_cast<Blk<T>*>(a.Dinv);
   const int lane = threadIdx.x & (a.C - 1), slot = threadIdx.x / a.C, S = blockDim.x / a.C;
   const int k = blockIdx.x * a.C + lane;
   const bool on = k < a.K && a.active[k];
+  if (!__syncthreads_or(on)) return;  // no case of this tile is iterating
   const size_t Kp = a.Kp;
   for (int l = 0; l < a.n_levels; ++l) {
     const int t0 = __ldg(a.lvl_ptr + l), t1 = __ldg(a.lvl_ptr + l + 1);
+    int t = t0 + slot;
+    int4 na, nb;  // the schedule entry of this slot's next target, fetched one step ahead
+    if (on && t < t1) {
+      na = __ldg(a.targets + 2 * t);
+      nb = __ldg(a.targets + 2 * t + 1);
+    }
     if (on)
-      for (int t = t0 + slot; t < t1; t += S) {
-        const int4 tg = __ldg(a.targets + t);
-        Blk<T> acc = ldb(F + (size_t)tg.x * Kp + k);
-        int p = tg.y;
-        for (; p + 1 < tg.z; p += 2) {
-          const int2 p0 = __ldg(a.pairs + p), p1 = __ldg(a.pairs + p + 1);
-          const Blk<T> l0 = ldb(F + (size_t)p0.x * Kp + k), u0 = ldb(F + (size_t)p0.y * Kp + k);
-          const Blk<T> l1 = ldb(F + (size_t)p1.x * Kp + k), u1 = ldb(F + (size_t)p1.y * Kp + k);
-          msub(acc, l0, u0);
-          msub(acc, l1, u1);
+      for (; t < t1; t += S) {
+        const int4 ta = na, tb = nb;
+        if (t + S < t1) {
+          na = __ldg(a.targets + 2 * (t + S));
+          nb = __ldg(a.targets + 2 * (t + S) + 1);
         }
-        if (p < tg.z) {
-          const int2 p0 = __ldg(a.pairs + p);
-          msub(acc, ldb(F + (size_t)p0.x * Kp + k), ldb(F + (size_t)p0.y * Kp + k));
+        Blk<T> acc = ldb(F + (size_t)ta.x * Kp + k);
+        apply_pairs(acc, F, a.pairs, ta.y, ta.z, Kp, k);
+        if (ta.w == NR_U) {
+          stb(F + (size_t)ta.x * Kp + k, acc);
+          continue;
         }
-        stb(F + (size_t)tg.x * Kp + k, acc);
-      }
-    __syncthreads();
-    if (on)
-      for (int t = t0 + slot; t < t1; t += S) {
-        const int4 tg = __ldg(a.targets + t);
-        if (tg.w == -1) continue;
+        Blk<T> d = acc;
+        if (ta.w == NR_L) {
+          d = ldb(F + (size_t)tb.x * Kp + k);
+          apply_pairs(d, F, a.pairs, tb.y, tb.z, Kp, k);
+        }
         Blk<T> di;
-        if (tg.w >= 0) {
-          inv2(ldb(F + (size_t)tg.w * Kp + k), di);
-          stb(F + (size_t)tg.x * Kp + k, mul(ldb(F + (size_t)tg.x * Kp + k), di));
-        } else {
-          if (!inv2(ldb(F + (size_t)tg.x * Kp + k), di)) a.bad[k] = 1;
-          stb(Dv + (size_t)(-2 - tg.w) * Kp + k, di);
+        const bool ok = inv2(d, di);
+        if (ta.w == NR_L) {
+          stb(F + (size_t)ta.x * Kp + k, mul(acc, di));
+          continue;
         }
-      }
-    __syncthreads();
-  }
-}
-
-// L y = b (unit block-lower), then U x = y with x_r = D_r^-1 (y_r - sum U x),
-// in place in X, level by level (forward: leaves first; backward: root first).
-template <class T>
-__global__ void __launch_bounds__(NR_THREADS) k_nr_solve(NrArgs a) {
-  const Blk<T>* F = static_cast<const Blk<T>*>(a.F);
-  const Blk<T>* Dv = static_cast<const Blk<T>*>(a.Dinv);
-  const int lane = threadIdx.x & (a.C - 1), slot = threadIdx.x / a.C, S = blockDim.x / a.C;
-  const int k = blockIdx.x * a.C + lane;
-  const bool on = k < a.K && a.active[k];
-  const size_t Kp = a.Kp;
-  for (int l = 0; l < a.n_levels; ++l) {
-    const int t0 = __ldg(a.rlvl_ptr + l), t1 = __ldg(a.rlvl_ptr + l + 1);
-    if (on)
-      for (int t = t0 + slot; t < t1; t += S) {
-        const int r = __ldg(a.rows + t);
+        if (!ok) a.bad[k] = 1;
+        const int r = tb.w;
+        stb(Dv + (size_t)r * Kp + k, di);
         const double2 b = a.X[(size_t)r * Kp + k];
         T y0 = (T)b.x, y1 = (T)b.y;
-        const int q1 = __ldg(a.fdiag + r);
+        const int q1 = ta.x;  // the row's L positions precede its diagonal
         for (int q = __ldg(a.frp + r); q < q1; ++q) {
           const Blk<T> m = ldb(F + (size_t)q * Kp + k);
           const double2 x = a.X[(size_t)__ldg(a.fcol + q) * Kp + k];
@@ -543,13 +584,13 @@ struct dpf_nr {
   NrSymbolic sym;
   int64_t launches = 0;
   // schedule (device)
-  int32_t *order = nullptr, *rank = nullptr, *frp = nullptr, *fcol = nullptr, *fdiag = nullptr, *prow = nullptr,
+  int32_t *order = nullptr, *rank = nullptr, *frp = nullptr, *fcol = nullptr, *fdiag = nullptr,
           *ymap = nullptr, *lvl_ptr = nullptr, *rlvl_ptr = nullptr, *rows = nullptr;
   int4* targets = nullptr;
   int2* pairs = nullptr;
   // state
   double *th = nullptr, *vm = nullptr, *Ps = nullptr, *Qs = nullptr;
-  double2 *V = nullptr, *I = nullptr, *X = nullptr;
+  double2 *V = nullptr, *U = nullptr, *I = nullptr, *X = nullptr;
   char* F = nullptr;
   char* Dinv = nullptr;
   int32_t *of = nullptr, *ot = nullptr, *active = nullptr, *status = nullptr, *iters = nullptr, *bad = nullptr,
@@ -560,9 +601,9 @@ struct dpf_nr {
 };
 
 static void nr_release(dpf_nr* h) {
-  dfree(h->order); dfree(h->rank); dfree(h->frp); dfree(h->fcol); dfree(h->fdiag); dfree(h->prow);
+  dfree(h->order); dfree(h->rank); dfree(h->frp); dfree(h->fcol); dfree(h->fdiag);
   dfree(h->ymap); dfree(h->lvl_ptr); dfree(h->rlvl_ptr); dfree(h->rows); dfree(h->targets); dfree(h->pairs);
-  dfree(h->th); dfree(h->vm); dfree(h->Ps); dfree(h->Qs); dfree(h->V); dfree(h->I); dfree(h->X);
+  dfree(h->th); dfree(h->vm); dfree(h->Ps); dfree(h->Qs); dfree(h->V); dfree(h->U); dfree(h->I); dfree(h->X);
   dfree(h->F); dfree(h->Dinv);
   dfree(h->of); dfree(h->ot); dfree(h->active); dfree(h->status); dfree(h->iters); dfree(h->bad);
   dfree(h->n_active); dfree(h->yff); dfree(h->yft); dfree(h->ytt); dfree(h->maxmis); dfree(h->loss);
@@ -579,12 +620,11 @@ static int nr_setup(dpf_nr* h) {
   TRY(upload(&h->frp, s.row_ptr));
   TRY(upload(&h->fcol, s.col));
   TRY(upload(&h->fdiag, s.diag));
-  TRY(upload(&h->prow, s.prow));
   TRY(upload(&h->ymap, s.ymap));
   TRY(upload(&h->lvl_ptr, s.lvl_ptr));
   TRY(upload(&h->rlvl_ptr, s.rlvl_ptr));
   TRY(upload(&h->rows, s.rows));
-  TRY(dalloc(&h->targets, s.targets.size() / 4));
+  TRY(dalloc(&h->targets, s.targets.size() / 4));  // two int4 per target
   CK(cudaMemcpy(h->targets, s.targets.data(), s.targets.size() * 4, cudaMemcpyHostToDevice));
   TRY(dalloc(&h->pairs, s.pairs.size() / 2));
   if (!s.pairs.empty()) CK(cudaMemcpy(h->pairs, s.pairs.data(), s.pairs.size() * 4, cudaMemcpyHostToDevice));
@@ -592,7 +632,7 @@ static int nr_setup(dpf_nr* h) {
   const size_t E = (size_t)n * Kp;
   TRY(dalloc(&h->th, E)); TRY(dalloc(&h->vm, E));
   TRY(dalloc(&h->Ps, E)); TRY(dalloc(&h->Qs, E));
-  TRY(dalloc(&h->V, E)); TRY(dalloc(&h->I, E)); TRY(dalloc(&h->X, E));
+  TRY(dalloc(&h->V, E)); TRY(dalloc(&h->U, E)); TRY(dalloc(&h->I, E)); TRY(dalloc(&h->X, E));
   TRY(dalloc(&h->F, npos * Kp * sizeof(Blk<double>)));
   TRY(dalloc(&h->Dinv, E * sizeof(Blk<double>)));
   TRY(dalloc(&h->of, Kp)); TRY(dalloc(&h->ot, Kp)); TRY(dalloc(&h->active, Kp)); TRY(dalloc(&h->status, Kp));
@@ -646,20 +686,29 @@ extern "C" int dpf_nr_stats(const dpf_nr* h, int64_t* n_pos, int64_t* n_pairs, i
 
 template <class T>
 static int nr_iterate_linear(dpf_nr* h, const NrArgs& a, cudaStream_t s) {
-  const size_t np = (size_t)a.npos * a.Kp;
-  k_nr_assemble<T><<<grid_for(np), 256, 0, s>>>(a);
-  const int ctas = a.Kp / a.C;
-  k_nr_factor<T><<<ctas, NR_THREADS, 0, s>>>(a);
-  k_nr_solve<T><<<ctas, NR_THREADS, 0, s>>>(a);
+  k_nr_assemble<T><<<grid_for((size_t)a.N * a.Kp), 256, 0, s>>>(a);
+  k_nr_lu<T><<<a.Kp / a.C, NR_THREADS, 0, s>>>(a);
   CKLAUNCH();
-  h->launches += 3;
+  h->launches += 2;
   return DPF_OK;
 }
 
-extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, double tol, int32_t max_iter,
-                            int32_t flat_start, void* stream) {
+extern "C" void dpf_nr_default_opts(dpf_nr_opts* o) {
+  if (!o) return;
+  o->precision = DPF_FP64;
+  o->tol = 1e-10;
+  o->max_iter = 20;
+  o->flat_start = 1;
+  o->lanes = 0;
+}
+
+extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o, void* stream) {
   clear_error();
-  if (!h || !b) return fail(DPF_E_INVALID, "dpf_nr_solve: NULL argument");
+  if (!h || !b || !o) return fail(DPF_E_INVALID, "dpf_nr_solve: NULL argument");
+  const int precision = o->precision, max_iter = o->max_iter, flat_start = o->flat_start;
+  const double tol = o->tol;
+  if (o->lanes < 0 || o->lanes > 32 || (o->lanes & (o->lanes - 1)))
+    return fail(DPF_E_INVALID, "dpf_nr_solve: lanes must be 0 or a power of 2 up to 32");
   const dpf_ybus* y = h->y;
   const int K = b->n_case;
   if (K <= 0 || K > h->max_case) return fail(DPF_E_INVALID, "dpf_nr_solve: n_case %d outside 1..%d", K, h->max_case);
@@ -688,11 +737,18 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, do
   a.N = y->n;
   a.K = K;
   a.Kp = (K + 31) / 32 * 32;
-  // cases per CTA: as many as keep every SM busy, at most 16
-  int C = 16;
-  const int sms = num_sms_nr();
-  while (C > 1 && (K + C - 1) / C < sms) C >>= 1;
-  a.C = C;
+  // cases per CTA: the C lanes of a slot share its schedule loads and read
+  // C consecutive blocks; few enough cases per CTA that every CTA of the
+  // batch is resident at once (each walks the whole tree: a second wave
+  // would double the time)
+  const int C_fixed = o->lanes;
+  auto lanes_for = [&](int n_active) {
+    if (C_fixed) return C_fixed;
+    int C = 4;
+    while (C > 1 && n_active / C < num_sms_nr()) C >>= 1;
+    return C;
+  };
+  a.C = lanes_for(K);
   a.va_slack = y->va_slack;
   a.tol = tol;
   a.inv_m = y->m_loss > 0 ? 1.0 / y->m_loss : 0.0;
@@ -710,7 +766,6 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, do
   a.frp = h->frp;
   a.fcol = h->fcol;
   a.fdiag = h->fdiag;
-  a.prow = h->prow;
   a.ymap = h->ymap;
   a.n_levels = sym.n_levels;
   a.lvl_ptr = h->lvl_ptr;
@@ -722,6 +777,7 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, do
   a.th = h->th;
   a.vm = h->vm;
   a.V = h->V;
+  a.U = h->U;
   a.I = h->I;
   a.X = h->X;
   a.Ps = b->p_spec ? h->Ps : nullptr;
@@ -750,12 +806,15 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, int32_t precision, do
     k_nr_volt<<<grid_for(E), 256, 0, s>>>(a);
     k_nr_eval<<<grid_for(E), 256, 0, s>>>(a);
     CK(cudaMemsetAsync(a.n_active, 0, 4, s));
-    k_nr_check<<<a.Kp / 32, 256, 0, s>>>(a);
+    k_nr_check<<<a.Kp / 32, 1024, 0, s>>>(a);
     CKLAUNCH();
     h->launches += 3;
     CK(cudaMemcpyAsync(h->h_nact, a.n_active, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (*h->h_nact == 0 || it > max_iter) break;
+    // few cases left: fewer cases per CTA, more slots per case (a shorter
+    // walk for each; CTAs whose cases have all stopped return at once)
+    a.C = lanes_for(*h->h_nact);
     if (precision == DPF_FP64) TRY(nr_iterate_linear<double>(h, a, s));
     else TRY(nr_iterate_linear<float>(h, a, s));
     k_nr_update<<<grid_for(E), 256, 0, s>>>(a);

@@ -20,6 +20,8 @@
 
 namespace dpf {
 
+enum { NR_U = 0, NR_DIAG = 1, NR_L = 2 };
+
 struct NrSymbolic {
   int n = 0;                       // block rows (buses)
   std::vector<int32_t> order;      // order[r] = internal bus at elimination step r
@@ -27,16 +29,18 @@ struct NrSymbolic {
   // filled block pattern of L + U in elimination order, CSR by rows with
   // sorted columns: row r = its L columns (< r), r itself, its U columns (> r)
   std::vector<int32_t> row_ptr, col, diag;  // diag[r]: position of (r, r)
-  std::vector<int32_t> prow;       // row of every position
   std::vector<int32_t> ymap;       // Y_bus CSR entry (internal order) of a position, -1 for fill
   std::vector<int32_t> level;      // elimination-tree height of every row (leaves 0)
   int n_levels = 0;
   // factorisation schedule: positions grouped by the level of their pivot
-  // min(row, col); each target {pos, pair_begin, pair_end, kind} with kind
-  // = diag position of the pivot (an L position), -1 (a U position), or
-  // -2 - r (the diagonal of row r)
+  // p = min(row, col), 8 ints per target:
+  //   {pos, pair_begin, pair_end, kind, dpos, dpair_begin, dpair_end, r}
+  // kind NR_U: a U position; NR_DIAG: the diagonal of row r (its inverse
+  // is stored; the forward substitution of row r follows); NR_L: an L
+  // position, which also needs the pivot's diagonal block: position dpos
+  // with its own update range
   std::vector<int32_t> lvl_ptr;    // [n_levels + 1] into targets
-  std::vector<int32_t> targets;    // 4 ints per target
+  std::vector<int32_t> targets;    // 8 ints per target
   std::vector<int32_t> pairs;      // 2 ints per pair: L(i,k) position, U(k,j) position
   // triangular solves: rows grouped by level
   std::vector<int32_t> rlvl_ptr;   // [n_levels + 1]

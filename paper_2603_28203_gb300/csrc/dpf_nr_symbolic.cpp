@@ -74,7 +74,6 @@ int nr_symbolic(const dpf_ybus* y, int64_t max_pairs, NrSymbolic* s) {
   for (int r = 0; r < n; ++r) s->row_ptr[r + 1] = s->row_ptr[r] + (int)low[r].size() + 1 + (int)up[r].size();
   const int64_t npos = s->row_ptr[n];
   s->col.resize(npos);
-  s->prow.resize(npos);
   s->diag.resize(n);
   for (int r = 0; r < n; ++r) {
     int q = s->row_ptr[r];
@@ -82,7 +81,6 @@ int nr_symbolic(const dpf_ybus* y, int64_t max_pairs, NrSymbolic* s) {
     s->diag[r] = q;
     s->col[q++] = r;
     for (int c : up[r]) s->col[q++] = c;
-    for (int p = s->row_ptr[r]; p < s->row_ptr[r + 1]; ++p) s->prow[p] = r;
   }
   auto pos = [&](int r, int c) -> int {
     const int32_t* b = s->col.data() + s->row_ptr[r];
@@ -143,26 +141,26 @@ int nr_symbolic(const dpf_ybus* y, int64_t max_pairs, NrSymbolic* s) {
   for (int r = 0; r < n; ++r) by_level[s->level[r]].push_back(r);
   s->lvl_ptr.assign(s->n_levels + 1, 0);
   s->targets.clear();
-  s->targets.reserve(4 * (size_t)npos);
+  s->targets.reserve(8 * (size_t)npos);
   s->rlvl_ptr.assign(s->n_levels + 1, 0);
   s->rows.clear();
   for (int l = 0; l < s->n_levels; ++l) {
     for (int p : by_level[l]) {
       s->rows.push_back(p);
+      const int dq = s->diag[p];
       auto add = [&](int q, int kind) {
-        s->targets.push_back(q);
-        s->targets.push_back((int32_t)cnt[q]);
-        s->targets.push_back((int32_t)cnt[q + 1]);
-        s->targets.push_back(kind);
+        const int32_t t[8] = {q, (int32_t)cnt[q], (int32_t)cnt[q + 1], kind,
+                              dq, (int32_t)cnt[dq], (int32_t)cnt[dq + 1], p};
+        s->targets.insert(s->targets.end(), t, t + 8);
       };
-      add(s->diag[p], -2 - p);
-      for (int i : up[p]) add(pos(i, p), s->diag[p]);  // L(i, p)
-      for (int j : up[p]) add(pos(p, j), -1);          // U(p, j)
+      add(dq, NR_DIAG);
+      for (int i : up[p]) add(pos(i, p), NR_L);
+      for (int j : up[p]) add(pos(p, j), NR_U);
     }
-    s->lvl_ptr[l + 1] = (int32_t)(s->targets.size() / 4);
+    s->lvl_ptr[l + 1] = (int32_t)(s->targets.size() / 8);
     s->rlvl_ptr[l + 1] = (int32_t)s->rows.size();
   }
-  if ((int64_t)s->targets.size() / 4 != npos) return fail(DPF_E_INVALID, "Newton analysis: target count");
+  if ((int64_t)s->targets.size() / 8 != npos) return fail(DPF_E_INVALID, "Newton analysis: target count");
   return DPF_OK;
 }
 

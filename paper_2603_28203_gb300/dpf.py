@@ -409,11 +409,14 @@ def dpf_nr_create(y: Ybus, max_case: int) -> NewtonSolver:
 
 
 def dpf_nr_solve(nr: NewtonSolver, precision=_abi.FP64, tol: float = 1e-10, max_iter: int = 20, flat_start=True,
-                 stream=None, **batch):
+                 lanes: int = 0, stream=None, **batch):
     """Newton-Raphson for every case; `batch` holds the dpf_batch fields as CUDA tensors (va, vm required)."""
     b = _batch_struct(**batch)
-    _check(lib().dpf_nr_solve(nr.handle, C.byref(b), int(precision), float(tol), int(max_iter),
-                              1 if flat_start else 0, _stream(stream)))
+    o = _abi.DpfNrOpts()
+    lib().dpf_nr_default_opts(C.byref(o))
+    o.precision, o.tol, o.max_iter = int(precision), float(tol), int(max_iter)
+    o.flat_start, o.lanes = (1 if flat_start else 0), int(lanes)
+    _check(lib().dpf_nr_solve(nr.handle, C.byref(b), C.byref(o), _stream(stream)))
 
 
 def dpf_paramid_begin(y: Ybus, ws: Workspace, va, vm, p_spec=None, q_spec=None, precision=_abi.FP32, stream=None):
