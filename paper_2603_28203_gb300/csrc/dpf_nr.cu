@@ -59,6 +59,7 @@ namespace {
 
 constexpr uint8_t NR_PQ = 0, NR_SLACK = 2;  // bus types (pv = 1)
 constexpr int NR_THREADS = 256;
+constexpr int NR_SMEM_THREADS = 1024;
 
 // 2x2 block: rows (P, Q), columns (theta, |V|), row-major.
 template <class T>
@@ -138,7 +139,7 @@ struct NrArgs {
   const int4* targets;
   const int2* pairs;
   const int32_t* rlvl_ptr;
-  const int32_t* rows;
+  const int4* rows;
   int64_t npos;
   // state [N][Kp]
   double* th;
@@ -339,104 +340,125 @@ __device__ __forceinline__ Cx<T> mul(Cx<T> a, Cx<T> b) {
   return Cx<T>{fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
 }
 
+// One block row of case k: its positions' blocks to dst[q * stride].
 template <class T>
-__global__ void k_nr_assemble(NrArgs a) {
-  Blk<T>* __restrict__ F = static_cast<Blk<T>*>(a.F);
+__device__ __forceinline__ void assemble_row(const NrArgs& a, int r, int k, Blk<T>* __restrict__ dst, size_t stride) {
+  const size_t Kp = a.Kp;
   const double2* __restrict__ U = a.U;
   const double* __restrict__ VM = a.vm;
+  const int i = __ldg(a.order + r);
+  const size_t ei = (size_t)i * Kp + k;
+  const Cx<T> vi = cx<T>(a.V[ei]), ii = cx<T>(a.I[ei]);
+  const Cx<T> si = mulc(vi, ii);             // S_i
+  const Cx<T> sdi = mulc(cx<T>(U[ei]), ii);  // S_i / |V|_i
+  const uint8_t ti = __ldg(a.type + i);
+  const bool rp = ti != NR_SLACK, rq = ti == NR_PQ;
+  const int of = a.of[k], ot = a.ot[k];
+  const int q1 = __ldg(a.frp + r + 1);
+  for (int q = __ldg(a.frp + r); q < q1; ++q) {
+    const int j = __ldg(a.order + __ldg(a.fcol + q));
+    const int yp = __ldg(a.ymap + q);
+    Blk<T> b{T(0), T(0), T(0), T(0)};
+    if (yp >= 0) {
+      double2 y = __ldg(a.yval + yp);
+      if (of >= 0) {
+        if (i == of && j == of) y = csub(y, a.yff[k]);
+        else if (i == ot && j == ot) y = csub(y, a.ytt[k]);
+        else if ((i == of && j == ot) || (i == ot && j == of)) y = csub(y, a.yft[k]);
+      }
+      const size_t ej = (size_t)j * Kp + k;
+      const Cx<T> w = mulc(vi, mul(cx<T>(y), cx<T>(U[ej])));
+      const T vmj = (T)VM[ej];
+      T ba, bb, bc, bd;
+      if (i != j) {
+        ba = vmj * w.y;
+        bc = -vmj * w.x;
+        bb = w.x;
+        bd = w.y;
+      } else {
+        ba = fma(vmj, w.y, -si.y);
+        bc = fma(-vmj, w.x, si.x);
+        bb = sdi.x + w.x;
+        bd = sdi.y + w.y;
+      }
+      const uint8_t tj = __ldg(a.type + j);
+      const bool ct = tj != NR_SLACK, cv = tj == NR_PQ;
+      b.a = (rp && ct) ? ba : T(0);
+      b.b = (rp && cv) ? bb : T(0);
+      b.c = (rq && ct) ? bc : T(0);
+      b.d = (rq && cv) ? bd : T(0);
+      if (i == j) {
+        if (!rp) b.a = T(1);
+        if (!rq) b.d = T(1);
+      }
+    }
+    stb(dst + (size_t)q * stride, b);
+  }
+}
+
+template <class T>
+__global__ void k_nr_assemble(NrArgs a) {
+  Blk<T>* F = static_cast<Blk<T>*>(a.F);
   const size_t n = (size_t)a.N * a.Kp, Kp = a.Kp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / Kp), k = (int)(e % Kp);
-    if (!a.active[k]) continue;
-    const int i = __ldg(a.order + r);
-    const size_t ei = (size_t)i * Kp + k;
-    const Cx<T> vi = cx<T>(a.V[ei]), ii = cx<T>(a.I[ei]);
-    const Cx<T> si = mulc(vi, ii);         // S_i
-    const Cx<T> sdi = mulc(cx<T>(U[ei]), ii);  // S_i / |V|_i
-    const uint8_t ti = __ldg(a.type + i);
-    const bool rp = ti != NR_SLACK, rq = ti == NR_PQ;
-    const int of = a.of[k], ot = a.ot[k];
-    const int q1 = __ldg(a.frp + r + 1);
-    for (int q = __ldg(a.frp + r); q < q1; ++q) {
-      const int j = __ldg(a.order + __ldg(a.fcol + q));
-      const int yp = __ldg(a.ymap + q);
-      Blk<T> b{T(0), T(0), T(0), T(0)};
-      if (yp >= 0) {
-        double2 y = __ldg(a.yval + yp);
-        if (of >= 0) {
-          if (i == of && j == of) y = csub(y, a.yff[k]);
-          else if (i == ot && j == ot) y = csub(y, a.ytt[k]);
-          else if ((i == of && j == ot) || (i == ot && j == of)) y = csub(y, a.yft[k]);
-        }
-        const size_t ej = (size_t)j * Kp + k;
-        const Cx<T> w = mulc(vi, mul(cx<T>(y), cx<T>(U[ej])));
-        const T vmj = (T)VM[ej];
-        T ba, bb, bc, bd;
-        if (i != j) {
-          ba = vmj * w.y;
-          bc = -vmj * w.x;
-          bb = w.x;
-          bd = w.y;
-        } else {
-          ba = fma(vmj, w.y, -si.y);
-          bc = fma(-vmj, w.x, si.x);
-          bb = sdi.x + w.x;
-          bd = sdi.y + w.y;
-        }
-        const uint8_t tj = __ldg(a.type + j);
-        const bool ct = tj != NR_SLACK, cv = tj == NR_PQ;
-        b.a = (rp && ct) ? ba : T(0);
-        b.b = (rp && cv) ? bb : T(0);
-        b.c = (rq && ct) ? bc : T(0);
-        b.d = (rq && cv) ? bd : T(0);
-        if (i == j) {
-          if (!rp) b.a = T(1);
-          if (!rq) b.d = T(1);
-        }
-      }
-      stb(F + (size_t)q * Kp + k, b);
-    }
+    if (a.active[k]) assemble_row(a, r, k, F + k, Kp);
   }
+}
+
+// Right-hand side / solution entries: FP64 pairs in global memory, pairs of
+// the factor's type in shared memory.
+template <class T>
+__device__ __forceinline__ Cx<T> ldx(const double2* p) {
+  const double2 v = *p;
+  return Cx<T>{(T)v.x, (T)v.y};
+}
+template <class T>
+__device__ __forceinline__ Cx<T> ldx(const Cx<T>* p) {
+  return *p;
+}
+template <class T>
+__device__ __forceinline__ void stx(double2* p, Cx<T> v) {
+  *p = make_double2((double)v.x, (double)v.y);
+}
+template <class T>
+__device__ __forceinline__ void stx(Cx<T>* p, Cx<T> v) {
+  *p = v;
 }
 
 // acc minus the updates of one target: sum over its pairs of L(i,k) U(k,j)
 template <class T>
-__device__ __forceinline__ void apply_pairs(Blk<T>& acc, const Blk<T>* __restrict__ F, const int2* __restrict__ pairs,
-                                            int p, int p1, size_t Kp, int k) {
+__device__ __forceinline__ void apply_pairs(Blk<T>& acc, const Blk<T>* F, size_t fs, const int2* __restrict__ pairs,
+                                            int p, int p1) {
   for (; p + 1 < p1; p += 2) {
     const int2 q0 = __ldg(pairs + p), q1 = __ldg(pairs + p + 1);
-    const Blk<T> l0 = ldb(F + (size_t)q0.x * Kp + k), u0 = ldb(F + (size_t)q0.y * Kp + k);
-    const Blk<T> l1 = ldb(F + (size_t)q1.x * Kp + k), u1 = ldb(F + (size_t)q1.y * Kp + k);
+    const Blk<T> l0 = ldb(F + (size_t)q0.x * fs), u0 = ldb(F + (size_t)q0.y * fs);
+    const Blk<T> l1 = ldb(F + (size_t)q1.x * fs), u1 = ldb(F + (size_t)q1.y * fs);
     msub(acc, l0, u0);
     msub(acc, l1, u1);
   }
   if (p < p1) {
     const int2 q0 = __ldg(pairs + p);
-    msub(acc, ldb(F + (size_t)q0.x * Kp + k), ldb(F + (size_t)q0.y * Kp + k));
+    msub(acc, ldb(F + (size_t)q0.x * fs), ldb(F + (size_t)q0.y * fs));
   }
 }
 
-// Block LU of every case in the tile and both triangular solves, in one
-// pass per level of the elimination tree (leaves first) and one back down.
-// At level l every target position (i, j) whose pivot p = min(i, j) sits on
-// level l takes its updates -L(i,k) U(k,j) from earlier pivots (all on lower
-// levels, final after the previous level's barrier); an L position also
-// forms its pivot's updated diagonal block D_p itself (a short list for this
-// kind of grid) and stores L(i,p) = A(i,p) D_p^-1, so one barrier per level
-// suffices; the diagonal target of row r stores D_r^-1 and the forward
-// substitution y_r = b_r - sum_c L(r,c) y_c (its L columns are descendants:
-// final).  The assembled diagonal blocks are only read.  Then, root first,
-// x_r = D_r^-1 (y_r - sum_c U(r,c) x_c), in place in X.  C cases per CTA
-// are the lanes, the remaining thread index is the slot a target goes to.
-template <class T>
-__global__ void __launch_bounds__(NR_THREADS) k_nr_lu(NrArgs a) {
-  Blk<T>* F = static_cast<Blk<T>*>(a.F);
-  Blk<T>* Dv = static_cast<Blk<T>*>(a.Dinv);
-  const int lane = threadIdx.x & (a.C - 1), slot = threadIdx.x / a.C, S = blockDim.x / a.C;
-  const int k = blockIdx.x * a.C + lane;
-  const bool on = k < a.K && a.active[k];
-  if (!__syncthreads_or(on)) return;  // no case of this tile is iterating
-  const size_t Kp = a.Kp;
+// Block LU of one case and both triangular solves, in one pass per level of
+// the elimination tree (leaves first) and one back down.  At level l every
+// target position (i, j) whose pivot p = min(i, j) sits on level l takes
+// its updates -L(i,k) U(k,j) from earlier pivots (all on lower levels, final
+// after the previous level's barrier); an L position also forms its pivot's
+// updated diagonal block D_p itself (a short list for this kind of grid) and
+// stores L(i,p) = A(i,p) D_p^-1, so one barrier per level suffices; the
+// diagonal target of row r stores D_r^-1 and the forward substitution
+// y_r = b_r - sum_c L(r,c) y_c (its L columns are descendants: final).  The
+// assembled diagonal blocks are only read.  Then, root first,
+// x_r = D_r^-1 (y_r - sum_c U(r,c) x_c), in place in X.  Block q of the case
+// is F[q * fs], the inverse diagonal of row r Dv[r * ds], its right-hand
+// side X[r * xs]; this thread takes every S-th target from `slot` on.
+template <class T, class XT>
+__device__ __forceinline__ void lu_levels(const NrArgs& a, Blk<T>* F, size_t fs, Blk<T>* Dv, size_t ds, XT* X,
+                                          size_t xs, int slot, int S, bool on, int32_t* bad) {
   for (int l = 0; l < a.n_levels; ++l) {
     const int t0 = __ldg(a.lvl_ptr + l), t1 = __ldg(a.lvl_ptr + l + 1);
     int t = t0 + slot;
@@ -452,36 +474,35 @@ __global__ void __launch_bounds__(NR_THREADS) k_nr_lu(NrArgs a) {
           na = __ldg(a.targets + 2 * (t + S));
           nb = __ldg(a.targets + 2 * (t + S) + 1);
         }
-        Blk<T> acc = ldb(F + (size_t)ta.x * Kp + k);
-        apply_pairs(acc, F, a.pairs, ta.y, ta.z, Kp, k);
+        Blk<T> acc = ldb(F + (size_t)ta.x * fs);
+        apply_pairs(acc, F, fs, a.pairs, ta.y, ta.z);
         if (ta.w == NR_U) {
-          stb(F + (size_t)ta.x * Kp + k, acc);
+          stb(F + (size_t)ta.x * fs, acc);
           continue;
         }
         Blk<T> d = acc;
         if (ta.w == NR_L) {
-          d = ldb(F + (size_t)tb.x * Kp + k);
-          apply_pairs(d, F, a.pairs, tb.y, tb.z, Kp, k);
+          d = ldb(F + (size_t)tb.x * fs);
+          apply_pairs(d, F, fs, a.pairs, tb.y, tb.z);
         }
         Blk<T> di;
         const bool ok = inv2(d, di);
         if (ta.w == NR_L) {
-          stb(F + (size_t)ta.x * Kp + k, mul(acc, di));
+          stb(F + (size_t)ta.x * fs, mul(acc, di));
           continue;
         }
-        if (!ok) a.bad[k] = 1;
+        if (!ok) *bad = 1;
         const int r = tb.w;
-        stb(Dv + (size_t)r * Kp + k, di);
-        const double2 b = a.X[(size_t)r * Kp + k];
-        T y0 = (T)b.x, y1 = (T)b.y;
-        const int q1 = ta.x;  // the row's L positions precede its diagonal
-        for (int q = __ldg(a.frp + r); q < q1; ++q) {
-          const Blk<T> m = ldb(F + (size_t)q * Kp + k);
-          const double2 x = a.X[(size_t)__ldg(a.fcol + q) * Kp + k];
-          y0 = fma(-m.a, (T)x.x, fma(-m.b, (T)x.y, y0));
-          y1 = fma(-m.c, (T)x.x, fma(-m.d, (T)x.y, y1));
+        stb(Dv + (size_t)r * ds, di);
+        Cx<T> y = ldx<T>(X + (size_t)r * xs);
+        const int q1 = ta.x;  // the row's L positions (from tb.x) precede its diagonal
+        for (int q = tb.x; q < q1; ++q) {
+          const Blk<T> m = ldb(F + (size_t)q * fs);
+          const Cx<T> x = ldx<T>(X + (size_t)__ldg(a.fcol + q) * xs);
+          y.x = fma(-m.a, x.x, fma(-m.b, x.y, y.x));
+          y.y = fma(-m.c, x.x, fma(-m.d, x.y, y.y));
         }
-        a.X[(size_t)r * Kp + k] = make_double2((double)y0, (double)y1);
+        stx(X + (size_t)r * xs, y);
       }
     __syncthreads();
   }
@@ -489,21 +510,60 @@ __global__ void __launch_bounds__(NR_THREADS) k_nr_lu(NrArgs a) {
     const int t0 = __ldg(a.rlvl_ptr + l), t1 = __ldg(a.rlvl_ptr + l + 1);
     if (on)
       for (int t = t0 + slot; t < t1; t += S) {
-        const int r = __ldg(a.rows + t);
-        const double2 b = a.X[(size_t)r * Kp + k];
-        T y0 = (T)b.x, y1 = (T)b.y;
-        const int q1 = __ldg(a.frp + r + 1);
-        for (int q = __ldg(a.fdiag + r) + 1; q < q1; ++q) {
-          const Blk<T> m = ldb(F + (size_t)q * Kp + k);
-          const double2 x = a.X[(size_t)__ldg(a.fcol + q) * Kp + k];
-          y0 = fma(-m.a, (T)x.x, fma(-m.b, (T)x.y, y0));
-          y1 = fma(-m.c, (T)x.x, fma(-m.d, (T)x.y, y1));
+        const int4 rw = __ldg(a.rows + t);  // {r, first U position, end of row}
+        const int r = rw.x;
+        Cx<T> y = ldx<T>(X + (size_t)r * xs);
+        for (int q = rw.y; q < rw.z; ++q) {
+          const Blk<T> m = ldb(F + (size_t)q * fs);
+          const Cx<T> x = ldx<T>(X + (size_t)__ldg(a.fcol + q) * xs);
+          y.x = fma(-m.a, x.x, fma(-m.b, x.y, y.x));
+          y.y = fma(-m.c, x.x, fma(-m.d, x.y, y.y));
         }
-        const Blk<T> di = ldb(Dv + (size_t)r * Kp + k);
-        a.X[(size_t)r * Kp + k] = make_double2((double)fma(di.a, y0, di.b * y1), (double)fma(di.c, y0, di.d * y1));
+        const Blk<T> di = ldb(Dv + (size_t)r * ds);
+        stx(X + (size_t)r * xs, Cx<T>{fma(di.a, y.x, di.b * y.y), fma(di.c, y.x, di.d * y.y)});
       }
     __syncthreads();
   }
+}
+
+// Global-memory form: C cases per CTA are the lanes (their blocks adjacent),
+// the remaining thread index is the slot.
+template <class T>
+__global__ void __launch_bounds__(NR_THREADS) k_nr_lu(NrArgs a) {
+  const int lane = threadIdx.x & (a.C - 1), slot = threadIdx.x / a.C, S = blockDim.x / a.C;
+  const int k = blockIdx.x * a.C + lane;
+  const bool on = k < a.K && a.active[k];
+  if (!__syncthreads_or(on)) return;  // no case of this tile is iterating
+  const size_t Kp = a.Kp;
+  lu_levels(a, static_cast<Blk<T>*>(a.F) + k, Kp, static_cast<Blk<T>*>(a.Dinv) + k, Kp, a.X + k, Kp, slot, S, on,
+            a.bad + k);
+}
+
+// Shared-memory form, for grids whose factor of one case fits: one CTA per
+// case assembles its Jacobian straight into shared memory (the factor never
+// goes to HBM), factorises and solves there, and writes dx back.
+template <class T>
+__global__ void __launch_bounds__(NR_SMEM_THREADS) k_nr_lu_smem(NrArgs a) {
+  extern __shared__ __align__(16) unsigned char nr_smem[];
+  const int k = blockIdx.x;
+  if (!a.active[k]) return;  // the same for the whole CTA
+  Blk<T>* Fs = reinterpret_cast<Blk<T>*>(nr_smem);
+  Blk<T>* Ds = Fs + a.npos;
+  Cx<T>* Xs = reinterpret_cast<Cx<T>*>(Ds + a.N);
+  const size_t Kp = a.Kp;
+  for (int r = threadIdx.x; r < a.N; r += blockDim.x) {
+    Xs[r] = ldx<T>(a.X + (size_t)r * Kp + k);
+    assemble_row(a, r, k, Fs, 1);
+  }
+  __syncthreads();
+  lu_levels(a, Fs, 1, Ds, 1, Xs, 1, (int)threadIdx.x, (int)blockDim.x, true, a.bad + k);
+  for (int r = threadIdx.x; r < a.N; r += blockDim.x) stx(a.X + (size_t)r * Kp + k, Xs[r]);
+}
+
+// Shared memory the shared-memory form needs for one case.
+template <class T>
+size_t lu_smem_bytes(int64_t npos, int n) {
+  return (size_t)(npos + n) * sizeof(Blk<T>) + (size_t)n * sizeof(Cx<T>);
 }
 
 __global__ void k_nr_update(NrArgs a) {
@@ -585,7 +645,8 @@ struct dpf_nr {
   int64_t launches = 0;
   // schedule (device)
   int32_t *order = nullptr, *rank = nullptr, *frp = nullptr, *fcol = nullptr, *fdiag = nullptr,
-          *ymap = nullptr, *lvl_ptr = nullptr, *rlvl_ptr = nullptr, *rows = nullptr;
+          *ymap = nullptr, *lvl_ptr = nullptr, *rlvl_ptr = nullptr;
+  int4* rows = nullptr;
   int4* targets = nullptr;
   int2* pairs = nullptr;
   // state
@@ -623,7 +684,8 @@ static int nr_setup(dpf_nr* h) {
   TRY(upload(&h->ymap, s.ymap));
   TRY(upload(&h->lvl_ptr, s.lvl_ptr));
   TRY(upload(&h->rlvl_ptr, s.rlvl_ptr));
-  TRY(upload(&h->rows, s.rows));
+  TRY(dalloc(&h->rows, s.rows.size() / 4));
+  CK(cudaMemcpy(h->rows, s.rows.data(), s.rows.size() * 4, cudaMemcpyHostToDevice));
   TRY(dalloc(&h->targets, s.targets.size() / 4));  // two int4 per target
   CK(cudaMemcpy(h->targets, s.targets.data(), s.targets.size() * 4, cudaMemcpyHostToDevice));
   TRY(dalloc(&h->pairs, s.pairs.size() / 2));
@@ -685,12 +747,27 @@ extern "C" int dpf_nr_stats(const dpf_nr* h, int64_t* n_pos, int64_t* n_pairs, i
 }
 
 template <class T>
-static int nr_iterate_linear(dpf_nr* h, const NrArgs& a, cudaStream_t s) {
+static int nr_iterate_linear(dpf_nr* h, const NrArgs& a, bool smem, cudaStream_t s) {
+  if (smem) {
+    const size_t bytes = lu_smem_bytes<T>(a.npos, a.N);
+    CK(cudaFuncSetAttribute(k_nr_lu_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    k_nr_lu_smem<T><<<a.K, NR_SMEM_THREADS, bytes, s>>>(a);
+    CKLAUNCH();
+    h->launches += 1;
+    return DPF_OK;
+  }
   k_nr_assemble<T><<<grid_for((size_t)a.N * a.Kp), 256, 0, s>>>(a);
   k_nr_lu<T><<<a.Kp / a.C, NR_THREADS, 0, s>>>(a);
   CKLAUNCH();
   h->launches += 2;
   return DPF_OK;
+}
+
+static size_t smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return (size_t)v;
 }
 
 extern "C" void dpf_nr_default_opts(dpf_nr_opts* o) {
@@ -749,6 +826,14 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
     return C;
   };
   a.C = lanes_for(K);
+  // The shared-memory form where one case's factor fits and the cases still
+  // iterating fit in one wave of one CTA per SM (its walk down the tree is
+  // shorter, but a second wave would double it); else the global-memory
+  // form.  Both give the same bits.  o->lanes > 0 forces the global form.
+  const size_t need = precision == DPF_FP64 ? lu_smem_bytes<double>(sym.row_ptr[sym.n], y->n)
+                                            : lu_smem_bytes<float>(sym.row_ptr[sym.n], y->n);
+  const bool fits = o->lanes == 0 && need <= smem_optin();
+  bool smem = false;
   a.va_slack = y->va_slack;
   a.tol = tol;
   a.inv_m = y->m_loss > 0 ? 1.0 / y->m_loss : 0.0;
@@ -815,8 +900,9 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
     // few cases left: fewer cases per CTA, more slots per case (a shorter
     // walk for each; CTAs whose cases have all stopped return at once)
     a.C = lanes_for(*h->h_nact);
-    if (precision == DPF_FP64) TRY(nr_iterate_linear<double>(h, a, s));
-    else TRY(nr_iterate_linear<float>(h, a, s));
+    smem = fits && *h->h_nact <= num_sms_nr();
+    if (precision == DPF_FP64) TRY(nr_iterate_linear<double>(h, a, smem, s));
+    else TRY(nr_iterate_linear<float>(h, a, smem, s));
     k_nr_update<<<grid_for(E), 256, 0, s>>>(a);
     CKLAUNCH();
     h->launches += 1;

@@ -36,15 +36,17 @@ struct NrSymbolic {
   // p = min(row, col), 8 ints per target:
   //   {pos, pair_begin, pair_end, kind, dpos, dpair_begin, dpair_end, r}
   // kind NR_U: a U position; NR_DIAG: the diagonal of row r (its inverse
-  // is stored; the forward substitution of row r follows); NR_L: an L
+  // is stored; the forward substitution of row r, over its L positions from
+  // dpos = row_ptr[r] up to the diagonal, follows); NR_L: an L
   // position, which also needs the pivot's diagonal block: position dpos
   // with its own update range
   std::vector<int32_t> lvl_ptr;    // [n_levels + 1] into targets
   std::vector<int32_t> targets;    // 8 ints per target
   std::vector<int32_t> pairs;      // 2 ints per pair: L(i,k) position, U(k,j) position
-  // triangular solves: rows grouped by level
+  // triangular solves: rows grouped by level, 4 ints per row:
+  // {r, first U position of row r, end of row r, 0}
   std::vector<int32_t> rlvl_ptr;   // [n_levels + 1]
-  std::vector<int32_t> rows;       // [n]
+  std::vector<int32_t> rows;       // [4 n]
 };
 
 // Minimum-degree order of Y_bus's graph, the filled pattern it produces, the

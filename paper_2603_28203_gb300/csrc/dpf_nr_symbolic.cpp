@@ -146,11 +146,12 @@ int nr_symbolic(const dpf_ybus* y, int64_t max_pairs, NrSymbolic* s) {
   s->rows.clear();
   for (int l = 0; l < s->n_levels; ++l) {
     for (int p : by_level[l]) {
-      s->rows.push_back(p);
       const int dq = s->diag[p];
+      const int32_t rw[4] = {p, dq + 1, s->row_ptr[p + 1], 0};
+      s->rows.insert(s->rows.end(), rw, rw + 4);
       auto add = [&](int q, int kind) {
         const int32_t t[8] = {q, (int32_t)cnt[q], (int32_t)cnt[q + 1], kind,
-                              dq, (int32_t)cnt[dq], (int32_t)cnt[dq + 1], p};
+                              kind == NR_DIAG ? s->row_ptr[p] : dq, (int32_t)cnt[dq], (int32_t)cnt[dq + 1], p};
         s->targets.insert(s->targets.end(), t, t + 8);
       };
       add(dq, NR_DIAG);
@@ -158,7 +159,7 @@ int nr_symbolic(const dpf_ybus* y, int64_t max_pairs, NrSymbolic* s) {
       for (int j : up[p]) add(pos(p, j), NR_U);
     }
     s->lvl_ptr[l + 1] = (int32_t)(s->targets.size() / 8);
-    s->rlvl_ptr[l + 1] = (int32_t)s->rows.size();
+    s->rlvl_ptr[l + 1] = (int32_t)(s->rows.size() / 4);
   }
   if ((int64_t)s->targets.size() / 8 != npos) return fail(DPF_E_INVALID, "Newton analysis: target count");
   return DPF_OK;
