@@ -1039,6 +1039,8 @@ def run_nr(args):
     out = {}
     steps_bytes = nr_bytes_per_step(g.n_bus, st["n_pos"], st["n_pairs"], 1)
     for prec, pname in ((dpf.FP64, "fp64"), (dpf.FP32, "fp32")):
+        if pname not in args.nr_precision.split(","):
+            continue
         for tol in (1e-6, 1e-10):
             r = state()
             wall = timed(lambda: dpf.dpf_nr_solve(nr, precision=prec, tol=tol, max_iter=args.nr_max_iter,
@@ -1188,6 +1190,7 @@ def main():
     ap.add_argument("--warm-max-iter", type=int, default=50000)
     ap.add_argument("--c1-cases", type=int, default=8192)
     ap.add_argument("--nr-max-iter", type=int, default=10)
+    ap.add_argument("--nr-precision", default="fp64,fp32", help="factor precisions the nr workload times")
     ap.add_argument("--pid-grids", type=int, default=16)
     ap.add_argument("--pid-steps", type=int, default=4000)
     ap.add_argument("--pid-lr", type=float, default=3e-3)
