@@ -6,6 +6,7 @@
 // Per Newton iteration, for every case still iterating:
 //   k_nr_volt      V = |V| e^{j theta} (FP64)
 //   k_nr_eval      I = Y' V, S = V conj(I), f, right-hand side -f (FP64)
+//   k_nr_partial   per case and chunk of rows: partial max |f| and ||f||^2
 //   k_nr_check     per case max |f|, loss, stop test (the host reads the
 //                  number of cases left)
 //   k_nr_assemble  the 2x2 Jacobian blocks of Alg. 2 on the filled pattern
@@ -60,6 +61,7 @@ namespace {
 constexpr uint8_t NR_PQ = 0, NR_SLACK = 2;  // bus types (pv = 1)
 constexpr int NR_THREADS = 256;
 constexpr int NR_SMEM_THREADS = 1024;
+constexpr int NR_CHUNKS = 16;  // row chunks of the per-case reduction
 
 // 2x2 block: rows (P, Q), columns (theta, |V|), row-major.
 template <class T>
@@ -165,6 +167,8 @@ struct NrArgs {
   double* maxmis;
   double* loss;
   int32_t* n_active;
+  double* pmax;  // [NR_CHUNKS][Kp] partials of the stop test
+  double* psum;
 };
 
 // Per case: outage data (pi-model block of the removed branch), state flags.
@@ -268,33 +272,54 @@ __global__ void k_nr_eval(NrArgs a) {
   }
 }
 
-// Per case (32 cases x 32 row groups per CTA, fixed summation order): max |f|,
-// loss (1/m) ||f||^2 and the stop test of Alg. 2.  `it` is the number of
-// Newton steps taken so far.
-__global__ void __launch_bounds__(1024) k_nr_check(NrArgs a) {
-  __shared__ double smax[32][32], ssum[32][32];
+// Per case and chunk of rows (32 cases x 8 row groups per CTA, fixed
+// summation order): partial max |f| (NaN if any entry is NaN) and partial
+// ||f||^2 from the right-hand side -f.
+__global__ void __launch_bounds__(256) k_nr_partial(NrArgs a) {
+  __shared__ double smax[8][32], ssum[8][32];
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int k = blockIdx.x * 32 + lane;
   const bool on = k < a.K && a.active[k];
+  const int rpc = (a.N + NR_CHUNKS - 1) / NR_CHUNKS;
+  const int r0 = blockIdx.y * rpc, r1 = min(a.N, r0 + rpc);
   double mx = 0.0, sm = 0.0;
+  bool nan = false;
   if (on)
-    for (int r = g; r < a.N; r += 32) {
+    for (int r = r0 + g; r < r1; r += 8) {
       const double2 x = a.X[(size_t)r * a.Kp + k];
+      nan = nan || !(x.x == x.x) || !(x.y == x.y);
       mx = fmax(mx, fmax(fabs(x.x), fabs(x.y)));
-      if (!(x.x == x.x) || !(x.y == x.y)) mx = __longlong_as_double(0x7ff8000000000000LL);
       sm = fma(x.x, x.x, fma(x.y, x.y, sm));
     }
-  smax[g][lane] = mx;
+  smax[g][lane] = nan ? __longlong_as_double(0x7ff8000000000000LL) : mx;
   ssum[g][lane] = sm;
   __syncthreads();
   if (g != 0 || !on) return;
-  bool nan = false;
-  for (int q = 0; q < 32; ++q) {
-    nan = nan || !(smax[q][lane] == smax[q][lane]);
-    mx = fmax(mx, smax[q][lane]);
-  }
+  mx = 0.0;
   sm = 0.0;
-  for (int q = 0; q < 32; ++q) sm += ssum[q][lane];
+  for (int q = 0; q < 8; ++q) {
+    const double m = smax[q][lane];
+    nan = nan || !(m == m);
+    mx = fmax(mx, m);
+    sm += ssum[q][lane];
+  }
+  a.pmax[(size_t)blockIdx.y * a.Kp + k] = nan ? __longlong_as_double(0x7ff8000000000000LL) : mx;
+  a.psum[(size_t)blockIdx.y * a.Kp + k] = sm;
+}
+
+// Per case: max |f|, loss (1/m) ||f||^2 from the chunks' partials (fixed
+// order) and the stop test of Alg. 2.
+__global__ void k_nr_check(NrArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.K || !a.active[k]) return;
+  double mx = 0.0, sm = 0.0;
+  bool nan = false;
+  for (int c = 0; c < NR_CHUNKS; ++c) {
+    const double m = a.pmax[(size_t)c * a.Kp + k];
+    nan = nan || !(m == m);
+    mx = fmax(mx, m);
+    sm += a.psum[(size_t)c * a.Kp + k];
+  }
   if (nan) mx = __longlong_as_double(0x7ff8000000000000LL);
   a.maxmis[k] = mx;
   a.loss[k] = sm * a.inv_m;
@@ -657,7 +682,7 @@ struct dpf_nr {
   int32_t *of = nullptr, *ot = nullptr, *active = nullptr, *status = nullptr, *iters = nullptr, *bad = nullptr,
           *n_active = nullptr;
   double2 *yff = nullptr, *yft = nullptr, *ytt = nullptr;
-  double *maxmis = nullptr, *loss = nullptr;
+  double *maxmis = nullptr, *loss = nullptr, *pmax = nullptr, *psum = nullptr;
   int32_t* h_nact = nullptr;  // pinned
 };
 
@@ -667,7 +692,7 @@ static void nr_release(dpf_nr* h) {
   dfree(h->th); dfree(h->vm); dfree(h->Ps); dfree(h->Qs); dfree(h->V); dfree(h->U); dfree(h->I); dfree(h->X);
   dfree(h->F); dfree(h->Dinv);
   dfree(h->of); dfree(h->ot); dfree(h->active); dfree(h->status); dfree(h->iters); dfree(h->bad);
-  dfree(h->n_active); dfree(h->yff); dfree(h->yft); dfree(h->ytt); dfree(h->maxmis); dfree(h->loss);
+  dfree(h->n_active); dfree(h->yff); dfree(h->yft); dfree(h->ytt); dfree(h->maxmis); dfree(h->loss); dfree(h->pmax); dfree(h->psum);
   if (h->h_nact) cudaFreeHost(h->h_nact);
   h->h_nact = nullptr;
 }
@@ -701,6 +726,7 @@ static int nr_setup(dpf_nr* h) {
   TRY(dalloc(&h->iters, Kp)); TRY(dalloc(&h->bad, Kp)); TRY(dalloc(&h->n_active, 1));
   TRY(dalloc(&h->yff, Kp)); TRY(dalloc(&h->yft, Kp)); TRY(dalloc(&h->ytt, Kp));
   TRY(dalloc(&h->maxmis, Kp)); TRY(dalloc(&h->loss, Kp));
+  TRY(dalloc(&h->pmax, (size_t)NR_CHUNKS * Kp)); TRY(dalloc(&h->psum, (size_t)NR_CHUNKS * Kp));
   CK(cudaMallocHost((void**)&h->h_nact, sizeof(int32_t)));
   return DPF_OK;
 }
@@ -881,6 +907,8 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
   a.maxmis = h->maxmis;
   a.loss = h->loss;
   a.n_active = h->n_active;
+  a.pmax = h->pmax;
+  a.psum = h->psum;
   const size_t E = (size_t)a.N * a.Kp;
   const int cb = (a.Kp + 255) / 256;
   k_nr_init<<<cb, 256, 0, s>>>(a, b->outage, d.br_f, d.br_t, d.br_r, d.br_x, d.br_bch, d.br_tap);
@@ -891,9 +919,10 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
     k_nr_volt<<<grid_for(E), 256, 0, s>>>(a);
     k_nr_eval<<<grid_for(E), 256, 0, s>>>(a);
     CK(cudaMemsetAsync(a.n_active, 0, 4, s));
-    k_nr_check<<<a.Kp / 32, 1024, 0, s>>>(a);
+    k_nr_partial<<<dim3(a.Kp / 32, NR_CHUNKS), 256, 0, s>>>(a);
+    k_nr_check<<<cb, 256, 0, s>>>(a);
     CKLAUNCH();
-    h->launches += 3;
+    h->launches += 4;
     CK(cudaMemcpyAsync(h->h_nact, a.n_active, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (*h->h_nact == 0 || it > max_iter) break;

@@ -234,3 +234,19 @@ def test_shared_and_global_memory_forms_agree_bit_for_bit(grid):
         b = _nr(y, nr, K, precision=prec, outage=_t(outs, torch.int32), lanes=4)
         for key in a:
             np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_single_case_on_the_10k_bus_grid():
+    """One case of the 10,000-bus grid: too large a factor for shared
+    memory, so the global-memory form runs with one case per CTA (256
+    slots walking the tree); against the oracle's NR."""
+    g = gridgen.config_grid("c2_10kbus")
+    Y = grid_ybus(g)
+    ref = oracle.nr_solve(Y, g.p_spec, g.q_spec, g.bus_type, g.vm_set, tol=TOL)
+    assert ref["converged"]
+    y = dpf.dpf_build_ybus(g)
+    nr = dpf.dpf_nr_create(y, 1)
+    r = _nr(y, nr, 1)
+    assert r["status"][0] == dpf.CASE_CONVERGED and r["iters"][0] == ref["iters"]
+    assert np.abs(r["va"][0] - ref["va"]).max() <= 1e-9
+    assert np.abs(r["vm"][0] - ref["vm"]).max() <= 1e-9
