@@ -637,6 +637,28 @@ def run_timeseries(args):
     for t in sample:
         f, _ = oracle.mismatch(Y, out["va"][t], out["vm"][t], P[t], Q[t], g.bus_type)
         err = max(err, abs(float(np.max(np.abs(f))) - float(out["max_mismatch"][t])))
+    # the first window's Alg. 1 solutions through Newton-Raphson (start and
+    # fallback; Fig. 4's caption, Sec. 6), later windows as before
+    nr = dpf.dpf_nr_create(y, 96)
+    with torch.cuda.stream(stream):
+        solve_time_series(y, ws, P[:96], Q[:96], window=96, stream=stream, first_newton=nr)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out_n = solve_time_series(y, ws, P, Q, window=96, stream=stream, first_newton=nr)
+        torch.cuda.synchronize()
+        wall_n = time.perf_counter() - t0
+    for t in (0, 95):
+        f, _ = oracle.mismatch(Y, out_n["va"][t], out_n["vm"][t], P[t], Q[t], g.bus_type)
+        err = max(err, abs(float(np.max(np.abs(f))) - float(out_n["max_mismatch"][t])))
+    nr.free()
+    newton_first = {
+        "wall_s": wall_n, "snapshots_per_s": T / wall_n,
+        "first_window_newton_converged_1e-10": int((out_n["status"][:96] == 0).sum()),
+        "first_window_newton_steps_p50": float(np.median(out_n["iters"][:96])),
+        "first_window_max_mismatch_p50": float(np.median(out_n["max_mismatch"][:96])),
+        "max_mismatch_p50_later_windows": float(np.median(out_n["max_mismatch"][96:])) if T > 96 else None,
+        "max_mismatch_p50_later_windows_dpf_first": float(np.median(out["max_mismatch"][96:])) if T > 96 else None,
+    }
     st = out["status"]
     it = out["iters"]
     print(json.dumps({
@@ -653,6 +675,7 @@ def run_timeseries(args):
         "max_mismatch_p99": float(np.percentile(out["max_mismatch"], 99)),
         "sampled_snapshots": sample,
         "reported_vs_fp64_oracle_mismatch_max_abs_diff": err,
+        "first_window_newton": newton_first,
     }), flush=True)
     ws.free()
     y.free()
@@ -1066,7 +1089,7 @@ def run_nr(args):
         def both():
             dpf.dpf_solve_batch(y, ws, o, n_case=K, outage=od, **r)
             dpf.dpf_nr_solve(nr, precision=dpf.FP64, tol=1e-10, max_iter=args.nr_max_iter, flat_start=False,
-                             n_case=K, outage=od, **r)
+                             fallback=True, n_case=K, outage=od, **r)
         wall = timed(both, reps=2)
         it, stt = r["iters"].cpu().numpy(), r["status"].cpu().numpy()
         conv = stt == 0

@@ -371,8 +371,13 @@ typedef struct {
   int32_t flat_start;        /* 1: ignore va/vm inputs, start flat              */
   int32_t lanes;             /* cases per CTA of the factor and solve kernels
                                 (power of 2 up to 32; 0 = auto)               */
+  int32_t fallback;          /* 1 (with flat_start = 0): a case Newton does not
+                                converge keeps the start passed in va/vm and
+                                reports the start's max |f| and loss (its
+                                status still says Newton failed): a DPF
+                                solution given as the start is the fallback  */
 } dpf_nr_opts;
-/* Defaults: DPF_FP64, tol 1e-10, max_iter 20, flat start, lanes auto. */
+/* Defaults: DPF_FP64, tol 1e-10, max_iter 20, flat start, lanes auto, no fallback. */
 void dpf_nr_default_opts(dpf_nr_opts* o);
 int dpf_nr_create(const dpf_ybus* y, int32_t max_case, dpf_nr** out);
 int dpf_nr_free(dpf_nr* h);

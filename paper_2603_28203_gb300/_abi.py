@@ -57,7 +57,7 @@ class DpfSolveOpts(C.Structure):
 
 class DpfNrOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("flat_start", C.c_int32), ("lanes", C.c_int32)]
+                ("flat_start", C.c_int32), ("lanes", C.c_int32), ("fallback", C.c_int32)]
 
 
 VP = C.c_void_p

@@ -265,6 +265,7 @@ struct dpf_workspace {
   int32_t* dci = nullptr;    // DC solver, per case: active, iters ([2][Kp]), then its active count
   int32_t* h_dc_nact = nullptr;  // pinned
   int cap_tiles = 0;
+  int tiles = 0;  // case tiles of the scheduler (tile_cnt holds their counters first)
   // user-layout staging for host_io
   double *st_a = nullptr, *st_b = nullptr, *st_c = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -543,6 +544,8 @@ static Plan<R> make_plan(dpf_workspace* w) {
   s.iters = w->iters;
   s.status = w->status;
   s.loss_part = (const R*)w->loss_part;
+  s.grp_part = (R*)w->loss_part + (size_t)w->gy * w->Kp;
+  s.grp_cnt = w->tile_cnt + w->tiles;
   s.mx32 = gated ? w->mx32 : nullptr;
   s.cand = w->cand;
   s.gate = w->opts.gate;
@@ -860,14 +863,17 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
 // per-tile counters for the forward pass's scheduler.
 static int upload_windows(dpf_workspace* w, cudaStream_t s) {
   const int tiles = std::max(w->Kp / std::max(1, w->lanes), w->Kp / 64 + 1);
-  if (tiles > w->cap_tiles) {
+  const int groups = (w->gy + SCHED_GROUP - 1) / SCHED_GROUP;
+  const int cnts = tiles * (1 + groups);  // tile counters, then per (tile, group) counters
+  if (cnts > w->cap_tiles) {
     dfree(w->tile_cnt);
     w->cap_tiles = 0;
-    TRY(dalloc(&w->tile_cnt, tiles));
-    w->cap_tiles = tiles;
+    TRY(dalloc(&w->tile_cnt, cnts));
+    w->cap_tiles = cnts;
   }
+  w->tiles = tiles;
   CK(cudaMemsetAsync(w->tile_cnt, 0, (size_t)w->cap_tiles * sizeof(unsigned int), s));
-  const size_t part = (size_t)w->gy * w->Kp;
+  const size_t part = (size_t)(w->gy + groups) * w->Kp;  // row-block partials, then group sums
   if (part > w->cap_part) {
     dfree(w->loss_part);
     w->cap_part = 0;

@@ -411,12 +411,16 @@ __device__ __forceinline__ typename Prec<R>::C row_spmv(const YS& ys, int p0, in
 }
 
 // ---- scheduler (one case) -------------------------------------------------
+constexpr int SCHED_GROUP = 16;  // row blocks per group of the two-level loss sum
+
 template <class R> struct SchedArgs {
   int Kp;
   int32_t* active;
   int32_t* iters;
   int32_t* status;
   const R* loss_part;  // [row blocks][Kp] the forward pass's loss partials
+  R* grp_part;         // [groups][Kp] sums of SCHED_GROUP row blocks' partials (> 64 row blocks)
+  unsigned int* grp_cnt;  // [tiles][groups] CTAs of a group done (reset by the group's last)
   unsigned int* mx32;  // FP32 max mismatch of the forward pass (or NULL)
   int32_t* cand;       // 1: the next FP64 test examines the case
   double gate;         // FP32 max mismatch below which the FP64 test runs (<= 0: always)
@@ -508,7 +512,14 @@ __device__ __forceinline__ void sched_case(const SchedArgs<R>& a, int k, R lsum)
 // sched_case for the tile's cases and resets the tile counter.  Every thread
 // of the CTA must call it.
 template <class R>
+__device__ __forceinline__ void tile_sched_grouped(const SchedArgs<R>& a, unsigned int* tile_cnt, int tile);
+
+template <class R>
 __device__ __forceinline__ void tile_sched(const SchedArgs<R>& a, unsigned int* tile_cnt, int tile) {
+  if (gridDim.y > 64) {
+    tile_sched_grouped(a, tile_cnt, tile);
+    return;
+  }
   __shared__ int last;
   __threadfence();
   __syncthreads();
@@ -518,43 +529,72 @@ __device__ __forceinline__ void tile_sched(const SchedArgs<R>& a, unsigned int* 
     if (last) tile_cnt[blockIdx.x] = 0u;
   }
   __syncthreads();
-  if (last) {
-    __threadfence();
-    // Each case's loss: its row blocks' partials summed in a fixed order, so
-    // that a solve repeats bit for bit (an atomic sum's order varies between
-    // runs): one thread per case for a few row blocks; for many (a single
-    // case over ~1,000 row blocks) a group of tpc threads per case takes
-    // strided slices, then a fixed tree.  blockDim.x <= 256 (launch bounds).
-    if (gridDim.y <= 64) {
-      for (int c = threadIdx.x; c < tile; c += blockDim.x) {
-        const int k = blockIdx.x * tile + c;
-        if (k >= a.Kp) continue;
-        R s = R(0);
-        for (int yb = 0; yb < (int)gridDim.y; ++yb) s += __ldcg(a.loss_part + (size_t)yb * a.Kp + k);
-        sched_case(a, k, s);
-      }
-      return;
+  if (!last) return;
+  __threadfence();
+  // Each case's loss: its row blocks' partials summed in a fixed order, so
+  // that a solve repeats bit for bit (an atomic sum's order varies between
+  // runs); one thread per case.
+  for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+    const int k = blockIdx.x * tile + c;
+    if (k >= a.Kp) continue;
+    R s = R(0);
+    for (int yb = 0; yb < (int)gridDim.y; ++yb) s += __ldcg(a.loss_part + (size_t)yb * a.Kp + k);
+    sched_case(a, k, s);
+  }
+}
+
+// Many row blocks: two levels, each in a fixed order.  The last CTA of each
+// group of SCHED_GROUP row blocks sums its group's partials (the groups' sums
+// run in parallel in different CTAs); the last group of the case tile sums
+// the groups' sums and takes the per-case step.
+template <class R>
+__device__ __forceinline__ void tile_sched_grouped(const SchedArgs<R>& a, unsigned int* tile_cnt, int tile) {
+  __shared__ int lastg, last;
+  const int ng = ((int)gridDim.y + SCHED_GROUP - 1) / SCHED_GROUP, g = (int)blockIdx.y / SCHED_GROUP;
+  const int y0 = g * SCHED_GROUP, gsz = min(SCHED_GROUP, (int)gridDim.y - y0);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int* c = a.grp_cnt + (size_t)blockIdx.x * ng + g;
+    const unsigned prev = atomicAdd(c, 1u);
+    lastg = (prev == (unsigned)gsz - 1);
+    if (lastg) *c = 0u;
+  }
+  __syncthreads();
+  if (!lastg) return;
+  __threadfence();
+  for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+    const int k = blockIdx.x * tile + c;
+    if (k >= a.Kp) continue;
+    R v[SCHED_GROUP];
+#pragma unroll
+    for (int u = 0; u < SCHED_GROUP; ++u) v[u] = u < gsz ? __ldcg(a.loss_part + (size_t)(y0 + u) * a.Kp + k) : R(0);
+    R s = R(0);
+#pragma unroll
+    for (int u = 0; u < SCHED_GROUP; ++u) s += v[u];
+    a.grp_part[(size_t)g * a.Kp + k] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(tile_cnt + blockIdx.x, 1u);
+    last = (prev == (unsigned)ng - 1);
+    if (last) tile_cnt[blockIdx.x] = 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+    const int k = blockIdx.x * tile + c;
+    if (k >= a.Kp) continue;
+    R s8[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    int q = 0;
+    for (; q + 8 <= ng; q += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s8[u] += __ldcg(a.grp_part + (size_t)(q + u) * a.Kp + k);
     }
-    __shared__ R part[256];
-    int tpc = 1;  // threads per case: a power of two with tile * tpc <= blockDim.x
-    while (2 * tpc * tile <= (int)blockDim.x) tpc *= 2;
-    const int cases_per_pass = max(1, (int)blockDim.x / tpc);
-    for (int c0 = 0; c0 < tile; c0 += cases_per_pass) {
-      const int c = c0 + (int)threadIdx.x / tpc, j = (int)threadIdx.x % tpc;
-      const int k = blockIdx.x * tile + c;
-      const bool mine = (int)threadIdx.x < cases_per_pass * tpc && c < tile && k < a.Kp;
-      R s = R(0);
-      if (mine)
-        for (int yb = j; yb < (int)gridDim.y; yb += tpc) s += __ldcg(a.loss_part + (size_t)yb * a.Kp + k);
-      part[threadIdx.x] = s;
-      __syncthreads();
-      for (int step = tpc >> 1; step > 0; step >>= 1) {
-        if (j < step) part[threadIdx.x] += part[threadIdx.x + step];
-        __syncthreads();
-      }
-      if (mine && j == 0) sched_case(a, k, part[threadIdx.x]);
-      __syncthreads();
-    }
+    for (; q < ng; ++q) s8[0] += __ldcg(a.grp_part + (size_t)q * a.Kp + k);
+    sched_case(a, k, ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7])));
   }
 }
 

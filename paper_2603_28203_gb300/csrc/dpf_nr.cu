@@ -169,6 +169,9 @@ struct NrArgs {
   int32_t* n_active;
   double* pmax;  // [NR_CHUNKS][Kp] partials of the stop test
   double* psum;
+  double* maxmis0;  // per case: max |f| and loss of the start
+  double* loss0;
+  int first;        // this evaluation is of the start
 };
 
 // Per case: outage data (pi-model block of the removed branch), state flags.
@@ -323,6 +326,10 @@ __global__ void k_nr_check(NrArgs a) {
   if (nan) mx = __longlong_as_double(0x7ff8000000000000LL);
   a.maxmis[k] = mx;
   a.loss[k] = sm * a.inv_m;
+  if (a.first) {
+    a.maxmis0[k] = mx;
+    a.loss0[k] = sm * a.inv_m;
+  }
   if (a.bad[k] || nan || isinf(mx)) {
     a.status[k] = DPF_CASE_DIVERGED;
     a.active[k] = 0;
@@ -605,25 +612,29 @@ __global__ void k_nr_update(NrArgs a) {
   }
 }
 
-// Solution and per-case results to the caller's arrays (case-major, user bus order).
-__global__ void k_nr_out(NrArgs a, double* __restrict__ va, double* __restrict__ vm) {
+// Solution and per-case results to the caller's arrays (case-major, user bus
+// order).  With `fallback`, a case that did not converge keeps the start the
+// caller passed in va/vm, and its start's max |f| and loss are reported.
+__global__ void k_nr_out(NrArgs a, double* __restrict__ va, double* __restrict__ vm, int fallback) {
   const size_t n = (size_t)a.N * a.Kp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / a.Kp), k = (int)(e % a.Kp);
-    if (k >= a.K) continue;
+    if (k >= a.K || (fallback && a.status[k] != DPF_CASE_CONVERGED)) continue;
     const size_t u = (size_t)k * a.N + __ldg(a.perm + i);
     va[u] = a.th[e];
     vm[u] = a.vm[e];
   }
 }
 
-__global__ void k_nr_case_out(NrArgs a, int32_t* iters, int32_t* status, double* maxmis, double* loss) {
+__global__ void k_nr_case_out(NrArgs a, int32_t* iters, int32_t* status, double* maxmis, double* loss,
+                              int fallback) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.K) return;
+  const bool keep = fallback && a.status[k] != DPF_CASE_CONVERGED;
   if (iters) iters[k] = a.iters[k];
   if (status) status[k] = a.status[k];
-  if (maxmis) maxmis[k] = a.maxmis[k];
-  if (loss) loss[k] = a.loss[k];
+  if (maxmis) maxmis[k] = keep ? a.maxmis0[k] : a.maxmis[k];
+  if (loss) loss[k] = keep ? a.loss0[k] : a.loss[k];
 }
 
 template <class T>
@@ -682,7 +693,8 @@ struct dpf_nr {
   int32_t *of = nullptr, *ot = nullptr, *active = nullptr, *status = nullptr, *iters = nullptr, *bad = nullptr,
           *n_active = nullptr;
   double2 *yff = nullptr, *yft = nullptr, *ytt = nullptr;
-  double *maxmis = nullptr, *loss = nullptr, *pmax = nullptr, *psum = nullptr;
+  double *maxmis = nullptr, *loss = nullptr, *pmax = nullptr, *psum = nullptr, *maxmis0 = nullptr,
+         *loss0 = nullptr;
   int32_t* h_nact = nullptr;  // pinned
 };
 
@@ -692,7 +704,7 @@ static void nr_release(dpf_nr* h) {
   dfree(h->th); dfree(h->vm); dfree(h->Ps); dfree(h->Qs); dfree(h->V); dfree(h->U); dfree(h->I); dfree(h->X);
   dfree(h->F); dfree(h->Dinv);
   dfree(h->of); dfree(h->ot); dfree(h->active); dfree(h->status); dfree(h->iters); dfree(h->bad);
-  dfree(h->n_active); dfree(h->yff); dfree(h->yft); dfree(h->ytt); dfree(h->maxmis); dfree(h->loss); dfree(h->pmax); dfree(h->psum);
+  dfree(h->n_active); dfree(h->yff); dfree(h->yft); dfree(h->ytt); dfree(h->maxmis); dfree(h->loss); dfree(h->pmax); dfree(h->psum); dfree(h->maxmis0); dfree(h->loss0);
   if (h->h_nact) cudaFreeHost(h->h_nact);
   h->h_nact = nullptr;
 }
@@ -727,6 +739,7 @@ static int nr_setup(dpf_nr* h) {
   TRY(dalloc(&h->yff, Kp)); TRY(dalloc(&h->yft, Kp)); TRY(dalloc(&h->ytt, Kp));
   TRY(dalloc(&h->maxmis, Kp)); TRY(dalloc(&h->loss, Kp));
   TRY(dalloc(&h->pmax, (size_t)NR_CHUNKS * Kp)); TRY(dalloc(&h->psum, (size_t)NR_CHUNKS * Kp));
+  TRY(dalloc(&h->maxmis0, Kp)); TRY(dalloc(&h->loss0, Kp));
   CK(cudaMallocHost((void**)&h->h_nact, sizeof(int32_t)));
   return DPF_OK;
 }
@@ -803,6 +816,7 @@ extern "C" void dpf_nr_default_opts(dpf_nr_opts* o) {
   o->max_iter = 20;
   o->flat_start = 1;
   o->lanes = 0;
+  o->fallback = 0;
 }
 
 extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o, void* stream) {
@@ -909,6 +923,8 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
   a.n_active = h->n_active;
   a.pmax = h->pmax;
   a.psum = h->psum;
+  a.maxmis0 = h->maxmis0;
+  a.loss0 = h->loss0;
   const size_t E = (size_t)a.N * a.Kp;
   const int cb = (a.Kp + 255) / 256;
   k_nr_init<<<cb, 256, 0, s>>>(a, b->outage, d.br_f, d.br_t, d.br_r, d.br_x, d.br_bch, d.br_tap);
@@ -920,6 +936,7 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
     k_nr_eval<<<grid_for(E), 256, 0, s>>>(a);
     CK(cudaMemsetAsync(a.n_active, 0, 4, s));
     k_nr_partial<<<dim3(a.Kp / 32, NR_CHUNKS), 256, 0, s>>>(a);
+    a.first = it == 0;
     k_nr_check<<<cb, 256, 0, s>>>(a);
     CKLAUNCH();
     h->launches += 4;
@@ -936,8 +953,9 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
     CKLAUNCH();
     h->launches += 1;
   }
-  k_nr_out<<<grid_for(E), 256, 0, s>>>(a, b->va, b->vm);
-  k_nr_case_out<<<cb, 256, 0, s>>>(a, b->iters, b->status, b->max_mismatch, b->loss);
+  const int fb = o->fallback && !flat_start;
+  k_nr_out<<<grid_for(E), 256, 0, s>>>(a, b->va, b->vm, fb);
+  k_nr_case_out<<<cb, 256, 0, s>>>(a, b->iters, b->status, b->max_mismatch, b->loss, fb);
   CKLAUNCH();
   h->launches += 2;
   return DPF_OK;

@@ -409,13 +409,14 @@ def dpf_nr_create(y: Ybus, max_case: int) -> NewtonSolver:
 
 
 def dpf_nr_solve(nr: NewtonSolver, precision=_abi.FP64, tol: float = 1e-10, max_iter: int = 20, flat_start=True,
-                 lanes: int = 0, stream=None, **batch):
-    """Newton-Raphson for every case; `batch` holds the dpf_batch fields as CUDA tensors (va, vm required)."""
+                 lanes: int = 0, fallback=False, stream=None, **batch):
+    """Newton-Raphson for every case; `batch` holds the dpf_batch fields as CUDA tensors (va, vm required).
+    fallback (with flat_start False): unconverged cases keep their start."""
     b = _batch_struct(**batch)
     o = _abi.DpfNrOpts()
     lib().dpf_nr_default_opts(C.byref(o))
     o.precision, o.tol, o.max_iter = int(precision), float(tol), int(max_iter)
-    o.flat_start, o.lanes = (1 if flat_start else 0), int(lanes)
+    o.flat_start, o.lanes, o.fallback = (1 if flat_start else 0), int(lanes), (1 if fallback else 0)
     _check(lib().dpf_nr_solve(nr.handle, C.byref(b), C.byref(o), _stream(stream)))
 
 

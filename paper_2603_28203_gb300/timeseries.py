@@ -9,13 +9,20 @@ day for a 96-hour window), with the t > 0 settings (Adam lr 0.00027, betas
 (0.7847, 0.6624), ReduceLROnPlateau 0.8 / 2 / 0.0388 / 4, <= 300 iterations).
 The solutions stay on the device between windows; only the window's
 injections are copied in.  All arithmetic runs in the library's kernels.
+
+With `first_newton`, the first window's Alg. 1 solutions are handed to
+Newton-Raphson on the GPU (dpf_nr_solve, FP32 factor, to 1e-10 p.u.) as
+start and fallback: a snapshot Newton solves leaves the window exact, one it
+cannot keeps Alg. 1's state.  (The caption of Fig. 4 notes the first full fit
+could be replaced by Newton-Raphson; Sec. 6 names gradient methods as the
+initialisers of Newton solves.)
 """
 from __future__ import annotations
 
 import numpy as np
 
 from . import _abi
-from .dpf import SolveOpts, Workspace, Ybus, dpf_solve_batch
+from .dpf import NewtonSolver, SolveOpts, Workspace, Ybus, dpf_nr_solve, dpf_solve_batch
 
 TABLE3_T0 = dict(lr=0.03564, beta1=0.9802, beta2=0.9440, sched=_abi.SCHED_STEP, step_size=100, gamma=0.773,
                  max_iter=1000)
@@ -24,10 +31,14 @@ TABLE3_T1 = dict(lr=0.00027, beta1=0.7847, beta2=0.6624, sched=_abi.SCHED_PLATEA
 
 
 def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 96, precision=_abi.FP32,
-                      first=None, later=None, check_every: int = 25, tol: float = 1e-6, stream=None):
+                      first=None, later=None, check_every: int = 25, tol: float = 1e-6, stream=None,
+                      first_newton: NewtonSolver | None = None):
     """Solve T snapshots ([T][N] injections, numpy or torch); returns numpy arrays.
 
     `first` / `later` override the Table 3 settings (dicts of SolveOpts fields).
+    `first_newton`: a NewtonSolver for `window` cases of this Y_bus; the first
+    window's Alg. 1 solutions then go through Newton-Raphson (start and
+    fallback; its `iters` and `status` are then Newton's).
     """
     import torch
 
@@ -56,6 +67,10 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
                          **settings)
         dpf_solve_batch(y, ws, opts, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
                         **{k: v[:K] for k, v in res.items()})
+        if w0 == 0 and first_newton is not None:
+            dpf_nr_solve(first_newton, precision=_abi.FP32, tol=1e-10, max_iter=20, flat_start=False,
+                         fallback=True, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
+                         **{k: v[:K] for k, v in res.items()})
         out["va"][w0:w0 + K] = va[:K].cpu().numpy()
         out["vm"][w0:w0 + K] = vm[:K].cpu().numpy()
         for k, v in res.items():

@@ -39,7 +39,8 @@ def _t(a, dtype=torch.float64):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
 
 
-def _nr(y, nr, K, precision=dpf.FP64, tol=TOL, max_iter=20, flat=True, va=None, vm=None, lanes=0, **kw):
+def _nr(y, nr, K, precision=dpf.FP64, tol=TOL, max_iter=20, flat=True, va=None, vm=None, lanes=0, fallback=False,
+        **kw):
     N = y.n_bus
     out = dict(va=_t(va) if va is not None else torch.zeros((K, N), dtype=torch.float64, device=DEV),
                vm=_t(vm) if vm is not None else torch.ones((K, N), dtype=torch.float64, device=DEV),
@@ -47,8 +48,8 @@ def _nr(y, nr, K, precision=dpf.FP64, tol=TOL, max_iter=20, flat=True, va=None, 
                status=torch.empty(K, dtype=torch.int32, device=DEV),
                max_mismatch=torch.empty(K, dtype=torch.float64, device=DEV),
                loss=torch.empty(K, dtype=torch.float64, device=DEV))
-    dpf.dpf_nr_solve(nr, precision=precision, tol=tol, max_iter=max_iter, flat_start=flat, lanes=lanes, n_case=K,
-                     **out, **kw)
+    dpf.dpf_nr_solve(nr, precision=precision, tol=tol, max_iter=max_iter, flat_start=flat, lanes=lanes,
+                     fallback=fallback, n_case=K, **out, **kw)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 
@@ -250,3 +251,31 @@ def test_single_case_on_the_10k_bus_grid():
     assert r["status"][0] == dpf.CASE_CONVERGED and r["iters"][0] == ref["iters"]
     assert np.abs(r["va"][0] - ref["va"]).max() <= 1e-9
     assert np.abs(r["vm"][0] - ref["vm"]).max() <= 1e-9
+
+
+def test_fallback_keeps_the_start_where_newton_fails():
+    """fallback (warm start): a case Newton cannot solve (8x load) comes back
+    as the start that was passed in, with the start's FP64 mismatch; the
+    other cases come back as without fallback."""
+    g = gridgen.config_grid("c3_n1_2kbus")
+    Y = grid_ybus(g)
+    K = 3
+    sc = np.array([1.0, 8.0, 1.02])[:, None]
+    P, Q = g.p_spec[None, :] * sc, g.q_spec[None, :] * sc
+    fva, fvm = oracle.flat_start(g.bus_type, g.vm_set, g.va_slack)
+    rng = np.random.default_rng(4)
+    va0 = np.tile(fva, (K, 1)) + 0.01 * rng.standard_normal((K, g.n_bus)) * (g.bus_type != dpf.SLACK)
+    vm0 = np.tile(fvm, (K, 1))
+    y = dpf.dpf_build_ybus(g)
+    nr = dpf.dpf_nr_create(y, K)
+    plain = _nr(y, nr, K, flat=False, va=va0, vm=vm0, p_spec=_t(P), q_spec=_t(Q))
+    fb = _nr(y, nr, K, flat=False, va=va0, vm=vm0, p_spec=_t(P), q_spec=_t(Q), fallback=True)
+    assert plain["status"][1] != dpf.CASE_CONVERGED and fb["status"][1] == plain["status"][1]
+    np.testing.assert_array_equal(fb["va"][1], va0[1])
+    np.testing.assert_array_equal(fb["vm"][1], vm0[1])
+    f, _ = oracle.mismatch(Y, va0[1], vm0[1], P[1], Q[1], g.bus_type)
+    assert abs(np.abs(f).max() - fb["max_mismatch"][1]) <= 1e-12 * np.abs(f).max()
+    for k in (0, 2):
+        assert fb["status"][k] == dpf.CASE_CONVERGED
+        for key in fb:
+            np.testing.assert_array_equal(fb[key][k], plain[key][k])
