@@ -1179,6 +1179,7 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
 extern "C" int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* p_spec,
                             const int32_t* outage, double tol, int32_t max_iter, double* va, int32_t* iters,
                             double* rel_residual, void* stream) {
+  dpf::Range nvtx_range("dpf_dc_solve");
   clear_error();
   cudaStream_t s = (cudaStream_t)stream;
   TRY(common_checks(y, w, n_case));
@@ -1215,6 +1216,7 @@ extern "C" int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* w, int32_t n_case,
 // ---------------------------------------------------------------------------
 extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b,
                                const dpf_solve_opts* o, void* stream) {
+  dpf::Range nvtx_range("dpf_solve_begin");
   clear_error();
   if (!b || !o) return fail(DPF_E_INVALID, "dpf_solve_begin: NULL argument");
   TRY(common_checks(y, w, b->n_case));
@@ -1265,6 +1267,7 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
 }
 
 extern "C" int dpf_solve_iterate(dpf_workspace* w, int32_t n_iter, void* stream) {
+  dpf::Range nvtx_range("dpf_solve_iterate");
   clear_error();
   if (!w || !w->begun) return fail(DPF_E_STATE, "dpf_solve_iterate before dpf_solve_begin");
   if (n_iter < 0) return fail(DPF_E_INVALID, "n_iter must be >= 0");
@@ -1340,6 +1343,7 @@ extern "C" int dpf_iterations_done(const dpf_workspace* w, int32_t* n_iter) {
 }
 
 extern "C" int dpf_solve_end(dpf_workspace* w, const dpf_batch* b, void* stream) {
+  dpf::Range nvtx_range("dpf_solve_end");
   clear_error();
   if (!w || !w->begun) return fail(DPF_E_STATE, "dpf_solve_end before dpf_solve_begin");
   if (!b || b->n_case != w->K) return fail(DPF_E_INVALID, "dpf_solve_end: batch differs from dpf_solve_begin");
@@ -1436,6 +1440,7 @@ static int solve_plain(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b, 
 
 extern "C" int dpf_solve_batch(const dpf_ybus* y, dpf_workspace* ws, const dpf_batch* b,
                                const dpf_solve_opts* o, void* stream) {
+  dpf::Range nvtx_range("dpf_solve_batch");
   clear_error();
   if (!y || !b || !o) return fail(DPF_E_INVALID, "dpf_solve_batch: NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1487,6 +1492,7 @@ extern "C" int dpf_adam_update(int32_t n, double* x, const double* grad, double*
 // ---------------------------------------------------------------------------
 extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b, dpf_solve_opts* o,
                             int32_t iters, void* stream) {
+  dpf::Range nvtx_range("dpf_autotune");
   clear_error();
   if (!y || !w || !b || !o) return fail(DPF_E_INVALID, "dpf_autotune: NULL argument");
   if (iters < 1) return fail(DPF_E_INVALID, "iters must be >= 1");
@@ -1621,6 +1627,7 @@ static int power_impl(dpf_workspace* w, double* p_calc, double* q_calc, cudaStre
 extern "C" int dpf_power(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* va,
                          const double* vm, const int32_t* outage, int32_t precision, double* p_calc,
                          double* q_calc, void* stream) {
+  dpf::Range nvtx_range("dpf_power");
   clear_error();
   cudaStream_t s = (cudaStream_t)stream;
   TRY(eval_setup(y, w, n_case, precision, va, vm, nullptr, nullptr, outage, s));
@@ -1732,6 +1739,7 @@ extern "C" int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* w, int32_t n_
                                  const int32_t* outage, const double* g_series, const double* b_series,
                                  int32_t precision, double* loss, double* d_va, double* d_vm, double* d_p,
                                  double* d_q, double* d_g, double* d_b, double* d_bch, void* stream) {
+  dpf::Range nvtx_range("dpf_loss_backward");
   clear_error();
   cudaStream_t s = (cudaStream_t)stream;
   if ((g_series == nullptr) != (b_series == nullptr))
@@ -1755,6 +1763,7 @@ extern "C" int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* w, int32_t n_
 extern "C" int dpf_paramid_begin(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* va,
                                  const double* vm, const double* p_spec, const double* q_spec, int32_t precision,
                                  void* stream) {
+  dpf::Range nvtx_range("dpf_paramid_begin");
   clear_error();
   cudaStream_t s = (cudaStream_t)stream;
   TRY(eval_setup(y, w, n_case, precision, va, vm, p_spec, q_spec, nullptr, s));
@@ -1784,6 +1793,7 @@ static int paramid_impl(dpf_workspace* w, double* d_g, double* d_b, double* d_bc
 extern "C" int dpf_paramid_step(const dpf_ybus* y, dpf_workspace* w, const double* g_series,
                                 const double* b_series, double* d_g, double* d_b, double* d_bch, double* loss,
                                 void* stream) {
+  dpf::Range nvtx_range("dpf_paramid_step");
   clear_error();
   if (!y || !w) return fail(DPF_E_INVALID, "dpf_paramid_step: NULL handle");
   if (w->y != y) return fail(DPF_E_INVALID, "workspace was created for another Y_bus");

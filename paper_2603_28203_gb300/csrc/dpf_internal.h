@@ -1,6 +1,7 @@
 // Internal definitions shared by the host-only and the CUDA parts of libdpf.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>  // header-only NVTX (ranges are no-ops without an attached tool)
 #include <stdint.h>
 #include <vector_types.h>  // int4, double2 (CUDA headers; no CUDA calls here)
 
@@ -10,6 +11,15 @@
 #include "dpf.h"
 
 namespace dpf {
+
+// A named NVTX range over a scope: the phases of the library's calls appear
+// on Nsight timelines (and can filter ncu captures with --nvtx-include).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Record a failure for dpf_last_error() and return `code`.
 int fail(int code, const char* fmt, ...);

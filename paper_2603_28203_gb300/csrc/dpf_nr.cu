@@ -745,6 +745,7 @@ static int nr_setup(dpf_nr* h) {
 }
 
 extern "C" int dpf_nr_create(const dpf_ybus* y, int32_t max_case, dpf_nr** out) {
+  dpf::Range nvtx_range("dpf_nr_create");
   clear_error();
   if (!y || !out || max_case <= 0) return fail(DPF_E_INVALID, "dpf_nr_create: NULL argument or max_case <= 0");
   *out = nullptr;
@@ -820,6 +821,7 @@ extern "C" void dpf_nr_default_opts(dpf_nr_opts* o) {
 }
 
 extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o, void* stream) {
+  dpf::Range nvtx_range("dpf_nr_solve");
   clear_error();
   if (!h || !b || !o) return fail(DPF_E_INVALID, "dpf_nr_solve: NULL argument");
   const int precision = o->precision, max_iter = o->max_iter, flat_start = o->flat_start;

@@ -16,8 +16,16 @@ start and fallback: a snapshot Newton solves leaves the window exact, one it
 cannot keeps Alg. 1's state.  (The caption of Fig. 4 notes the first full fit
 could be replaced by Newton-Raphson; Sec. 6 names gradient methods as the
 initialisers of Newton solves.)
+
+With `checkpoint` (a directory), every solved window is saved as
+window_<first snapshot>.npz (its solutions, iterations, statuses, mismatches
+and losses); with `resume`, saved windows are loaded instead of solved, and
+the last loaded window's solutions warm-start the next one, so an
+interrupted series continues where it stopped.
 """
 from __future__ import annotations
+
+import os
 
 import numpy as np
 
@@ -32,13 +40,15 @@ TABLE3_T1 = dict(lr=0.00027, beta1=0.7847, beta2=0.6624, sched=_abi.SCHED_PLATEA
 
 def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 96, precision=_abi.FP32,
                       first=None, later=None, check_every: int = 25, tol: float = 1e-6, stream=None,
-                      first_newton: NewtonSolver | None = None):
+                      first_newton: NewtonSolver | None = None, checkpoint: str | None = None,
+                      resume: bool = False):
     """Solve T snapshots ([T][N] injections, numpy or torch); returns numpy arrays.
 
     `first` / `later` override the Table 3 settings (dicts of SolveOpts fields).
     `first_newton`: a NewtonSolver for `window` cases of this Y_bus; the first
     window's Alg. 1 solutions then go through Newton-Raphson (start and
     fallback; its `iters` and `status` are then Newton's).
+    `checkpoint` / `resume`: per-window save and restart (module docstring).
     """
     import torch
 
@@ -57,8 +67,20 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
                status=torch.zeros(window, dtype=torch.int32, device=dev),
                max_mismatch=torch.zeros(window, dtype=torch.float64, device=dev),
                loss=torch.zeros(window, dtype=torch.float64, device=dev))
+    if checkpoint:
+        os.makedirs(checkpoint, exist_ok=True)
     for w0 in range(0, T, window):
         K = min(window, T - w0)
+        path = os.path.join(checkpoint, f"window_{w0:06d}.npz") if checkpoint else None
+        if resume and path and os.path.exists(path):
+            with np.load(path) as z:
+                if z["va"].shape != (K, N):
+                    raise ValueError(f"{path}: saved window has shape {z['va'].shape}, expected {(K, N)}")
+                for k in out:
+                    out[k][w0:w0 + K] = z[k]
+            va[:K] = torch.as_tensor(out["va"][w0:w0 + K], device=dev)
+            vm[:K] = torch.as_tensor(out["vm"][w0:w0 + K], device=dev)
+            continue
         p = P[w0:w0 + K].to(dev).contiguous()
         q = Q[w0:w0 + K].to(dev).contiguous()
         settings = dict(TABLE3_T0 if w0 == 0 else TABLE3_T1)
@@ -75,4 +97,8 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
         out["vm"][w0:w0 + K] = vm[:K].cpu().numpy()
         for k, v in res.items():
             out[k][w0:w0 + K] = v[:K].cpu().numpy()
+        if path:
+            tmp = path + ".tmp.npz"
+            np.savez(tmp, **{k: out[k][w0:w0 + K] for k in out})
+            os.replace(tmp, path)  # a window file is complete or absent
     return out

@@ -139,6 +139,34 @@ def test_c4_time_series_fp32_close_to_fp64():
     assert np.abs(a["max_mismatch"] - b["max_mismatch"]).max() <= 0.05 * a["max_mismatch"].max()
 
 
+def test_time_series_resumes_from_its_checkpoints(tmp_path):
+    """An interrupted series (the first two windows saved) resumed to the end
+    equals the uninterrupted series bit for bit: saved windows are loaded,
+    the last one warm-starts the next (solves are deterministic).  The
+    reported FP64 loss of the final evaluation is summed by atomics, so it
+    is compared to rounding (1e-12 relative)."""
+    g = gridgen.make_grid(300, 3, load_scale=0.1)
+    T, window = 24, 8
+    P, Q = gridgen.time_series(g, T, seed=4)
+    first, later = dict(max_iter=200), dict(max_iter=50)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, window)
+    full = solve_time_series(y, ws, P, Q, window=window, first=first, later=later)
+    ck = str(tmp_path / "ck")
+    part = solve_time_series(y, ws, P[:16], Q[:16], window=window, first=first, later=later, checkpoint=ck)
+    def same(a, b):
+        for key in b:
+            if key == "loss":
+                np.testing.assert_allclose(a[key], b[key], rtol=1e-12, atol=0)
+            else:
+                np.testing.assert_array_equal(a[key], b[key])
+    same(part, {k: v[:16] for k, v in full.items()})
+    rest = solve_time_series(y, ws, P, Q, window=window, first=first, later=later, checkpoint=ck, resume=True)
+    same(rest, full)
+    import os
+    assert sorted(os.listdir(ck)) == ["window_000000.npz", "window_000008.npz", "window_000016.npz"]
+
+
 def test_c3_full_batch_in_the_benchmark_shape():
     """The whole N-1 batch (2,000 buses, every non-bridge outage) in the launch
     shape the autotuner picks (what bench.py times), FP32, 50 iterations.
