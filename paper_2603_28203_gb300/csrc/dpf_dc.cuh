@@ -214,12 +214,24 @@ __global__ void __launch_bounds__(256) k_dc_update_case(DCArgs a) {
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
   const int k = mp.k;
   const size_t Kp = (size_t)a.Kp;
+  // alpha = rz / pq once per case of the tile (an FP64 divide is dear here),
+  // shared with the CTA's other threads of that case
+  __shared__ double s_alpha[32];
+  if ((int)threadIdx.x < a.lanes) {
+    const int kk = blockIdx.x * a.lanes + threadIdx.x;
+    double al = 0.0;
+    if (kk < a.Kp) {
+      const double pq = __ldcg(a.pq + kk);
+      al = pq != 0.0 ? __ldcg(a.rz + kk) / pq : 0.0;
+    }
+    s_alpha[threadIdx.x] = al;
+  }
+  __syncthreads();
   double rz = 0.0, rr = 0.0;
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
     const double ob = a.ob[k];
-    const double pq = __ldcg(a.pq + k);
-    const double alpha = pq != 0.0 ? __ldcg(a.rz + k) / pq : 0.0;
+    const double alpha = s_alpha[mp.kl];
     for (int i = mp.i0; i < mp.r1; i += mp.istride) {
       if (__ldg(a.type + i) == BUS_SLACK) continue;
       const size_t e = (size_t)i * Kp + k;
