@@ -160,10 +160,19 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
       dcval[p] = -bdc[l];
       dcval[y->idpos[i]] += bdc[l];
     }
-  std::vector<double> dcinv(n);
+  // as double-float pairs (hi, lo) for the DC solver
+  auto pair = [](double v) {
+    const float hi = (float)v;
+    float2 r;
+    r.x = hi;
+    r.y = (float)(v - (double)hi);
+    return r;
+  };
+  std::vector<float2> dcval2(nnz), dcinv2(n);
+  for (int p = 0; p < nnz; ++p) dcval2[p] = pair(dcval[p]);
   for (int i = 0; i < n; ++i) {
     const double dii = dcval[y->idpos[i]];
-    dcinv[i] = dii != 0.0 ? 1.0 / dii : 0.0;
+    dcinv2[i] = pair(dii != 0.0 ? 1.0 / dii : 0.0);
   }
   int rc = DPF_OK;
   do {
@@ -173,8 +182,8 @@ extern "C" int dpf_ybus_upload(dpf_ybus* y, void* stream) {
     if ((rc = upload(&d.ppos, y->ippos, s))) break;
     if ((rc = upload(&d.col, y->icol, s))) break;
     if ((rc = upload(&d.val64, v64, s))) break;
-    if ((rc = upload(&d.dcval, dcval, s))) break;
-    if ((rc = upload(&d.dcinv, dcinv, s))) break;
+    if ((rc = upload(&d.dcval, dcval2, s))) break;
+    if ((rc = upload(&d.dcinv, dcinv2, s))) break;
     if ((rc = upload(&d.ebr, y->iebr, s))) break;
     if ((rc = upload(&d.dpos, y->idpos, s))) break;
     if ((rc = upload(&d.type, type, s))) break;
@@ -1131,13 +1140,14 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   a.va_slack = y->va_slack;
   a.of = w->has_outage ? w->of : nullptr;
   a.ot = w->has_outage ? w->ot : nullptr;
-  a.x = w->tmp_a;
-  a.r = w->tmp_b;
-  a.z = w->tmp_c;
+  // double-float vectors (8 bytes per element, as the FP64 buffers they use)
+  a.x = (float2*)w->tmp_a;
+  a.r = (float2*)w->tmp_b;
+  a.z = (float2*)w->tmp_c;
   const size_t E0 = (size_t)y->n * Kp;
-  a.p = (double*)w->V64;            // the two direction buffers share V64's 16 B/element
-  a.p_new = (double*)w->V64 + E0;
-  a.q = (double*)w->sbuf;
+  a.p = (float2*)w->V64;            // the two direction buffers share V64's 16 B/element
+  a.p_new = (float2*)w->V64 + E0;
+  a.q = (float2*)w->sbuf;
   a.rpb = w->rpb;
   a.tile_cnt = w->tile_cnt;
   double* c = w->dcs;
@@ -1173,6 +1183,8 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
       if (*w->h_dc_nact == 0) break;
     }
   }
+  k_dc_widen<<<std::max(nb, 1), 256, 0, s>>>(a.x, E);  // the FP64 solution, in place
+  CKLAUNCH();
   return DPF_OK;
 }
 

@@ -8,9 +8,9 @@
 // Y_bus.  An outaged branch is the rank-one correction
 // B' = B - b_l (e_f - e_t)(e_f - e_t)^T of the shared B, as for the N-1 Y_bus.
 //
-// Solver: conjugate gradients with the Jacobi preconditioner, in FP64, all
-// cases at once in the case-minor layout (element (i, k) at i*Kp + k), each
-// CTA on a contiguous block of rows.  One iteration is two launches:
+// Solver: conjugate gradients with the Jacobi preconditioner, all cases at
+// once in the case-minor layout (element (i, k) at i*Kp + k), each CTA on a
+// contiguous block of rows.  One iteration is two launches:
 //   k_dc_spmv_dir     the new direction p' = z + beta p and q' = B' p', formed
 //                     as B' z + beta q from the previous q = B' p (so no CTA
 //                     waits for another's p' and p is never gathered), and the
@@ -19,25 +19,71 @@
 //                     z = r / diag(B'); partial sums of r.z and r.r; the last
 //                     CTA of each case tile then takes the per-case step:
 //                     stop when |r| <= tol |r0|, else beta = rz' / rz
-// The recurrence for q' is the same arithmetic as B' p' up to rounding.  On
-// this GPU the loop is bound by FP64 issue (a few FP64 FMA per clock per SM),
-// so the Jacobi step multiplies by the inverse diagonal uploaded with B rather
-// than dividing, except at the two rows an outage changes.  The two direction
-// buffers alternate.  Slack rows are not unknowns: their
-// r, z, p stay 0 and their x holds the slack angle.
+// The recurrence for q' is the same arithmetic as B' p' up to rounding.  The
+// two direction buffers alternate.  Slack rows are not unknowns: their r, z,
+// p stay 0 and their x holds the slack angle.
+//
+// Precision.  GB300 issues FP64 at a small fraction of its FP32 rate, and in
+// FP64 this loop kept the FP64 pipe 73-86% busy.  So the vectors are double-float:
+// an unevaluated sum hi + lo of two floats (about 48 significant bits, far
+// below the 1e-10 residual the solver is asked for), in the same 8 bytes as a
+// double, with per-element arithmetic built from the error-free
+// transformations of Knuth (two-sum) and Dekker (two-product, here with an
+// FMA), as in the double-double arithmetic of Hida, Li and Bailey.  B and
+// 1 / B_ii are uploaded as hi/lo pairs; the per-case scalars (alpha, beta, the
+// dot products' totals, the stop test) stay FP64.  x is widened to FP64 in
+// place at the end.
 #pragma once
 
 #include "dpf_kernels.cuh"
 
 namespace dpf {
 
+// ---- double-float arithmetic (float2: x = hi, y = lo, |lo| <= ulp(hi) / 2) --
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 df_quick(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// a + b with one two-sum of the high words and the low words added plainly:
+// its error is about 2^-48 of |a| + |b| (not of the result), ample for a
+// residual asked to fall to 1e-10 of the initial one
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float2 s = df_two_sum(a.x, b.x);
+  return df_quick(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) { return df_add(df_mul(a, b), c); }
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_from(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ double df_val(float2 a) { return (double)a.x + (double)a.y; }
+// a / b: the quotient of the high words refined by one correction step
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {
+  const float q0 = __fdiv_rn(a.x, b.x);
+  const float2 r = df_add(a, df_neg(df_mul(make_float2(q0, 0.f), b)));
+  return df_quick(q0, __fdiv_rn(r.x, b.x));
+}
+
 struct DCArgs {
   int N, Kp, lanes, K;
   const int32_t* __restrict__ rp;
   const int32_t* __restrict__ col;
-  const double* __restrict__ bval;  // B values in CSR order
+  const float2* __restrict__ bval;   // B values in CSR order (hi, lo)
   const int32_t* __restrict__ dpos;  // position of each row's diagonal entry
-  const double* __restrict__ dinv;  // [N] 1 / B_ii
+  const float2* __restrict__ dinv;   // [N] 1 / B_ii (hi, lo)
   const uint8_t* __restrict__ type;
   const double* pspec;  // [N][Kp] per case or [N]
   int spec_per_case;
@@ -45,12 +91,12 @@ struct DCArgs {
   const int32_t* of;  // per case: internal from/to bus of the outaged branch (-1: none)
   const int32_t* ot;
   double* ob;         // per case: its susceptance b_l
-  double* x;
-  double* r;
-  double* z;
-  double* p;       // direction of the previous iteration
-  double* p_new;   // direction of this iteration
-  double* q;       // B' p of the previous iteration, then of this one
+  float2* x;       // double-float vectors [N][Kp]
+  float2* r;
+  float2* z;
+  float2* p;       // direction of the previous iteration
+  float2* p_new;   // direction of this iteration
+  float2* q;       // B' p of the previous iteration, then of this one
   int rpb;                  // rows per CTA
   unsigned int* tile_cnt;   // per case tile: CTAs done with the update (reset by the last)
   // per case
@@ -95,25 +141,24 @@ __device__ __forceinline__ void case_sum2_atomic(double a, double b, int lanes, 
   }
 }
 
-// (B' v)_i for case k (v in the case-minor layout).
-__device__ __forceinline__ double dc_row(const DCArgs& a, const double* __restrict__ v, int i, int k, size_t Kp,
-                                         int of, int ot, double ob) {
-  double s = 0.0;
+// (B' v)_i for case k (v in the case-minor layout); ob2 = the outaged
+// branch's b_l as a double-float.
+__device__ __forceinline__ float2 dc_row(const DCArgs& a, const float2* __restrict__ v, int i, int k, size_t Kp,
+                                         int of, int ot, float2 ob2) {
+  float2 s = make_float2(0.f, 0.f);
   const int p1 = __ldg(a.rp + i + 1);
-  for (int p = __ldg(a.rp + i); p < p1; ++p) s = fma(__ldg(a.bval + p), v[(size_t)__ldg(a.col + p) * Kp + k], s);
-  if (i == of) s -= ob * (v[(size_t)of * Kp + k] - v[(size_t)ot * Kp + k]);
-  else if (i == ot) s -= ob * (v[(size_t)ot * Kp + k] - v[(size_t)of * Kp + k]);
+  for (int p = __ldg(a.rp + i); p < p1; ++p) s = df_fma(__ldg(a.bval + p), v[(size_t)__ldg(a.col + p) * Kp + k], s);
+  if (i == of || i == ot) {
+    const float2 d = df_add(v[(size_t)of * Kp + k], df_neg(v[(size_t)ot * Kp + k]));  // v_f - v_t
+    s = df_fma(i == of ? df_neg(ob2) : ob2, d, s);
+  }
   return s;
 }
 
-__device__ __forceinline__ double dc_diag(const DCArgs& a, int i, int of, int ot, double ob) {
-  const double d = __ldg(a.bval + __ldg(a.dpos + i));
-  return (i == of || i == ot) ? d - ob : d;
-}
-
 // Jacobi step z_i = r_i / B'_ii.
-__device__ __forceinline__ double dc_jacobi(const DCArgs& a, double r, int i, int of, int ot, double ob) {
-  return (i == of || i == ot) ? r / dc_diag(a, i, of, ot, ob) : r * __ldg(a.dinv + i);
+__device__ __forceinline__ float2 dc_jacobi(const DCArgs& a, float2 r, int i, int of, int ot, float2 ob2) {
+  if (i == of || i == ot) return df_div(r, df_add(__ldg(a.bval + __ldg(a.dpos + i)), df_neg(ob2)));
+  return df_mul(r, __ldg(a.dinv + i));
 }
 
 // Per case: the outaged branch's susceptance, the solver state reset.
@@ -133,12 +178,13 @@ __global__ void k_dc_case_init(DCArgs a, const int32_t* __restrict__ outage, con
 // x0 (slack angle at slack buses, 0 elsewhere) for every element; p, q zeroed.
 __global__ void k_dc_x0(DCArgs a) {
   const size_t n = (size_t)a.N * a.Kp;
+  const float2 zero = make_float2(0.f, 0.f), vs = df_from(a.va_slack);
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / a.Kp);
-    a.x[e] = (__ldg(a.type + i) == BUS_SLACK) ? a.va_slack : 0.0;
-    a.p[e] = 0.0;
-    a.p_new[e] = 0.0;
-    a.q[e] = 0.0;  // q' = B' z + beta q reads it with beta = 0 first
+    a.x[e] = (__ldg(a.type + i) == BUS_SLACK) ? vs : zero;
+    a.p[e] = zero;
+    a.p_new[e] = zero;
+    a.q[e] = zero;  // q' = B' z + beta q reads it with beta = 0 first
   }
 }
 
@@ -147,47 +193,47 @@ __global__ void __launch_bounds__(1024) k_dc_start(DCArgs a) {
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
   const size_t Kp = (size_t)a.Kp;
-  double rz = 0.0, rr = 0.0;
+  float2 rz = make_float2(0.f, 0.f), rr = rz;
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const double ob = a.ob[k];
+    const float2 ob2 = df_from(a.ob[k]);
     for (int i = mp.row0; i < a.N; i += mp.rstride) {
       const size_t e = (size_t)i * Kp + k;
-      double r = 0.0, z = 0.0;
+      float2 r = make_float2(0.f, 0.f), z = r;
       if (__ldg(a.type + i) != BUS_SLACK) {
-        const double P = a.spec_per_case ? a.pspec[e] : a.pspec[i];
-        r = P - dc_row(a, a.x, i, k, Kp, of, ot, ob);
-        z = dc_jacobi(a, r, i, of, ot, ob);
+        const float2 P = df_from(a.spec_per_case ? a.pspec[e] : a.pspec[i]);
+        r = df_add(P, df_neg(dc_row(a, a.x, i, k, Kp, of, ot, ob2)));
+        z = dc_jacobi(a, r, i, of, ot, ob2);
       }
       a.r[e] = r;
       a.z[e] = z;
       a.p[e] = z;
-      rz = fma(r, z, rz);
-      rr = fma(r, r, rr);
+      rz = df_fma(r, z, rz);
+      rr = df_fma(r, r, rr);
     }
   }
-  case_sum2_atomic(rz, rr, a.lanes, a.rz, a.rr0, a.Kp);
+  case_sum2_atomic(df_val(rz), df_val(rr), a.lanes, a.rz, a.rr0, a.Kp);
 }
 
 __global__ void __launch_bounds__(256) k_dc_spmv_dir(DCArgs a) {
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
   const int k = mp.k;
   const size_t Kp = (size_t)a.Kp;
-  double pq = 0.0;
+  float2 pq = make_float2(0.f, 0.f);
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const double ob = a.ob[k], beta = a.beta[k];
+    const float2 ob2 = df_from(a.ob[k]), beta = df_from(a.beta[k]);
     for (int i = mp.i0; i < mp.r1; i += mp.istride) {
       if (__ldg(a.type + i) == BUS_SLACK) continue;  // p, q stay 0 there
       const size_t e = (size_t)i * Kp + k;
-      const double pn = fma(beta, a.p[e], a.z[e]);
-      const double q = fma(beta, a.q[e], dc_row(a, a.z, i, k, Kp, of, ot, ob));
+      const float2 pn = df_fma(beta, a.p[e], a.z[e]);
+      const float2 q = df_fma(beta, a.q[e], dc_row(a, a.z, i, k, Kp, of, ot, ob2));
       a.p_new[e] = pn;
       a.q[e] = q;
-      pq = fma(pn, q, pq);
+      pq = df_fma(pn, q, pq);
     }
   }
-  case_sum2_atomic(pq, 0.0, a.lanes, a.pq, nullptr, a.Kp);
+  case_sum2_atomic(df_val(pq), 0.0, a.lanes, a.pq, nullptr, a.Kp);
 }
 
 // Per case, after all row blocks' sums: convergence test and the next beta.
@@ -227,24 +273,24 @@ __global__ void __launch_bounds__(256) k_dc_update_case(DCArgs a) {
     s_alpha[threadIdx.x] = al;
   }
   __syncthreads();
-  double rz = 0.0, rr = 0.0;
+  float2 rz = make_float2(0.f, 0.f), rr = rz;
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const double ob = a.ob[k];
-    const double alpha = s_alpha[mp.kl];
+    const float2 ob2 = df_from(a.ob[k]);
+    const float2 alpha = df_from(s_alpha[mp.kl]), nalpha = df_neg(alpha);
     for (int i = mp.i0; i < mp.r1; i += mp.istride) {
       if (__ldg(a.type + i) == BUS_SLACK) continue;
       const size_t e = (size_t)i * Kp + k;
-      a.x[e] = fma(alpha, a.p_new[e], a.x[e]);
-      const double r = fma(-alpha, a.q[e], a.r[e]);
-      const double z = dc_jacobi(a, r, i, of, ot, ob);
+      a.x[e] = df_fma(alpha, a.p_new[e], a.x[e]);
+      const float2 r = df_fma(nalpha, a.q[e], a.r[e]);
+      const float2 z = dc_jacobi(a, r, i, of, ot, ob2);
       a.r[e] = r;
       a.z[e] = z;
-      rz = fma(r, z, rz);
-      rr = fma(r, r, rr);
+      rz = df_fma(r, z, rz);
+      rr = df_fma(r, r, rr);
     }
   }
-  case_sum2_atomic(rz, rr, a.lanes, a.rzn, a.rr, a.Kp);
+  case_sum2_atomic(df_val(rz), df_val(rr), a.lanes, a.rzn, a.rr, a.Kp);
   // the last CTA of the case tile (every CTA counts itself after fencing its
   // atomics) takes the per-case step for the tile's cases
   __shared__ int last;
@@ -262,6 +308,15 @@ __global__ void __launch_bounds__(256) k_dc_update_case(DCArgs a) {
       const int kk = blockIdx.x * a.lanes + c;
       if (kk < a.Kp) dc_case_step(a, kk);
     }
+  }
+}
+
+// The double-float solution widened to FP64 in place (each element's 8 bytes
+// are read before they are written).
+__global__ void k_dc_widen(float2* x, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = x[e];
+    reinterpret_cast<double*>(x)[e] = df_val(v);
   }
 }
 

@@ -35,8 +35,9 @@ struct DeviceYbus {
   int32_t* ppos = nullptr;      // [prow_ptr[n]] CSR position of a padded slot, -(row+1) for a pad
   int32_t* col = nullptr;       // [nnz]
   double2* val64 = nullptr;     // [nnz]
-  double* dcval = nullptr;      // [nnz] DC matrix B (susceptances 1/(x tau)) in the same CSR
-  double* dcinv = nullptr;      // [n] 1 / B_ii (0 where B_ii = 0): the Jacobi preconditioner
+  float2* dcval = nullptr;      // [nnz] DC matrix B (susceptances 1/(x tau)) in the same CSR, as
+                                //   double-float pairs (hi, lo): hi + lo is the FP64 value
+  float2* dcinv = nullptr;      // [n] 1 / B_ii (0 where B_ii = 0), the Jacobi preconditioner, ditto
   int32_t* ebr = nullptr;       // [nnz] branch of an off-diagonal entry, -1 on the diagonal
   int32_t* dpos = nullptr;      // [n] position of the diagonal entry in its row
   uint8_t* type = nullptr;      // [n]
