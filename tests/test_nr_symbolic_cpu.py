@@ -102,3 +102,23 @@ def test_fill_of_the_contingency_grid_is_moderate(dpf):
     nnz = g.n_bus + 2 * g.n_branch
     assert nnz <= s["n_pos"] <= 6 * nnz
     assert s["n_levels"] < g.n_bus
+
+
+def test_block_diagonal_batch_keeps_its_islands_apart(dpf):
+    """Several grids in one Y_bus (one slack per island, the uneven batch):
+    the elimination fills only within an island, and the filled pattern is
+    still exactly the fill of dense elimination in the reported order."""
+    grids = [gridgen.make_grid(n, 100 + i, n_branch=int(1.35 * n), n_pv=max(1, n // 8))
+             for i, n in enumerate((40, 120, 75))]
+    cat = gridgen.concat_grids(grids)
+    y = dpf.dpf_build_ybus_host(cat)
+    p = dpf.dpf_nr_pattern(y)
+    n = cat.n_bus
+    island = np.repeat(np.arange(len(grids)), [g.n_bus for g in grids])
+    order, rp, col = p["order"], p["row_ptr"], p["col"]
+    pat = np.zeros((n, n), bool)
+    for r in range(n):
+        c = col[rp[r]:rp[r + 1]]
+        assert np.all(island[order[c]] == island[order[r]])
+        pat[r, c] = True
+    np.testing.assert_array_equal(pat, _dense_fill(cat, order, 7))
