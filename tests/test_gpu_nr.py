@@ -279,3 +279,24 @@ def test_fallback_keeps_the_start_where_newton_fails():
         assert fb["status"][k] == dpf.CASE_CONVERGED
         for key in fb:
             np.testing.assert_array_equal(fb[key][k], plain[key][k])
+
+
+def test_block_diagonal_batch_of_grids():
+    """Three grids in one Y_bus (one slack per island): Newton on the whole
+    batch against the oracle's NR on the same block-diagonal system, with
+    per-case loads (two operating points)."""
+    grids = [gridgen.make_grid(n, 100 + i, n_branch=int(1.35 * n), n_pv=max(1, n // 8), load_scale=0.1)
+             for i, n in enumerate((40, 120, 75))]
+    cat = gridgen.concat_grids(grids)
+    Y = grid_ybus(cat)
+    sc = np.array([1.0, 0.9])[:, None]
+    P, Q = cat.p_spec[None, :] * sc, cat.q_spec[None, :] * sc
+    y = dpf.dpf_build_ybus(cat)
+    nr = dpf.dpf_nr_create(y, 2)
+    r = _nr(y, nr, 2, p_spec=_t(P), q_spec=_t(Q))
+    for k in range(2):
+        ref = oracle.nr_solve(Y, P[k], Q[k], cat.bus_type, cat.vm_set, tol=TOL)
+        assert ref["converged"] and r["status"][k] == dpf.CASE_CONVERGED
+        assert r["iters"][k] == ref["iters"]
+        assert np.abs(r["va"][k] - ref["va"]).max() <= 1e-9
+        assert np.abs(r["vm"][k] - ref["vm"]).max() <= 1e-9
