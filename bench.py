@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -261,8 +262,9 @@ def run_ours(args):
         stream.synchronize()
         n_active0 = dpf.dpf_active_count(ws, stream=stream)
 
-        clocks = ClockSampler(ClockSampler.gpu_id(local), os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+        # raw clock samples (the line carries their summary); DPF_CLOCKS_DIR picks the folder
+        clocks_dir = os.environ.get("DPF_CLOCKS_DIR") or tempfile.gettempdir()
+        clocks = ClockSampler(ClockSampler.gpu_id(local), os.path.join(clocks_dir, f"clocks_rank{rank}.csv"))
         time.sleep(0.3)
         if world > 1:
             dist.barrier()
