@@ -1153,8 +1153,26 @@ def _oracle_nr_sample(sample, cores):
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
+def _oracle_steps_worker(args):
+    """`warmup` untimed and `steps` timed steps of `iters` oracle DPF
+    iterations on N-1 case `ell` (one process); returns (iterations, seconds)
+    of the timed steps."""
+    ell, iters, warmup, steps = args
+    for _ in range(warmup):
+        _oracle_worker((ell, iters))
+    n, t = 0, 0.0
+    for _ in range(steps):
+        k, dt, _st = _oracle_worker((ell, iters))
+        n += k
+        t += dt
+    return n, t
+
+
 def run_reference(args):
-    """Each step: every host core runs `--ref-iters` oracle iterations on its own N-1 case."""
+    """Each step: every host core runs `--ref-iters` oracle iterations on its
+    own N-1 case.  Every core runs its warm-up and timed steps in one call
+    (no per-step inter-process round trip); the run's time is the slowest
+    core's."""
     import multiprocessing as mp
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -1163,21 +1181,16 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0))
     cases = _sample_cases(outages, cores)
     ctx = mp.get_context("spawn")
-    total_iters, total_t = 0, 0.0
     with ctx.Pool(cores) as pool:
         pool.map(_oracle_worker, [(c, 1) for c in cases])  # start-up, untimed
-        for s in range(args.warmup + args.steps):
-            t0 = time.perf_counter()
-            res = pool.map(_oracle_worker, [(c, args.ref_iters) for c in cases])
-            dt = time.perf_counter() - t0
-            if s >= args.warmup:
-                total_iters += sum(r[0] for r in res)
-                total_t += dt
+        res = pool.map(_oracle_steps_worker, [(c, args.ref_iters, args.warmup, args.steps) for c in cases])
+    total_iters = sum(r[0] for r in res)
+    total_t = max(r[1] for r in res)
     v = total_iters / ITERS_PER_SOLVE / total_t
     cpu = dict(value=v, unit="solves/s", cores=cores, kind="oracle",
                sample=f"per step {cores} N-1 cases x {args.ref_iters} DPF iterations (FP64 numpy/scipy "
                       f"oracle, one case per core, spawn pool); {args.steps} timed steps, "
-                      f"{total_iters} case-iterations in {total_t:.1f} s")
+                      f"{total_iters} case-iterations in {total_t:.1f} s (slowest core)")
     vals = [v]
     line = {
         "impl": "reference",
