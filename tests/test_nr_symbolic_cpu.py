@@ -144,3 +144,26 @@ def test_block_diagonal_batch_keeps_its_islands_apart(dpf):
         assert np.all(island[order[c]] == island[order[r]])
         pat[r, c] = True
     np.testing.assert_array_equal(pat, _structural_fill(cat, order))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_grids_fill_and_levels(dpf, seed):
+    """Random small grids (sizes 4..90, branch ratios 1.0..1.8): the filled
+    pattern equals graph-elimination fill in the reported order, every
+    position's pivot sits on a level no higher than either of its rows, and
+    the L columns of a row are on strictly lower levels."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(4, 91))
+    m = max(n - 1, int(round(n * rng.uniform(1.0, 1.8))))
+    g = gridgen.make_grid(n, 500 + seed, n_branch=m, n_pv=max(1, n // 6))
+    y = dpf.dpf_build_ybus_host(g)
+    p = dpf.dpf_nr_pattern(y)
+    order, rp, col, level = p["order"], p["row_ptr"], p["col"], p["level"]
+    assert np.array_equal(np.sort(order), np.arange(n))
+    pat = np.zeros((n, n), bool)
+    for r in range(n):
+        c = col[rp[r]:rp[r + 1]]
+        pat[r, c] = True
+        lo = c[c < r]
+        assert np.all(level[lo] < level[r])
+    np.testing.assert_array_equal(pat, _structural_fill(g, order))
