@@ -129,3 +129,55 @@ def test_default_opts_are_table2(dpf):
 def test_status_strings(dpf):
     for c in (0, -1, -2, -3, -4, -5, -6):
         assert dpf.dpf_status_str(c) and dpf.dpf_status_str(c) != "unknown status"
+
+
+def test_c_program_builds_and_calls_the_library(dpf, tmp_path):
+    """The header is plain C99: a C program compiles against it, links
+    libdpf.so and calls host-only entry points (Y_bus build and validation,
+    the Newton analysis, defaults, error reporting; no CUDA call)."""
+    import shutil
+    import subprocess
+    from paper_2603_28203_gb300.build import LIB
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_dpf.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "dpf.h"
+int main(void) {
+  /* two buses, one line: slack 0 feeding a PQ load at bus 1 */
+  const uint8_t type[2] = {DPF_SLACK, DPF_PQ};
+  const double p[2] = {0.0, -0.5}, q[2] = {0.0, -0.1}, vm[2] = {1.0, 1.0};
+  const int32_t f[1] = {0}, t[1] = {1};
+  const double r[1] = {0.01}, x[1] = {0.1}, bch[1] = {0.0}, tap[1] = {0.0};
+  dpf_grid g = {2, 1, type, p, q, vm, 0.0, f, t, r, x, bch, tap, NULL};
+  dpf_ybus* y = NULL;
+  if (dpf_build_ybus_host(&g, &y) != DPF_OK) { printf("build: %s\n", dpf_last_error()); return 1; }
+  int32_t n = 0, m = 0, nnz = 0;
+  dpf_ybus_info(y, &n, &m, &nnz);
+  int64_t npos = 0, npairs = 0;
+  int32_t nl = 0;
+  if (dpf_nr_analyze(y, &npos, &npairs, &nl) != DPF_OK) return 2;
+  dpf_nr_opts o;
+  dpf_nr_default_opts(&o);
+  dpf_solve_opts so;
+  dpf_default_opts(&so);
+  g.n_branch = -1; /* invalid: must be rejected with a message, not a crash */
+  dpf_ybus* bad = NULL;
+  const int rc = dpf_build_ybus_host(&g, &bad);
+  printf("%d %d %d %lld %lld %d %d %d %d\n", n, m, nnz, (long long)npos, (long long)npairs, nl, o.max_iter,
+         so.max_iter, rc == DPF_E_INVALID);
+  dpf_ybus_free(y);
+  return 0;
+}
+''')
+    exe = tmp_path / "use_dpf"
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I" + inc, str(src), "-o", str(exe), "-L" + libdir,
+                    "-ldpf", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    n, m, nnz, npos, npairs, nl, nr_iter, dpf_iter, rejected = map(int, out)
+    assert (n, m, nnz) == (2, 1, 4)
+    assert (npos, npairs, nl) == (4, 1, 2)     # one elimination: the 2x2 pattern, one product, two levels
+    assert nr_iter == 20 and dpf_iter == 1000 and rejected == 1
