@@ -181,3 +181,16 @@ int main(void) {
     assert (n, m, nnz) == (2, 1, 4)
     assert (npos, npairs, nl) == (4, 1, 2)     # one elimination: the 2x2 pattern, one product, two levels
     assert nr_iter == 20 and dpf_iter == 1000 and rejected == 1
+
+
+def test_newton_handle_needs_an_uploaded_ybus(dpf):
+    """dpf_nr_create on a host-only Y_bus is refused (DPF_E_STATE) before any
+    CUDA call; bad arguments are DPF_E_INVALID."""
+    g = gridgen.config_grid("c1_30bus_fp64")
+    y = dpf.dpf_build_ybus_host(g)
+    with pytest.raises(dpf.DPFError) as e:
+        dpf.dpf_nr_create(y, 4)
+    assert e.value.code == dpf._abi.DPF_E_STATE
+    with pytest.raises(dpf.DPFError) as e:
+        dpf.dpf_nr_create(y, 0)
+    assert e.value.code == dpf._abi.DPF_E_INVALID
