@@ -1,0 +1,31 @@
+"""CPU checks of bench.py's accounting: the workload it times and the
+algorithmic byte counts its roofline divides by (the figures the design
+notes quote for the N-1 batch)."""
+import numpy as np
+
+import bench
+
+
+def test_n1_workload_and_algorithmic_bytes():
+    g, outages = bench._workload()
+    n_pv = int((g.bus_type == 1).sum())
+    n_pq = int((g.bus_type == 0).sum())
+    nnz = g.n_bus + 2 * g.n_branch
+    assert (g.n_bus, n_pv, n_pq, nnz, outages.size) == (2000, 300, 1699, 7400, 2379)
+    fwd, adj = bench.algorithmic_bytes(g.n_bus, n_pv, n_pq, nnz, outages.size)
+    # per case: forward 16 N + 4 n_pv, adjoint 8 N + 60 n_pv + 80 n_pq; Y and the shared P/Q once per pass
+    shared = 16 * nnz + 4 * (g.n_bus + 1) + g.n_bus + 8 * g.n_bus
+    assert fwd == outages.size * (16 * g.n_bus + 4 * n_pv) + shared
+    assert adj == outages.size * (8 * g.n_bus + 60 * n_pv + 80 * n_pq) + shared
+    assert round(fwd / 1e6, 1) == 79.1 and round(adj / 1e6, 1) == 404.4
+
+
+def test_dc_and_newton_byte_models_scale_with_the_cases():
+    b1 = bench.dc_bytes_per_iteration(2000, 7400, 1)
+    b2 = bench.dc_bytes_per_iteration(2000, 7400, 2)
+    assert b2 - b1 == 2000 * 96                       # 96 B per element and CG iteration
+    n1 = bench.nr_bytes_per_step(2000, 10594, 10851, 1)
+    n2 = bench.nr_bytes_per_step(2000, 10594, 10851, 2)
+    assert n2["fp64"] == 2 * n1["fp64"] and n2["fp32"] == 2 * n1["fp32"]
+    assert n1["fp32"] < n1["fp64"]
+    assert np.isclose(bench.dc_flops_per_iteration(2000, 7400, 1, 1), 2 * 7400 + 1999 * 15)
