@@ -363,6 +363,11 @@ def run_ours(args):
                         "algorithmic_bytes_per_launch": fwd_b, "avg_launch_ms": fwd_avg,
                         "traffic": _ncu_traffic("k_fwd")},
                 "fwd_adj_combined_gbs": (fwd_b + adj_b) / ((fwd_avg + adj_avg) / 1e3) / 1e9,
+                # the same bytes over the timed iteration (its forward and adjoint overlap
+                # through programmatic dependent launch; it also holds the FP64 test every
+                # check interval): the pipeline's own rate
+                "fwd_adj_per_iteration_gbs": (fwd_b + adj_b) / (t_max / args.steps / 1e3) / 1e9,
+                "fwd_adj_per_iteration_frac": (fwd_b + adj_b) / (t_max / args.steps / 1e3) / 1e9 / peak,
                 "timed_launches": n_adj,
             },
             "gpu_launches": int(launches),
