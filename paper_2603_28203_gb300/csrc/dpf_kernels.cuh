@@ -582,19 +582,30 @@ __device__ __forceinline__ void tile_sched_grouped(const SchedArgs<R>& a, unsign
     if (last) tile_cnt[blockIdx.x] = 0u;
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return;  // the same for every thread of the CTA
   __threadfence();
-  for (int c = threadIdx.x; c < tile; c += blockDim.x) {
+  // tpc threads per case (a power of two, tile * tpc <= blockDim.x <= 256)
+  // take strided slices of the groups' sums, then a fixed tree: a single
+  // case over hundreds of groups is summed by the whole CTA
+  __shared__ R part[256];
+  int tpc = 1;
+  while (2 * tpc * tile <= (int)blockDim.x) tpc *= 2;
+  const int per_pass = max(1, (int)blockDim.x / tpc);
+  for (int c0 = 0; c0 < tile; c0 += per_pass) {
+    const int c = c0 + (int)threadIdx.x / tpc, j = (int)threadIdx.x % tpc;
     const int k = blockIdx.x * tile + c;
-    if (k >= a.Kp) continue;
-    R s8[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    int q = 0;
-    for (; q + 8 <= ng; q += 8) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s8[u] += __ldcg(a.grp_part + (size_t)(q + u) * a.Kp + k);
+    const bool mine = (int)threadIdx.x < per_pass * tpc && c < tile && k < a.Kp;
+    R s = R(0);
+    if (mine)
+      for (int q = j; q < ng; q += tpc) s += __ldcg(a.grp_part + (size_t)q * a.Kp + k);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int step = tpc >> 1; step > 0; step >>= 1) {
+      if (j < step) part[threadIdx.x] += part[threadIdx.x + step];
+      __syncthreads();
     }
-    for (; q < ng; ++q) s8[0] += __ldcg(a.grp_part + (size_t)q * a.Kp + k);
-    sched_case(a, k, ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7])));
+    if (mine && j == 0) sched_case(a, k, part[threadIdx.x]);
+    __syncthreads();
   }
 }
 
