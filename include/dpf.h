@@ -64,8 +64,19 @@ enum { DPF_PQ = 0, DPF_PV = 1, DPF_SLACK = 2 };            /* bus types (Sec. 2.
  * mismatch and its weights) in FP64 over FP64 voltages, the adjoint and the
  * optimiser in FP32 on the double-float master: it resolves mismatches below
  * the FP32 current's error of a few |Y_ii| 2^-24 (~1e-5 p.u. with short
- * lines) at about the FP32 cost of the adjoint. */
-enum { DPF_FP32 = 0, DPF_FP64 = 1, DPF_MIXED = 2 };
+ * lines) at about the FP32 cost of the adjoint.
+ * DPF_FP32R (solves only) -- refined FP32 iterations: every arithmetic step
+ * of an iteration is FP32 as in DPF_FP32, but the forward pass evaluates the
+ * mismatch as a correction to the FP64 residual of the case's most recent
+ * convergence test, f = f_ref + dV conj(I_ref) + V conj(Y dV), where dV (the
+ * change of V since that test, carried in FP32 and advanced from each
+ * optimiser step) is small near convergence; the FP32 rounding error then
+ * scales with dV instead of with |Y_ii| |V|, and the iterations reach
+ * mismatches far below DPF_FP32's limit.  The FP64 test (every check_every
+ * iterations, on the cases the gate admits, and on every active case at
+ * every 4th test) renews f_ref, I_ref and V_ref.  Until a case's first test
+ * its iterations equal DPF_FP32 ones. */
+enum { DPF_FP32 = 0, DPF_FP64 = 1, DPF_MIXED = 2, DPF_FP32R = 3 };
 enum { DPF_SCHED_CONST = 0, DPF_SCHED_PLATEAU = 1, DPF_SCHED_STEP = 2 };
 enum { DPF_OPT_ADAM = 0, DPF_OPT_SGD = 1, DPF_OPT_RMSPROP = 2 };    /* Sec. 5.3's optimisers */
 
@@ -144,6 +155,12 @@ typedef struct {
   int32_t* status;           /* [n_case] out: DPF_CASE_*                      */
   double* max_mismatch;      /* [n_case] out: FP64 max |f| of the returned V  */
   double* loss;              /* [n_case] out: FP64 loss of the returned V     */
+  const double* va_start;    /* [n_bus] or NULL: one warm start shared by    */
+  const double* vm_start;    /* every case (given together; with flat_start =
+                                0 they replace va/vm as the start, and va/vm
+                                are outputs only) -- e.g. the base-case state
+                                from which the cases of an N-1 batch start.
+                                dpf_solve_* only (dpf_nr_solve: NULL)        */
 } dpf_batch;
 
 /* Iteration options.  Defaults (dpf_default_opts): Table 2 of the paper --
@@ -253,6 +270,18 @@ int dpf_profile_enable(dpf_workspace* ws, int32_t on);
 int dpf_kernel_times(dpf_workspace* ws, double* fwd_ms, double* adj_ms, int32_t* n_fwd, int32_t* n_adj,
                      void* stream);
 int dpf_kernel_launches(const dpf_workspace* ws, int64_t* n);
+
+/* Read-bandwidth probe (a measurement hook; the paper has no counterpart):
+ * a plain kernel reads the caller's device buffer `buf` of `bytes` bytes
+ * (16-byte aligned, bytes a multiple of 16) with 16-byte loads that bypass
+ * L1 (ld.global.cg), grid = SMs x 8 CTAs of 256 threads; a launch reads the
+ * buffer `passes` = min(64, max(1, 256 MB / bytes)) times; two untimed
+ * launches, then `reps` launches between CUDA events on `stream`.
+ * *gbs = bytes x passes x reps / elapsed time (GB/s).  A buffer far below
+ * the L2's 129 MB measures the L2 read bandwidth, one far above it the HBM
+ * read bandwidth.  Synchronises `stream`.  Errors: DPF_E_INVALID (NULL,
+ * alignment, size, reps < 1), DPF_E_CUDA. */
+int dpf_read_bandwidth(const void* buf, int64_t bytes, int32_t reps, double* gbs, void* stream);
 
 /* ---- forward evaluation (Eq. powerbalance) --------------------------------
  * The evaluation entry points take (va, vm) verbatim, set-points included.

@@ -7,7 +7,7 @@ DPF_OK = 0
 DPF_E_INVALID, DPF_E_ISLANDED, DPF_E_CUDA, DPF_E_OOM, DPF_E_UNSUPPORTED, DPF_E_STATE = -1, -2, -3, -4, -5, -6
 CASE_CONVERGED, CASE_MAX_ITER, CASE_DIVERGED = 0, 1, 2
 PQ, PV, SLACK = 0, 1, 2
-FP32, FP64, MIXED = 0, 1, 2
+FP32, FP64, MIXED, FP32R = 0, 1, 2, 3
 SCHED_CONST, SCHED_PLATEAU, SCHED_STEP = 0, 1, 2
 OPT_ADAM, OPT_SGD, OPT_RMSPROP = 0, 1, 2
 NOALLOC_MAX_ELEMS = 1 << 18
@@ -34,7 +34,7 @@ class DpfBatch(C.Structure):
         ("p_spec", C.c_void_p), ("q_spec", C.c_void_p), ("vm_set", C.c_void_p),
         ("outage", C.c_void_p), ("va", C.c_void_p), ("vm", C.c_void_p),
         ("iters", C.c_void_p), ("status", C.c_void_p), ("max_mismatch", C.c_void_p),
-        ("loss", C.c_void_p),
+        ("loss", C.c_void_p), ("va_start", C.c_void_p), ("vm_start", C.c_void_p),
     ]
 
 
@@ -99,6 +99,7 @@ SIGNATURES = {
     "dpf_profile_enable": (C.c_int, [VP, I32]),
     "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),
     "dpf_kernel_launches": (C.c_int, [VP, C.POINTER(C.c_int64)]),
+    "dpf_read_bandwidth": (C.c_int, [VP, C.c_int64, C.c_int32, C.POINTER(C.c_double), VP]),
     "dpf_adam_update": (C.c_int, [I32, VP, VP, VP, VP, VP, I32, C.c_double, C.c_double, C.c_double, C.c_double,
                                   VP]),
     "dpf_last_error": (C.c_char_p, []),

@@ -534,6 +534,10 @@ static Plan<R> make_plan(dpf_workspace* w) {
   a.m_half = (R)(0.5 * y->m_loss);
   a.n_active = w->n_active;
   if constexpr (sizeof(R) == 4) {
+    if (w->precision == DPF_FP32R) {  // references of the refined iterations (solve-loop buffers)
+      a.vref = (const float2*)w->cbuf;
+      a.irf = (const float4*)w->sbuf;
+    }
     if (w->precision == DPF_MIXED) {
       a.V64m = (double2*)w->V;
       a.Y64.col = d.col;
@@ -599,6 +603,9 @@ static Plan<R> make_plan(dpf_workspace* w) {
   c.spec_per_case = w->spec_per_case ? 1 : 0;
   c.active = w->active;
   c.cand = gated ? w->cand : nullptr;
+  c.iters = w->iters;
+  // refined FP32: every 4th test also re-anchors the cases the gate keeps out
+  c.full_every = (gated && w->precision == DPF_FP32R) ? 4 * std::max(1, w->opts.check_every) : 0;
   c.of = w->of;
   c.ot = w->ot;
   c.yff = w->yff64;
@@ -608,6 +615,12 @@ static Plan<R> make_plan(dpf_workspace* w) {
   c.maxmis = w->maxmis;
   c.loss64 = w->loss64;
   c.n_active = w->n_active;
+  c.refresh = 0;
+  if (sizeof(R) == 4 && w->precision == DPF_FP32R) {
+    c.vref = (float2*)w->cbuf;
+    c.irf = (float4*)w->sbuf;
+    c.dv = (float2*)w->V;
+  }
 
   ApplyArgs& p = P.ap;
   p.K = w->K;
@@ -617,6 +630,8 @@ static Plan<R> make_plan(dpf_workspace* w) {
   p.inv_m = y->m_loss > 0 ? 1.0 / y->m_loss : 0.0;
   p.active = w->active;
   p.cand = gated ? w->cand : nullptr;
+  p.iters = w->iters;
+  p.full_every = c.full_every;
   p.status = w->status;
   p.maxmis = w->maxmis;
   p.loss64 = w->loss64;
@@ -644,6 +659,7 @@ template <class R>
 static int launch_check(dpf_workspace* w, cudaStream_t s, bool final_pass) {
   Plan<R> P = make_plan<R>(w);
   P.ck.all_cases = final_pass ? 1 : 0;
+  P.ck.refresh = (w->precision == DPF_FP32R && !final_pass) ? 1 : 0;
   P.ap.final_pass = final_pass ? 1 : 0;
   using M = typename Prec<R>::M;
   const bool pdl = w->opts.pdl != 0;
@@ -671,17 +687,20 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
     CK(cudaEventRecord(e0, s));
   }
   if constexpr (sizeof(R) == 4) {
+    const bool ref = w->precision == DPF_FP32R;
     if (w->precision == DPF_MIXED) CK(launch(k_fwd_mixed, P.grid, P.block, P.smem, s, pdl, P.it));
-    else if (w->pair_fwd) CK(launch(k_fwd2, P.pgrid, P.block, P.smem, s, pdl, P.it));
-    else CK(launch(k_fwd<R>, P.grid, P.block, P.smem, s, pdl, P.it));
+    else if (w->pair_fwd) CK(launch(ref ? k_fwd2<true> : k_fwd2<false>, P.pgrid, P.block, P.smem, s, pdl, P.it));
+    else CK(launch(ref ? k_fwd<float, true> : k_fwd<float, false>, P.grid, P.block, P.smem, s, pdl, P.it));
   } else {
     CK(launch(k_fwd<R>, P.grid, P.block, P.smem, s, pdl, P.it));
   }
   if (w->profile) CK(cudaEventRecord(e1, s));
   if constexpr (sizeof(R) == 4) {
+    const bool ref = w->precision == DPF_FP32R;
     if (w->precision == DPF_MIXED) CK(launch(k_adj<float, true>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
-    else if (w->pair_adj) CK(launch(k_adj2, P.pgridb, P.block, P.ysmem, s, pdl, P.itb));
-    else CK(launch(k_adj<R>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
+    else if (w->pair_adj) CK(launch(ref ? k_adj2<true> : k_adj2<false>, P.pgridb, P.block, P.ysmem, s, pdl, P.itb));
+    else CK(launch(ref ? k_adj<float, false, true> : k_adj<float, false, false>, P.gridb, P.block, P.ysmem, s, pdl,
+                   P.itb));
   } else {
     CK(launch(k_adj<R>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
   }
@@ -753,6 +772,7 @@ struct StateIn {
   bool host_io;
   bool enforce_fixed;  // solve: set-points override the given state; evaluation: state as given
   const double *va, *vm, *vmset, *p, *q;  // user layout [K][N] or NULL
+  const double *va0, *vm0;                 // one start [N] shared by every case, or NULL
   const int32_t* outage;
 };
 
@@ -762,7 +782,8 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   lanes = pow2ceil(lanes);
   w->lanes = lanes;
   // FP32 solve loop over >= 64 cases at 32 lanes: two cases per thread
-  w->pairs = o && o->precision == DPF_FP32 && lanes == 32 && K >= 64 && o->pair_cases != 0;
+  w->pairs = o && (o->precision == DPF_FP32 || o->precision == DPF_FP32R) && lanes == 32 && K >= 64 &&
+             o->pair_cases != 0;
   w->pair_fwd = w->pairs && (o->pair_cases & 1);
   w->pair_adj = w->pairs && (o->pair_cases & 2);
   const int tile = w->pairs ? 64 : lanes;
@@ -783,6 +804,7 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   const int prec = o ? o->precision : w->precision;
   const bool fp64 = prec == DPF_FP64;        // FP64 adjoint (and forward)
   const bool mixed = prec == DPF_MIXED;      // FP64 forward, FP32 adjoint
+  const bool refined = prec == DPF_FP32R;    // FP32 iterations on FP64 references
   const bool fp64_fwd = fp64 || mixed;       // the forward pass stages FP64 Y rows
   // bytes of one staged window row: the case tile's line of V (not in mixed mode)
   const bool stage_v = o && o->stage_v && !mixed;
@@ -834,11 +856,13 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
     int occ_f = 0, occ_b = 0;
     const void* kf = fp64          ? (const void*)k_fwd<double>
                      : mixed       ? (const void*)k_fwd_mixed
-                     : w->pair_fwd ? (const void*)k_fwd2
+                     : w->pair_fwd ? (refined ? (const void*)k_fwd2<true> : (const void*)k_fwd2<false>)
+                     : refined     ? (const void*)k_fwd<float, true>
                                    : (const void*)k_fwd<float>;
     const void* kb = fp64          ? (const void*)k_adj<double>
                      : mixed       ? (const void*)k_adj<float, true>
-                     : w->pair_adj ? (const void*)k_adj2
+                     : w->pair_adj ? (refined ? (const void*)k_adj2<true> : (const void*)k_adj2<false>)
+                     : refined     ? (const void*)k_adj<float, false, true>
                                    : (const void*)k_adj<float>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, block, w->smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, kb, block, w->smem);
@@ -909,8 +933,12 @@ static int set_smem_attr(int bytes) {
     CK(cudaFuncSetAttribute(k_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     CK(cudaFuncSetAttribute(k_adj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if constexpr (sizeof(R) == 4) {
-      CK(cudaFuncSetAttribute(k_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-      CK(cudaFuncSetAttribute(k_adj2, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_fwd2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_adj2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_fwd2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_adj2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_fwd<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      CK(cudaFuncSetAttribute(k_adj<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
       CK(cudaFuncSetAttribute(k_fwd_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
       CK(cudaFuncSetAttribute(k_adj<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     }
@@ -971,7 +999,24 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   double* va_t = nullptr;
   double* vm_t = nullptr;
   double* vms_t = nullptr;
-  if (in.va && in.vm) {
+  bool shared = false;
+  if (in.va0 && in.vm0) {  // one state for every case: [N] in internal bus order
+    const double* src[2] = {in.va0, in.vm0};
+    double* stage[2] = {w->st_a, w->st_b};
+    double* dst[2] = {w->tmp_a, w->tmp_b};
+    for (int j = 0; j < 2; ++j) {
+      const double* d = src[j];
+      if (hio) {
+        CK(cudaMemcpyAsync(stage[j], src[j], (size_t)y->n * 8, cudaMemcpyHostToDevice, s));
+        d = stage[j];
+      }
+      k_to_internal<<<dim3((y->n + 31) / 32, 1), dim3(32, 8), 0, s>>>(d, dst[j], 1, y->n, 1, y->dev.iperm);
+      CKLAUNCH();
+    }
+    va_t = w->tmp_a;
+    vm_t = w->tmp_b;
+    shared = true;
+  } else if (in.va && in.vm) {
     TRY(to_internal(w, in.va, hio, w->st_a, w->tmp_a, s));
     TRY(to_internal(w, in.vm, hio, w->st_b, w->tmp_b, s));
     va_t = w->tmp_a;
@@ -999,6 +1044,7 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   ia.vms_t = vms_t;
   ia.va_t = va_t;
   ia.vm_t = vm_t;
+  ia.shared_start = shared ? 1 : 0;
   ia.va_slack = y->va_slack;
   ia.p64 = w->spec_per_case ? w->p64 : nullptr;
   ia.q64 = w->spec_per_case ? w->q64 : nullptr;
@@ -1088,7 +1134,8 @@ static int validate_opts(const dpf_solve_opts* o) {
     return fail(DPF_E_INVALID, "invalid StepLR parameters");
   if (o->max_iter < 0 || o->check_every < 1 || !(o->tol >= 0))
     return fail(DPF_E_INVALID, "invalid max_iter / check_every / tol");
-  if (o->precision != DPF_FP32 && o->precision != DPF_FP64 && o->precision != DPF_MIXED)
+  if (o->precision != DPF_FP32 && o->precision != DPF_FP64 && o->precision != DPF_MIXED &&
+      o->precision != DPF_FP32R)
     return fail(DPF_E_INVALID, "unknown precision");
   if (!(o->gate >= 0.0)) return fail(DPF_E_INVALID, "gate must be >= 0");
   if (o->pdl != 0 && o->pdl != 1) return fail(DPF_E_INVALID, "pdl must be 0 or 1");
@@ -1233,7 +1280,9 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   if (!b || !o) return fail(DPF_E_INVALID, "dpf_solve_begin: NULL argument");
   TRY(common_checks(y, w, b->n_case));
   TRY(validate_opts(o));
-  if (!o->flat_start && (!b->va || !b->vm)) return fail(DPF_E_INVALID, "warm start needs va and vm");
+  if ((b->va_start == nullptr) != (b->vm_start == nullptr))
+    return fail(DPF_E_INVALID, "va_start and vm_start must be given together");
+  if (!o->flat_start && !b->va_start && (!b->va || !b->vm)) return fail(DPF_E_INVALID, "warm start needs va and vm");
   cudaStream_t s = (cudaStream_t)stream;
   w->begun = false;
   w->pid_ready = false;
@@ -1255,6 +1304,8 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   if (!o->flat_start) {
     in.va = b->va;
     in.vm = b->vm;
+    in.va0 = b->va_start;
+    in.vm0 = b->vm_start;
   }
   in.vmset = b->vm_set;
   in.p = b->p_spec;
@@ -1271,6 +1322,15 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
     else
       k_dc_apply<float><<<nb, 256, 0, s>>>(w->tmp_a, (float4*)w->ms, (float2*)w->V, y->dev.type, y->n, w->K, w->Kp);
     if (w->precision == DPF_MIXED) k_mixed_v64<<<nb, 256, 0, s>>>((const float4*)w->ms, (double2*)w->V, E);
+    CKLAUNCH();
+  }
+  if (w->precision == DPF_FP32R) {  // (after the DC start, which uses these buffers)
+    const size_t E = (size_t)y->n * w->Kp;
+    const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+    k_ref_init<<<std::max(nb, 1), 256, 0, s>>>(y->dev.type, w->spec_per_case ? (const float*)w->p : y->dev.p32,
+                                                w->spec_per_case ? (const float*)w->q : y->dev.q32,
+                                                w->spec_per_case ? 1 : 0, w->Kp, E, (float2*)w->cbuf,
+                                                (float4*)w->sbuf);
     CKLAUNCH();
   }
   w->t_done = 0;
@@ -1346,6 +1406,61 @@ extern "C" int dpf_kernel_launches(const dpf_workspace* w, int64_t* n) {
   if (!w || !n) return fail(DPF_E_INVALID, "dpf_kernel_launches: NULL argument");
   *n = w->launches;
   return DPF_OK;
+}
+
+// Read-bandwidth probe: every thread sums its 16-byte words (four loads in
+// flight per step); the sums feed a store no input can trigger, so the loads
+// cannot be dropped.
+__global__ void __launch_bounds__(256) k_read_probe(const float4* __restrict__ p, size_t n4, int passes,
+                                                    float* __restrict__ sink) {
+  float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int pass = 0; pass < passes; ++pass) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n4; i += 4 * stride) {
+    const float4 v0 = __ldcg(p + i), v1 = __ldcg(p + i + stride), v2 = __ldcg(p + i + 2 * stride),
+                 v3 = __ldcg(p + i + 3 * stride);
+    ax += (v0.x + v1.x) + (v2.x + v3.x);
+    ay += (v0.y + v1.y) + (v2.y + v3.y);
+    az += (v0.z + v1.z) + (v2.z + v3.z);
+    aw += (v0.w + v1.w) + (v2.w + v3.w);
+  }
+  for (; i < n4; i += stride) {
+    const float4 v = __ldcg(p + i);
+    ax += v.x; ay += v.y; az += v.z; aw += v.w;
+  }
+  }
+  const float t = (ax + ay) + (az + aw);
+  if (t == -1.2345e-38f) sink[blockIdx.x] = t;  // never true for the probe's data
+}
+
+extern "C" int dpf_read_bandwidth(const void* buf, int64_t bytes, int32_t reps, double* gbs, void* stream) {
+  clear_error();
+  if (!buf || !gbs || bytes <= 0 || reps < 1) return fail(DPF_E_INVALID, "dpf_read_bandwidth: bad argument");
+  if (((uintptr_t)buf & 15) != 0 || (bytes & 15) != 0)
+    return fail(DPF_E_INVALID, "dpf_read_bandwidth: buffer and size must be multiples of 16 bytes");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n4 = (size_t)bytes / 16;
+  const int grid = num_sms() * 8;
+  // buffers that fit the L2 are read several times per launch (>= 256 MB per
+  // launch), so that launch gaps do not dilute the measurement
+  const int passes = (int)std::max<int64_t>(1, std::min<int64_t>(64, (256ll << 20) / bytes));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = DPF_OK;
+  for (int r = 0; r < 2; ++r) k_read_probe<<<grid, 256, 0, s>>>((const float4*)buf, n4, passes, nullptr);
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) k_read_probe<<<grid, 256, 0, s>>>((const float4*)buf, n4, passes, nullptr);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e != cudaSuccess) rc = fail(DPF_E_CUDA, "dpf_read_bandwidth: %s", cudaGetErrorString(e));
+  else *gbs = (double)bytes * passes * reps / (ms * 1e-3) / 1e9;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 extern "C" int dpf_iterations_done(const dpf_workspace* w, int32_t* n_iter) {
@@ -1437,6 +1552,8 @@ static int solve_plain(const dpf_ybus* y, dpf_workspace* w, const dpf_batch* b, 
     one.status = b->status ? b->status + k : nullptr;
     one.max_mismatch = b->max_mismatch ? b->max_mismatch + k : nullptr;
     one.loss = b->loss ? b->loss + k : nullptr;
+    one.va_start = b->va_start;
+    one.vm_start = b->vm_start;
     TRY(dpf_solve_begin(y, w, &one, &po, s));
     while (w->t_done < po.max_iter) {
       TRY(dpf_solve_iterate(w, 1, s));
@@ -1525,7 +1642,7 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
   std::vector<int> lanes_c = {auto_lanes};
   if (auto_lanes >= 8) { lanes_c.push_back(auto_lanes / 2); lanes_c.push_back(auto_lanes / 4); }
   std::vector<int> pair_c = {0};
-  if (o->precision == DPF_FP32 && K >= 64) pair_c = {0, 1, 2, 3};
+  if ((o->precision == DPF_FP32 || o->precision == DPF_FP32R) && K >= 64) pair_c = {0, 1, 2, 3};
   // row blocks: the automatic choice and multiples of it
   dpf_solve_opts base = *o;
   base.max_iter = 2 * iters + 4 * std::max(1, o->check_every) + 8;

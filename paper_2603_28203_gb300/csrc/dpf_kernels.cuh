@@ -188,6 +188,14 @@ __device__ __forceinline__ float2 volt(float2 th, float2 vm) {
   const float m = vm.x + vm.y;
   return make_float2(m * c2, m * s2);
 }
+// The same, also returning the unit phasor u = e^{j theta} (V = |V| u).
+__device__ __forceinline__ float2 volt(float2 th, float2 vm, float2& u) {
+  float s, c;
+  sincosf(th.x, &s, &c);
+  u = make_float2(fmaf(-th.y, s, c), fmaf(th.y, c, s));
+  const float m = vm.x + vm.y;
+  return make_float2(m * u.x, m * u.y);
+}
 __device__ __forceinline__ double2 volt(double th, double vm) {
   double s, c;
   sincos(th, &s, &c);
@@ -667,6 +675,13 @@ template <class R> struct IterArgs {
   const double2* yft64;
   const double2* ytt64;
   double inv_m2_64;        // 2 / m in FP64
+  // refined FP32 iterations (DPF_FP32R): V holds dV = V - V_ref, the change
+  // of the voltages since the case's last FP64 test (or since 0 before its
+  // first); vref = V_ref rounded to FP32, irf = (I_ref, f_ref) with I_ref the
+  // FP64 current and f_ref the FP64 mismatch (dP, dQ; Q_calc at pv buses) at
+  // V_ref, rounded to FP32.  NULL otherwise.
+  const float2* vref;
+  const float4* irf;
   // optional outputs (evaluation entry points); NULL in the solve loop
   C* sbuf;   // S_calc
   C* cbuf;   // c = (2/m)(dP + j dQ)
@@ -721,7 +736,19 @@ __device__ __forceinline__ void stage_window(const float4* __restrict__ src, uns
 }
 
 // ---- forward: SpMV + power + mismatch + loss --------------------------------
-template <class R>
+// Refined FP32 epilogue (DPF_FP32R): with V = V_ref + dV and I = I_ref + Y dV,
+//   S - S_spec = f_ref + dV conj(I_ref) + V conj(Y dV),
+// so every FP32 rounding error scales with the change dV since the last FP64
+// test (or with the small f_ref), not with |Y_ii| |V|.  Returns (dP, dQ) at
+// pq buses, (dP, Q_calc) at pv buses; the caller masks by bus type.
+__device__ __forceinline__ float2 refined_mismatch(float2 dv, float2 e, float2 vr, float4 rf, float2& v) {
+  v = make_float2(vr.x + dv.x, vr.y + dv.y);
+  const float2 t0 = power_of(dv, make_float2(rf.x, rf.y));
+  const float2 t1 = power_of(v, e);
+  return make_float2(rf.z + (t0.x + t1.x), rf.w + (t0.y + t1.y));
+}
+
+template <class R, bool REF = false>
 __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -768,24 +795,35 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
       const size_t e = (size_t)i * Kp + k;
       const int ty = ys.ty[i];
       const size_t si = a.spec_per_case ? e : (size_t)i;
-      const C vi = staged ? Vsh[(size_t)i * 32] : V[e];
-      const R ps = a.pspec[si], qs = a.qspec[si];
+      // (refined mode: the gathered operand is dV, and I below is Y dV)
+      const C xi = staged ? Vsh[(size_t)i * 32] : V[e];
       C I = staged ? row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], Vsh) : row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], V + k);
       if (i == of) {
-        cfms(I, yff, vi);
+        cfms(I, yff, xi);
         cfms(I, yft, V[(size_t)ot * Kp + k]);
       } else if (i == ot) {
         cfms(I, yft, V[(size_t)of * Kp + k]);
-        cfms(I, ytt, vi);
+        cfms(I, ytt, xi);
       }
-      const C S = power_of(vi, I);
-      const R P = S.x, Q = S.y;
-      const R dP = (ty != BUS_SLACK) ? P - ps : R(0);
-      const R dQ = (ty == BUS_PQ) ? Q - qs : R(0);
+      C vi;
+      R dP, dQ, Q;
+      if constexpr (REF) {
+        const float2 d = refined_mismatch(xi, I, ld_stream(a.vref + e), ld_stream(a.irf + e), vi);
+        dP = (ty != BUS_SLACK) ? d.x : R(0);
+        dQ = (ty == BUS_PQ) ? d.y : R(0);
+        Q = d.y;
+      } else {
+        vi = xi;
+        const R ps = a.pspec[si], qs = a.qspec[si];
+        const C S = power_of(vi, I);
+        Q = S.y;
+        dP = (ty != BUS_SLACK) ? S.x - ps : R(0);
+        dQ = (ty == BUS_PQ) ? Q - qs : R(0);
+        if (a.sbuf) a.sbuf[e] = S;
+      }
       const R ca = a.inv_m2 * dP, cb = a.inv_m2 * dQ;
       a.W[e] = w_of(ca, cb, vi);
       if (ty == BUS_PV) st_stream(a.qpv + e, Q);
-      if (a.sbuf) a.sbuf[e] = mkc(P, Q);
       if (a.cbuf) a.cbuf[e] = mkc(ca, cb);
       acc = fmaT(dP, dP, fmaT(dQ, dQ, acc));
       const float am = fmaxf(fabsf((float)dP), fabsf((float)dQ));
@@ -813,20 +851,42 @@ __device__ __forceinline__ C conj_c_s(C w, C v, int ty, R ps, R qs, R qpv, R m_h
 // One optimiser step on a master value (Sec. 5.3's optimisers, PyTorch
 // semantics).  step = lr (bias-corrected lr / (1 - beta1^t) for Adam), isb =
 // 1 / sqrt(1 - beta2^t) (Adam); m, v are the per-element optimiser state.
+// The amount subtracted from x is returned in d (the step, which the refined
+// FP32 mode turns into the voltage change).
+template <class R, class M>
+__device__ __forceinline__ M opt_update(int opt, M x, R g, R& m, R& v, R b1, R b2, R step, R isb, R eps, R mom,
+                                        R alpha, R& d) {
+  if (opt == OPT_SGD) {
+    m = (mom != R(0)) ? madd_step(mom, m, g) : g;
+    d = step * m;
+  } else if (opt == OPT_RMSPROP) {
+    v = madd_step(alpha, v, ((R(1) - alpha) * g) * g);
+    d = div_step(step * g, sqrt_step(v) + eps);
+  } else {
+    m = madd_step(b1, m, (R(1) - b1) * g);
+    v = madd_step(b2, v, ((R(1) - b2) * g) * g);
+    d = div_step(step * m, madd_step(sqrt_step(v), isb, eps));
+  }
+  return msub(x, d);
+}
 template <class R, class M>
 __device__ __forceinline__ M opt_update(int opt, M x, R g, R& m, R& v, R b1, R b2, R step, R isb, R eps, R mom,
                                         R alpha) {
-  if (opt == OPT_SGD) {
-    m = (mom != R(0)) ? madd_step(mom, m, g) : g;
-    return msub(x, step * m);
-  }
-  if (opt == OPT_RMSPROP) {
-    v = madd_step(alpha, v, ((R(1) - alpha) * g) * g);
-    return msub(x, div_step(step * g, sqrt_step(v) + eps));
-  }
-  m = madd_step(b1, m, (R(1) - b1) * g);
-  v = madd_step(b2, v, ((R(1) - b2) * g) * g);
-  return msub(x, div_step(step * m, madd_step(sqrt_step(v), isb, eps)));
+  R d;
+  return opt_update(opt, x, g, m, v, b1, b2, step, isb, eps, mom, alpha, d);
+}
+
+// Refined FP32 mode: the change of V = |V| e^{j theta} over one step from the
+// step itself, accurate relative to the change (no difference of two rounded
+// voltages):  V' - V = u [|V| E + d|V| (1 + E)],  u = e^{j theta},
+// E = e^{j dth} - 1 = 2 s (-s + j c) with (s, c) = (sin, cos)(dth / 2).
+// (Written with the unit phasor, it stays exact where |V| passes near 0.)
+__device__ __forceinline__ float2 volt_change(float2 u, float m, float dth, float dm) {
+  float s, c;
+  sincosf(0.5f * dth, &s, &c);
+  const float ex = -2.f * s * s, ey = 2.f * s * c;
+  const float fx = fmaf(dm, 1.f + ex, m * ex), fy = fmaf(dm, ey, m * ey);
+  return make_float2(fmaf(u.x, fx, -(u.y * fy)), fmaf(u.x, fy, u.y * fx));
 }
 
 #ifndef DPF_ADJ_ROWS
@@ -841,11 +901,13 @@ template <class R> struct AdjRow {
   int i, ty;
   size_t e;
   C wi, vi, z;
+  C dv;       // refined FP32 mode: dV = V - V_ref before the step
+  C u;        // refined FP32 mode: e^{j theta} before the step (vi = |V| u)
   R ps, qs, qp, m1, v1, m2, v2;
   M th, vm;
 };
 
-template <class R, class YS, bool MIXED = false>
+template <class R, class YS, bool MIXED = false, bool REF = false>
 __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, AdjRow<R>& r, int i, int r1, int k,
                                          size_t Kp, bool grad_only) {
   r.live = false;
@@ -870,6 +932,9 @@ __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, Adj
   if constexpr (MIXED) {  // the FP64 voltage, rounded for the FP32 adjoint
     const double2 v = a.V64m[e];
     r.vi = mkc((R)v.x, (R)v.y);
+  } else if constexpr (REF) {  // V from the master (the V buffer holds dV)
+    r.dv = a.V[e];
+    r.vi = volt(r.th, r.vm, r.u);
   } else {
     r.vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
   }
@@ -900,7 +965,7 @@ __device__ __forceinline__ void adj_gather(const IterArgs<R>& a, const YS& ys, A
   }
 }
 
-template <class R, bool MIXED = false>
+template <class R, bool MIXED = false, bool REF = false>
 __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, bool grad_only, R step, R isb, R b1,
                                            R b2, R eps) {
   using C = typename Prec<R>::C;
@@ -917,18 +982,27 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
     return;
   }
   // optimiser step on theta (pv and pq buses) and on |V| (pq buses)
-  r.th = opt_update(a.opt, r.th, g_th, r.m1, r.v1, b1, b2, step, isb, eps, a.mom, a.alpha);
-  if (r.ty == BUS_PQ) r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha);
+  R d_th = R(0), d_vm = R(0);
+  const R vm_old = mwork(r.vm);
+  r.th = opt_update(a.opt, r.th, g_th, r.m1, r.v1, b1, b2, step, isb, eps, a.mom, a.alpha, d_th);
+  if (r.ty == BUS_PQ)
+    r.vm = opt_update(a.opt, r.vm, g_vm, r.m2, r.v2, b1, b2, step, isb, eps, a.mom, a.alpha, d_vm);
   st_stream(a.ms + e, ms_make(r.th, r.vm));
   mom_store(a.os + e, Mom<R>{r.m1, r.v1, r.m2, r.v2});
-  if constexpr (MIXED) a.V64m[e] = volt64(r.th, r.vm);  // FP64 voltage from the master (FP64 sincos)
-  else a.V[e] = volt(r.th, r.vm);
+  if constexpr (MIXED) {
+    a.V64m[e] = volt64(r.th, r.vm);  // FP64 voltage from the master (FP64 sincos)
+  } else if constexpr (REF) {        // dV grows by this step's change of V
+    const float2 dd = volt_change(r.u, vm_old, -d_th, -d_vm);
+    a.V[e] = make_float2(r.dv.x + dd.x, r.dv.y + dd.y);
+  } else {
+    a.V[e] = volt(r.th, r.vm);
+  }
 }
 
 #ifndef DPF_ADJ_MINB
 #define DPF_ADJ_MINB 4
 #endif
-template <class R, bool MIXED = false>
+template <class R, bool MIXED = false, bool REF = false>
 __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   using C = typename Prec<R>::C;
   using M = typename Prec<R>::M;
@@ -966,13 +1040,13 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
     AdjRow<R> rw[NR];
 #pragma unroll
     for (int u = 0; u < NR; ++u)
-      adj_load<R, YSmem<R>, MIXED>(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
+      adj_load<R, YSmem<R>, MIXED, REF>(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
       if (rw[u].live) adj_gather(a, ys, rw[u], k, Kp, of, ot, yff, yft, ytt);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
-      if (rw[u].live) adj_finish<R, MIXED>(a, rw[u], grad_only, step, isb, b1, b2, eps);
+      if (rw[u].live) adj_finish<R, MIXED, REF>(a, rw[u], grad_only, step, isb, b1, b2, eps);
   }
 }
 
@@ -1155,9 +1229,25 @@ __device__ __forceinline__ void fwd_epilogue(float2 vi, float2 I, int ty, float 
   mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);
 }
 
+// The same for the refined FP32 mode: dv = dV, e = Y dV (see refined_mismatch).
+__device__ __forceinline__ void fwd_epilogue_ref(float2 dv, float2 e, float2 vr, float4 rf, int ty, float inv_m2,
+                                                 float2& w, float& q, float& acc, float& mx) {
+  float2 v;
+  const float2 d = refined_mismatch(dv, e, vr, rf, v);
+  const float dP = (ty != BUS_SLACK) ? d.x : 0.f;
+  const float dQ = (ty == BUS_PQ) ? d.y : 0.f;
+  const float ca = inv_m2 * dP, cb = inv_m2 * dQ;
+  w = w_of(ca, cb, v);
+  q = d.y;
+  acc = fmaf(dP, dP, fmaf(dQ, dQ, acc));
+  const float am = fmaxf(fabsf(dP), fabsf(dQ));
+  mx = (am != am) ? __int_as_float(0x7f800000) : fmaxf(mx, am);
+}
+
 #ifndef DPF_FWD2_MINB
 #define DPF_FWD2_MINB 4
 #endif
+template <bool REF = false>
 __global__ void __launch_bounds__(256, DPF_FWD2_MINB) k_fwd2(IterArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -1187,9 +1277,14 @@ __global__ void __launch_bounds__(256, DPF_FWD2_MINB) k_fwd2(IterArgs<float> a) 
     for (int i = r0 + warp; i < r1; i += wpb) {
       const unsigned e = (unsigned)i * hKp + h0;  // pair index
       const int ty = ys.ty[i];
-      const float4 v = a.wlo ? Vs[(size_t)i * 32] : V[e];
-      float ps0, ps1, qs0, qs1;
-      if (a.spec_per_case) {
+      const float4 v = a.wlo ? Vs[(size_t)i * 32] : V[e];  // (refined mode: dV)
+      float ps0 = 0.f, ps1 = 0.f, qs0 = 0.f, qs1 = 0.f;
+      float4 vr, rf0, rf1;
+      if constexpr (REF) {
+        vr = ld_stream((const float4*)a.vref + e);
+        rf0 = ld_stream(a.irf + 2 * (size_t)e);
+        rf1 = ld_stream(a.irf + 2 * (size_t)e + 1);
+      } else if (a.spec_per_case) {
         const float2 pp = ((const float2*)a.pspec)[e], qq = ((const float2*)a.qspec)[e];
         ps0 = pp.x; ps1 = pp.y; qs0 = qq.x; qs1 = qq.y;
       } else {
@@ -1219,8 +1314,13 @@ __global__ void __launch_bounds__(256, DPF_FWD2_MINB) k_fwd2(IterArgs<float> a) 
       }
       float2 w0, w1;
       float q0, q1;
-      fwd_epilogue(vi0, I0, ty, ps0, qs0, a.inv_m2, w0, q0, acc0, mx0);
-      fwd_epilogue(vi1, I1, ty, ps1, qs1, a.inv_m2, w1, q1, acc1, mx1);
+      if constexpr (REF) {
+        fwd_epilogue_ref(vi0, I0, make_float2(vr.x, vr.y), rf0, ty, a.inv_m2, w0, q0, acc0, mx0);
+        fwd_epilogue_ref(vi1, I1, make_float2(vr.z, vr.w), rf1, ty, a.inv_m2, w1, q1, acc1, mx1);
+      } else {
+        fwd_epilogue(vi0, I0, ty, ps0, qs0, a.inv_m2, w0, q0, acc0, mx0);
+        fwd_epilogue(vi1, I1, ty, ps1, qs1, a.inv_m2, w1, q1, acc1, mx1);
+      }
       W[e] = make_float4(w0.x, w0.y, w1.x, w1.y);
       if (ty == BUS_PV) st_stream((float2*)a.qpv + e, make_float2(q0, q1));
     }
@@ -1232,6 +1332,7 @@ __global__ void __launch_bounds__(256, DPF_FWD2_MINB) k_fwd2(IterArgs<float> a) 
 }
 
 
+template <bool REF = false>
 __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -1264,7 +1365,8 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     }
     const float2 qp = (ty == BUS_PV) ? ld_stream((const float2*)a.qpv + e) : make_float2(0.f, 0.f);
     const float4 s0 = ld_stream(a.ms + 2 * (size_t)e), s1 = ld_stream(a.ms + 2 * (size_t)e + 1);
-    const float4 vv4 = ((const float4*)a.V)[e];  // current V of both cases (no second sincos)
+    // current V of both cases (no second sincos); refined mode: dV (V from the master)
+    const float4 vv4 = ((const float4*)a.V)[e];
     Mom<float> o0 = mom_load(a.os + 2 * (size_t)e), o1 = mom_load(a.os + 2 * (size_t)e + 1);
     float2 z0, z1;
     row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W + h0, z0, z1);
@@ -1288,30 +1390,55 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     }
     float2 th0 = ms_th(s0), th1 = ms_th(s1);
     float2 vm0 = ms_vm(s0), vm1 = ms_vm(s1);
-    const float2 v0 = make_float2(vv4.x, vv4.y), v1 = make_float2(vv4.z, vv4.w);
+    float2 u0, u1, v0, v1;
+    if constexpr (REF) {
+      v0 = volt(ms_th(s0), ms_vm(s0), u0);
+      v1 = volt(ms_th(s1), ms_vm(s1), u1);
+    } else {
+      v0 = make_float2(vv4.x, vv4.y);
+      v1 = make_float2(vv4.z, vv4.w);
+    }
     const float2 g0 = conj_c_s(make_float2(wi.x, wi.y), v0, ty, ps0, qs0, qp.x, a.m_half);
     const float2 g1 = conj_c_s(make_float2(wi.z, wi.w), v1, ty, ps1, qs1, qp.y, a.m_half);
     const float2 h0 = adj_h(g0, v0, z0), h1 = adj_h(g1, v1, z1);
     const float hr0 = h0.x, hi0 = h0.y, hr1 = h1.x, hi1 = h1.y;
     // optimiser step on theta (pv and pq buses); an inactive case keeps its state
-    if (q.on0) th0 = opt_update(a.opt, th0, -hi0, o0.m1, o0.v1, b1, b2, st0, ib0, eps, a.mom, a.alpha);
-    if (q.on1) th1 = opt_update(a.opt, th1, -hi1, o1.m1, o1.v1, b1, b2, st1, ib1, eps, a.mom, a.alpha);
+    float dth0 = 0.f, dth1 = 0.f, dvm0 = 0.f, dvm1 = 0.f;
+    const float m0 = mwork(vm0), m1 = mwork(vm1);
+    if (q.on0) th0 = opt_update(a.opt, th0, -hi0, o0.m1, o0.v1, b1, b2, st0, ib0, eps, a.mom, a.alpha, dth0);
+    if (q.on1) th1 = opt_update(a.opt, th1, -hi1, o1.m1, o1.v1, b1, b2, st1, ib1, eps, a.mom, a.alpha, dth1);
     if (ty == BUS_PQ) {  // and on |V| (pq buses)
-      if (q.on0) vm0 = opt_update(a.opt, vm0, div_step(hr0, mwork(vm0)), o0.m2, o0.v2, b1, b2, st0, ib0, eps, a.mom,
-                                  a.alpha);
-      if (q.on1) vm1 = opt_update(a.opt, vm1, div_step(hr1, mwork(vm1)), o1.m2, o1.v2, b1, b2, st1, ib1, eps, a.mom,
-                                  a.alpha);
+      if (q.on0) vm0 = opt_update(a.opt, vm0, div_step(hr0, m0), o0.m2, o0.v2, b1, b2, st0, ib0, eps, a.mom,
+                                  a.alpha, dvm0);
+      if (q.on1) vm1 = opt_update(a.opt, vm1, div_step(hr1, m1), o1.m2, o1.v2, b1, b2, st1, ib1, eps, a.mom,
+                                  a.alpha, dvm1);
     }
     st_stream(a.ms + 2 * (size_t)e, ms_make(th0, vm0));
     st_stream(a.ms + 2 * (size_t)e + 1, ms_make(th1, vm1));
     mom_store(a.os + 2 * (size_t)e, o0);
     mom_store(a.os + 2 * (size_t)e + 1, o1);
-    const float2 n0 = q.on0 ? volt(th0, vm0) : v0, n1 = q.on1 ? volt(th1, vm1) : v1;
-    ((float4*)a.V)[e] = make_float4(n0.x, n0.y, n1.x, n1.y);
+    if constexpr (REF) {  // dV grows by this step's change of V (an inactive case has a zero step)
+      const float2 d0 = volt_change(u0, m0, -dth0, -dvm0);
+      const float2 d1 = volt_change(u1, m1, -dth1, -dvm1);
+      ((float4*)a.V)[e] = make_float4(vv4.x + d0.x, vv4.y + d0.y, vv4.z + d1.x, vv4.w + d1.y);
+    } else {
+      const float2 n0 = q.on0 ? volt(th0, vm0) : v0, n1 = q.on1 ? volt(th1, vm1) : v1;
+      ((float4*)a.V)[e] = make_float4(n0.x, n0.y, n1.x, n1.y);
+    }
   }
 }
 
 // ---- FP64 convergence test --------------------------------------------------
+// Whether the test examines active case k: every case without a gate (cand
+// NULL), else the cases the gate admitted, plus -- with full_every > 0 (the
+// refined FP32 mode) -- every case whose step count is a multiple of
+// full_every, so that no case runs on one reference for long (its FP32
+// bookkeeping of dV drifts by a few 1e-9 per step).  The three test kernels
+// take the same decision from the same inputs.
+__device__ __forceinline__ bool examined(const int32_t* cand, const int32_t* iters, int full_every, int k) {
+  return !cand || cand[k] || (full_every > 0 && iters[k] % full_every == 0);
+}
+
 template <class M> struct Check64Args {
   int N, Kp, lanes, all_cases;
   const int32_t* __restrict__ rp;
@@ -1325,6 +1452,8 @@ template <class M> struct Check64Args {
   int spec_per_case;
   const int32_t* active;
   const int32_t* cand;  // NULL: every active case; else only cases with cand[k] = 1
+  const int32_t* iters;  // per-case step counts (full_every)
+  int full_every;        // > 0: also every case whose step count is a multiple of this
   const int32_t* of;
   const int32_t* ot;
   const double2* yff;
@@ -1334,6 +1463,13 @@ template <class M> struct Check64Args {
   unsigned long long* maxmis;
   double* loss64;
   const int32_t* n_active;
+  // refined FP32 mode, tests inside the loop: every examined case restarts its
+  // FP32 iterations from this test's FP64 values (vref, irf: see IterArgs;
+  // dv, the V buffer of the iterations, is set to 0)
+  int refresh;
+  float2* vref;
+  float4* irf;
+  float2* dv;
 };
 
 // V64 = |V| e^{j theta} from the master state (FP64 sincos).
@@ -1344,7 +1480,7 @@ __global__ void __launch_bounds__(1024) k_volt64(Check64Args<M> a) {
   if (!a.all_cases && *a.n_active == 0) return;
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
-  if (k >= a.Kp || !(a.all_cases || (a.active[k] && (!a.cand || a.cand[k])))) return;
+  if (k >= a.Kp || !(a.all_cases || (a.active[k] && examined(a.cand, a.iters, a.full_every, k)))) return;
   for (int i = mp.row0; i < a.N; i += mp.rstride) {
     const size_t e = (size_t)i * a.Kp + k;
     const auto s = a.ms[e];
@@ -1359,7 +1495,7 @@ __global__ void __launch_bounds__(1024) k_check64(Check64Args<M> a) {
   if (!a.all_cases && *a.n_active == 0) return;
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
-  const bool on = (k < a.Kp) && (a.all_cases || (a.active[k] && (!a.cand || a.cand[k])));
+  const bool on = (k < a.Kp) && (a.all_cases || (a.active[k] && examined(a.cand, a.iters, a.full_every, k)));
   double mx = 0.0, sq = 0.0;
   if (on) {
     int of = -1, ot = -1;
@@ -1396,6 +1532,11 @@ __global__ void __launch_bounds__(1024) k_check64(Check64Args<M> a) {
                                                  : fmax(fabs(dP), fabs(dQ));
       mx = fmax(mx, am);
       sq += dP * dP + dQ * dQ;
+      if (a.refresh) {
+        a.vref[e] = make_float2((float)vi.x, (float)vi.y);
+        a.irf[e] = make_float4((float)I.x, (float)I.y, (float)dP, (float)((ty == BUS_PV) ? Q : dQ));
+        a.dv[e] = make_float2(0.f, 0.f);
+      }
     }
   }
   case_max_sum_atomic(mx, sq, a.lanes, a.maxmis, a.loss64, a.Kp);
@@ -1409,6 +1550,8 @@ struct ApplyArgs {
   double tol, inv_m;
   int32_t* active;
   const int32_t* cand;
+  const int32_t* iters;
+  int full_every;
   int32_t* status;
   unsigned long long* maxmis;
   double* loss64;
@@ -1431,7 +1574,7 @@ __global__ void k_apply(ApplyArgs a) {
         a.out_loss[k] = L;
         if (a.active[k]) a.status[k] = (mx <= a.tol) ? CASE_CONVERGED : CASE_MAX_ITER;
         a.active[k] = 0;
-      } else if (a.active[k] && (!a.cand || a.cand[k]) && mx <= a.tol) {
+      } else if (a.active[k] && examined(a.cand, a.iters, a.full_every, k) && mx <= a.tol) {
         a.active[k] = 0;
         a.status[k] = CASE_CONVERGED;
         a.out_max[k] = mx;
@@ -1449,6 +1592,23 @@ __global__ void k_apply(ApplyArgs a) {
     int s = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += cnt[w];
     *a.n_active = s;
+  }
+}
+
+// Initial reference of the refined FP32 mode: V_ref = 0, I_ref = 0, so the
+// first iterations evaluate f = V conj(Y V) - S_spec like plain FP32 ones (the
+// V buffer holds dV = V) until the case's first FP64 test.  f_ref = -S_spec
+// (pv buses: Q_calc(V_ref) = 0).  p, q: FP32 specification, [N][Kp] if
+// per_case, else [N].
+__global__ void k_ref_init(const uint8_t* __restrict__ type, const float* __restrict__ p,
+                           const float* __restrict__ q, int per_case, int Kp, size_t n, float2* __restrict__ vref,
+                           float4* __restrict__ irf) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / Kp);
+    const int ty = type[i];
+    const size_t si = per_case ? e : (size_t)i;
+    vref[e] = make_float2(0.f, 0.f);
+    irf[e] = make_float4(0.f, 0.f, (ty != BUS_SLACK) ? -p[si] : 0.f, (ty == BUS_PQ) ? -q[si] : 0.f);
   }
 }
 
@@ -1502,8 +1662,9 @@ template <class R> struct InitArgs {
   const uint8_t* type;
   const double* vmset_grid;  // [N]
   const double* vms_t;       // [N][Kp] or NULL
-  const double* va_t;        // [N][Kp] or NULL
+  const double* va_t;        // [N][Kp] ([N] if shared_start) or NULL
   const double* vm_t;
+  int shared_start;          // 1: va_t / vm_t hold one state [N] for every case
   double va_slack;
   const double* p64;         // per-case spec (FP64, [N][Kp]) or NULL
   const double* q64;
@@ -1523,7 +1684,11 @@ __global__ void k_init(InitArgs<R> a) {
     const int ty = a.type[i];
     double th = 0.0, vm = 1.0;
     if (k < a.K) {
-      if (a.va_t) { th = a.va_t[e]; vm = a.vm_t[e]; }
+      if (a.va_t) {
+        const size_t si = a.shared_start ? (size_t)i : e;
+        th = a.va_t[si];
+        vm = a.vm_t[si];
+      }
       if (a.enforce_fixed || !a.va_t) {
         const double set = a.vms_t ? a.vms_t[e] : a.vmset_grid[i];
         if (ty != BUS_PQ) vm = set;

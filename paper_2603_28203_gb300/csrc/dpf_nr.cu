@@ -833,6 +833,7 @@ extern "C" int dpf_nr_solve(dpf_nr* h, const dpf_batch* b, const dpf_nr_opts* o,
   if (K <= 0 || K > h->max_case) return fail(DPF_E_INVALID, "dpf_nr_solve: n_case %d outside 1..%d", K, h->max_case);
   if (b->host_io) return fail(DPF_E_INVALID, "dpf_nr_solve: device pointers only (host_io = 0)");
   if (!b->va || !b->vm) return fail(DPF_E_INVALID, "dpf_nr_solve: va and vm are required");
+  if (b->va_start || b->vm_start) return fail(DPF_E_INVALID, "dpf_nr_solve: va_start / vm_start are not supported");
   if ((b->p_spec == nullptr) != (b->q_spec == nullptr))
     return fail(DPF_E_INVALID, "dpf_nr_solve: p_spec and q_spec are given together");
   if (precision != DPF_FP32 && precision != DPF_FP64)

@@ -222,12 +222,13 @@ def dpf_workspace_create(y: Ybus, max_case: int) -> Workspace:
 
 # ---- batched solve -----------------------------------------------------------
 def _batch_struct(n_case, host_io=False, p_spec=None, q_spec=None, vm_set=None, outage=None, va=None,
-                  vm=None, iters=None, status=None, max_mismatch=None, loss=None):
+                  vm=None, iters=None, status=None, max_mismatch=None, loss=None, va_start=None, vm_start=None):
     b = _abi.DpfBatch()
     b.n_case = int(n_case)
     b.host_io = 1 if host_io else 0
     for name, t in dict(p_spec=p_spec, q_spec=q_spec, vm_set=vm_set, outage=outage, va=va, vm=vm,
-                        iters=iters, status=status, max_mismatch=max_mismatch, loss=loss).items():
+                        iters=iters, status=status, max_mismatch=max_mismatch, loss=loss,
+                        va_start=va_start, vm_start=vm_start).items():
         setattr(b, name, _ptr(t))
     return b
 
@@ -296,6 +297,14 @@ def dpf_kernel_launches(ws: Workspace) -> int:
     n = C.c_int64()
     _check(lib().dpf_kernel_launches(ws.handle, C.byref(n)))
     return n.value
+
+
+def dpf_read_bandwidth(buf, reps: int = 20, stream=None) -> float:
+    """GB/s of the library's read probe over a device tensor (see include/dpf.h)."""
+    g = C.c_double()
+    _check(lib().dpf_read_bandwidth(_ptr(buf), int(buf.numel() * buf.element_size()), int(reps), C.byref(g),
+                                    _stream(stream)))
+    return g.value
 
 
 def dpf_iterations_done(ws: Workspace) -> int:

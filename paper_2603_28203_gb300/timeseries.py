@@ -19,12 +19,18 @@ initialisers of Newton solves.)
 
 With `checkpoint` (a directory), every solved window is saved as
 window_<first snapshot>.npz (its solutions, iterations, statuses, mismatches
-and losses); with `resume`, saved windows are loaded instead of solved, and
+and losses, and a fingerprint of what it was solved from: the window's
+injections, the precision, tolerance, test interval and optimiser settings,
+and whether its start was flat or the previous window's); with `resume`,
+saved windows are loaded instead of solved -- a file whose fingerprint
+differs from the one this call would solve is rejected (ValueError) -- and
 the last loaded window's solutions warm-start the next one, so an
 interrupted series continues where it stopped.
 """
 from __future__ import annotations
 
+import hashlib
+import json
 import os
 
 import numpy as np
@@ -36,6 +42,17 @@ TABLE3_T0 = dict(lr=0.03564, beta1=0.9802, beta2=0.9440, sched=_abi.SCHED_STEP, 
                  max_iter=1000)
 TABLE3_T1 = dict(lr=0.00027, beta1=0.7847, beta2=0.6624, sched=_abi.SCHED_PLATEAU, factor=0.8, patience=2,
                  threshold=0.0388, cooldown=4, max_iter=300)
+
+
+def _fingerprint(p, q, precision, tol, check_every, settings, first_newton, w0, window):
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(p.cpu().numpy()).tobytes())
+    h.update(np.ascontiguousarray(q.cpu().numpy()).tobytes())
+    h.update(json.dumps(dict(precision=int(precision), tol=float(tol), check_every=int(check_every),
+                             settings={k: settings[k] for k in sorted(settings)},
+                             newton=bool(first_newton is not None and w0 == 0), warm=w0 > 0,
+                             window=int(window)), sort_keys=True).encode())
+    return h.hexdigest()
 
 
 def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 96, precision=_abi.FP32,
@@ -72,10 +89,16 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
     for w0 in range(0, T, window):
         K = min(window, T - w0)
         path = os.path.join(checkpoint, f"window_{w0:06d}.npz") if checkpoint else None
+        settings = dict(TABLE3_T0 if w0 == 0 else TABLE3_T1)
+        settings.update((first if w0 == 0 else later) or {})
+        fp = _fingerprint(P[w0:w0 + K], Q[w0:w0 + K], precision, tol, check_every, settings, first_newton, w0,
+                          window) if path else None
         if resume and path and os.path.exists(path):
             with np.load(path) as z:
                 if z["va"].shape != (K, N):
                     raise ValueError(f"{path}: saved window has shape {z['va'].shape}, expected {(K, N)}")
+                if "fingerprint" not in z.files or str(z["fingerprint"]) != fp:
+                    raise ValueError(f"{path}: saved window was solved from other inputs or settings")
                 for k in out:
                     out[k][w0:w0 + K] = z[k]
             va[:K] = torch.as_tensor(out["va"][w0:w0 + K], device=dev)
@@ -83,8 +106,6 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
             continue
         p = P[w0:w0 + K].to(dev).contiguous()
         q = Q[w0:w0 + K].to(dev).contiguous()
-        settings = dict(TABLE3_T0 if w0 == 0 else TABLE3_T1)
-        settings.update((first if w0 == 0 else later) or {})
         opts = SolveOpts(precision=precision, check_every=check_every, tol=tol, flat_start=1 if w0 == 0 else 0,
                          **settings)
         dpf_solve_batch(y, ws, opts, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
@@ -99,6 +120,6 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
             out[k][w0:w0 + K] = v[:K].cpu().numpy()
         if path:
             tmp = path + ".tmp.npz"
-            np.savez(tmp, **{k: out[k][w0:w0 + K] for k in out})
+            np.savez(tmp, fingerprint=np.array(fp), **{k: out[k][w0:w0 + K] for k in out})
             os.replace(tmp, path)  # a window file is complete or absent
     return out

@@ -29,3 +29,27 @@ def test_dc_and_newton_byte_models_scale_with_the_cases():
     assert n2["fp64"] == 2 * n1["fp64"] and n2["fp32"] == 2 * n1["fp32"]
     assert n1["fp32"] < n1["fp64"]
     assert np.isclose(bench.dc_flops_per_iteration(2000, 7400, 1, 1), 2 * 7400 + 1999 * 15)
+
+
+def test_refined_byte_model_and_presets():
+    g, outages = bench._workload()
+    n_pv = int((g.bus_type == 1).sum())
+    n_pq = int((g.bus_type == 0).sum())
+    nnz = g.n_bus + 2 * g.n_branch
+    K = outages.size
+    f32, a32 = bench.algorithmic_bytes(g.n_bus, n_pv, n_pq, nnz, K)
+    f, a = bench.algorithmic_bytes(g.n_bus, n_pv, n_pq, nnz, K, refined=True)
+    # refined FP32: the forward pass reads V_ref (8) and (I_ref, f_ref) (16) per element instead of the
+    # shared P/Q; the adjoint moves the same bytes (dV in V's place)
+    assert f - f32 == K * 24 * g.n_bus - 8 * g.n_bus
+    assert a == a32
+    # the warm-started N-1 settings are solve options the binding and the oracle both accept
+    import dataclasses
+    from paper_2603_28203_gb300.dpf import SolveOpts
+    from paper_2603_28203_gb300.presets import N1_WARM, TABLE2
+    names = {fl.name for fl in dataclasses.fields(SolveOpts)}
+    assert set(N1_WARM) <= names and set(TABLE2) <= names
+    o = bench._oracle_dpf_options(3000)
+    assert (o.lr, o.beta1, o.beta2, o.eps, o.sched, o.threshold, o.max_iter, o.check_every) == \
+        (N1_WARM["lr"], N1_WARM["beta1"], N1_WARM["beta2"], N1_WARM["eps"], "plateau", N1_WARM["threshold"], 3000,
+         bench.CHECK_EVERY)
