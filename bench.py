@@ -8,9 +8,10 @@ correction.
 A step is one whole batched solve, inputs resident on the GPU: the base case
 (no outage) by the library's Newton-Raphson, then every N-1 case by Alg. 1
 started from the base case's solution (the warm start of Sec. 5.4.2),
-refined FP32 iterations (DPF_FP32R) with the FP64 convergence test every 25
-iterations and per-case early stopping at 1e-6 p.u., up to `--n1-budget`
-(3,000) iterations, optimiser settings presets.N1_WARM.  `value` counts only
+refined FP32 iterations (DPF_FP32R) with the FP64 convergence test every 50
+iterations (cases whose FP32 mismatch is within 5e-6 p.u.; every case every
+100 iterations) and per-case early stopping at 1e-6 p.u., up to
+`--n1-budget` (3,000) iterations, optimiser settings presets.N1_WARM.  `value` counts only
 the cases the FP64 test declares converged (max |f| <= 1e-6 p.u.), per
 second; the others are reported, not counted.  A solve takes ~0.4 s and moves
 ~1 GB per iteration-pair, far beyond the 129 MB L2 (no flush needed).
@@ -44,6 +45,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 ITERS_PER_SOLVE = 1000  # Table 2: maximum iterations of one DPF solve from the flat start
 N1_BUDGET = 3000        # iterations of one warm-started N-1 solve
+N1_CHECK_EVERY = 50     # FP64 test interval of the warm-started N-1 solve
+N1_GATE = 5e-6          # its FP32 gate: the refined FP32 mismatch is accurate far below this
 CHECK_EVERY = 25
 TOL = 1e-6
 LR = 1e-3               # flat-start FP32 iterations of the N-1 batch (Table 2 otherwise)
@@ -83,7 +86,7 @@ def _oracle_dpf_options(budget):
     return oracle.DPFOptions(lr=N1_WARM["lr"], beta1=N1_WARM["beta1"], beta2=N1_WARM["beta2"], eps=N1_WARM["eps"],
                              sched=sched, factor=N1_WARM["factor"], patience=N1_WARM["patience"],
                              threshold=N1_WARM["threshold"], cooldown=N1_WARM["cooldown"], max_iter=budget, tol=TOL,
-                             check_every=CHECK_EVERY)
+                             check_every=N1_CHECK_EVERY)
 
 
 def _oracle_case(args):
@@ -305,8 +308,8 @@ class N1Job:
                          vm=torch.zeros((1, self.N), dtype=torch.float64, device=dev),
                          status=torch.zeros(1, dtype=torch.int32, device=dev))
         self.res = _outputs(torch, self.K, self.N, dev)
-        self.opts = dpf.SolveOpts(precision=dpf.FP32R, tol=TOL, check_every=CHECK_EVERY, max_iter=budget,
-                                  flat_start=0, lanes=args.lanes or None, warps=args.warps or None,
+        self.opts = dpf.SolveOpts(precision=dpf.FP32R, tol=TOL, check_every=N1_CHECK_EVERY, gate=N1_GATE,
+                                  max_iter=budget, flat_start=0, lanes=args.lanes or None, warps=args.warps or None,
                                   row_blocks=args.row_blocks or None, pdl=0 if args.no_pdl else None, **N1_WARM)
         self.shape_by = "command line" if (args.lanes or args.warps or args.row_blocks) else \
             "library default" if args.no_autotune else "dpf_autotune"
@@ -339,7 +342,7 @@ class N1Job:
         with self.torch.cuda.stream(self.stream):
             d.dpf_solve_begin(self.y, self.ws, self.opts, stream=self.stream, n_case=self.K, outage=self.outage,
                               va_start=self.base["va"][0], vm_start=self.base["vm"][0])
-            d.dpf_solve_iterate(self.ws, CHECK_EVERY, stream=self.stream)
+            d.dpf_solve_iterate(self.ws, N1_CHECK_EVERY, stream=self.stream)
             d.dpf_profile_enable(self.ws, True)
             d.dpf_solve_iterate(self.ws, n_iter, stream=self.stream)
             t = d.dpf_kernel_times(self.ws, stream=self.stream)
@@ -433,7 +436,7 @@ def run_ours(args):
         subs["uneven"] = uneven_record(dpf, torch, args)
 
     if rank == 0:
-        ce = CHECK_EVERY
+        ce = N1_CHECK_EVERY
         line = {
             "metric": METRIC,
             "value": value,
@@ -453,7 +456,7 @@ def run_ours(args):
                             "+ per-case branch-removal correction; each case warm-started from the base case "
                             "(solved by Newton-Raphson in the same step)",
                 "n_bus": N, "n_branch": g.n_branch, "cases_per_gpu": int(K), "nnz": job.y.nnz,
-                "iteration_precision": "fp32r", "check_every": ce, "tol_pu": TOL,
+                "iteration_precision": "fp32r", "check_every": ce, "gate_pu": N1_GATE, "tol_pu": TOL,
                 "budget_iterations": args.n1_budget,
                 "optimizer": "Adam + ReduceLROnPlateau, presets.N1_WARM (searched, Sec. 5.3's procedure)",
                 "solve_definition": f"Alg. 1 from the base case's solution until FP64 max mismatch <= {TOL} p.u. "
@@ -609,6 +612,7 @@ def run_flat_fp32(dpf, torch, job, args, peak, l2):
         dpf.dpf_solve_batch(job.y, job.ws, dataclasses.replace(opts, max_iter=ITERS_PER_SOLVE), stream=s, n_case=K,
                             outage=job.outage, **r)
         s.synchronize()
+    barrier_us = dpf.dpf_grid_barrier_cost(4, 2000, stream=s)
     n_pv = int((g.bus_type == 1).sum())
     n_pq = int((g.bus_type == 0).sum())
     fwd_b, adj_b = algorithmic_bytes(N, n_pv, n_pq, job.y.nnz, K)
@@ -636,6 +640,12 @@ def run_flat_fp32(dpf, torch, job, args, peak, l2):
                          "pair_cases": opts.pair_cases, "stage_v": opts.stage_v},
         "after_table2_budget": {"iterations": ITERS_PER_SOLVE, "converged": int((st == 0).sum()),
                                 "mismatch_p50": float(np.median(mm)), "mismatch_max": float(mm.max())},
+        "persistent_launch": {
+            "grid_barrier_us": barrier_us, "ctas_per_sm": 4,
+            "pipelined_iteration_us": 1e3 * ms / n_it, "bracketed_fwd_plus_adj_us": 1e3 * (fa + aa),
+            "note": "one persistent kernel per iteration would replace the two programmatic-dependent launches by "
+                    "two grid-wide barriers (forward -> adjoint -> next forward); the pipelined pair already runs "
+                    "below the sum of the separately bracketed kernels"},
     }
 
 
@@ -962,6 +972,18 @@ def run_timeseries(args):
     prec = dict(fp32r=dpf.FP32R, fp32=dpf.FP32)[args.ts_precision]
     print(json.dumps({"workload": "timeseries", **timeseries_record(dpf, torch, args.ts_hours, newton=True,
                                                                       precision=prec)}), flush=True)
+
+
+def run_flat(args):
+    """--workload flat: the flat-start FP32 iteration rate of the N-1 batch
+    alone (the n1_flat_fp32 sub-record; one JSON line)."""
+    dpf, torch = _lib_for_workload()
+    g, outages = _workload()
+    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    job = N1Job(dpf, torch, g, outages, stream, args.n1_budget, args)
+    peak, _ = _peaks()
+    l2 = _l2_read_peak(dpf, torch, stream)
+    print(json.dumps({"workload": "flat", **run_flat_fp32(dpf, torch, job, args, peak, l2)}), flush=True)
 
 
 def run_c1batch(args):
@@ -1445,9 +1467,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10, help="timed steps (whole batched solves)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n1", choices=["n1", "scaling", "uneven", "timeseries", "paramid", "dc",
-                                                         "warmstart", "c1batch", "nr"],
-                    help="n1: the N-1 contingency batch (the benchmark line); scaling: node/edge sweep; "
+    ap.add_argument("--workload", default="n1", choices=["n1", "flat", "scaling", "uneven", "timeseries", "paramid",
+                                                         "dc", "warmstart", "c1batch", "nr"],
+                    help="n1: the N-1 contingency batch (the benchmark line); flat: its flat-start FP32 "
+                         "iteration rate alone; scaling: node/edge sweep; "
                          "uneven: 64-grid block-diagonal batch + parameter identification; "
                          "timeseries: the 10k-bus grid over a year of hourly snapshots; "
                          "paramid: branch identification against the oracle's operating points; "
@@ -1486,6 +1509,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "flat":
+        run_flat(args)
     elif args.workload == "scaling":
         run_scaling(args)
     elif args.workload == "uneven":

@@ -74,8 +74,9 @@ enum { DPF_PQ = 0, DPF_PV = 1, DPF_SLACK = 2 };            /* bus types (Sec. 2.
  * scales with dV instead of with |Y_ii| |V|, and the iterations reach
  * mismatches far below DPF_FP32's limit.  The FP64 test (every check_every
  * iterations, on the cases the gate admits, and on every active case at
- * every 4th test) renews f_ref, I_ref and V_ref.  Until a case's first test
- * its iterations equal DPF_FP32 ones. */
+ * the test of every 100th step -- or at every test if check_every > 50)
+ * renews f_ref, I_ref and V_ref.  Until a case's first test its iterations
+ * equal DPF_FP32 ones. */
 enum { DPF_FP32 = 0, DPF_FP64 = 1, DPF_MIXED = 2, DPF_FP32R = 3 };
 enum { DPF_SCHED_CONST = 0, DPF_SCHED_PLATEAU = 1, DPF_SCHED_STEP = 2 };
 enum { DPF_OPT_ADAM = 0, DPF_OPT_SGD = 1, DPF_OPT_RMSPROP = 2 };    /* Sec. 5.3's optimisers */
@@ -283,6 +284,16 @@ int dpf_kernel_launches(const dpf_workspace* ws, int64_t* n);
  * alignment, size, reps < 1), DPF_E_CUDA. */
 int dpf_read_bandwidth(const void* buf, int64_t bytes, int32_t reps, double* gbs, void* stream);
 
+/* Grid-barrier probe (a measurement hook; the paper has no counterpart): the
+ * cost of one grid-wide barrier in a persistent (cooperative) launch of
+ * num_SMs x ctas_per_sm CTAs of 256 threads -- the synchronisation a single
+ * persistent kernel would need between the forward and adjoint passes of an
+ * iteration.  Times a cooperative launch with `reps` barriers and one with
+ * none (CUDA events on `stream`); *us_per_barrier = their difference / reps.
+ * Synchronises `stream`.  Errors: DPF_E_INVALID (bad argument, or more CTAs
+ * per SM than can be resident), DPF_E_CUDA. */
+int dpf_grid_barrier_cost(int32_t ctas_per_sm, int32_t reps, double* us_per_barrier, void* stream);
+
 /* ---- forward evaluation (Eq. powerbalance) --------------------------------
  * The evaluation entry points take (va, vm) verbatim, set-points included.
  * S_calc = V (Y V)^* for n_case voltage vectors (case-major device arrays),
@@ -305,7 +316,9 @@ int dpf_power(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
  * the library holds until the process exits; n_case * n_bus above that limit
  * is rejected with DPF_E_INVALID.  The first call on a device looks up the
  * array's device address (once per device, with that device current); make
- * that first call before any stream capture.  All calls share the one array,
+ * that first call before any stream capture.  The address is kept for the
+ * life of the process: do not use this entry point on a device after a
+ * cudaDeviceReset (the reset destroys the context it belongs to).  All calls share the one array,
  * so calls whose work overlaps on the GPU (different streams, or host threads
  * without ordering) race: serialise them, e.g. on one stream.  The scratch
  * is fully rewritten by each call before it is read.  Inputs va, vm

@@ -14,7 +14,7 @@ from ._abi import (CASE_CONVERGED, CASE_DIVERGED, CASE_MAX_ITER, FP32, FP32R, FP
                    SCHED_PLATEAU, SCHED_STEP, SLACK)
 from .dpf import (DPFError, SolveOpts, Workspace, Ybus, dpf_active_count, dpf_adam_update, dpf_autotune, dpf_build_ybus,
                   dpf_build_ybus_host, dpf_default_opts, dpf_iterations_done, dpf_kernel_launches, dpf_kernel_times,
-                  dpf_last_error, dpf_profile_enable, dpf_read_bandwidth,
+                  dpf_last_error, dpf_profile_enable, dpf_read_bandwidth, dpf_grid_barrier_cost,
                   dpf_dc_solve, dpf_loss_backward, NewtonSolver, dpf_nr_analyze, dpf_nr_create, dpf_nr_pattern,
                   dpf_nr_solve, dpf_paramid_begin, dpf_paramid_step, dpf_power,
                   dpf_power_noalloc,

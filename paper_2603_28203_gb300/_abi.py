@@ -100,6 +100,7 @@ SIGNATURES = {
     "dpf_kernel_times": (C.c_int, [VP, p_f64, p_f64, p_i32, p_i32, VP]),
     "dpf_kernel_launches": (C.c_int, [VP, C.POINTER(C.c_int64)]),
     "dpf_read_bandwidth": (C.c_int, [VP, C.c_int64, C.c_int32, C.POINTER(C.c_double), VP]),
+    "dpf_grid_barrier_cost": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double), VP]),
     "dpf_adam_update": (C.c_int, [I32, VP, VP, VP, VP, VP, I32, C.c_double, C.c_double, C.c_double, C.c_double,
                                   VP]),
     "dpf_last_error": (C.c_char_p, []),

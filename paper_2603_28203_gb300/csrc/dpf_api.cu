@@ -1,6 +1,7 @@
 // CUDA part of libdpf: device copies of Y_bus, workspaces, launch
 // configuration, the batched solve (Alg. 1 for every case) and the
 // evaluation entry points (S_calc; loss + adjoint gradients).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -604,8 +605,10 @@ static Plan<R> make_plan(dpf_workspace* w) {
   c.active = w->active;
   c.cand = gated ? w->cand : nullptr;
   c.iters = w->iters;
-  // refined FP32: every 4th test also re-anchors the cases the gate keeps out
-  c.full_every = (gated && w->precision == DPF_FP32R) ? 4 * std::max(1, w->opts.check_every) : 0;
+  // refined FP32: the test at every 100th step (or every test, with longer
+  // intervals) also re-anchors the cases the gate keeps out
+  const int ce = std::max(1, w->opts.check_every);
+  c.full_every = (gated && w->precision == DPF_FP32R) ? std::max(ce, 100 / ce * ce) : 0;
   c.of = w->of;
   c.ot = w->ot;
   c.yff = w->yff64;
@@ -1461,6 +1464,50 @@ extern "C" int dpf_read_bandwidth(const void* buf, int64_t bytes, int32_t reps, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
+}
+
+// Grid-wide barrier probe: `reps` barriers of a cooperative grid (all CTAs
+// co-resident, guaranteed by the cooperative launch, which fails rather than
+// waits if they cannot be).
+__global__ void __launch_bounds__(256) k_barrier_probe(int reps, int* __restrict__ sink) {
+  cooperative_groups::grid_group g = cooperative_groups::this_grid();
+  for (int r = 0; r < reps; ++r) g.sync();
+  if (reps < 0 && threadIdx.x == 0) sink[blockIdx.x] = reps;  // never taken
+}
+
+extern "C" int dpf_grid_barrier_cost(int32_t ctas_per_sm, int32_t reps, double* us_per_barrier, void* stream) {
+  clear_error();
+  if (ctas_per_sm < 1 || reps < 1 || !us_per_barrier) return fail(DPF_E_INVALID, "dpf_grid_barrier_cost: bad argument");
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_barrier_probe, 256, 0));
+  if (occ < ctas_per_sm) return fail(DPF_E_INVALID, "dpf_grid_barrier_cost: at most %d CTAs per SM fit", occ);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = num_sms() * ctas_per_sm;
+  int* sink = nullptr;
+  cudaEvent_t e[4];
+  for (auto& x : e) CK(cudaEventCreate(&x));
+  int n0 = 0, n1 = reps;
+  void* a0[] = {&n0, &sink};
+  void* a1[] = {&n1, &sink};
+  cudaError_t err = cudaLaunchCooperativeKernel((const void*)k_barrier_probe, grid, 256, a1, 0, s);  // warm-up
+  float t0 = 0.f, t1 = 0.f;
+  if (err == cudaSuccess) {
+    cudaEventRecord(e[0], s);
+    err = cudaLaunchCooperativeKernel((const void*)k_barrier_probe, grid, 256, a0, 0, s);
+    cudaEventRecord(e[1], s);
+  }
+  if (err == cudaSuccess) {
+    cudaEventRecord(e[2], s);
+    err = cudaLaunchCooperativeKernel((const void*)k_barrier_probe, grid, 256, a1, 0, s);
+    cudaEventRecord(e[3], s);
+  }
+  if (err == cudaSuccess) err = cudaEventSynchronize(e[3]);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&t0, e[0], e[1]);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&t1, e[2], e[3]);
+  for (auto& x : e) cudaEventDestroy(x);
+  if (err != cudaSuccess) return fail(DPF_E_CUDA, "dpf_grid_barrier_cost: %s", cudaGetErrorString(err));
+  *us_per_barrier = 1e3 * (double)(t1 - t0) / reps;
+  return DPF_OK;
 }
 
 extern "C" int dpf_iterations_done(const dpf_workspace* w, int32_t* n_iter) {

@@ -764,14 +764,10 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   const int k = mp.k;
   const bool inb = k < a.Kp;
   const int act = inb ? a.active[k] : 0;
-  int of = -1, ot = -1;
-  C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
+  int of = -1, ot = -1;  // (the outaged branch's block is loaded at its two rows)
   if (inb && a.has_outage) {
     of = a.of[k];
     ot = a.ot[k];
-    yff = a.yff[k];
-    yft = a.yft[k];
-    ytt = a.ytt[k];
   }
   if (cta_idle(a.n_active)) {  // every CTA still counts itself for the scheduler
     if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
@@ -799,11 +795,11 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
       const C xi = staged ? Vsh[(size_t)i * 32] : V[e];
       C I = staged ? row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], Vsh) : row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], V + k);
       if (i == of) {
-        cfms(I, yff, xi);
-        cfms(I, yft, V[(size_t)ot * Kp + k]);
+        cfms(I, a.yff[k], xi);
+        cfms(I, a.yft[k], V[(size_t)ot * Kp + k]);
       } else if (i == ot) {
-        cfms(I, yft, V[(size_t)of * Kp + k]);
-        cfms(I, ytt, xi);
+        cfms(I, a.yft[k], V[(size_t)of * Kp + k]);
+        cfms(I, a.ytt[k], xi);
       }
       C vi;
       R dP, dQ, Q;
@@ -879,12 +875,24 @@ __device__ __forceinline__ M opt_update(int opt, M x, R g, R& m, R& v, R b1, R b
 // Refined FP32 mode: the change of V = |V| e^{j theta} over one step from the
 // step itself, accurate relative to the change (no difference of two rounded
 // voltages):  V' - V = u [|V| E + d|V| (1 + E)],  u = e^{j theta},
-// E = e^{j dth} - 1 = 2 s (-s + j c) with (s, c) = (sin, cos)(dth / 2).
-// (Written with the unit phasor, it stays exact where |V| passes near 0.)
+// E = e^{j dth} - 1 = (cos dth - 1) + j sin dth.  (Written with the unit
+// phasor, it stays exact where |V| passes near 0.)  Optimiser steps are
+// small: for |dth| <= 1/8 E comes from its Taylor series, cos x - 1 =
+// -x^2/2 + x^4/24 - x^6/720 and sin x = x - x^3/6 + x^5/120 - x^7/5040
+// (the first omitted terms are below 3e-11 relative), larger steps take
+// E = 2 s (-s + j c) with (s, c) = (sin, cos)(dth / 2).
 __device__ __forceinline__ float2 volt_change(float2 u, float m, float dth, float dm) {
-  float s, c;
-  sincosf(0.5f * dth, &s, &c);
-  const float ex = -2.f * s * s, ey = 2.f * s * c;
+  float ex, ey;
+  if (fabsf(dth) <= 0.125f) {
+    const float x2 = dth * dth;
+    ex = 0.5f * x2 * fmaf(x2, fmaf(x2, -1.f / 360.f, 1.f / 12.f), -1.f);
+    ey = dth * fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 5040.f, 1.f / 120.f), -1.f / 6.f), 1.f);
+  } else {
+    float s, c;
+    sincosf(0.5f * dth, &s, &c);
+    ex = -2.f * s * s;
+    ey = 2.f * s * c;
+  }
   const float fx = fmaf(dm, 1.f + ex, m * ex), fy = fmaf(dm, ey, m * ey);
   return make_float2(fmaf(u.x, fx, -(u.y * fy)), fmaf(u.x, fy, u.y * fx));
 }
@@ -932,9 +940,8 @@ __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, Adj
   if constexpr (MIXED) {  // the FP64 voltage, rounded for the FP32 adjoint
     const double2 v = a.V64m[e];
     r.vi = mkc((R)v.x, (R)v.y);
-  } else if constexpr (REF) {  // V from the master (the V buffer holds dV)
+  } else if constexpr (REF) {  // the V buffer holds dV; V comes from the master (adj_finish)
     r.dv = a.V[e];
-    r.vi = volt(r.th, r.vm, r.u);
   } else {
     r.vi = a.V[e];  // = volt(th, vm), stored by the previous update (no second sincos)
   }
@@ -952,16 +959,15 @@ __device__ __forceinline__ void adj_load(const IterArgs<R>& a, const YS& ys, Adj
 
 template <class R, class YS>
 __device__ __forceinline__ void adj_gather(const IterArgs<R>& a, const YS& ys, AdjRow<R>& r, int k, size_t Kp,
-                                           int of, int ot, typename Prec<R>::C yff, typename Prec<R>::C yft,
-                                           typename Prec<R>::C ytt) {
+                                           int of, int ot) {
   const int i = r.i;
   r.z = row_spmv<R>(ys, ys.rp[i], ys.rp[i + 1], a.W + k);
-  if (i == of) {
-    cfms(r.z, yff, r.wi);
-    cfms(r.z, yft, a.W[(size_t)ot * Kp + k]);
+  if (i == of) {  // the outaged branch's block, loaded at its two rows
+    cfms(r.z, a.yff[k], r.wi);
+    cfms(r.z, a.yft[k], a.W[(size_t)ot * Kp + k]);
   } else if (i == ot) {
-    cfms(r.z, yft, a.W[(size_t)of * Kp + k]);
-    cfms(r.z, ytt, r.wi);
+    cfms(r.z, a.yft[k], a.W[(size_t)of * Kp + k]);
+    cfms(r.z, a.ytt[k], r.wi);
   }
 }
 
@@ -970,6 +976,7 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
                                            R b2, R eps) {
   using C = typename Prec<R>::C;
   const size_t e = r.e;
+  if constexpr (REF) r.vi = volt(r.th, r.vm, r.u);  // (after the gather: fewer live registers across it)
   const C vi = r.vi, z = r.z;
   const C g0 = conj_c_s(r.wi, vi, r.ty, r.ps, r.qs, r.qp, a.m_half);
   const C h = adj_h(g0, vi, z);
@@ -1019,13 +1026,9 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
   const bool grad_only = (a.gva != nullptr);
   const int act = inb ? a.active[k] : 0;
   int of = -1, ot = -1;
-  C yff = mkc(R(0), R(0)), yft = yff, ytt = yff;
   if (inb && a.has_outage) {
     of = a.of[k];
     ot = a.ot[k];
-    yff = a.yff[k];
-    yft = a.yft[k];
-    ytt = a.ytt[k];
   }
   R step = 0, isb = 1;
   if (inb && !grad_only) { step = a.step_size[k]; isb = a.isbc2[k]; }
@@ -1043,7 +1046,7 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
       adj_load<R, YSmem<R>, MIXED, REF>(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
-      if (rw[u].live) adj_gather(a, ys, rw[u], k, Kp, of, ot, yff, yft, ytt);
+      if (rw[u].live) adj_gather(a, ys, rw[u], k, Kp, of, ot);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
       if (rw[u].live) adj_finish<R, MIXED, REF>(a, rw[u], grad_only, step, isb, b1, b2, eps);
@@ -1133,32 +1136,41 @@ struct Pair {
   int k0;
   bool on0, on1;
   int of0, ot0, of1, ot1;
-  float2 yff0, yft0, ytt0, yff1, yft1, ytt1;
 };
 
 // One round of independent loads: k0 is even and k0 + 1 < Kp (Kp is a
-// multiple of 64 here), so each two-case access is one aligned 8- or 16-byte
-// load.  The outage data is read whether or not a case has an outage (the
-// arrays span Kp; an unused entry never matches a row).
+// multiple of 64 here), so each two-case access is one aligned 8-byte load.
+// The outage rows are read whether or not a case has an outage (the arrays
+// span Kp; an unused entry never matches a row).  The outaged branch's 2x2
+// block is not kept in registers across the row loop: the two rows of a case
+// that need it load it there (out_block).
 __device__ __forceinline__ Pair load_pair(const IterArgs<float>& a, int k0) {
   Pair q;
   q.k0 = k0;
   const int2 act = *(const int2*)(a.active + k0);
   q.of0 = q.ot0 = q.of1 = q.ot1 = -1;
-  q.yff0 = q.yft0 = q.ytt0 = q.yff1 = q.yft1 = q.ytt1 = make_float2(0.f, 0.f);
   if (a.has_outage) {
     const int2 of = *(const int2*)(a.of + k0), ot = *(const int2*)(a.ot + k0);
-    const float4 ff = *(const float4*)(a.yff + k0), ft = *(const float4*)(a.yft + k0),
-                 tt = *(const float4*)(a.ytt + k0);
     q.of0 = of.x; q.of1 = of.y;
     q.ot0 = ot.x; q.ot1 = ot.y;
-    q.yff0 = make_float2(ff.x, ff.y); q.yff1 = make_float2(ff.z, ff.w);
-    q.yft0 = make_float2(ft.x, ft.y); q.yft1 = make_float2(ft.z, ft.w);
-    q.ytt0 = make_float2(tt.x, tt.y); q.ytt1 = make_float2(tt.z, tt.w);
   }
   q.on0 = act.x != 0;
   q.on1 = act.y != 0;
   return q;
+}
+
+// acc -= the outaged branch's block applied at row i of case k (i is that
+// case's from-bus `of` or to-bus `ot`): x_i is the case's own operand at row
+// i, x_o its operand at the branch's other end.
+__device__ __forceinline__ void out_block(const IterArgs<float>& a, int k, bool from, float2 x_i, float2 x_o,
+                                          float2& acc) {
+  if (from) {  // row f: Y_ff x_f + Y_ft x_t
+    cfms(acc, a.yff[k], x_i);
+    cfms(acc, a.yft[k], x_o);
+  } else {     // row t: Y_tf x_f + Y_tt x_t (Y_tf = Y_ft)
+    cfms(acc, a.yft[k], x_o);
+    cfms(acc, a.ytt[k], x_i);
+  }
 }
 
 // sum_p Y[p] X[offset(p)] for two adjacent cases (X as float4 pairs, already
@@ -1294,23 +1306,13 @@ __global__ void __launch_bounds__(256, DPF_FWD2_MINB) k_fwd2(IterArgs<float> a) 
       float2 I0, I1;
       row_spmv2(ys, ys.rp[i], ys.rp[i + 1], a.wlo ? Vs : V + h0, I0, I1);
       const float2 vi0 = make_float2(v.x, v.y), vi1 = make_float2(v.z, v.w);
-      if (i == q.of0) {
-        cfms(I0, q.yff0, vi0);
-        const float4 t = V[(unsigned)q.ot0 * hKp + h0];
-        cfms(I0, q.yft0, make_float2(t.x, t.y));
-      } else if (i == q.ot0) {
-        const float4 t = V[(unsigned)q.of0 * hKp + h0];
-        cfms(I0, q.yft0, make_float2(t.x, t.y));
-        cfms(I0, q.ytt0, vi0);
+      if (i == q.of0 || i == q.ot0) {
+        const float4 t = V[(unsigned)(i == q.of0 ? q.ot0 : q.of0) * hKp + h0];
+        out_block(a, q.k0, i == q.of0, vi0, make_float2(t.x, t.y), I0);
       }
-      if (i == q.of1) {
-        cfms(I1, q.yff1, vi1);
-        const float4 t = V[(unsigned)q.ot1 * hKp + h0];
-        cfms(I1, q.yft1, make_float2(t.z, t.w));
-      } else if (i == q.ot1) {
-        const float4 t = V[(unsigned)q.of1 * hKp + h0];
-        cfms(I1, q.yft1, make_float2(t.z, t.w));
-        cfms(I1, q.ytt1, vi1);
+      if (i == q.of1 || i == q.ot1) {
+        const float4 t = V[(unsigned)(i == q.of1 ? q.ot1 : q.of1) * hKp + h0];
+        out_block(a, q.k0 + 1, i == q.of1, vi1, make_float2(t.z, t.w), I1);
       }
       float2 w0, w1;
       float q0, q1;
@@ -1370,23 +1372,13 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
     Mom<float> o0 = mom_load(a.os + 2 * (size_t)e), o1 = mom_load(a.os + 2 * (size_t)e + 1);
     float2 z0, z1;
     row_spmv2(ys, ys.rp[i], ys.rp[i + 1], W + h0, z0, z1);
-    if (i == q.of0) {
-      cfms(z0, q.yff0, make_float2(wi.x, wi.y));
-      const float4 t = W[(unsigned)q.ot0 * hKp + h0];
-      cfms(z0, q.yft0, make_float2(t.x, t.y));
-    } else if (i == q.ot0) {
-      const float4 t = W[(unsigned)q.of0 * hKp + h0];
-      cfms(z0, q.yft0, make_float2(t.x, t.y));
-      cfms(z0, q.ytt0, make_float2(wi.x, wi.y));
+    if (i == q.of0 || i == q.ot0) {
+      const float4 t = W[(unsigned)(i == q.of0 ? q.ot0 : q.of0) * hKp + h0];
+      out_block(a, q.k0, i == q.of0, make_float2(wi.x, wi.y), make_float2(t.x, t.y), z0);
     }
-    if (i == q.of1) {
-      cfms(z1, q.yff1, make_float2(wi.z, wi.w));
-      const float4 t = W[(unsigned)q.ot1 * hKp + h0];
-      cfms(z1, q.yft1, make_float2(t.z, t.w));
-    } else if (i == q.ot1) {
-      const float4 t = W[(unsigned)q.of1 * hKp + h0];
-      cfms(z1, q.yft1, make_float2(t.z, t.w));
-      cfms(z1, q.ytt1, make_float2(wi.z, wi.w));
+    if (i == q.of1 || i == q.ot1) {
+      const float4 t = W[(unsigned)(i == q.of1 ? q.ot1 : q.of1) * hKp + h0];
+      out_block(a, q.k0 + 1, i == q.of1, make_float2(wi.z, wi.w), make_float2(t.z, t.w), z1);
     }
     float2 th0 = ms_th(s0), th1 = ms_th(s1);
     float2 vm0 = ms_vm(s0), vm1 = ms_vm(s1);
@@ -1431,10 +1423,10 @@ __global__ void __launch_bounds__(256, 4) k_adj2(IterArgs<float> a) {
 // ---- FP64 convergence test --------------------------------------------------
 // Whether the test examines active case k: every case without a gate (cand
 // NULL), else the cases the gate admitted, plus -- with full_every > 0 (the
-// refined FP32 mode) -- every case whose step count is a multiple of
-// full_every, so that no case runs on one reference for long (its FP32
-// bookkeeping of dV drifts by a few 1e-9 per step).  The three test kernels
-// take the same decision from the same inputs.
+// refined FP32 mode, ~100 steps) -- every case whose step count is a
+// multiple of full_every, so that no case runs on one reference for long
+// (with large steps its FP32 bookkeeping of dV drifts by a few 1e-9 per
+// step).  The three test kernels take the same decision from the same inputs.
 __device__ __forceinline__ bool examined(const int32_t* cand, const int32_t* iters, int full_every, int k) {
   return !cand || cand[k] || (full_every > 0 && iters[k] % full_every == 0);
 }

@@ -27,7 +27,10 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double2 g_noalloc_v[DPF_NOALLOC_MAX_ELEMS];
 
 // Device address of g_noalloc_v, one per device (host code cannot use the
-// symbol's name as a device pointer).
+// symbol's name as a device pointer).  Looked up on the first call on each
+// device and kept for the life of the process: a cudaDeviceReset destroys the
+// context the address belongs to, so the entry point must not be used on a
+// device after it has been reset.
 double2* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
@@ -96,7 +99,8 @@ extern "C" int dpf_power_noalloc(const dpf_ybus* y, int32_t n_case, const double
                      "dpf_power_noalloc: n_case * n_bus = %lld exceeds the fixed scratch of %d elements",
                      elems, DPF_NOALLOC_MAX_ELEMS);
   int dev = -1;
-  cudaGetDevice(&dev);
+  const cudaError_t ge = cudaGetDevice(&dev);
+  if (ge != cudaSuccess) return dpf::fail(DPF_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ge));
   if (dev != y->dev.device)
     return dpf::fail(DPF_E_STATE, "current device %d differs from the Y_bus device %d", dev, y->dev.device);
   double2* V = nullptr;

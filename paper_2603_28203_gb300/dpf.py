@@ -307,6 +307,13 @@ def dpf_read_bandwidth(buf, reps: int = 20, stream=None) -> float:
     return g.value
 
 
+def dpf_grid_barrier_cost(ctas_per_sm: int = 4, reps: int = 1000, stream=None) -> float:
+    """Microseconds per grid-wide barrier of a cooperative launch (see include/dpf.h)."""
+    us = C.c_double()
+    _check(lib().dpf_grid_barrier_cost(int(ctas_per_sm), int(reps), C.byref(us), _stream(stream)))
+    return us.value
+
+
 def dpf_iterations_done(ws: Workspace) -> int:
     n = C.c_int32()
     _check(lib().dpf_iterations_done(ws.handle, C.byref(n)))
@@ -314,9 +321,26 @@ def dpf_iterations_done(ws: Workspace) -> int:
 
 
 # ---- evaluation ----------------------------------------------------------------
+def _check_states(y: Ybus, *tensors):
+    """The per-case arrays of an evaluation call: float64 CUDA tensors of one
+    shape (K, n_bus) on one device, contiguous (the C ABI sees only K)."""
+    import torch
+    ref = tensors[0]
+    if ref.dim() != 2 or ref.shape[1] != y.n_bus or ref.shape[0] < 1:
+        raise ValueError(f"expected a (n_case, {y.n_bus}) array, got {tuple(ref.shape)}")
+    for t in tensors:
+        if t is None:
+            continue
+        if not torch.is_tensor(t) or t.dtype != torch.float64 or not t.is_cuda:
+            raise ValueError("per-case arrays must be float64 CUDA tensors")
+        if tuple(t.shape) != tuple(ref.shape) or t.device != ref.device or not t.is_contiguous():
+            raise ValueError("per-case arrays must share one contiguous (n_case, n_bus) shape and device")
+
+
 def dpf_power(y: Ybus, ws: Workspace, va, vm, outage=None, precision=_abi.FP32, stream=None):
     """(P_calc, Q_calc) [K][N] float64 CUDA tensors."""
     import torch
+    _check_states(y, va, vm)
     p = torch.empty_like(va)
     q = torch.empty_like(va)
     _check(lib().dpf_power(y.handle, ws.handle, int(va.shape[0]), _ptr(va), _ptr(vm), _ptr(outage),
@@ -330,6 +354,7 @@ def dpf_power_noalloc(y: Ybus, va, vm, p_calc, q_calc, stream=None):
     For callers that cannot allocate device memory (see include/dpf.h); the
     library's fixed scratch limits n_case * n_bus to NOALLOC_MAX_ELEMS.
     """
+    _check_states(y, va, vm, p_calc, q_calc)
     _check(lib().dpf_power_noalloc(y.handle, int(va.shape[0]), _ptr(va), _ptr(vm), _ptr(p_calc), _ptr(q_calc),
                                    _stream(stream)))
 

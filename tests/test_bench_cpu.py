@@ -52,4 +52,4 @@ def test_refined_byte_model_and_presets():
     o = bench._oracle_dpf_options(3000)
     assert (o.lr, o.beta1, o.beta2, o.eps, o.sched, o.threshold, o.max_iter, o.check_every) == \
         (N1_WARM["lr"], N1_WARM["beta1"], N1_WARM["beta2"], N1_WARM["eps"], "plateau", N1_WARM["threshold"], 3000,
-         bench.CHECK_EVERY)
+         bench.N1_CHECK_EVERY)

@@ -236,3 +236,48 @@ def test_c3_full_batch_in_the_benchmark_shape():
         assert np.abs(r["va"][k] - ref["va"]).max() <= 5e-3, k
         assert np.abs(r["vm"][k] - ref["vm"]).max() <= 5e-3, k
         assert abs(r["max_mismatch"][k] - ref["max_mismatch"]) <= 0.05 * ref["max_mismatch"], k
+
+
+@pytest.fixture(scope="module")
+def grid_1m():
+    """A generated 1,000,000-bus grid (1.35M branches, nnz 3.7M) and its
+    oracle Y_bus: the node-scaling sizes of Sec. 5.4.3."""
+    g = gridgen.make_grid(1_000_000, 9, load_scale=0.1)
+    return g, grid_ybus(g)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_million_bus_power_and_adjoint_against_oracle(grid_1m, precision):
+    """S_calc (dpf_power) and the loss with its voltage gradient
+    (dpf_loss_backward) on the 1,000,000-bus grid for two cases, element by
+    element against the oracle: FP64 kernels to 1e-10 of the largest
+    magnitude, FP32 kernels S within 1e-4 p.u. and gradients within 1e-4 of
+    the gradient's max-abs (the bars of the small-grid parity tests; the
+    kernels' per-element arithmetic does not depend on the grid's size).  The
+    FP64 loss is 1e-12 relative in both."""
+    g, Y = grid_1m
+    N, K = g.n_bus, 2
+    prec = dict(fp64=dpf.FP64, fp32=dpf.FP32)[precision]
+    rng = np.random.default_rng(17)
+    va = 0.05 * rng.standard_normal((K, N))
+    vm = 1.0 + 0.02 * rng.standard_normal((K, N))
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=DEV)
+    p, q = dpf.dpf_power(y, ws, t(va), t(vm), precision=prec)
+    out = dpf.dpf_loss_backward(y, ws, t(va), t(vm), precision=prec, want=("loss", "d_va", "d_vm"))
+    p, q = p.cpu().numpy(), q.cpu().numpy()
+    o = {k: v.cpu().numpy() for k, v in out.items()}
+    rel = 1e-10 if prec == dpf.FP64 else 1e-4
+    for k in range(K):
+        S = oracle.s_calc(Y, vm[k] * np.exp(1j * va[k]))
+        tol = 1e-10 * np.abs(S).max() if prec == dpf.FP64 else 1e-4
+        assert np.abs(p[k] - S.real).max() <= tol
+        assert np.abs(q[k] - S.imag).max() <= tol
+        L, d_va, d_vm = oracle.loss_grad(Y, va[k], vm[k], g.p_spec, g.q_spec, g.bus_type)
+        assert abs(o["loss"][k] - L) <= 1e-12 * L
+        sc = max(np.abs(d_va).max(), np.abs(d_vm).max())
+        assert np.abs(o["d_va"][k] - d_va).max() <= rel * sc
+        assert np.abs(o["d_vm"][k] - d_vm).max() <= rel * sc
+    ws.free()
+    y.free()

@@ -10,6 +10,8 @@ import numpy as np
 import pytest
 
 import gridgen
+import oracle
+from oracle.ybus import grid_ybus
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,6 +55,11 @@ def test_noalloc_matches_dpf_power_twice(name, K):
         scale = max(p_ref.abs().max().item(), q_ref.abs().max().item())
         assert (p - p_ref).abs().max().item() <= 1e-10 * scale
         assert (q - q_ref).abs().max().item() <= 1e-10 * scale
+        # and one case straight against the oracle's S = V (Y V)^*
+        k = K - 1
+        S = oracle.s_calc(grid_ybus(g), vm[k].cpu().numpy() * np.exp(1j * va[k].cpu().numpy()))
+        assert np.abs(p[k].cpu().numpy() - S.real).max() <= 1e-10 * scale
+        assert np.abs(q[k].cpu().numpy() - S.imag).max() <= 1e-10 * scale
 
 
 def test_noalloc_rejects_oversized_batch():
@@ -63,3 +70,9 @@ def test_noalloc_rejects_oversized_batch():
     with pytest.raises(dpf.DPFError) as e:
         dpf.dpf_power_noalloc(y, va, va, va.clone(), va.clone())
     assert e.value.code == -1 and "scratch" in str(e.value)
+    # outputs that do not match the inputs' shape or precision are refused before the call
+    small = torch.zeros((2, g.n_bus), dtype=torch.float64, device=DEV)
+    with pytest.raises(ValueError):
+        dpf.dpf_power_noalloc(y, small, small, torch.zeros((1, g.n_bus), dtype=torch.float64, device=DEV), small.clone())
+    with pytest.raises(ValueError):
+        dpf.dpf_power_noalloc(y, small, small, small.float(), small.clone())
