@@ -912,14 +912,20 @@ def run_scaling(args):
     import paper_2603_28203_gb300 as dpf
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
-    base = gridgen.make_grid(10_000, 1, load_scale=0.1)
-    grids = [("nodes", gridgen.make_grid(n, 1, load_scale=0.1)) for n in (10_000, 100_000, 1_000_000)]
-    grids += [("edges", gridgen.add_random_branches(base, m, 7)) for m in (5_000, 20_000, 80_000)]
+    sizes = [int(x) for x in args.scaling_sizes.split(",") if x]
+    extra = [int(x) for x in args.scaling_edges.split(",") if x]
+    grids = [("nodes", gridgen.make_grid(n, 1, load_scale=0.1)) for n in sizes]
+    if extra:
+        base = gridgen.make_grid(10_000, 1, load_scale=0.1)
+        grids += [("edges", gridgen.add_random_branches(base, m, 7)) for m in extra]
     for kind, g in grids:
         y = dpf.dpf_build_ybus(g, stream=stream)
         ws = dpf.dpf_workspace_create(y, 1)
-        opts = dpf.SolveOpts(lr=1e-3, precision=dpf.FP32, check_every=25, max_iter=10 ** 6)
+        opts = dpf.SolveOpts(lr=1e-3, precision=dpf.FP32, check_every=25, max_iter=10 ** 6,
+                             lanes=args.lanes or None, warps=args.warps or None, row_blocks=args.row_blocks or None)
         with torch.cuda.stream(stream):
+            if not (args.no_autotune or args.lanes or args.warps or args.row_blocks):
+                opts = dpf.dpf_autotune(y, ws, opts, iters=50, stream=stream, n_case=1)
             dpf.dpf_solve_begin(y, ws, opts, stream=stream, n_case=1)
             dpf.dpf_solve_iterate(ws, 50, stream=stream)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -930,6 +936,10 @@ def run_scaling(args):
             e1.record(stream)
             stream.synchronize()
             ms = e0.elapsed_time(e1) / n_it
+            dpf.dpf_profile_enable(ws, True)
+            dpf.dpf_solve_iterate(ws, 50, stream=stream)
+            f_ms, a_ms, nf, na = dpf.dpf_kernel_times(ws, stream=stream)
+            dpf.dpf_profile_enable(ws, False)
             # sampled parity of the forward evaluation against the oracle
             rng = np.random.default_rng(0)
             va = torch.tensor(0.05 * rng.standard_normal((1, g.n_bus)), dtype=torch.float64, device=dev)
@@ -944,6 +954,9 @@ def run_scaling(args):
         fwd_b, adj_b = algorithmic_bytes(g.n_bus, n_pv, n_pq, y.nnz, 1)
         print(json.dumps({"workload": "scaling", "kind": kind, "n_bus": g.n_bus, "n_branch": g.n_branch,
                           "nnz": y.nnz, "ms_per_iteration": ms, "us_per_iteration_per_1k_nnz": 1e3 * ms / (y.nnz / 1e3),
+                          "fwd_us": 1e3 * f_ms / max(nf, 1), "adj_us": 1e3 * a_ms / max(na, 1),
+                          "launch_shape": {"lanes": opts.lanes, "warps": opts.warps, "row_blocks": opts.row_blocks,
+                                           "stage_y": opts.stage_y},
                           "algorithmic_gbs": (fwd_b + adj_b) / (ms / 1e3) / 1e9,
                           "fp32_S_max_abs_error_vs_fp64_oracle": float(err)}), flush=True)
         ws.free()
@@ -1482,6 +1495,8 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--flat-iters", type=int, default=2000, help="timed flat-start FP32 iterations (sub-record)")
     ap.add_argument("--uneven-iters", type=int, default=300)
+    ap.add_argument("--scaling-sizes", default="10000,100000,1000000", help="bus counts of the node sweep")
+    ap.add_argument("--scaling-edges", default="5000,20000,80000", help="branches added to the 10k grid")
     ap.add_argument("--ts-hours", type=int, default=8760)
     ap.add_argument("--ts-precision", default="fp32r", choices=["fp32r", "fp32"])
     ap.add_argument("--warm-max-iter", type=int, default=50000)

@@ -212,6 +212,12 @@ typedef struct {
   int32_t dc_start;          /* 1 (with flat_start): the angles start from the
                                 DC approximation (dpf_dc_solve, relative
                                 residual 1e-10), |V| from the flat start    */
+  int32_t stage_y;           /* single-case FP32 / FP32R solves (lanes = 1):
+                                0 -- the passes read their Y_bus rows from
+                                global memory, one wave of CTAs each owning
+                                many rows (no reuse to stage for when every
+                                entry serves one case); 1 -- stage each row
+                                block's rows in shared memory like batches */
 } dpf_solve_opts;
 
 void dpf_default_opts(dpf_solve_opts* o);

@@ -51,7 +51,7 @@ class DpfSolveOpts(C.Structure):
         ("lanes", C.c_int32), ("warps", C.c_int32), ("row_blocks", C.c_int32),
         ("use_graph", C.c_int32), ("pair_cases", C.c_int32), ("pdl", C.c_int32), ("stage_v", C.c_int32),
         ("plain", C.c_int32),
-        ("dc_start", C.c_int32),
+        ("dc_start", C.c_int32), ("stage_y", C.c_int32),
     ]
 
 

@@ -292,6 +292,9 @@ struct dpf_workspace {
   bool staged = false;
   int ysmem = 0;
   bool pair_fwd = false, pair_adj = false;
+  bool direct = false;    // single-case FP32 solve: Y rows read from global memory (no staging)
+  int4* pent = nullptr;   // padded Y entries of the direct view
+  size_t cap_pent = 0;
   bool pid_ready = false;  // operating points staged by dpf_paramid_begin
   std::vector<std::pair<std::vector<long long>, std::vector<int>>> tune_cache;  // key -> (lanes, warps, rb, pairs)
   bool spec_per_case = false, has_outage = false;
@@ -321,6 +324,8 @@ static void ws_free_buffers(dpf_workspace* w) {
   dfree(w->dcs); dfree(w->dci);
   dfree(w->st_a); dfree(w->st_b); dfree(w->st_c);
   dfree(w->d_wlo); dfree(w->d_whi);
+  dfree(w->pent);
+  w->cap_pent = 0;
   w->cap_wblocks = 0;
   dfree(w->tile_cnt);
   w->cap_tiles = 0;
@@ -489,6 +494,7 @@ static Plan<R> make_plan(dpf_workspace* w) {
   const bool gated = (sizeof(R) == 4) && w->opts.gate > 0.0;
   a.prp = d.prow_ptr;
   a.ppos = d.ppos;
+  a.pent = w->pent;
   const int4* ent = w->use_local_y ? w->ent_loc : d.ent32;
   const double2* v64 = w->use_local_y ? w->val_loc : d.val64;
   if constexpr (sizeof(R) == 4) {
@@ -692,6 +698,8 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
   if constexpr (sizeof(R) == 4) {
     const bool ref = w->precision == DPF_FP32R;
     if (w->precision == DPF_MIXED) CK(launch(k_fwd_mixed, P.grid, P.block, P.smem, s, pdl, P.it));
+    else if (w->direct)
+      CK(launch(ref ? k_fwd<float, true, true> : k_fwd<float, false, true>, P.grid, P.block, 0, s, pdl, P.it));
     else if (w->pair_fwd) CK(launch(ref ? k_fwd2<true> : k_fwd2<false>, P.pgrid, P.block, P.smem, s, pdl, P.it));
     else CK(launch(ref ? k_fwd<float, true> : k_fwd<float, false>, P.grid, P.block, P.smem, s, pdl, P.it));
   } else {
@@ -701,6 +709,9 @@ static int launch_iteration(dpf_workspace* w, cudaStream_t s, bool with_check) {
   if constexpr (sizeof(R) == 4) {
     const bool ref = w->precision == DPF_FP32R;
     if (w->precision == DPF_MIXED) CK(launch(k_adj<float, true>, P.gridb, P.block, P.ysmem, s, pdl, P.itb));
+    else if (w->direct)
+      CK(launch(ref ? k_adj<float, false, true, true> : k_adj<float, false, false, true>, P.gridb, P.block, 0, s,
+                pdl, P.itb));
     else if (w->pair_adj) CK(launch(ref ? k_adj2<true> : k_adj2<false>, P.pgridb, P.block, P.ysmem, s, pdl, P.itb));
     else CK(launch(ref ? k_adj<float, false, true> : k_adj<float, false, false>, P.gridb, P.block, P.ysmem, s, pdl,
                    P.itb));
@@ -805,6 +816,8 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   const std::vector<int32_t>& prp = w->y->iprow_ptr;  // padded rows: the staged entries
   const std::vector<int32_t>& col = w->y->icol;
   const int prec = o ? o->precision : w->precision;
+  // a single-case FP32 solve reads its Y rows from global memory (no reuse to stage for)
+  w->direct = o && lanes == 1 && (prec == DPF_FP32 || prec == DPF_FP32R) && o->plain == 0 && o->stage_y == 0;
   const bool fp64 = prec == DPF_FP64;        // FP64 adjoint (and forward)
   const bool mixed = prec == DPF_MIXED;      // FP64 forward, FP32 adjoint
   const bool refined = prec == DPF_FP32R;    // FP32 iterations on FP64 references
@@ -812,6 +825,21 @@ static void choose_shape(dpf_workspace* w, const dpf_solve_opts* o, int K) {
   // bytes of one staged window row: the case tile's line of V (not in mixed mode)
   const bool stage_v = o && o->stage_v && !mixed;
   const int line = !stage_v ? 0 : w->pair_fwd ? 512 : (lanes == 32 ? 32 * (fp64 ? 16 : 8) : 0);
+  if (w->direct) {  // no staged rows: any row-block size fits
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_adj<float, false, false, true>,
+                                                  w->warps * 32, 0);
+    cudaGetLastError();
+    if (!(o && o->row_blocks > 0)) gy = std::min(gy_max, num_sms() * std::max(1, occ));
+    const int rpb = (n + gy - 1) / gy;
+    w->rpb = w->rpb_b = rpb;
+    w->gy = w->gy_b = (n + rpb - 1) / rpb;
+    w->ysmem = w->ysmem_b = w->smem = 0;
+    w->staged = false;
+    w->h_wlo.assign(w->gy, 0);
+    w->h_whi.assign(w->gy, 0);
+    return;
+  }
   // shrink row blocks until the staged Y rows (and the V window) fit
   for (int tries = 0;; ++tries) {
     const int rpb = (n + gy - 1) / gy;
@@ -1143,6 +1171,7 @@ static int validate_opts(const dpf_solve_opts* o) {
   if (!(o->gate >= 0.0)) return fail(DPF_E_INVALID, "gate must be >= 0");
   if (o->pdl != 0 && o->pdl != 1) return fail(DPF_E_INVALID, "pdl must be 0 or 1");
   if (o->dc_start != 0 && o->dc_start != 1) return fail(DPF_E_INVALID, "dc_start must be 0 or 1");
+  if (o->stage_y != 0 && o->stage_y != 1) return fail(DPF_E_INVALID, "stage_y must be 0 or 1");
   if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 8 || o->row_blocks < 0)
     return fail(DPF_E_INVALID, "invalid launch shape (lanes 0..32, warps 0..8, row_blocks >= 0)");
   return DPF_OK;
@@ -1325,6 +1354,18 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
     else
       k_dc_apply<float><<<nb, 256, 0, s>>>(w->tmp_a, (float4*)w->ms, (float2*)w->V, y->dev.type, y->n, w->K, w->Kp);
     if (w->precision == DPF_MIXED) k_mixed_v64<<<nb, 256, 0, s>>>((const float4*)w->ms, (double2*)w->V, E);
+    CKLAUNCH();
+  }
+  if (w->direct) {  // padded entries of the direct view
+    const size_t np = (size_t)y->iprow_ptr[y->n];
+    if (np > w->cap_pent) {
+      dfree(w->pent);
+      w->cap_pent = 0;
+      TRY(dalloc(&w->pent, np));
+      w->cap_pent = np;
+    }
+    const int nb = (int)std::min<size_t>((np + 255) / 256, (size_t)num_sms() * 16);
+    k_pad_entries<<<std::max(nb, 1), 256, 0, s>>>(y->dev.ppos, y->dev.ent32, (int)np, w->pent);
     CKLAUNCH();
   }
   if (w->precision == DPF_FP32R) {  // (after the DC start, which uses these buffers)
@@ -1682,6 +1723,7 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
       o->row_blocks = kv.second[2];
       o->pair_cases = kv.second[3];
       o->stage_v = kv.second[4];
+      o->stage_y = kv.second[5];
       return DPF_OK;
     }
   const int K = b->n_case;
@@ -1698,7 +1740,11 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
   base.row_blocks = 0;
   base.pair_cases = 0;
   base.stage_v = 0;
+  base.stage_y = 0;
   choose_shape(w, &base, K);
+  // single-case FP32 solves: global-memory or staged Y rows
+  std::vector<int> sy_c = {0};
+  if (auto_lanes == 1 && (o->precision == DPF_FP32 || o->precision == DPF_FP32R)) sy_c = {0, 1};
   const int gy_auto = w->gy;
   std::vector<int> rb_c = {0, gy_auto, 2 * gy_auto, 4 * gy_auto};  // 0: wave-aligned automatic choice
   cudaEvent_t e0, e1;
@@ -1711,7 +1757,8 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
     for (int pc : pair_c)
       for (int wp : {4, 8})
         for (int rb : rb_c)
-          for (int sv : {0, 1}) {
+          for (int sv : {0, 1})
+            for (int sy : sy_c) {
           if (pc && ln != 32) continue;
           if (sv && ln != 32) continue;
           dpf_solve_opts c = base;
@@ -1720,6 +1767,7 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
           c.warps = wp;
           c.row_blocks = rb;
           c.stage_v = sv;
+          c.stage_y = sy;
           if ((rc = dpf_solve_begin(y, w, b, &c, s)) != DPF_OK) break;
           const int ce = std::max(1, c.check_every);
           if ((rc = dpf_solve_iterate(w, ce, s)) != DPF_OK) break;  // warm-up, builds the graph
@@ -1746,7 +1794,9 @@ extern "C" int dpf_autotune(const dpf_ybus* y, dpf_workspace* w, const dpf_batch
   o->row_blocks = best.row_blocks;
   o->pair_cases = best.pair_cases;
   o->stage_v = best.stage_v;
-  w->tune_cache.push_back({key, {best.lanes, best.warps, best.row_blocks, best.pair_cases, best.stage_v}});
+  o->stage_y = best.stage_y;
+  w->tune_cache.push_back({key, {best.lanes, best.warps, best.row_blocks, best.pair_cases, best.stage_v,
+                                 best.stage_y}});
   return DPF_OK;
 }
 

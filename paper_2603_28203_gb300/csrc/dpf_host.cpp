@@ -381,4 +381,5 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->pdl = 1;
   o->plain = 0;
   o->dc_start = 0;
+  o->stage_y = 0;
 }

@@ -395,6 +395,32 @@ template <> struct YSmem<double> {
   }
 };
 
+// Single-case solves (one case per thread, Kp = 1): each Y_bus entry is used
+// by exactly one thread, so staging the rows in shared memory buys no reuse
+// and costs a round trip and a barrier per CTA.  This view reads the padded
+// rows straight from global memory (entries {col, re bits, im bits, 0}, the
+// pads pointing at their own row with weight 0, built per solve by
+// k_pad_entries), so a CTA can own many rows and the grid one wave.
+struct YDirect {
+  const int* rp;      // padded row pointers, indexed by global row
+  const int4* ent;
+  const uint8_t* ty;
+  __device__ __forceinline__ void get(int p, unsigned& o, float2& y) const {
+    const int4 e = __ldg(ent + p);
+    o = (unsigned)e.x;
+    y = make_float2(__int_as_float(e.y), __int_as_float(e.z));
+  }
+  // Before the wait for the predecessor kernel (Y_bus does not change during
+  // a solve): the thread's first row's entries and bus type toward L1, which
+  // the staged view gets by staging before the wait.
+  __device__ __forceinline__ void prefetch_row(int i, int r1) const {
+    if (i >= r1) return;
+    const int q0 = __ldg(rp + i);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ent + q0));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(ty + i));
+  }
+};
+
 // acc_row = sum_p Y[p] * X[offset(p)] over the row's padded entries [p0, p1)
 // (X already points at this thread's case).  Four entries per step, so four
 // independent gathers are in flight per thread; a pad adds an exact zero.
@@ -634,6 +660,7 @@ template <class R> struct IterArgs {
   int N, Kp, lanes, rpb;
   const int32_t* __restrict__ prp;   // padded row pointers (rows of 4k entries)
   const int32_t* __restrict__ ppos;  // padded slot -> CSR position, -(row+1) for a pad
+  const int4* __restrict__ pent;     // padded entries in global memory (single-case direct view)
   YView<R> Y;
   const int32_t* wlo;  // per row block: first and last row its nonzeros reference
   const int32_t* whi;  //   (NULL: neighbour gathers read global memory)
@@ -748,17 +775,11 @@ __device__ __forceinline__ float2 refined_mismatch(float2 dv, float2 e, float2 v
   return make_float2(rf.z + (t0.x + t1.x), rf.w + (t0.y + t1.y));
 }
 
-template <class R, bool REF = false>
-__global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
+// The forward pass after its Y rows are in place (staged or direct).
+template <class R, bool REF, class YS>
+__device__ __forceinline__ void fwd_body(const IterArgs<R>& a, const YS& ys, const BMap& mp, bool staged,
+                                         unsigned char* smem) {
   using C = typename Prec<R>::C;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const BMap mp = block_map(a.lanes, a.N, a.rpb);
-  // window of V in shared memory (lanes = 32: one 32-case line per row)
-  const bool staged = a.wlo && a.lanes == 32 && mp.r0 < mp.r1;
-  YSmem<R> ys;
-  ys.stage(a.prp, a.ppos, a.Y, a.type, mp.r0, mp.r1, staged ? 32u : (unsigned)a.Kp, smem);
-  pdl_wait();
-  pdl_release();
   // the case's data in one round of independent loads, in flight during the
   // idle test (the outage arrays span Kp; an unused entry never matches a row)
   const int k = mp.k;
@@ -828,6 +849,27 @@ __global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
   }
   if (a.loss_part || a.mx32) case_sum_max_atomic(acc, mx, a.lanes, a.loss_part, a.mx32, a.Kp);
   if (a.tile_cnt) tile_sched(a.sc, a.tile_cnt, a.lanes);
+}
+
+template <class R, bool REF = false, bool DIRECT = false>
+__global__ void __launch_bounds__(256, 5) k_fwd(IterArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BMap mp = block_map(a.lanes, a.N, a.rpb);
+  if constexpr (DIRECT) {
+    const YDirect ys{a.prp, a.pent, a.type};
+    ys.prefetch_row(mp.i0, mp.r1);
+    pdl_wait();
+    pdl_release();
+    fwd_body<R, REF>(a, ys, mp, false, smem);
+  } else {
+    // window of V in shared memory (lanes = 32: one 32-case line per row)
+    const bool staged = a.wlo && a.lanes == 32 && mp.r0 < mp.r1;
+    YSmem<R> ys;
+    ys.stage(a.prp, a.ppos, a.Y, a.type, mp.r0, mp.r1, staged ? 32u : (unsigned)a.Kp, smem);
+    pdl_wait();
+    pdl_release();
+    fwd_body<R, REF>(a, ys, mp, staged, smem);
+  }
 }
 
 // conj(c_i) S_i rebuilt from w_i = c_i conj(V_i):  c = w V / |V|^2;
@@ -1009,16 +1051,10 @@ __device__ __forceinline__ void adj_finish(const IterArgs<R>& a, AdjRow<R>& r, b
 #ifndef DPF_ADJ_MINB
 #define DPF_ADJ_MINB 4
 #endif
-template <class R, bool MIXED = false, bool REF = false>
-__global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
+// The adjoint pass after its Y rows are in place (staged or direct).
+template <class R, bool MIXED, bool REF, class YS>
+__device__ __forceinline__ void adj_body(const IterArgs<R>& a, const YS& ys, const BMap& mp) {
   using C = typename Prec<R>::C;
-  using M = typename Prec<R>::M;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const BMap mp = block_map(a.lanes, a.N, a.rpb);
-  YSmem<R> ys;
-  ys.stage(a.prp, a.ppos, a.Y, a.type, mp.r0, mp.r1, (unsigned)a.Kp, smem);
-  pdl_wait();
-  pdl_release();
   // the case's data in one round of independent loads, in flight during the
   // idle test (the outage arrays span Kp; an unused entry never matches a row)
   const int k = mp.k;
@@ -1043,13 +1079,49 @@ __global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
     AdjRow<R> rw[NR];
 #pragma unroll
     for (int u = 0; u < NR; ++u)
-      adj_load<R, YSmem<R>, MIXED, REF>(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
+      adj_load<R, YS, MIXED, REF>(a, ys, rw[u], i0 + u * mp.istride, mp.r1, k, Kp, grad_only);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
       if (rw[u].live) adj_gather(a, ys, rw[u], k, Kp, of, ot);
 #pragma unroll
     for (int u = 0; u < NR; ++u)
       if (rw[u].live) adj_finish<R, MIXED, REF>(a, rw[u], grad_only, step, isb, b1, b2, eps);
+  }
+}
+
+template <class R, bool MIXED = false, bool REF = false, bool DIRECT = false>
+__global__ void __launch_bounds__(256, DPF_ADJ_MINB) k_adj(IterArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BMap mp = block_map(a.lanes, a.N, a.rpb);
+  if constexpr (DIRECT) {
+    const YDirect ys{a.prp, a.pent, a.type};
+    ys.prefetch_row(mp.i0, mp.r1);
+    pdl_wait();
+    pdl_release();
+    adj_body<R, MIXED, REF>(a, ys, mp);
+  } else {
+    YSmem<R> ys;
+    ys.stage(a.prp, a.ppos, a.Y, a.type, mp.r0, mp.r1, (unsigned)a.Kp, smem);
+    pdl_wait();
+    pdl_release();
+    adj_body<R, MIXED, REF>(a, ys, mp);
+  }
+}
+
+// Padded entries of the direct view: slot p of the padded rows gets its
+// CSR entry {col, re, im}, a pad {row, 0, 0} (weight 0 on its own row).
+__global__ void k_pad_entries(const int32_t* __restrict__ ppos, const int4* __restrict__ ent, int n_pad,
+                              int4* __restrict__ pent) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += gridDim.x * blockDim.x) {
+    const int pos = ppos[p];
+    int4 e;
+    if (pos >= 0) {
+      e = ent[pos];
+      e.w = 0;
+    } else {
+      e = make_int4(ysmem_pad_row(pos), 0, 0, 0);
+    }
+    pent[p] = e;
   }
 }
 

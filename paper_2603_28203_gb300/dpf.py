@@ -180,6 +180,7 @@ class SolveOpts:
     stage_v: int | None = None
     plain: int | None = None
     dc_start: int | None = None
+    stage_y: int | None = None
 
     def to_c(self) -> _abi.DpfSolveOpts:
         o = _abi.DpfSolveOpts()
@@ -261,8 +262,8 @@ def dpf_autotune(y: Ybus, ws: Workspace, opts=None, iters: int = 25, stream=None
     _check(lib().dpf_autotune(y.handle, ws.handle, C.byref(b), C.byref(o), int(iters), _stream(stream)))
     out = SolveOpts(**{f.name: getattr(opts, f.name) for f in dataclasses.fields(SolveOpts)}) \
         if isinstance(opts, SolveOpts) else SolveOpts()
-    out.lanes, out.warps, out.row_blocks, out.pair_cases, out.stage_v = (o.lanes, o.warps, o.row_blocks,
-                                                                        o.pair_cases, o.stage_v)
+    out.lanes, out.warps, out.row_blocks, out.pair_cases, out.stage_v, out.stage_y = (
+        o.lanes, o.warps, o.row_blocks, o.pair_cases, o.stage_v, o.stage_y)
     return out
 
 

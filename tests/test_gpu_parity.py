@@ -480,3 +480,28 @@ def test_mixed_n1_batch_against_oracle():
                                oracle.DPFOptions(lr=1e-3, max_iter=60, check_every=10), va_slack=g.va_slack)
         assert np.abs(r["va"][k] - ref["va"]).max() <= 5e-3
         assert np.abs(r["vm"][k] - ref["vm"]).max() <= 5e-3
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32r"])
+def test_single_case_direct_rows_match_staged(precision):
+    """A single-case FP32 solve reads its Y_bus rows straight from global
+    memory (one wave of CTAs, no shared-memory staging); a batch of two runs
+    the staged kernels.  With a constant rate (no loss-dependent schedule,
+    whose sum order follows the row blocks) case 0 of the pair and the single
+    case take identical steps: same iterates to the bit."""
+    g = GRIDS["g300"]()
+    prec = dict(fp32=dpf.FP32, fp32r=dpf.FP32R)[precision]
+    opts = dpf.SolveOpts(precision=prec, max_iter=200, check_every=10, lr=1e-3, sched=dpf.SCHED_CONST)
+    y = dpf.dpf_build_ybus(g)
+    ws1 = dpf.dpf_workspace_create(y, 1)
+    ws2 = dpf.dpf_workspace_create(y, 2)
+    a = _solve(y, ws1, 1, opts)
+    b = _solve(y, ws2, 2, opts)
+    assert np.array_equal(a["va"][0], b["va"][0]) and np.array_equal(a["vm"][0], b["vm"][0])
+    assert a["iters"][0] == b["iters"][0] and a["max_mismatch"][0] == b["max_mismatch"][0]
+    c = _solve(y, ws1, 1, dpf.SolveOpts(stage_y=1, **{f: getattr(opts, f) for f in
+                                                      ("precision", "max_iter", "check_every", "lr", "sched")}))
+    assert np.array_equal(a["va"], c["va"]) and np.array_equal(a["vm"], c["vm"])
+    Y = grid_ybus(g)
+    f, _ = oracle.mismatch(Y, a["va"][0], a["vm"][0], g.p_spec, g.q_spec, g.bus_type)
+    assert abs(np.abs(f).max() - a["max_mismatch"][0]) <= 1e-12 * np.abs(f).max()
