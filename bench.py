@@ -11,7 +11,7 @@ started from the base case's solution (the warm start of Sec. 5.4.2),
 refined FP32 iterations (DPF_FP32R) with the FP64 convergence test every 50
 iterations (cases whose FP32 mismatch is within 5e-6 p.u.; every case every
 100 iterations) and per-case early stopping at 1e-6 p.u., up to
-`--n1-budget` (3,000) iterations, optimiser settings presets.N1_WARM.  `value` counts only
+`--n1-budget` (4,000) iterations, optimiser settings presets.N1_WARM.  `value` counts only
 the cases the FP64 test declares converged (max |f| <= 1e-6 p.u.), per
 second; the others are reported, not counted.  A solve takes ~0.4 s and moves
 ~1 GB per iteration-pair, far beyond the 129 MB L2 (no flush needed).
@@ -44,7 +44,7 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 ITERS_PER_SOLVE = 1000  # Table 2: maximum iterations of one DPF solve from the flat start
-N1_BUDGET = 3000        # iterations of one warm-started N-1 solve
+from paper_2603_28203_gb300.presets import N1_BUDGET  # iterations of one warm-started N-1 solve  # noqa: E402
 N1_CHECK_EVERY = 50     # FP64 test interval of the warm-started N-1 solve
 N1_GATE = 5e-6          # its FP32 gate: the refined FP32 mismatch is accurate far below this
 CHECK_EVERY = 25
