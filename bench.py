@@ -1072,8 +1072,9 @@ def run_paramid(args):
     with torch.cuda.stream(stream):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        pid_prec = dict(fp32=dpf.FP32, fp64=dpf.FP64)[args.pid_precision]
         g, b, hist = identify_branches(y, ws, t(va), t(vm), t(P), t(Q), g0, b0, n, lr=args.pid_lr,
-                                       precision=dpf.FP32, record_every=max(1, n // 4), stream=stream)
+                                       precision=pid_prec, record_every=max(1, n // 4), stream=stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         out0 = dpf.dpf_loss_backward(y, ws, t(va), t(vm), t(P), t(Q), g_series=g0, b_series=b0,
@@ -1095,7 +1096,7 @@ def run_paramid(args):
                    "hours_with_a_solution": f"{int(ok.sum())} of the first {H}",
                    "measurements": "FP64 oracle Newton-Raphson at the true parameters",
                    "perturbation": "r, x x U(0.9, 1.1) per branch (seed 5)",
-                   "steps": n, "lr": args.pid_lr, "precision": "fp32 adjoint, FP64 loss"},
+                   "steps": n, "lr": args.pid_lr, "precision": f"{args.pid_precision} forward and adjoint, FP64 loss"},
         "oracle_nr_s": t_nr,
         "error_before": stats(z0), "error_after": stats(z1),
         "loss_fp64_before": float(out0["loss"].sum()), "loss_fp64_after": float(out1["loss"].sum()),
@@ -1506,6 +1507,7 @@ def main():
     ap.add_argument("--pid-grids", type=int, default=16)
     ap.add_argument("--pid-steps", type=int, default=4000)
     ap.add_argument("--pid-lr", type=float, default=3e-3)
+    ap.add_argument("--pid-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--uneven-pid-steps", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)

@@ -236,3 +236,39 @@ def test_refined_option_checks():
         dpf.dpf_power(y, ws, va, va + 1, precision=dpf.FP32R)
     with pytest.raises(dpf.DPFError):
         dpf.dpf_loss_backward(y, ws, va, va + 1, precision=dpf.FP32R)
+
+
+def test_300_bus_n1_converged_cases_within_state_bar():
+    """A 300-bus grid (seed 3; ||J^-1||_inf ~130), every N-1 case started from
+    the base case (oracle-independent: the library's Newton-Raphson), refined
+    FP32 at the tighter tolerance 1e-7 p.u. (which implies the 1e-6 bar), the
+    warm-start settings, 10,000 iterations.  Every converged case (at least 3)
+    has its reported FP64 mismatch equal to the oracle's recomputation and
+    |V| within 1e-5 p.u., theta within 1e-5 rad of the oracle's Newton
+    solution of that case: the target's state bars, met here at 1e-7 (at
+    1e-6 the residual's first-order image reaches ~7e-5 on this grid)."""
+    g = gridgen.make_grid(300, 3, load_scale=0.1)
+    outs = gridgen.n1_outages(g).astype(np.int32)
+    K, N = outs.size, g.n_bus
+    y = dpf.dpf_build_ybus(g)
+    nrh = dpf.dpf_nr_create(y, 1)
+    bva = torch.zeros((1, N), dtype=torch.float64, device=DEV)
+    bvm = torch.zeros((1, N), dtype=torch.float64, device=DEV)
+    bst = torch.zeros(1, dtype=torch.int32, device=DEV)
+    dpf.dpf_nr_solve(nrh, precision=dpf.FP64, tol=1e-10, max_iter=20, n_case=1, va=bva, vm=bvm, status=bst)
+    torch.cuda.synchronize()
+    assert int(bst[0]) == dpf.CASE_CONVERGED
+    nrh.free()
+    ws = dpf.dpf_workspace_create(y, K)
+    opts = dpf.SolveOpts(precision=dpf.FP32R, tol=1e-7, max_iter=10000, check_every=25, flat_start=0, **N1_WARM)
+    r = _solve(y, ws, K, opts, va_start=bva[0], vm_start=bvm[0], outage=_t(outs, torch.int32))
+    conv = np.nonzero(r["status"] == dpf.CASE_CONVERGED)[0]
+    assert conv.size >= 3, conv.size
+    for k in conv:
+        Yk = _ybus_without(g, int(outs[k]))
+        f, _ = oracle.mismatch(Yk, r["va"][k], r["vm"][k], g.p_spec, g.q_spec, g.bus_type)
+        assert abs(np.abs(f).max() - r["max_mismatch"][k]) <= 1e-12 and r["max_mismatch"][k] <= 1e-7, k
+        nr = oracle.nr_solve(Yk, g.p_spec, g.q_spec, g.bus_type, g.vm_set, va_slack=g.va_slack)
+        assert nr["converged"], k
+        assert np.abs(r["vm"][k] - nr["vm"]).max() < 1e-5, (k, np.abs(r["vm"][k] - nr["vm"]).max())
+        assert np.abs(r["va"][k] - nr["va"]).max() < 1e-5, (k, np.abs(r["va"][k] - nr["va"]).max())
