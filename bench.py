@@ -1512,7 +1512,7 @@ def main():
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--row-blocks", type=int, default=0)
-    ap.add_argument("--cpu-rounds", type=int, default=2, help="warm-started N-1 cases per host core (cpu_baseline)")
+    ap.add_argument("--cpu-rounds", type=int, default=3, help="warm-started N-1 cases per host core (cpu_baseline)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
