@@ -751,6 +751,20 @@ def timeseries_record(dpf, torch, T, newton=False, precision=None):
         f, _ = oracle.mismatch(Y, out["va"][t], out["vm"][t], P[t], Q[t], g.bus_type)
         err = max(err, abs(float(np.max(np.abs(f))) - float(out["max_mismatch"][t])))
     st, it = out["status"], out["iters"]
+    # which snapshots have a power-flow solution at all: Newton-Raphson (Alg. 2,
+    # the library's, FP64) from the flat start, window by window
+    nrh = dpf.dpf_nr_create(y, 96)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    feas = 0
+    for w0 in range(0, T, 96):
+        Kw = min(96, T - w0)
+        nst = torch.zeros(Kw, dtype=torch.int32, device=dev)
+        buf = {k: torch.zeros((Kw, g.n_bus), dtype=torch.float64, device=dev) for k in ("va", "vm")}
+        dpf.dpf_nr_solve(nrh, precision=dpf.FP64, tol=1e-8, max_iter=30, n_case=Kw,
+                         p_spec=torch.tensor(P[w0:w0 + Kw], device=dev), q_spec=torch.tensor(Q[w0:w0 + Kw], device=dev),
+                         status=nst, **buf)
+        feas += int((nst == dpf.CASE_CONVERGED).sum())
+    nrh.free()
     n_pv = int((g.bus_type == 1).sum())
     n_pq = int((g.bus_type == 0).sum())
     fwd_b, adj_b = algorithmic_bytes(g.n_bus, n_pv, n_pq, y.nnz, 1, spec_per_case=True,
@@ -763,6 +777,7 @@ def timeseries_record(dpf, torch, T, newton=False, precision=None):
         "precision": "fp32r" if precision == dpf.FP32R else "fp32", "tol_pu": TOL,
         "generation_s": t_gen, "wall_s": wall, "snapshots_per_s": T / wall,
         "converged": int((st == 0).sum()), "solves_to_1e-6_per_s": int((st == 0).sum()) / wall,
+        "snapshots_with_a_newton_solution": feas,
         "iterations_total": int(it.sum()), "iterations_p50": float(np.median(it)),
         "iterations_first_window_p50": float(np.median(it[:96])),
         "status_counts": {str(k): int((st == k).sum()) for k in (0, 1, 2)},
