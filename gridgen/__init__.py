@@ -31,6 +31,10 @@ Recipe (one grid):
     only up to ~20% and the 10,000-bus grid up to ~12% of it (long pendant
     chains of PQ buses behind single branches collapse in voltage), so the
     large workloads use load_scale = 0.1; the 30-bus grid solves at full load.
+    The 10,000-bus time-series grid uses 0.05: its load model peaks at 1.44x
+    the base load (winter noon), and at 0.1 Newton-Raphson from a flat or
+    base-case start fails on the peak hours (42% of the year) while at 0.05
+    it solves every hour.
 
 Specified injections are net (generation - load) in p.u.
 """
@@ -371,7 +375,7 @@ CONFIGS = {
     "c1_30bus_fp64": dict(n_bus=30, seed=0, n_branch=41, n_pv=5),
     "c2_10kbus": dict(n_bus=10_000, seed=1, load_scale=0.1),
     "c3_n1_2kbus": dict(n_bus=2_000, seed=2, load_scale=0.1),
-    "c4_timeseries_10kbus": dict(n_bus=10_000, seed=3, load_scale=0.1),
+    "c4_timeseries_10kbus": dict(n_bus=10_000, seed=3, load_scale=0.05),
 }
 
 

@@ -15,7 +15,9 @@ Newton-Raphson on the GPU (dpf_nr_solve, FP32 factor, to 1e-10 p.u.) as
 start and fallback: a snapshot Newton solves leaves the window exact, one it
 cannot keeps Alg. 1's state.  (The caption of Fig. 4 notes the first full fit
 could be replaced by Newton-Raphson; Sec. 6 names gradient methods as the
-initialisers of Newton solves.)
+initialisers of Newton solves.)  With `newton_from="flat"` the first window
+skips the Alg. 1 fit: Newton-Raphson solves it from the flat start, and
+Alg. 1 runs only on the warm-started windows after it.
 
 With `checkpoint` (a directory), every solved window is saved as
 window_<first snapshot>.npz (its solutions, iterations, statuses, mismatches
@@ -44,29 +46,33 @@ TABLE3_T1 = dict(lr=0.00027, beta1=0.7847, beta2=0.6624, sched=_abi.SCHED_PLATEA
                  threshold=0.0388, cooldown=4, max_iter=300)
 
 
-def _fingerprint(p, q, precision, tol, check_every, settings, first_newton, w0, window):
+def _fingerprint(p, q, precision, tol, check_every, settings, first_newton, w0, window, newton_from="dpf"):
     h = hashlib.sha256()
     h.update(np.ascontiguousarray(p.cpu().numpy()).tobytes())
     h.update(np.ascontiguousarray(q.cpu().numpy()).tobytes())
     h.update(json.dumps(dict(precision=int(precision), tol=float(tol), check_every=int(check_every),
                              settings={k: settings[k] for k in sorted(settings)},
-                             newton=bool(first_newton is not None and w0 == 0), warm=w0 > 0,
+                             newton=(newton_from if first_newton is not None and w0 == 0 else False), warm=w0 > 0,
                              window=int(window)), sort_keys=True).encode())
     return h.hexdigest()
 
 
 def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 96, precision=_abi.FP32,
                       first=None, later=None, check_every: int = 25, tol: float = 1e-6, stream=None,
-                      first_newton: NewtonSolver | None = None, checkpoint: str | None = None,
-                      resume: bool = False):
+                      first_newton: NewtonSolver | None = None, newton_from: str = "dpf",
+                      checkpoint: str | None = None, resume: bool = False):
     """Solve T snapshots ([T][N] injections, numpy or torch); returns numpy arrays.
 
     `first` / `later` override the Table 3 settings (dicts of SolveOpts fields).
     `first_newton`: a NewtonSolver for `window` cases of this Y_bus; the first
     window's Alg. 1 solutions then go through Newton-Raphson (start and
-    fallback; its `iters` and `status` are then Newton's).
+    fallback; its `iters` and `status` are then Newton's); with
+    `newton_from="flat"` Newton-Raphson alone solves the first window from
+    the flat start.
     `checkpoint` / `resume`: per-window save and restart (module docstring).
     """
+    if newton_from not in ("dpf", "flat"):
+        raise ValueError(f"newton_from must be 'dpf' or 'flat', not {newton_from!r}")
     import torch
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -92,7 +98,7 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
         settings = dict(TABLE3_T0 if w0 == 0 else TABLE3_T1)
         settings.update((first if w0 == 0 else later) or {})
         fp = _fingerprint(P[w0:w0 + K], Q[w0:w0 + K], precision, tol, check_every, settings, first_newton, w0,
-                          window) if path else None
+                          window, newton_from) if path else None
         if resume and path and os.path.exists(path):
             with np.load(path) as z:
                 if z["va"].shape != (K, N):
@@ -108,12 +114,14 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
         q = Q[w0:w0 + K].to(dev).contiguous()
         opts = SolveOpts(precision=precision, check_every=check_every, tol=tol, flat_start=1 if w0 == 0 else 0,
                          **settings)
-        dpf_solve_batch(y, ws, opts, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
-                        **{k: v[:K] for k, v in res.items()})
+        newton_only = w0 == 0 and first_newton is not None and newton_from == "flat"
+        if not newton_only:
+            dpf_solve_batch(y, ws, opts, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
+                            **{k: v[:K] for k, v in res.items()})
         if w0 == 0 and first_newton is not None:
-            dpf_nr_solve(first_newton, precision=_abi.FP32, tol=1e-10, max_iter=20, flat_start=False,
-                         fallback=True, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
-                         **{k: v[:K] for k, v in res.items()})
+            dpf_nr_solve(first_newton, precision=_abi.FP32, tol=1e-10, max_iter=20, flat_start=newton_only,
+                         fallback=not newton_only, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K],
+                         vm=vm[:K], **{k: v[:K] for k, v in res.items()})
         out["va"][w0:w0 + K] = va[:K].cpu().numpy()
         out["vm"][w0:w0 + K] = vm[:K].cpu().numpy()
         for k, v in res.items():

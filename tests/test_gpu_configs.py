@@ -150,6 +150,42 @@ def test_c4_time_series_fp32_against_oracle(precision):
         assert abs(np.abs(f).max() - b["max_mismatch"][t]) <= 1e-12 * max(1.0, np.abs(f).max()), t
 
 
+def test_time_series_first_window_by_newton_from_flat():
+    """newton_from="flat": Newton-Raphson alone solves the first window from
+    the flat start (the caption of Fig. 4: the first full fit may be replaced
+    by Newton-Raphson); those snapshots equal the oracle's Newton solutions
+    (1e-8 on |V| and theta, both at 1e-10 p.u.), and the later windows are
+    Alg. 1 runs warm-started from them: the oracle's FP64 Alg. 1 from the
+    oracle's Newton state takes the same iterations and statuses and ends
+    within 1e-8 -- the two starts already differ by up to 1e-8 (two Newton
+    roots at 1e-10 p.u.), which the 40 steps carry along."""
+    g = gridgen.make_grid(300, 3, load_scale=0.1)
+    T, window = 12, 6
+    P, Q = gridgen.time_series(g, T, seed=4)
+    later = dict(max_iter=40)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, window)
+    nr = dpf.dpf_nr_create(y, window)
+    r = solve_time_series(y, ws, P, Q, window=window, precision=dpf.FP64, later=later, check_every=1,
+                          first_newton=nr, newton_from="flat")
+    Y = grid_ybus(g)
+    s = dict(TABLE3_T1, **later)
+    o = oracle.DPFOptions(lr=s["lr"], beta1=s["beta1"], beta2=s["beta2"], sched="plateau", factor=s["factor"],
+                          patience=s["patience"], threshold=s["threshold"], cooldown=s["cooldown"],
+                          max_iter=s["max_iter"], tol=1e-6, check_every=1)
+    for t in range(window):
+        n = oracle.nr_solve(Y, P[t], Q[t], g.bus_type, g.vm_set, tol=1e-10)
+        assert n["converged"] and r["status"][t] == dpf.CASE_CONVERGED and r["max_mismatch"][t] < 1e-10
+        assert np.abs(r["va"][t] - n["va"]).max() < 1e-8 and np.abs(r["vm"][t] - n["vm"]).max() < 1e-8
+        d = oracle.dpf_solve(Y, P[t + window], Q[t + window], g.bus_type, g.vm_set, o, va0=n["va"], vm0=n["vm"])
+        assert r["iters"][t + window] == d["iters"] and r["status"][t + window] == d["status"]
+        assert np.abs(r["va"][t + window] - d["va"]).max() < 1e-8
+        assert np.abs(r["vm"][t + window] - d["vm"]).max() < 1e-8
+    with pytest.raises(ValueError):
+        solve_time_series(y, ws, P, Q, window=window, first_newton=nr, newton_from="newton")
+    nr.free()
+
+
 def test_time_series_resumes_from_its_checkpoints(tmp_path):
     """An interrupted series (the first two windows saved) resumed to the end
     equals the uninterrupted series bit for bit: saved windows are loaded,
