@@ -7,14 +7,16 @@ correction.
 
 A step is one whole batched solve, inputs resident on the GPU: the base case
 (no outage) by the library's Newton-Raphson, then every N-1 case by Alg. 1
-started from the base case's solution (the warm start of Sec. 5.4.2),
-refined FP32 iterations (DPF_FP32R) with the FP64 convergence test every 50
-iterations (cases whose FP32 mismatch is within 5e-6 p.u.; every case every
-100 iterations) and per-case early stopping at 1e-6 p.u., up to
-`--n1-budget` (4,000) iterations, optimiser settings presets.N1_WARM.  `value` counts only
-the cases the FP64 test declares converged (max |f| <= 1e-6 p.u.), per
-second; the others are reported, not counted.  A solve takes ~0.4 s and moves
-~1 GB per iteration-pair, far beyond the 129 MB L2 (no flush needed).
+started from the base case's solution (the warm start of Sec. 5.4.2) shifted
+by the DC angle change of its outage (`--n1-start dc`, the default; `base`:
+no shift), refined FP32 iterations (DPF_FP32R) with the FP64 convergence
+test every 50 iterations (cases whose FP32 mismatch is within 5e-6 p.u.;
+every case every 100 iterations) and per-case early stopping at 1e-6 p.u.,
+up to `--n1-budget` iterations (3,500 with the shift, settings
+presets.N1_DC; 4,000 without, presets.N1_WARM).  `value` counts only the
+cases the FP64 test declares converged (max |f| <= 1e-6 p.u.), per second;
+the others are reported, not counted.  A solve takes ~0.5 s and moves ~0.5 GB
+per iteration, far beyond the 129 MB L2 (no flush needed).
 
 Sub-records on the same line: the flat-start FP32 iteration rate of the same
 batch (Table 2, the kernels' own roofline; no case reaches 1e-6 from the flat
@@ -24,7 +26,7 @@ start within Table 2's budget), the 30-bus batch where every case converges
 (`uneven`).
 
 --impl reference times the CPU FP64 oracle on the same warm-started N-1 solves
-(a bounded sample of the cases per step) on the host cores.
+(a bounded sample of the cases per step, the same start) on the host cores.
 """
 from __future__ import annotations
 
@@ -44,7 +46,7 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 ITERS_PER_SOLVE = 1000  # Table 2: maximum iterations of one DPF solve from the flat start
-from paper_2603_28203_gb300.presets import N1_BUDGET  # iterations of one warm-started N-1 solve  # noqa: E402
+from paper_2603_28203_gb300.presets import N1_BUDGET, N1_DC_BUDGET  # iterations of one N-1 solve  # noqa: E402
 N1_CHECK_EVERY = 50     # FP64 test interval of the warm-started N-1 solve
 N1_GATE = 5e-6          # its FP32 gate: the refined FP32 mismatch is accurate far below this
 CHECK_EVERY = 25
@@ -78,49 +80,65 @@ def _oracle_base():
     return _ORACLE_CACHE["grid"], _ORACLE_CACHE["base"]
 
 
-def _oracle_dpf_options(budget):
+def n1_settings(start):
+    """(optimiser settings, start options, default budget) of the N-1 solve:
+    start "dc" = the base case's solution shifted by each outage's DC angle
+    change, "base" = the base case's solution."""
+    from paper_2603_28203_gb300 import presets
+    if start == "dc":
+        return presets.N1_DC, presets.N1_DC_START, N1_DC_BUDGET
+    if start == "base":
+        return presets.N1_WARM, {}, N1_BUDGET
+    raise ValueError(f"unknown N-1 start {start!r}")
+
+
+def _oracle_dpf_options(budget, start):
     import oracle
     from paper_2603_28203_gb300 import _abi
-    from paper_2603_28203_gb300.presets import N1_WARM
-    sched = {_abi.SCHED_PLATEAU: "plateau", _abi.SCHED_STEP: "step", _abi.SCHED_CONST: "const"}[N1_WARM["sched"]]
-    return oracle.DPFOptions(lr=N1_WARM["lr"], beta1=N1_WARM["beta1"], beta2=N1_WARM["beta2"], eps=N1_WARM["eps"],
-                             sched=sched, factor=N1_WARM["factor"], patience=N1_WARM["patience"],
-                             threshold=N1_WARM["threshold"], cooldown=N1_WARM["cooldown"], max_iter=budget, tol=TOL,
+    s = n1_settings(start)[0]
+    sched = {_abi.SCHED_PLATEAU: "plateau", _abi.SCHED_STEP: "step", _abi.SCHED_CONST: "const"}[s["sched"]]
+    return oracle.DPFOptions(lr=s["lr"], beta1=s["beta1"], beta2=s["beta2"], eps=s["eps"],
+                             sched=sched, factor=s["factor"], patience=s["patience"],
+                             threshold=s["threshold"], cooldown=s["cooldown"], max_iter=budget, tol=TOL,
                              check_every=N1_CHECK_EVERY)
 
 
 def _oracle_case(args):
-    """One warm-started N-1 case through the oracle's Alg. 1 loop: (iterations,
-    seconds, status)."""
+    """One warm-started N-1 case through the oracle: the DC outage shift of
+    the base case's angles (start "dc"; a sparse direct solve), then the
+    Alg. 1 loop: (iterations, seconds, status)."""
     import oracle
     from oracle.ybus import grid_ybus
-    ell, budget = args
+    ell, budget, start = args
     g, base = _oracle_base()
     Y = grid_ybus(g.without_branch(int(ell)))
     t0 = time.perf_counter()
-    r = oracle.dpf_solve(Y, g.p_spec, g.q_spec, g.bus_type, g.vm_set, _oracle_dpf_options(budget),
-                         va0=base["va"], vm0=base["vm"], va_slack=g.va_slack)
+    va0 = base["va"]
+    if start == "dc":
+        va0 = va0 + oracle.dc_outage_shift(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, va0, int(ell))
+    r = oracle.dpf_solve(Y, g.p_spec, g.q_spec, g.bus_type, g.vm_set, _oracle_dpf_options(budget, start),
+                         va0=va0, vm0=base["vm"], va_slack=g.va_slack)
     return r["iters"], time.perf_counter() - t0, r["status"]
 
 
 def _oracle_cases(args):
     """Several cases in one process: (case-iterations, seconds, converged)."""
-    cases, budget = args
+    cases, budget, start = args
     n, t, c = 0, 0.0, 0
     for ell in cases:
-        it, dt, st = _oracle_case((ell, budget))
+        it, dt, st = _oracle_case((ell, budget, start))
         n, t, c = n + it, t + dt, c + int(st == 0)
     return n, t, c
 
 
-def _oracle_pool_run(chunks, budget):
+def _oracle_pool_run(chunks, budget, start):
     """Run `chunks` (one list of cases per host core) through a spawn pool;
     the time is the slowest core's."""
     import multiprocessing as mp
     cores = len(chunks)
     with mp.get_context("spawn").Pool(cores) as pool:
         pool.map(_oracle_base_init, range(cores))  # start-up and the base case, untimed
-        res = pool.map(_oracle_cases, [(c, budget) for c in chunks])
+        res = pool.map(_oracle_cases, [(c, budget, start) for c in chunks])
     return sum(r[0] for r in res), max(r[1] for r in res), sum(r[2] for r in res)
 
 
@@ -129,17 +147,18 @@ def _oracle_base_init(_):
     return 0
 
 
-def cpu_oracle_sample(outages, budget, rounds):
+def cpu_oracle_sample(outages, budget, rounds, start):
     """The oracle on `rounds` warm-started N-1 cases per host core (seeded
     sample without replacement); solves/s counts the converged ones."""
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(7)
     pick = [int(c) for c in rng.choice(outages, size=min(outages.size, cores * rounds), replace=False)]
     chunks = [pick[i::cores] for i in range(cores)]
-    n_it, t, conv = _oracle_pool_run(chunks, budget)
+    n_it, t, conv = _oracle_pool_run(chunks, budget, start)
+    shift = "the DC outage shift of the base case, then " if start == "dc" else ""
     return dict(value=conv / t, unit="solves/s", cores=cores, kind="oracle",
                 sample=f"{len(pick)} warm-started N-1 cases ({rounds} per core), each through the FP64 "
-                       f"numpy/scipy oracle's Alg. 1 loop to 1e-6 p.u. or {budget} iterations; "
+                       f"numpy/scipy oracle ({shift}Alg. 1 loop to 1e-6 p.u. or {budget} iterations); "
                        f"{conv} converged; {n_it} case-iterations in {t:.1f} s (slowest core)",
                 converged=conv, cases=len(pick), case_iterations_per_s=n_it / t)
 
@@ -293,10 +312,11 @@ def _outputs(torch, K, N, dev, pinned=False):
 
 class N1Job:
     """One step of the benchmark: the base case by Newton-Raphson, then every
-    N-1 case warm-started from it (refined FP32 DPF iterations)."""
+    N-1 case warm-started from it (shifted by its outage's DC angle change
+    for start "dc"; refined FP32 DPF iterations)."""
 
     def __init__(self, dpf, torch, g, outages, stream, budget, args):
-        from paper_2603_28203_gb300.presets import N1_WARM
+        settings, start_opts, _ = n1_settings(args.n1_start)
         self.dpf, self.torch, self.g, self.stream = dpf, torch, g, stream
         dev = torch.device("cuda", torch.cuda.current_device())
         self.K, self.N = outages.size, g.n_bus
@@ -310,7 +330,8 @@ class N1Job:
         self.res = _outputs(torch, self.K, self.N, dev)
         self.opts = dpf.SolveOpts(precision=dpf.FP32R, tol=TOL, check_every=N1_CHECK_EVERY, gate=N1_GATE,
                                   max_iter=budget, flat_start=0, lanes=args.lanes or None, warps=args.warps or None,
-                                  row_blocks=args.row_blocks or None, pdl=0 if args.no_pdl else None, **N1_WARM)
+                                  row_blocks=args.row_blocks or None, pdl=0 if args.no_pdl else None, **settings,
+                                  **start_opts)
         self.shape_by = "command line" if (args.lanes or args.warps or args.row_blocks) else \
             "library default" if args.no_autotune else "dpf_autotune"
 
@@ -363,7 +384,7 @@ def run_ours(args):
     g, outages = _workload()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(outages, args.n1_budget, args.cpu_rounds)
+        cpu = cpu_oracle_sample(outages, args.n1_budget, args.cpu_rounds, args.n1_start)
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -454,14 +475,23 @@ def run_ours(args):
                 "workload": "N-1 contingency batch: 2,000-bus synthetic grid, 2,700 branches, "
                             f"{K} non-islanding single-branch outages per GPU, shared CSR Y_bus (nnz {job.y.nnz}) "
                             "+ per-case branch-removal correction; each case warm-started from the base case "
-                            "(solved by Newton-Raphson in the same step)",
+                            "(solved by Newton-Raphson in the same step)"
+                            + (", shifted by the DC angle change of its outage (CG in the same step)"
+                               if args.n1_start == "dc" else ""),
+                "n1_start": args.n1_start,
                 "n_bus": N, "n_branch": g.n_branch, "cases_per_gpu": int(K), "nnz": job.y.nnz,
                 "iteration_precision": "fp32r", "check_every": ce, "gate_pu": N1_GATE, "tol_pu": TOL,
                 "budget_iterations": args.n1_budget,
-                "optimizer": "Adam + ReduceLROnPlateau, presets.N1_WARM (searched, Sec. 5.3's procedure)",
-                "solve_definition": f"Alg. 1 from the base case's solution until FP64 max mismatch <= {TOL} p.u. "
-                                    f"(counted) or {args.n1_budget} iterations (not counted)",
-                "step": "one whole batched solve: base case (Newton-Raphson, FP64) + all N-1 cases (DPF)",
+                "optimizer": "Adam + ReduceLROnPlateau, presets."
+                             + ("N1_DC" if args.n1_start == "dc" else "N1_WARM")
+                             + " (searched, Sec. 5.3's procedure)",
+                "dc_shift": ({k: getattr(job.opts, k) for k in ("dc_tol", "dc_max_iter")}
+                             if args.n1_start == "dc" else None),
+                "solve_definition": f"Alg. 1 from the (shifted) base case's solution until FP64 max mismatch <= "
+                                    f"{TOL} p.u. (counted) or {args.n1_budget} iterations (not counted)",
+                "step": "one whole batched solve: base case (Newton-Raphson, FP64)"
+                        + (" + the DC outage shift of every case (CG)" if args.n1_start == "dc" else "")
+                        + " + all N-1 cases (DPF)",
                 "l2": "per-iteration traffic ~0.6 GB >> 129 MB L2 (no flush needed)",
                 "parallelism": f"replicas x{world} (independent cases, no data-path collective)",
                 "launch_shape": {"lanes": job.opts.lanes, "warps": job.opts.warps, "row_blocks": job.opts.row_blocks,
@@ -1456,10 +1486,10 @@ def _oracle_nr_sample(sample, cores):
 def _oracle_steps_worker(args):
     """One host core: its warm-up cases untimed, then its timed cases (one per
     step); returns (case-iterations, seconds, converged) of the timed ones."""
-    warm, timed, budget = args
+    warm, timed, budget, start = args
     for ell in warm:
-        _oracle_case((ell, budget))
-    return _oracle_cases((timed, budget))
+        _oracle_case((ell, budget, start))
+    return _oracle_cases((timed, budget, start))
 
 
 def run_reference(args):
@@ -1478,8 +1508,8 @@ def run_reference(args):
     rng = np.random.default_rng(11)
     need = cores * per
     pick = [int(c) for c in rng.choice(outages, size=need, replace=need > outages.size)]
-    jobs = [(pick[c * per: c * per + args.warmup], pick[c * per + args.warmup: (c + 1) * per], args.n1_budget)
-            for c in range(cores)]
+    jobs = [(pick[c * per: c * per + args.warmup], pick[c * per + args.warmup: (c + 1) * per], args.n1_budget,
+             args.n1_start) for c in range(cores)]
     with mp.get_context("spawn").Pool(cores) as pool:
         pool.map(_oracle_base_init, range(cores))  # start-up and the base case, untimed
         res = pool.map(_oracle_steps_worker, jobs)
@@ -1489,7 +1519,8 @@ def run_reference(args):
     v = conv / t
     cpu = dict(value=v, unit="solves/s", cores=cores, kind="oracle",
                sample=f"per step {cores} warm-started N-1 cases (one per core, distinct, seeded) through the FP64 "
-                      f"numpy/scipy oracle's Alg. 1 loop to 1e-6 p.u. or {args.n1_budget} iterations; "
+                      f"numpy/scipy oracle ({'the DC outage shift, then ' if args.n1_start == 'dc' else ''}"
+                      f"Alg. 1 loop to 1e-6 p.u. or {args.n1_budget} iterations); "
                       f"{args.steps} timed steps: {conv} of {cores * args.steps} cases converged, "
                       f"{n_it} case-iterations in {t:.1f} s (slowest core)",
                case_iterations_per_s=n_it / t)
@@ -1498,9 +1529,11 @@ def run_reference(args):
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "N-1 contingency batch: 2,000-bus synthetic grid, each case warm-started from the "
-                               "base case (the oracle on a bounded sample of its cases per step)",
-                   "solve_definition": f"Alg. 1 from the base case's solution until FP64 max mismatch <= {TOL} "
-                                       f"p.u. (counted) or {args.n1_budget} iterations (not counted)"},
+                               "base case" + (" shifted by its outage's DC angle change" if args.n1_start == "dc"
+                                              else "") + " (the oracle on a bounded sample of its cases per step)",
+                   "n1_start": args.n1_start,
+                   "solve_definition": f"Alg. 1 from the (shifted) base case's solution until FP64 max mismatch <= "
+                                       f"{TOL} p.u. (counted) or {args.n1_budget} iterations (not counted)"},
         "cpu_baseline": cpu,
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1524,7 +1557,10 @@ def main():
                          "warmstart: iterations from flat vs warm starts on the 30-bus grid; "
                          "c1batch: solves/s to 1e-6 on a batch of 30-bus load variants; "
                          "nr: Newton-Raphson on the GPU over the N-1 batch, and the DPF-then-Newton hybrid")
-    ap.add_argument("--n1-budget", type=int, default=N1_BUDGET, help="iterations of one warm-started N-1 solve")
+    ap.add_argument("--n1-start", default="dc", choices=["dc", "base"],
+                    help="N-1 start: the base case's solution shifted by the outage's DC angle change, or unshifted")
+    ap.add_argument("--n1-budget", type=int, default=None,
+                    help="iterations of one N-1 solve (default: 3,500 with the DC shift, 4,000 without)")
     ap.add_argument("--profile-steps", type=int, default=100)
     ap.add_argument("--flat-iters", type=int, default=2000, help="timed flat-start FP32 iterations (sub-record)")
     ap.add_argument("--uneven-iters", type=int, default=300)
@@ -1554,6 +1590,8 @@ def main():
     ap.add_argument("--plain-cases", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.n1_budget is None:
+        args.n1_budget = n1_settings(args.n1_start)[2]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

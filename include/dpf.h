@@ -209,15 +209,33 @@ typedef struct {
                                 host stop test (FP64 check + device-to-host
                                 read) after every iteration; check_every is
                                 taken as 1.  Used as the unbatched baseline. */
-  int32_t dc_start;          /* 1 (with flat_start): the angles start from the
-                                DC approximation (dpf_dc_solve, relative
-                                residual 1e-10), |V| from the flat start    */
+  int32_t dc_start;          /* 1 with flat_start: the angles start from the
+                                DC approximation (dpf_dc_solve to dc_tol),
+                                |V| from the flat start.
+                                1 with a warm start (va/vm or va_start/
+                                vm_start) and outages: a case whose branch
+                                l = (f, t) is out starts from its start
+                                angles plus the DC angle change of the
+                                outage: dtheta solves B' dtheta =
+                                b_l (theta_f - theta_t) (e_f - e_t), with B'
+                                the DC matrix without l, b_l = 1/(x_l tau_l)
+                                and theta the case's start angles -- the
+                                branch's pre-outage DC flow put back at its
+                                ends -- and dtheta = 0 at slack buses;
+                                |V| as started.  Cases without an outage
+                                keep their start.                           */
   int32_t stage_y;           /* single-case FP32 / FP32R solves (lanes = 1):
                                 0 -- the passes read their Y_bus rows from
                                 global memory, one wave of CTAs each owning
                                 many rows (no reuse to stage for when every
                                 entry serves one case); 1 -- stage each row
                                 block's rows in shared memory like batches */
+  double dc_tol;             /* dc_start: relative residual at which a case's
+                                conjugate-gradient DC solve stops (> 0;
+                                default 1e-10)                              */
+  int32_t dc_max_iter;       /* dc_start: CG iterations at most (>= 1; default
+                                10000); a case still above dc_tol then
+                                starts from its last CG iterate             */
 } dpf_solve_opts;
 
 void dpf_default_opts(dpf_solve_opts* o);
@@ -272,7 +290,9 @@ int dpf_iterations_done(const dpf_workspace* ws, int32_t* n_iter);
  * dpf_kernel_times: summed durations (ms) and launch counts of the
  * bracketed launches since the last enable (synchronises `stream`).
  * dpf_kernel_launches: number of kernels the workspace has enqueued since it
- * was created (graph replays count their kernel nodes). */
+ * was created -- by the solve (begin, iterations, convergence tests, end, the
+ * DC start), dpf_power, dpf_loss_backward and identification calls; graph
+ * replays count their kernel nodes. */
 int dpf_profile_enable(dpf_workspace* ws, int32_t on);
 int dpf_kernel_times(dpf_workspace* ws, double* fwd_ms, double* adj_ms, int32_t* n_fwd, int32_t* n_adj,
                      void* stream);

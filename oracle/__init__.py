@@ -22,6 +22,8 @@ statement of the problem:
   nr.nr_solve          Newton-Raphson (Alg. 2), the ground-truth solver
   dc.dc_solve          DC approximation B theta = P (Sec. 2 comparison model,
                        Alg. 2's optional initialisation)
+  dc.dc_outage_shift   DC angle change of an outage, B' dtheta = (B - B') theta
+                       (a start for warm-started N-1 cases)
 
 Pins (tests/test_oracle_*.py) tie each of these to something other than the
 oracle itself: closed forms (two-bus line, Y_bus hand values), the
@@ -36,11 +38,11 @@ from .gradient import loss_grad, param_grad
 from .optim import SGD, Adam, ReduceLROnPlateau, RMSprop, StepLR
 from .dpf import DPFOptions, dpf_solve, flat_start
 from .nr import nr_solve
-from .dc import dc_branch_flows, dc_matrix, dc_solve, dc_susceptance
+from .dc import dc_branch_flows, dc_matrix, dc_outage_shift, dc_solve, dc_susceptance
 
 __all__ = [
     "build_ybus", "branch_blocks", "s_calc", "mismatch", "loss", "learnable_sets",
     "dS_dVm_dVa", "jacobian_f", "loss_grad", "param_grad", "Adam", "SGD", "RMSprop",
     "ReduceLROnPlateau", "StepLR", "DPFOptions", "dpf_solve", "flat_start",
-    "nr_solve", "dc_solve", "dc_matrix", "dc_susceptance", "dc_branch_flows",
+    "nr_solve", "dc_solve", "dc_matrix", "dc_susceptance", "dc_branch_flows", "dc_outage_shift",
 ]

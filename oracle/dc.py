@@ -12,6 +12,16 @@ from-bus; tau 0 read as 1), and the injections satisfy
 over the pv and pq buses, the slack angles being fixed (one slack per
 island).  An outaged branch is left out of B.  scipy's sparse solve is the
 linear-algebra step.
+
+Outage shift (a start for the N-1 cases of a warm-started batch, built on the
+DC model above; the paper's warm starts of Sec. 5.4.2 and its DC
+initialisation combined): for angles theta and an outaged branch l, the
+angle change that removing l causes in the DC model,
+
+    B' dtheta = (B - B') theta   on the pv and pq rows,  dtheta = 0 at slacks,
+
+with B' the matrix without l, so that B' (theta + dtheta) = B theta there:
+the injections theta implies stay, carried by the remaining branches.
 """
 from __future__ import annotations
 
@@ -59,3 +69,19 @@ def dc_branch_flows(f_bus, t_bus, x, tap, theta):
     b = dc_susceptance(x, tap)
     theta = np.asarray(theta, np.float64)
     return b * (theta[np.asarray(f_bus)] - theta[np.asarray(t_bus)])
+
+
+def dc_outage_shift(n_bus, f_bus, t_bus, x, tap, bus_type, theta, outage):
+    """dtheta [n_bus] with B' dtheta = (B - B') theta on the non-slack rows and
+    dtheta = 0 at the slack buses (B' without branch `outage`; zero for -1)."""
+    theta = np.asarray(theta, np.float64)
+    if outage is None or outage < 0:
+        return np.zeros(n_bus)
+    bus_type = np.asarray(bus_type)
+    B = dc_matrix(n_bus, f_bus, t_bus, x, tap)
+    Bo = dc_matrix(n_bus, f_bus, t_bus, x, tap, outage)
+    u = np.where(bus_type != SLACK)[0]
+    rhs = ((B - Bo) @ theta)[u]
+    d = np.zeros(n_bus)
+    d[u] = spl.spsolve(Bo[u][:, u].tocsc(), rhs)
+    return d

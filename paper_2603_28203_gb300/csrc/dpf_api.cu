@@ -271,7 +271,7 @@ struct dpf_workspace {
   unsigned int* tile_cnt = nullptr;  // per case tile, for the forward pass's scheduler
   void* loss_part = nullptr;         // [row blocks][Kp] the forward pass's loss partials (8 B each)
   size_t cap_part = 0;
-  double* dcs = nullptr;     // DC solver, per case: rz, rz', pq, rr, rr0, beta, res, b_out ([8][Kp])
+  double* dcs = nullptr;     // DC solver, per case: rz, rz', pq, rr, rr0, beta, res, b_out, flow ([9][Kp])
   int32_t* dci = nullptr;    // DC solver, per case: active, iters ([2][Kp]), then its active count
   int32_t* h_dc_nact = nullptr;  // pinned
   int cap_tiles = 0;
@@ -388,7 +388,7 @@ static int ws_reserve(dpf_workspace* w, int Kp, size_t stage) {
     TRY(dalloc(&w->yff64, Kp)); TRY(dalloc(&w->yft64, Kp)); TRY(dalloc(&w->ytt64, Kp));
     TRY(dalloc(&w->maxmis, Kp)); TRY(dalloc(&w->outage_dev, Kp));
     TRY(dalloc(&w->b1t, Kp)); TRY(dalloc(&w->b2t, Kp)); TRY(dalloc(&w->cand, Kp)); TRY(dalloc(&w->mx32, Kp));
-    TRY(dalloc(&w->dcs, (size_t)8 * Kp)); TRY(dalloc(&w->dci, (size_t)2 * Kp + 1));
+    TRY(dalloc(&w->dcs, (size_t)9 * Kp)); TRY(dalloc(&w->dci, (size_t)2 * Kp + 1));
     CK(cudaMemset(w->p64, 0, E * 8));
     CK(cudaMemset(w->q64, 0, E * 8));
     w->cap_elems = E;
@@ -989,6 +989,7 @@ static int to_internal(dpf_workspace* w, const double* src, bool host_io, double
   dim3 g((y->n + 31) / 32, (w->K + 31) / 32), b(32, 8);
   k_to_internal<<<g, b, 0, s>>>(dsrc, dst, w->K, y->n, w->Kp, y->dev.iperm);
   CKLAUNCH();
+  w->launches++;
   return DPF_OK;
 }
 
@@ -999,6 +1000,7 @@ static int to_user(dpf_workspace* w, const double* src, bool host_io, double* st
   dim3 g((y->n + 31) / 32, (w->K + 31) / 32), b(32, 8);
   k_to_user<<<g, b, 0, s>>>(src, ddst, w->K, y->n, w->Kp, y->dev.iperm);
   CKLAUNCH();
+  w->launches++;
   if (host_io) CK(cudaMemcpyAsync(dst, stage, (size_t)w->K * y->n * 8, cudaMemcpyDeviceToHost, s));
   return DPF_OK;
 }
@@ -1043,6 +1045,7 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
       }
       k_to_internal<<<dim3((y->n + 31) / 32, 1), dim3(32, 8), 0, s>>>(d, dst[j], 1, y->n, 1, y->dev.iperm);
       CKLAUNCH();
+      w->launches++;
     }
     va_t = w->tmp_a;
     vm_t = w->tmp_b;
@@ -1088,10 +1091,12 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
   k_init<R><<<std::max(nb, 1), 256, 0, s>>>(ia);
   CKLAUNCH();
+  w->launches++;
   if constexpr (sizeof(R) == 4) {
     if (w->precision == DPF_MIXED) {  // FP64 voltages for the mixed forward pass
       k_mixed_v64<<<std::max(nb, 1), 256, 0, s>>>((const float4*)w->ms, (double2*)w->V, E);
       CKLAUNCH();
+      w->launches++;
     }
   }
 
@@ -1147,6 +1152,7 @@ static int init_state(dpf_workspace* w, const StateIn& in, cudaStream_t s) {
   ca.opt = w->opts.optimizer;
   k_case_init<R><<<(w->Kp + 255) / 256, 256, 0, s>>>(ca);
   CKLAUNCH();
+  w->launches++;
   CK(cudaMemcpyAsync(w->n_active, &w->K, 4, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));  // &w->K is host memory that may change later
   return DPF_OK;
@@ -1171,6 +1177,8 @@ static int validate_opts(const dpf_solve_opts* o) {
   if (!(o->gate >= 0.0)) return fail(DPF_E_INVALID, "gate must be >= 0");
   if (o->pdl != 0 && o->pdl != 1) return fail(DPF_E_INVALID, "pdl must be 0 or 1");
   if (o->dc_start != 0 && o->dc_start != 1) return fail(DPF_E_INVALID, "dc_start must be 0 or 1");
+  if (o->dc_start && (!(o->dc_tol > 0 && o->dc_tol < 1e300) || o->dc_max_iter < 1))
+    return fail(DPF_E_INVALID, "dc_start needs dc_tol > 0 and dc_max_iter >= 1");
   if (o->stage_y != 0 && o->stage_y != 1) return fail(DPF_E_INVALID, "stage_y must be 0 or 1");
   if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 8 || o->row_blocks < 0)
     return fail(DPF_E_INVALID, "invalid launch shape (lanes 0..32, warps 0..8, row_blocks >= 0)");
@@ -1198,7 +1206,11 @@ static int common_checks(const dpf_ybus* y, dpf_workspace* w, int K) {
 // ---------------------------------------------------------------------------
 __global__ void k_dc_set_count(int32_t* n, int K) { *n = K; }
 
-static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int max_iter, cudaStream_t s) {
+// B' x = P for every case (shift = false), or the outage shift of the cases'
+// start angles in the master state (shift = true; x0 = 0, right-hand side
+// from k_dc_flow).  x ends in tmp_a as FP64.
+static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int max_iter, cudaStream_t s,
+                  bool shift = false) {
   const dpf_ybus* y = w->y;
   const DeviceYbus& d = y->dev;
   const int Kp = w->Kp;
@@ -1238,6 +1250,8 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   a.beta = c + 5 * (size_t)Kp;
   a.res = c + 6 * (size_t)Kp;
   a.ob = c + 7 * (size_t)Kp;
+  a.flow = shift ? c + 8 * (size_t)Kp : nullptr;
+  if (shift) a.va_slack = 0.0;  // x is an angle change: 0 at the slack buses
   a.active = w->dci;
   a.iters = w->dci + Kp;
   a.n_active = w->dci + 2 * (size_t)Kp;
@@ -1247,14 +1261,23 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   const size_t E = (size_t)y->n * Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
   k_dc_case_init<<<cb, 256, 0, s>>>(a, outage_dev, d.br_x, d.br_tap);
+  if (shift) {
+    if (!a.of) return fail(DPF_E_INVALID, "the outage shift needs outages");
+    if (w->precision == DPF_FP64)
+      k_dc_flow<double><<<cb, 256, 0, s>>>((const double2*)w->ms, a.of, a.ot, a.ob, c + 8 * (size_t)Kp, w->K, Kp);
+    else
+      k_dc_flow<float><<<cb, 256, 0, s>>>((const float4*)w->ms, a.of, a.ot, a.ob, c + 8 * (size_t)Kp, w->K, Kp);
+  }
   k_dc_set_count<<<1, 1, 0, s>>>(a.n_active, w->K);
   k_dc_x0<<<std::max(nb, 1), 256, 0, s>>>(a);
   k_dc_start<<<grid, block, 0, s>>>(a);
   CKLAUNCH();
+  w->launches += shift ? 5 : 4;
   for (int it = 0; it < max_iter; ++it) {
     k_dc_spmv_dir<<<grid, block, 0, s>>>(a);
     k_dc_update_case<<<grid, block, 0, s>>>(a);
     CKLAUNCH();
+    w->launches += 2;
     std::swap(a.p, a.p_new);
     if ((it & 15) == 15 || it == max_iter - 1) {
       CK(cudaMemcpyAsync(w->h_dc_nact, a.n_active, 4, cudaMemcpyDeviceToHost, s));
@@ -1264,6 +1287,7 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   }
   k_dc_widen<<<std::max(nb, 1), 256, 0, s>>>(a.x, E);  // the FP64 solution, in place
   CKLAUNCH();
+  w->launches++;
   return DPF_OK;
 }
 
@@ -1344,17 +1368,24 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
   in.q = b->q_spec;
   in.outage = b->outage;
   TRY(w->precision == DPF_FP64 ? init_state<double>(w, in, s) : init_state<float>(w, in, s));
-  if (o->flat_start && o->dc_start) {  // angles from the DC approximation, |V| as initialised
+  // angles from the DC approximation (flat start) or shifted by the DC angle
+  // change of each case's outage (warm start); |V| as initialised
+  const bool dc_shift = o->dc_start && !o->flat_start && b->outage;
+  if ((o->flat_start && o->dc_start) || dc_shift) {
     const int32_t* od = b->outage ? (b->host_io ? w->outage_dev : b->outage) : nullptr;
-    TRY(dc_run(w, od, 1e-10, 10000, s));
+    TRY(dc_run(w, od, o->dc_tol, o->dc_max_iter, s, dc_shift));
     const size_t E = (size_t)y->n * w->Kp;
     const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
+    const int add = dc_shift ? 1 : 0;
     if (w->precision == DPF_FP64)
-      k_dc_apply<double><<<nb, 256, 0, s>>>(w->tmp_a, (double2*)w->ms, (double2*)w->V, y->dev.type, y->n, w->K, w->Kp);
+      k_dc_apply<double><<<nb, 256, 0, s>>>(w->tmp_a, (double2*)w->ms, (double2*)w->V, y->dev.type, y->n, w->K, w->Kp,
+                                            add);
     else
-      k_dc_apply<float><<<nb, 256, 0, s>>>(w->tmp_a, (float4*)w->ms, (float2*)w->V, y->dev.type, y->n, w->K, w->Kp);
+      k_dc_apply<float><<<nb, 256, 0, s>>>(w->tmp_a, (float4*)w->ms, (float2*)w->V, y->dev.type, y->n, w->K, w->Kp,
+                                           add);
     if (w->precision == DPF_MIXED) k_mixed_v64<<<nb, 256, 0, s>>>((const float4*)w->ms, (double2*)w->V, E);
     CKLAUNCH();
+    w->launches += (w->precision == DPF_MIXED) ? 2 : 1;
   }
   if (w->direct) {  // padded entries of the direct view
     const size_t np = (size_t)y->iprow_ptr[y->n];
@@ -1367,6 +1398,7 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
     const int nb = (int)std::min<size_t>((np + 255) / 256, (size_t)num_sms() * 16);
     k_pad_entries<<<std::max(nb, 1), 256, 0, s>>>(y->dev.ppos, y->dev.ent32, (int)np, w->pent);
     CKLAUNCH();
+    w->launches++;
   }
   if (w->precision == DPF_FP32R) {  // (after the DC start, which uses these buffers)
     const size_t E = (size_t)y->n * w->Kp;
@@ -1376,6 +1408,7 @@ extern "C" int dpf_solve_begin(const dpf_ybus* y, dpf_workspace* w, const dpf_ba
                                                 w->spec_per_case ? 1 : 0, w->Kp, E, (float2*)w->cbuf,
                                                 (float4*)w->sbuf);
     CKLAUNCH();
+    w->launches++;
   }
   w->t_done = 0;
   w->begun = true;
@@ -1575,6 +1608,7 @@ extern "C" int dpf_solve_end(dpf_workspace* w, const dpf_batch* b, void* stream)
       k_master64<float4><<<nb, 256, 0, s>>>((const float4*)w->ms, w->tmp_a, w->tmp_b, E);
     }
     CKLAUNCH();
+    w->launches++;
     if (b->va) TRY(to_user(w, w->tmp_a, hio, w->st_a, b->va, s));
     if (b->vm) TRY(to_user(w, w->tmp_b, hio, w->st_b, b->vm, s));
   }
@@ -1840,10 +1874,13 @@ static int power_impl(dpf_workspace* w, double* p_calc, double* q_calc, cudaStre
   P.it.n_active = nullptr;
   P.it.tile_cnt = nullptr;
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  w->launches++;
   const size_t E = (size_t)w->y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
   k_widen<R><<<nb, 256, 0, s>>>((const R*)w->sbuf, w->tmp_a, E, 2, 1.0);
+  w->launches++;
   k_widen<R><<<nb, 256, 0, s>>>((const R*)w->sbuf + 1, w->tmp_b, E, 2, 1.0);
+  w->launches++;
   CKLAUNCH();
   if (p_calc) TRY(to_user(w, w->tmp_a, false, nullptr, p_calc, s));
   if (q_calc) TRY(to_user(w, w->tmp_b, false, nullptr, q_calc, s));
@@ -1886,6 +1923,7 @@ static int launch_edge_grad(dpf_workspace* w, double* d_g, double* d_b, double* 
   const int rpw = 32 / w->lanes;
   const int gy = std::max(1, std::min((y->m + w->warps * rpw - 1) / (w->warps * rpw), 65535));
   k_edge_grad<R><<<dim3(w->gx, gy), dim3(w->warps * 32), 0, s>>>(ea);
+  w->launches++;
   CKLAUNCH();
   return DPF_OK;
 }
@@ -1902,6 +1940,7 @@ static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, doub
   P.it.n_active = nullptr;
   P.it.tile_cnt = nullptr;
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);
+  w->launches++;
   CKLAUNCH();
   const size_t E = (size_t)y->n * w->Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
@@ -1911,25 +1950,30 @@ static int loss_backward_impl(dpf_workspace* w, double* loss, double* d_va, doub
     P.itb = P.it;
     P.itb.rpb = w->rpb_b;
     k_adj<R><<<P.gridb, P.block, P.ysmem, s>>>(P.itb);
+    w->launches++;
     CKLAUNCH();
   }
   if (d_va) {
     k_widen<R><<<nb, 256, 0, s>>>((const R*)w->tmp_c, w->tmp_a, E, 1, 1.0);
+    w->launches++;
     CKLAUNCH();
     TRY(to_user(w, w->tmp_a, false, nullptr, d_va, s));
   }
   if (d_vm) {
     k_widen<R><<<nb, 256, 0, s>>>((const R*)w->sbuf, w->tmp_a, E, 1, 1.0);
+    w->launches++;
     CKLAUNCH();
     TRY(to_user(w, w->tmp_a, false, nullptr, d_vm, s));
   }
   if (d_p) {
     k_widen<R><<<nb, 256, 0, s>>>((const R*)w->cbuf, w->tmp_a, E, 2, -1.0);
+    w->launches++;
     CKLAUNCH();
     TRY(to_user(w, w->tmp_a, false, nullptr, d_p, s));
   }
   if (d_q) {
     k_widen<R><<<nb, 256, 0, s>>>((const R*)w->cbuf + 1, w->tmp_a, E, 2, -1.0);
+    w->launches++;
     CKLAUNCH();
     TRY(to_user(w, w->tmp_a, false, nullptr, d_q, s));
   }
@@ -2000,6 +2044,7 @@ extern "C" int dpf_paramid_begin(const dpf_ybus* y, dpf_workspace* w, int32_t n_
 template <class R>
 static int paramid_impl(dpf_workspace* w, double* d_g, double* d_b, double* d_bch, double* loss, cudaStream_t s) {
   k_activate<<<(w->Kp + 255) / 256, 256, 0, s>>>(w->active, w->K, w->Kp);
+  w->launches++;
   Plan<R> P = make_plan<R>(w);
   P.it.cbuf = nullptr;
   P.it.loss_part = nullptr;
@@ -2007,6 +2052,7 @@ static int paramid_impl(dpf_workspace* w, double* d_g, double* d_b, double* d_bc
   P.it.n_active = nullptr;
   P.it.tile_cnt = nullptr;
   k_fwd<R><<<P.grid, P.block, P.smem, s>>>(P.it);  // w = c conj(V) at the staged points (V unchanged)
+  w->launches++;
   CKLAUNCH();
   if (d_g || d_b || d_bch) TRY(launch_edge_grad<R>(w, d_g, d_b, d_bch, s));
   if (loss) {

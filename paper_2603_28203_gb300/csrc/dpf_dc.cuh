@@ -23,6 +23,12 @@
 // two direction buffers alternate.  Slack rows are not unknowns: their r, z,
 // p stay 0 and their x holds the slack angle.
 //
+// Outage shift (dc_start with a warm start): the right-hand side of case k is
+// the outaged branch's DC flow at the case's start angles, c_k = b_l
+// (theta_f - theta_t), put back at its ends (+c_k at f, -c_k at t, 0 elsewhere)
+// and x0 = 0 everywhere, so x is the angle change B'^-1 (B - B') theta that
+// removing the branch causes in the DC model; it is added to the start angles.
+//
 // Precision.  GB300 issues FP64 at a small fraction of its FP32 rate, and in
 // FP64 this loop kept the FP64 pipe 73-86% busy.  So the vectors are double-float:
 // an unevaluated sum hi + lo of two floats (about 48 significant bits, far
@@ -91,6 +97,7 @@ struct DCArgs {
   const int32_t* of;  // per case: internal from/to bus of the outaged branch (-1: none)
   const int32_t* ot;
   double* ob;         // per case: its susceptance b_l
+  const double* flow; // per case: c_k of the outage shift (NULL: solve B' x = P)
   float2* x;       // double-float vectors [N][Kp]
   float2* r;
   float2* z;
@@ -201,7 +208,9 @@ __global__ void __launch_bounds__(1024) k_dc_start(DCArgs a) {
       const size_t e = (size_t)i * Kp + k;
       float2 r = make_float2(0.f, 0.f), z = r;
       if (__ldg(a.type + i) != BUS_SLACK) {
-        const float2 P = df_from(a.spec_per_case ? a.pspec[e] : a.pspec[i]);
+        const double Pi = a.flow ? (i == of ? a.flow[k] : i == ot ? -a.flow[k] : 0.0)
+                                 : (a.spec_per_case ? a.pspec[e] : a.pspec[i]);
+        const float2 P = df_from(Pi);
         r = df_add(P, df_neg(dc_row(a, a.x, i, k, Kp, of, ot, ob2)));
         z = dc_jacobi(a, r, i, of, ot, ob2);
       }
@@ -320,18 +329,33 @@ __global__ void k_dc_widen(float2* x, size_t n) {
   }
 }
 
-// DPF started from the DC angles: theta = x at the pv and pq buses (|V| as
-// initialised), V rebuilt from the master pair.
+// Outage shift: c_k = b_l (theta_f - theta_t) from case k's start angles in
+// the master state (0 for a case without an outage).  After k_dc_case_init.
+template <class R>
+__global__ void k_dc_flow(const typename Prec<R>::MS* __restrict__ ms, const int32_t* __restrict__ of,
+                          const int32_t* __restrict__ ot, const double* __restrict__ ob, double* __restrict__ flow,
+                          int K, int Kp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Kp) return;
+  const int f = k < K ? of[k] : -1, t = k < K ? ot[k] : -1;
+  flow[k] = (f >= 0 && t >= 0)
+                ? ob[k] * (mval(ms_th(ms[(size_t)f * Kp + k])) - mval(ms_th(ms[(size_t)t * Kp + k])))
+                : 0.0;
+}
+
+// DPF started from the DC angles: theta = x (add = 0) or theta + x (add = 1,
+// the outage shift) at the pv and pq buses, |V| as initialised, V rebuilt
+// from the master pair.
 template <class R>
 __global__ void k_dc_apply(const double* __restrict__ x, typename Prec<R>::MS* __restrict__ ms,
                            typename Prec<R>::C* __restrict__ V, const uint8_t* __restrict__ type, int N, int K,
-                           int Kp) {
+                           int Kp, int add) {
   using M = typename Prec<R>::M;
   const size_t n = (size_t)N * Kp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / Kp), k = (int)(e % Kp);
     if (k >= K || __ldg(type + i) == BUS_SLACK) continue;
-    const M th = mfrom<M>(x[e]);
+    const M th = mfrom<M>(add ? mval(ms_th(ms[e])) + x[e] : x[e]);
     const M vm = ms_vm(ms[e]);
     ms[e] = ms_make(th, vm);
     V[e] = volt(th, vm);

@@ -382,4 +382,6 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->plain = 0;
   o->dc_start = 0;
   o->stage_y = 0;
+  o->dc_tol = 1e-10;
+  o->dc_max_iter = 10000;
 }

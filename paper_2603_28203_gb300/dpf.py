@@ -181,6 +181,8 @@ class SolveOpts:
     plain: int | None = None
     dc_start: int | None = None
     stage_y: int | None = None
+    dc_tol: float | None = None
+    dc_max_iter: int | None = None
 
     def to_c(self) -> _abi.DpfSolveOpts:
         o = _abi.DpfSolveOpts()

@@ -46,10 +46,12 @@ def test_refined_byte_model_and_presets():
     # the warm-started N-1 settings are solve options the binding and the oracle both accept
     import dataclasses
     from paper_2603_28203_gb300.dpf import SolveOpts
-    from paper_2603_28203_gb300.presets import N1_WARM, TABLE2
+    from paper_2603_28203_gb300.presets import N1_DC, N1_DC_START, N1_WARM, TABLE2
     names = {fl.name for fl in dataclasses.fields(SolveOpts)}
-    assert set(N1_WARM) <= names and set(TABLE2) <= names
-    o = bench._oracle_dpf_options(3000)
-    assert (o.lr, o.beta1, o.beta2, o.eps, o.sched, o.threshold, o.max_iter, o.check_every) == \
-        (N1_WARM["lr"], N1_WARM["beta1"], N1_WARM["beta2"], N1_WARM["eps"], "plateau", N1_WARM["threshold"], 3000,
-         bench.N1_CHECK_EVERY)
+    assert set(N1_WARM) <= names and set(TABLE2) <= names and set(N1_DC) <= names and set(N1_DC_START) <= names
+    for start, s in (("base", N1_WARM), ("dc", N1_DC)):
+        o = bench._oracle_dpf_options(3000, start)
+        assert (o.lr, o.beta1, o.beta2, o.eps, o.sched, o.threshold, o.max_iter, o.check_every) == \
+            (s["lr"], s["beta1"], s["beta2"], s["eps"], "plateau", s["threshold"], 3000, bench.N1_CHECK_EVERY)
+        assert bench.n1_settings(start)[0] is s
+    assert bench.n1_settings("dc")[1]["dc_start"] == 1 and bench.n1_settings("base")[1] == {}

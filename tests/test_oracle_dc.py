@@ -73,3 +73,42 @@ def test_bus_order_invariance():
     th = oracle.dc_solve(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, g.p_spec)
     thp = oracle.dc_solve(g.n_bus, inv[g.f_bus], inv[g.t_bus], g.x, g.tap, g.bus_type[perm], g.p_spec[perm])
     assert np.abs(thp - th[perm]).max() < 1e-12
+
+
+def test_outage_shift_is_superposition_of_dc_solutions():
+    """DC linearity: the base-case DC angles plus the outage shift of those
+    angles are the DC angles of the outage case (the shift's right-hand side
+    is the injection the removed branch carried)."""
+    g = gridgen.make_grid(80, 7, load_scale=0.3)
+    th0 = oracle.dc_solve(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, g.p_spec, va_slack=0.2)
+    for ell in gridgen.n1_outages(g)[::9]:
+        d = oracle.dc_outage_shift(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, th0, int(ell))
+        th1 = oracle.dc_solve(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, g.p_spec, va_slack=0.2,
+                              outage=int(ell))
+        assert np.abs(th0 + d - th1).max() < 1e-10
+        assert np.all(d[g.bus_type == SLACK] == 0.0)
+
+
+def test_outage_shift_keeps_the_injections_of_arbitrary_angles():
+    """For any angles (here random, as AC angles would be), the shifted angles
+    over the remaining branches give every non-slack bus the net injection
+    the original angles gave it over all branches; no outage: no shift."""
+    g = gridgen.make_grid(60, 2, load_scale=0.2)
+    th = np.random.default_rng(5).normal(0.0, 0.3, g.n_bus)
+    ell = int(gridgen.n1_outages(g)[11])
+    d = oracle.dc_outage_shift(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, th, ell)
+
+    def net(f, t, x, tap, theta):
+        F = oracle.dc_branch_flows(f, t, x, tap, theta)
+        n = np.zeros(g.n_bus)
+        np.add.at(n, f, F)
+        np.add.at(n, t, -F)
+        return n
+
+    keep = np.arange(g.n_branch) != ell
+    before = net(g.f_bus, g.t_bus, g.x, g.tap, th)
+    after = net(g.f_bus[keep], g.t_bus[keep], g.x[keep], g.tap[keep], th + d)
+    u = g.bus_type != SLACK
+    assert np.abs(after[u] - before[u]).max() < 1e-10 * max(1.0, np.abs(before).max())
+    assert np.abs(d).max() > 1e-3  # the removed flow did move the angles
+    assert np.all(oracle.dc_outage_shift(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, th, -1) == 0.0)
