@@ -232,7 +232,8 @@ typedef struct {
                                 block's rows in shared memory like batches */
   double dc_tol;             /* dc_start: relative residual at which a case's
                                 conjugate-gradient DC solve stops (> 0;
-                                default 1e-10)                              */
+                                default 1e-10; >= 1e-5 runs it on FP32
+                                vectors, as dpf_dc_solve)                   */
   int32_t dc_max_iter;       /* dc_start: CG iterations at most (>= 1; default
                                 10000); a case still above dc_tol then
                                 starts from its last CG iterate             */
@@ -384,8 +385,9 @@ int dpf_loss_backward(const dpf_ybus* y, dpf_workspace* ws, int32_t n_case,
  * slack per island).  For n_case cases: p_spec [n_case][n_bus] FP64 device
  * (NULL = the grid's), outage [n_case] device (-1 = none; NULL = none; a
  * bridge is DPF_E_ISLANDED) as for dpf_solve_batch.  Conjugate gradients
- * with the Jacobi preconditioner in FP64 on the GPU, per case until
- * |r| <= tol |r0| or max_iter iterations.  Outputs (caller-owned device
+ * with the Jacobi preconditioner on the GPU, per case until |r| <= tol |r0|
+ * or max_iter iterations; the vectors are double-float pairs (~48 bits)
+ * for tol < 1e-5 and FP32 for tol >= 1e-5, the per-case scalars FP64.  Outputs (caller-owned device
  * arrays): va [n_case][n_bus] (required), iters [n_case] and rel_residual
  * [n_case] (|r| / |r0| at the stop; either may be NULL).  Uses (and
  * resets) the workspace like the other calls. */

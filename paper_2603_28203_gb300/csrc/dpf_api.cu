@@ -1208,13 +1208,16 @@ __global__ void k_dc_set_count(int32_t* n, int K) { *n = K; }
 
 // B' x = P for every case (shift = false), or the outage shift of the cases'
 // start angles in the master state (shift = true; x0 = 0, right-hand side
-// from k_dc_flow).  x ends in tmp_a as FP64.
-static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int max_iter, cudaStream_t s,
-                  bool shift = false) {
+// from k_dc_flow).  x ends in tmp_a as FP64.  T = float2: double-float
+// vectors (8 bytes per element, in the FP64 buffers); T = float: FP32 vectors,
+// all but z in V64's 16 bytes per element.
+template <class T>
+static int dc_run_t(dpf_workspace* w, const int32_t* outage_dev, double tol, int max_iter, cudaStream_t s,
+                    bool shift) {
   const dpf_ybus* y = w->y;
   const DeviceYbus& d = y->dev;
   const int Kp = w->Kp;
-  DCArgs a;
+  DCArgs<T> a;
   memset(&a, 0, sizeof a);
   a.N = y->n;
   a.Kp = Kp;
@@ -1231,14 +1234,22 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   a.va_slack = y->va_slack;
   a.of = w->has_outage ? w->of : nullptr;
   a.ot = w->has_outage ? w->ot : nullptr;
-  // double-float vectors (8 bytes per element, as the FP64 buffers they use)
-  a.x = (float2*)w->tmp_a;
-  a.r = (float2*)w->tmp_b;
-  a.z = (float2*)w->tmp_c;
-  const size_t E0 = (size_t)y->n * Kp;
-  a.p = (float2*)w->V64;            // the two direction buffers share V64's 16 B/element
-  a.p_new = (float2*)w->V64 + E0;
-  a.q = (float2*)w->sbuf;
+  const size_t E = (size_t)y->n * Kp;
+  if constexpr (sizeof(T) == 8) {
+    a.x = (T*)w->tmp_a;
+    a.r = (T*)w->tmp_b;
+    a.z = (T*)w->tmp_c;
+    a.p = (T*)w->V64;  // the two direction buffers share V64's 16 B/element
+    a.p_new = (T*)w->V64 + E;
+    a.q = (T*)w->sbuf;
+  } else {
+    a.p = (T*)w->V64;
+    a.p_new = (T*)w->V64 + E;
+    a.x = (T*)w->V64 + 2 * E;
+    a.r = (T*)w->V64 + 3 * E;
+    a.z = (T*)w->tmp_c;
+    a.q = (T*)w->sbuf;
+  }
   a.rpb = w->rpb;
   a.tile_cnt = w->tile_cnt;
   double* c = w->dcs;
@@ -1258,9 +1269,8 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
   a.tol2 = tol * tol;
   const dim3 grid(Kp / w->lanes, w->gy), block(w->warps * 32);
   const int cb = (Kp + 255) / 256;
-  const size_t E = (size_t)y->n * Kp;
   const int nb = (int)std::min<size_t>((E + 255) / 256, (size_t)num_sms() * 16);
-  k_dc_case_init<<<cb, 256, 0, s>>>(a, outage_dev, d.br_x, d.br_tap);
+  k_dc_case_init<T><<<cb, 256, 0, s>>>(a, outage_dev, d.br_x, d.br_tap);
   if (shift) {
     if (!a.of) return fail(DPF_E_INVALID, "the outage shift needs outages");
     if (w->precision == DPF_FP64)
@@ -1269,13 +1279,13 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
       k_dc_flow<float><<<cb, 256, 0, s>>>((const float4*)w->ms, a.of, a.ot, a.ob, c + 8 * (size_t)Kp, w->K, Kp);
   }
   k_dc_set_count<<<1, 1, 0, s>>>(a.n_active, w->K);
-  k_dc_x0<<<std::max(nb, 1), 256, 0, s>>>(a);
-  k_dc_start<<<grid, block, 0, s>>>(a);
+  k_dc_x0<T><<<std::max(nb, 1), 256, 0, s>>>(a);
+  k_dc_start<T><<<grid, block, 0, s>>>(a);
   CKLAUNCH();
   w->launches += shift ? 5 : 4;
   for (int it = 0; it < max_iter; ++it) {
-    k_dc_spmv_dir<<<grid, block, 0, s>>>(a);
-    k_dc_update_case<<<grid, block, 0, s>>>(a);
+    k_dc_spmv_dir<T><<<grid, block, 0, s>>>(a);
+    k_dc_update_case<T><<<grid, block, 0, s>>>(a);
     CKLAUNCH();
     w->launches += 2;
     std::swap(a.p, a.p_new);
@@ -1285,10 +1295,17 @@ static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int m
       if (*w->h_dc_nact == 0) break;
     }
   }
-  k_dc_widen<<<std::max(nb, 1), 256, 0, s>>>(a.x, E);  // the FP64 solution, in place
+  k_dc_widen<T><<<std::max(nb, 1), 256, 0, s>>>(a.x, w->tmp_a, E);  // the FP64 solution
   CKLAUNCH();
   w->launches++;
   return DPF_OK;
+}
+
+// Relative residuals of 1e-5 and above run on FP32 vectors.
+static int dc_run(dpf_workspace* w, const int32_t* outage_dev, double tol, int max_iter, cudaStream_t s,
+                  bool shift = false) {
+  return tol >= 1e-5 ? dc_run_t<float>(w, outage_dev, tol, max_iter, s, shift)
+                     : dc_run_t<float2>(w, outage_dev, tol, max_iter, s, shift);
 }
 
 extern "C" int dpf_dc_solve(const dpf_ybus* y, dpf_workspace* w, int32_t n_case, const double* p_spec,

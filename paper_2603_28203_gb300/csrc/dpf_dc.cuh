@@ -37,8 +37,11 @@
 // transformations of Knuth (two-sum) and Dekker (two-product, here with an
 // FMA), as in the double-double arithmetic of Hida, Li and Bailey.  B and
 // 1 / B_ii are uploaded as hi/lo pairs; the per-case scalars (alpha, beta, the
-// dot products' totals, the stop test) stay FP64.  x is widened to FP64 in
-// place at the end.
+// dot products' totals, the stop test) stay FP64.  x is widened to FP64 at the
+// end.  A solve asked for a relative residual of 1e-5 or more (a start for
+// the DPF iterations, not an answer) runs the same kernels on plain FP32
+// vectors (T = float: half the bytes, no two-sums), B and 1 / B_ii their
+// high words.
 #pragma once
 
 #include "dpf_kernels.cuh"
@@ -82,8 +85,25 @@ __device__ __forceinline__ float2 df_div(float2 a, float2 b) {
   const float2 r = df_add(a, df_neg(df_mul(make_float2(q0, 0.f), b)));
   return df_quick(q0, __fdiv_rn(r.x, b.x));
 }
+// The same operations on plain FP32 vectors (T = float).
+__device__ __forceinline__ float df_add(float a, float b) { return a + b; }
+__device__ __forceinline__ float df_mul(float a, float b) { return a * b; }
+__device__ __forceinline__ float df_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float df_neg(float a) { return -a; }
+__device__ __forceinline__ double df_val(float a) { return (double)a; }
+__device__ __forceinline__ float df_div(float a, float b) { return __fdiv_rn(a, b); }
+template <class T> __device__ __forceinline__ T df_cast(double v);
+template <> __device__ __forceinline__ float2 df_cast<float2>(double v) { return df_from(v); }
+template <> __device__ __forceinline__ float df_cast<float>(double v) { return (float)v; }
+// B entries (uploaded as hi/lo pairs) in the vector type
+template <class T> __device__ __forceinline__ T df_coef(float2 v);
+template <> __device__ __forceinline__ float2 df_coef<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ float df_coef<float>(float2 v) { return v.x; }
+template <class T> __device__ __forceinline__ T df_zero();
+template <> __device__ __forceinline__ float2 df_zero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ float df_zero<float>() { return 0.f; }
 
-struct DCArgs {
+template <class T> struct DCArgs {
   int N, Kp, lanes, K;
   const int32_t* __restrict__ rp;
   const int32_t* __restrict__ col;
@@ -98,12 +118,12 @@ struct DCArgs {
   const int32_t* ot;
   double* ob;         // per case: its susceptance b_l
   const double* flow; // per case: c_k of the outage shift (NULL: solve B' x = P)
-  float2* x;       // double-float vectors [N][Kp]
-  float2* r;
-  float2* z;
-  float2* p;       // direction of the previous iteration
-  float2* p_new;   // direction of this iteration
-  float2* q;       // B' p of the previous iteration, then of this one
+  T* x;            // vectors [N][Kp] (double-float pairs or FP32)
+  T* r;
+  T* z;
+  T* p;            // direction of the previous iteration
+  T* p_new;        // direction of this iteration
+  T* q;            // B' p of the previous iteration, then of this one
   int rpb;                  // rows per CTA
   unsigned int* tile_cnt;   // per case tile: CTAs done with the update (reset by the last)
   // per case
@@ -149,27 +169,31 @@ __device__ __forceinline__ void case_sum2_atomic(double a, double b, int lanes, 
 }
 
 // (B' v)_i for case k (v in the case-minor layout); ob2 = the outaged
-// branch's b_l as a double-float.
-__device__ __forceinline__ float2 dc_row(const DCArgs& a, const float2* __restrict__ v, int i, int k, size_t Kp,
-                                         int of, int ot, float2 ob2) {
-  float2 s = make_float2(0.f, 0.f);
+// branch's b_l in the vector type.
+template <class T>
+__device__ __forceinline__ T dc_row(const DCArgs<T>& a, const T* __restrict__ v, int i, int k, size_t Kp, int of,
+                                    int ot, T ob2) {
+  T s = df_zero<T>();
   const int p1 = __ldg(a.rp + i + 1);
-  for (int p = __ldg(a.rp + i); p < p1; ++p) s = df_fma(__ldg(a.bval + p), v[(size_t)__ldg(a.col + p) * Kp + k], s);
+  for (int p = __ldg(a.rp + i); p < p1; ++p)
+    s = df_fma(df_coef<T>(__ldg(a.bval + p)), v[(size_t)__ldg(a.col + p) * Kp + k], s);
   if (i == of || i == ot) {
-    const float2 d = df_add(v[(size_t)of * Kp + k], df_neg(v[(size_t)ot * Kp + k]));  // v_f - v_t
+    const T d = df_add(v[(size_t)of * Kp + k], df_neg(v[(size_t)ot * Kp + k]));  // v_f - v_t
     s = df_fma(i == of ? df_neg(ob2) : ob2, d, s);
   }
   return s;
 }
 
 // Jacobi step z_i = r_i / B'_ii.
-__device__ __forceinline__ float2 dc_jacobi(const DCArgs& a, float2 r, int i, int of, int ot, float2 ob2) {
-  if (i == of || i == ot) return df_div(r, df_add(__ldg(a.bval + __ldg(a.dpos + i)), df_neg(ob2)));
-  return df_mul(r, __ldg(a.dinv + i));
+template <class T>
+__device__ __forceinline__ T dc_jacobi(const DCArgs<T>& a, T r, int i, int of, int ot, T ob2) {
+  if (i == of || i == ot) return df_div(r, df_add(df_coef<T>(__ldg(a.bval + __ldg(a.dpos + i))), df_neg(ob2)));
+  return df_mul(r, df_coef<T>(__ldg(a.dinv + i)));
 }
 
 // Per case: the outaged branch's susceptance, the solver state reset.
-__global__ void k_dc_case_init(DCArgs a, const int32_t* __restrict__ outage, const double* __restrict__ br_x,
+template <class T>
+__global__ void k_dc_case_init(DCArgs<T> a, const int32_t* __restrict__ outage, const double* __restrict__ br_x,
                                const double* __restrict__ br_tap) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.Kp) return;
@@ -183,9 +207,10 @@ __global__ void k_dc_case_init(DCArgs a, const int32_t* __restrict__ outage, con
 }
 
 // x0 (slack angle at slack buses, 0 elsewhere) for every element; p, q zeroed.
-__global__ void k_dc_x0(DCArgs a) {
+template <class T>
+__global__ void k_dc_x0(DCArgs<T> a) {
   const size_t n = (size_t)a.N * a.Kp;
-  const float2 zero = make_float2(0.f, 0.f), vs = df_from(a.va_slack);
+  const T zero = df_zero<T>(), vs = df_cast<T>(a.va_slack);
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / a.Kp);
     a.x[e] = (__ldg(a.type + i) == BUS_SLACK) ? vs : zero;
@@ -196,21 +221,22 @@ __global__ void k_dc_x0(DCArgs a) {
 }
 
 // r0 = P - B' x0 at the unknowns, z0 = r0 / diag, p0 = z0; sums r.z, r.r.
-__global__ void __launch_bounds__(1024) k_dc_start(DCArgs a) {
+template <class T>
+__global__ void __launch_bounds__(1024) k_dc_start(DCArgs<T> a) {
   const Map mp = thread_map(a.lanes);
   const int k = mp.k;
   const size_t Kp = (size_t)a.Kp;
-  float2 rz = make_float2(0.f, 0.f), rr = rz;
+  T rz = df_zero<T>(), rr = rz;
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const float2 ob2 = df_from(a.ob[k]);
+    const T ob2 = df_cast<T>(a.ob[k]);
     for (int i = mp.row0; i < a.N; i += mp.rstride) {
       const size_t e = (size_t)i * Kp + k;
-      float2 r = make_float2(0.f, 0.f), z = r;
+      T r = df_zero<T>(), z = r;
       if (__ldg(a.type + i) != BUS_SLACK) {
         const double Pi = a.flow ? (i == of ? a.flow[k] : i == ot ? -a.flow[k] : 0.0)
                                  : (a.spec_per_case ? a.pspec[e] : a.pspec[i]);
-        const float2 P = df_from(Pi);
+        const T P = df_cast<T>(Pi);
         r = df_add(P, df_neg(dc_row(a, a.x, i, k, Kp, of, ot, ob2)));
         z = dc_jacobi(a, r, i, of, ot, ob2);
       }
@@ -224,19 +250,20 @@ __global__ void __launch_bounds__(1024) k_dc_start(DCArgs a) {
   case_sum2_atomic(df_val(rz), df_val(rr), a.lanes, a.rz, a.rr0, a.Kp);
 }
 
-__global__ void __launch_bounds__(256) k_dc_spmv_dir(DCArgs a) {
+template <class T>
+__global__ void __launch_bounds__(256) k_dc_spmv_dir(DCArgs<T> a) {
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
   const int k = mp.k;
   const size_t Kp = (size_t)a.Kp;
-  float2 pq = make_float2(0.f, 0.f);
+  T pq = df_zero<T>();
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const float2 ob2 = df_from(a.ob[k]), beta = df_from(a.beta[k]);
+    const T ob2 = df_cast<T>(a.ob[k]), beta = df_cast<T>(a.beta[k]);
     for (int i = mp.i0; i < mp.r1; i += mp.istride) {
       if (__ldg(a.type + i) == BUS_SLACK) continue;  // p, q stay 0 there
       const size_t e = (size_t)i * Kp + k;
-      const float2 pn = df_fma(beta, a.p[e], a.z[e]);
-      const float2 q = df_fma(beta, a.q[e], dc_row(a, a.z, i, k, Kp, of, ot, ob2));
+      const T pn = df_fma(beta, a.p[e], a.z[e]);
+      const T q = df_fma(beta, a.q[e], dc_row(a, a.z, i, k, Kp, of, ot, ob2));
       a.p_new[e] = pn;
       a.q[e] = q;
       pq = df_fma(pn, q, pq);
@@ -246,7 +273,8 @@ __global__ void __launch_bounds__(256) k_dc_spmv_dir(DCArgs a) {
 }
 
 // Per case, after all row blocks' sums: convergence test and the next beta.
-__device__ __forceinline__ void dc_case_step(const DCArgs& a, int k) {
+template <class T>
+__device__ __forceinline__ void dc_case_step(const DCArgs<T>& a, int k) {
   if (a.active[k]) {
     a.iters[k] += 1;
     const double rr = __ldcg(a.rr + k), rr0 = __ldcg(a.rr0 + k), rzn = __ldcg(a.rzn + k);
@@ -265,7 +293,8 @@ __device__ __forceinline__ void dc_case_step(const DCArgs& a, int k) {
   a.rr[k] = 0.0;
 }
 
-__global__ void __launch_bounds__(256) k_dc_update_case(DCArgs a) {
+template <class T>
+__global__ void __launch_bounds__(256) k_dc_update_case(DCArgs<T> a) {
   const BMap mp = block_map(a.lanes, a.N, a.rpb);
   const int k = mp.k;
   const size_t Kp = (size_t)a.Kp;
@@ -282,17 +311,17 @@ __global__ void __launch_bounds__(256) k_dc_update_case(DCArgs a) {
     s_alpha[threadIdx.x] = al;
   }
   __syncthreads();
-  float2 rz = make_float2(0.f, 0.f), rr = rz;
+  T rz = df_zero<T>(), rr = rz;
   if (k < a.Kp && a.active[k]) {
     const int of = a.of ? a.of[k] : -1, ot = a.ot ? a.ot[k] : -1;
-    const float2 ob2 = df_from(a.ob[k]);
-    const float2 alpha = df_from(s_alpha[mp.kl]), nalpha = df_neg(alpha);
+    const T ob2 = df_cast<T>(a.ob[k]);
+    const T alpha = df_cast<T>(s_alpha[mp.kl]), nalpha = df_neg(alpha);
     for (int i = mp.i0; i < mp.r1; i += mp.istride) {
       if (__ldg(a.type + i) == BUS_SLACK) continue;
       const size_t e = (size_t)i * Kp + k;
       a.x[e] = df_fma(alpha, a.p_new[e], a.x[e]);
-      const float2 r = df_fma(nalpha, a.q[e], a.r[e]);
-      const float2 z = dc_jacobi(a, r, i, of, ot, ob2);
+      const T r = df_fma(nalpha, a.q[e], a.r[e]);
+      const T z = dc_jacobi(a, r, i, of, ot, ob2);
       a.r[e] = r;
       a.z[e] = z;
       rz = df_fma(r, z, rz);
@@ -320,12 +349,13 @@ __global__ void __launch_bounds__(256) k_dc_update_case(DCArgs a) {
   }
 }
 
-// The double-float solution widened to FP64 in place (each element's 8 bytes
-// are read before they are written).
-__global__ void k_dc_widen(float2* x, size_t n) {
+// The solution widened to FP64: in place for double-float pairs (each
+// element's 8 bytes are read before they are written), into `out` for FP32.
+template <class T>
+__global__ void k_dc_widen(T* x, double* out, size_t n) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const float2 v = x[e];
-    reinterpret_cast<double*>(x)[e] = df_val(v);
+    const T v = x[e];
+    out[e] = df_val(v);
   }
 }
 

@@ -188,10 +188,19 @@ __device__ __forceinline__ float2 volt(float2 th, float2 vm) {
   const float m = vm.x + vm.y;
   return make_float2(m * c2, m * s2);
 }
-// The same, also returning the unit phasor u = e^{j theta} (V = |V| u).
+// The same, also returning the unit phasor u = e^{j theta} (V = |V| u); the
+// refined FP32 adjoint's voltage.  The high word is first reduced to
+// [-pi, pi] (Cody and Waite's reduction: k = rint(theta / 2 pi), theta - k 2 pi
+// with 2 pi split into 6.28125, exact in 8 bits so that k * 6.28125 is exact,
+// plus the float nearest 2 pi - 6.28125), then the SFU sine and cosine
+// (__sincosf: absolute error below 4e-7 on [-pi, pi]).  u only scales the
+// gradient and the step's voltage change, for which that suffices; the
+// mismatch itself comes from the FP64 residual and dV.
 __device__ __forceinline__ float2 volt(float2 th, float2 vm, float2& u) {
   float s, c;
-  sincosf(th.x, &s, &c);
+  const float kk = rintf(th.x * 0.15915494f);  // 1 / (2 pi)
+  const float red = fmaf(-kk, 1.93530718e-3f, fmaf(-kk, 6.28125f, th.x));
+  __sincosf(red, &s, &c);
   u = make_float2(fmaf(-th.y, s, c), fmaf(th.y, c, s));
   const float m = vm.x + vm.y;
   return make_float2(m * u.x, m * u.y);

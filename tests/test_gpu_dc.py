@@ -54,6 +54,29 @@ def test_dc_n1_and_per_case_injections_match_oracle():
         assert th[k][g.bus_type == SLACK][0] == g.va_slack
 
 
+def test_dc_fp32_vectors_at_a_loose_tolerance():
+    """tol >= 1e-5 runs the CG on FP32 vectors: every case stops with the
+    recurrence's |r| / |r0| <= tol, and the true relative residual of the
+    returned angles, recomputed by the oracle in FP64, stays within 10 tol
+    (the FP32 recurrence drifts from it by rounding only)."""
+    g = gridgen.config_grid("c3_n1_2kbus")
+    K = 40
+    ells = np.concatenate([[-1], np.random.default_rng(5).choice(gridgen.n1_outages(g), K - 1, replace=False)])
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    tol = 1e-4
+    out = dpf.dpf_dc_solve(y, ws, K, outage=_t(ells.astype(np.int32), torch.int32), tol=tol)
+    th = out["va"].cpu().numpy()
+    assert (out["rel_residual"].cpu().numpy() <= tol).all()
+    u = np.where(g.bus_type != SLACK)[0]
+    for k in range(K):
+        B = oracle.dc_matrix(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, int(ells[k]))
+        rhs = g.p_spec[u] - B[u][:, g.bus_type == SLACK] @ np.full((g.bus_type == SLACK).sum(), g.va_slack)
+        true = np.linalg.norm((B[u][:, u] @ th[k][u]) - rhs) / np.linalg.norm(rhs)
+        assert true <= 10 * tol, (k, true)
+        assert th[k][g.bus_type == SLACK][0] == g.va_slack
+
+
 def test_dc_islands_and_single_case():
     grids = [gridgen.make_grid(n, 40 + i, load_scale=0.2) for i, n in enumerate([30, 55, 80])]
     cat = gridgen.concat_grids(grids)
