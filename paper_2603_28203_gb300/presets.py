@@ -33,8 +33,8 @@ iteration), the budget chosen with them.  The shift lowers the median
 starting mismatch from 0.106 to 0.061 p.u. and, with N1_WARM's settings,
 raises the converged cases from 61 to 138 within 4,000 iterations; the
 search then brought a rate 3x lower.  The CG solve of the shift stops at a
-relative residual of 1e-4 or after 241 iterations, about 35 ms on the
-2,000-bus batch.
+relative residual of 1e-4 or after 241 iterations (FP32 vectors, about 19 ms
+on the 2,000-bus batch).
 """
 from . import _abi
 
