@@ -10,10 +10,11 @@ A step is one whole batched solve, inputs resident on the GPU: the base case
 started from the base case's solution (the warm start of Sec. 5.4.2) shifted
 by the DC angle change of its outage (`--n1-start dc`, the default; `base`:
 no shift), refined FP32 iterations (DPF_FP32R) with the FP64 convergence
-test every 50 iterations (cases whose FP32 mismatch is within 5e-6 p.u.;
-every case every 100 iterations) and per-case early stopping at 1e-6 p.u.,
-up to `--n1-budget` iterations (3,500 with the shift, settings
-presets.N1_DC; 4,000 without, presets.N1_WARM).  `value` counts only the
+test every 100 iterations on the cases whose FP32 mismatch is within 5e-6
+p.u. and every 500 on every case (presets.N1_DC_TEST; unshifted: 50 and 100)
+and per-case early stopping at 1e-6 p.u., up to `--n1-budget` iterations
+(3,500 with the shift, settings presets.N1_DC; 4,000 without,
+presets.N1_WARM).  `value` counts only the
 cases the FP64 test declares converged (max |f| <= 1e-6 p.u.), per second;
 the others are reported, not counted.  A solve takes ~0.5 s and moves ~0.5 GB
 per iteration, far beyond the 129 MB L2 (no flush needed).
@@ -47,8 +48,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 ITERS_PER_SOLVE = 1000  # Table 2: maximum iterations of one DPF solve from the flat start
 from paper_2603_28203_gb300.presets import N1_BUDGET, N1_DC_BUDGET  # iterations of one N-1 solve  # noqa: E402
-N1_CHECK_EVERY = 50     # FP64 test interval of the warm-started N-1 solve
-N1_GATE = 5e-6          # its FP32 gate: the refined FP32 mismatch is accurate far below this
 CHECK_EVERY = 25
 TOL = 1e-6
 LR = 1e-3               # flat-start FP32 iterations of the N-1 batch (Table 2 otherwise)
@@ -81,26 +80,27 @@ def _oracle_base():
 
 
 def n1_settings(start):
-    """(optimiser settings, start options, default budget) of the N-1 solve:
-    start "dc" = the base case's solution shifted by each outage's DC angle
-    change, "base" = the base case's solution."""
+    """(optimiser settings, start and test options, default budget) of the
+    N-1 solve: start "dc" = the base case's solution shifted by each outage's
+    DC angle change, "base" = the base case's solution.  The test options
+    hold the FP64 test interval (check_every) and the FP32 gate."""
     from paper_2603_28203_gb300 import presets
     if start == "dc":
-        return presets.N1_DC, presets.N1_DC_START, N1_DC_BUDGET
+        return presets.N1_DC, dict(presets.N1_DC_START, **presets.N1_DC_TEST), N1_DC_BUDGET
     if start == "base":
-        return presets.N1_WARM, {}, N1_BUDGET
+        return presets.N1_WARM, dict(presets.N1_TEST), N1_BUDGET
     raise ValueError(f"unknown N-1 start {start!r}")
 
 
 def _oracle_dpf_options(budget, start):
     import oracle
     from paper_2603_28203_gb300 import _abi
-    s = n1_settings(start)[0]
+    s, t, _ = n1_settings(start)
     sched = {_abi.SCHED_PLATEAU: "plateau", _abi.SCHED_STEP: "step", _abi.SCHED_CONST: "const"}[s["sched"]]
     return oracle.DPFOptions(lr=s["lr"], beta1=s["beta1"], beta2=s["beta2"], eps=s["eps"],
                              sched=sched, factor=s["factor"], patience=s["patience"],
                              threshold=s["threshold"], cooldown=s["cooldown"], max_iter=budget, tol=TOL,
-                             check_every=N1_CHECK_EVERY)
+                             check_every=t["check_every"])
 
 
 def _oracle_case(args):
@@ -329,8 +329,8 @@ class N1Job:
                          vm=torch.zeros((1, self.N), dtype=torch.float64, device=dev),
                          status=torch.zeros(1, dtype=torch.int32, device=dev))
         self.res = _outputs(torch, self.K, self.N, dev)
-        self.opts = dpf.SolveOpts(precision=dpf.FP32R, tol=TOL, check_every=N1_CHECK_EVERY, gate=N1_GATE,
-                                  max_iter=budget, flat_start=0, lanes=args.lanes or None, warps=args.warps or None,
+        self.opts = dpf.SolveOpts(precision=dpf.FP32R, tol=TOL, max_iter=budget, flat_start=0,
+                                  lanes=args.lanes or None, warps=args.warps or None,
                                   row_blocks=args.row_blocks or None, pdl=0 if args.no_pdl else None, **settings,
                                   **start_opts)
         self.shape_by = "command line" if (args.lanes or args.warps or args.row_blocks) else \
@@ -364,7 +364,7 @@ class N1Job:
         with self.torch.cuda.stream(self.stream):
             d.dpf_solve_begin(self.y, self.ws, self.opts, stream=self.stream, n_case=self.K, outage=self.outage,
                               va_start=self.base["va"][0], vm_start=self.base["vm"][0])
-            d.dpf_solve_iterate(self.ws, N1_CHECK_EVERY, stream=self.stream)
+            d.dpf_solve_iterate(self.ws, self.opts.check_every, stream=self.stream)
             d.dpf_profile_enable(self.ws, True)
             d.dpf_solve_iterate(self.ws, n_iter, stream=self.stream)
             t = d.dpf_kernel_times(self.ws, stream=self.stream)
@@ -458,7 +458,7 @@ def run_ours(args):
         subs["uneven"] = uneven_record(dpf, torch, args)
 
     if rank == 0:
-        ce = N1_CHECK_EVERY
+        ce = job.opts.check_every
         line = {
             "metric": METRIC,
             "value": value,
@@ -481,7 +481,8 @@ def run_ours(args):
                                if args.n1_start == "dc" else ""),
                 "n1_start": args.n1_start,
                 "n_bus": N, "n_branch": g.n_branch, "cases_per_gpu": int(K), "nnz": job.y.nnz,
-                "iteration_precision": "fp32r", "check_every": ce, "gate_pu": N1_GATE, "tol_pu": TOL,
+                "iteration_precision": "fp32r", "check_every": ce, "gate_pu": job.opts.gate,
+                "refresh_every": job.opts.refresh_every or 100, "tol_pu": TOL,
                 "budget_iterations": args.n1_budget,
                 "optimizer": "Adam + ReduceLROnPlateau, presets."
                              + ("N1_DC" if args.n1_start == "dc" else "N1_WARM")

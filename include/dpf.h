@@ -74,8 +74,8 @@ enum { DPF_PQ = 0, DPF_PV = 1, DPF_SLACK = 2 };            /* bus types (Sec. 2.
  * scales with dV instead of with |Y_ii| |V|, and the iterations reach
  * mismatches far below DPF_FP32's limit.  The FP64 test (every check_every
  * iterations, on the cases the gate admits, and on every active case at
- * the test of every 100th step -- or at every test if check_every > 50)
- * renews f_ref, I_ref and V_ref.  Until a case's first test its iterations
+ * the test of every refresh_every-th step, 100 by default -- or at every
+ * test if check_every is larger) renews f_ref, I_ref and V_ref.  Until a case's first test its iterations
  * equal DPF_FP32 ones. */
 enum { DPF_FP32 = 0, DPF_FP64 = 1, DPF_MIXED = 2, DPF_FP32R = 3 };
 enum { DPF_SCHED_CONST = 0, DPF_SCHED_PLATEAU = 1, DPF_SCHED_STEP = 2 };
@@ -237,6 +237,13 @@ typedef struct {
   int32_t dc_max_iter;       /* dc_start: CG iterations at most (>= 1; default
                                 10000); a case still above dc_tol then
                                 starts from its last CG iterate             */
+  int32_t refresh_every;     /* DPF_FP32R with a gate: every active case is
+                                tested, and its references renewed, when its
+                                step count is a multiple of this (rounded
+                                down to a multiple of check_every, at least
+                                check_every); 0 = 100 (default).  The
+                                refined mismatch's rounding grows with |dV|,
+                                the distance moved since the last renewal. */
 } dpf_solve_opts;
 
 void dpf_default_opts(dpf_solve_opts* o);

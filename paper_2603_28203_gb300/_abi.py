@@ -52,7 +52,7 @@ class DpfSolveOpts(C.Structure):
         ("use_graph", C.c_int32), ("pair_cases", C.c_int32), ("pdl", C.c_int32), ("stage_v", C.c_int32),
         ("plain", C.c_int32),
         ("dc_start", C.c_int32), ("stage_y", C.c_int32),
-        ("dc_tol", C.c_double), ("dc_max_iter", C.c_int32),
+        ("dc_tol", C.c_double), ("dc_max_iter", C.c_int32), ("refresh_every", C.c_int32),
     ]
 
 

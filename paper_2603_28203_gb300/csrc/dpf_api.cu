@@ -614,7 +614,8 @@ static Plan<R> make_plan(dpf_workspace* w) {
   // refined FP32: the test at every 100th step (or every test, with longer
   // intervals) also re-anchors the cases the gate keeps out
   const int ce = std::max(1, w->opts.check_every);
-  c.full_every = (gated && w->precision == DPF_FP32R) ? std::max(ce, 100 / ce * ce) : 0;
+  const int re = w->opts.refresh_every > 0 ? w->opts.refresh_every : 100;
+  c.full_every = (gated && w->precision == DPF_FP32R) ? std::max(ce, re / ce * ce) : 0;
   c.of = w->of;
   c.ot = w->ot;
   c.yff = w->yff64;
@@ -1180,6 +1181,7 @@ static int validate_opts(const dpf_solve_opts* o) {
   if (o->dc_start && (!(o->dc_tol > 0 && o->dc_tol < 1e300) || o->dc_max_iter < 1))
     return fail(DPF_E_INVALID, "dc_start needs dc_tol > 0 and dc_max_iter >= 1");
   if (o->stage_y != 0 && o->stage_y != 1) return fail(DPF_E_INVALID, "stage_y must be 0 or 1");
+  if (o->refresh_every < 0) return fail(DPF_E_INVALID, "refresh_every must be >= 0");
   if (o->lanes < 0 || o->lanes > 32 || o->warps < 0 || o->warps > 8 || o->row_blocks < 0)
     return fail(DPF_E_INVALID, "invalid launch shape (lanes 0..32, warps 0..8, row_blocks >= 0)");
   return DPF_OK;

@@ -384,4 +384,5 @@ extern "C" void dpf_default_opts(dpf_solve_opts* o) {
   o->stage_y = 0;
   o->dc_tol = 1e-10;
   o->dc_max_iter = 10000;
+  o->refresh_every = 0;
 }

@@ -183,6 +183,7 @@ class SolveOpts:
     stage_y: int | None = None
     dc_tol: float | None = None
     dc_max_iter: int | None = None
+    refresh_every: int | None = None
 
     def to_c(self) -> _abi.DpfSolveOpts:
         o = _abi.DpfSolveOpts()

@@ -52,6 +52,9 @@ def test_refined_byte_model_and_presets():
     for start, s in (("base", N1_WARM), ("dc", N1_DC)):
         o = bench._oracle_dpf_options(3000, start)
         assert (o.lr, o.beta1, o.beta2, o.eps, o.sched, o.threshold, o.max_iter, o.check_every) == \
-            (s["lr"], s["beta1"], s["beta2"], s["eps"], "plateau", s["threshold"], 3000, bench.N1_CHECK_EVERY)
+            (s["lr"], s["beta1"], s["beta2"], s["eps"], "plateau", s["threshold"], 3000,
+             bench.n1_settings(start)[1]["check_every"])
         assert bench.n1_settings(start)[0] is s
-    assert bench.n1_settings("dc")[1]["dc_start"] == 1 and bench.n1_settings("base")[1] == {}
+    assert bench.n1_settings("dc")[1]["dc_start"] == 1 and "dc_start" not in bench.n1_settings("base")[1]
+    for start in ("dc", "base"):
+        assert set(bench.n1_settings(start)[1]) <= names

@@ -143,6 +143,54 @@ def test_n1_warm_start_converged_cases_match_newton():
         assert abs(np.abs(f).max() - r["max_mismatch"][k]) <= 1e-12 * max(1.0, np.abs(f).max()), k
 
 
+def test_n1_benchmark_configuration_dc_shift():
+    """The benchmark's N-1 step as bench.py runs it: the base case by the
+    library's Newton-Raphson, every case's start shifted by the DC angle
+    change of its outage, presets.N1_DC / N1_DC_START / N1_DC_TEST, the
+    budget N1_DC_BUDGET, the autotuned launch shape.  At least 150 of the
+    2,379 cases converge (219 when this was written; the count moves by
+    ~10% with the last bits of the arithmetic).  Sampled converged cases: the
+    reported FP64 mismatch is the oracle's on Y_bus rebuilt without the
+    branch, and the state is the oracle's Newton root up to J^-1 f (1e-7);
+    sampled unconverged cases report their true mismatch."""
+    from paper_2603_28203_gb300.presets import N1_DC, N1_DC_BUDGET, N1_DC_START, N1_DC_TEST
+    import scipy.sparse.linalg as spla
+    g = gridgen.config_grid("c3_n1_2kbus")
+    outs = gridgen.n1_outages(g)
+    K, N = outs.size, g.n_bus
+    y = dpf.dpf_build_ybus(g)
+    nrh = dpf.dpf_nr_create(y, 1)
+    bva = torch.zeros((1, N), dtype=torch.float64, device=DEV)
+    bvm = torch.zeros((1, N), dtype=torch.float64, device=DEV)
+    dpf.dpf_nr_solve(nrh, precision=dpf.FP64, tol=1e-10, max_iter=20, n_case=1, va=bva, vm=bvm)
+    nrh.free()
+    ws = dpf.dpf_workspace_create(y, K)
+    od = _t(outs, torch.int32)
+    opts = dpf.SolveOpts(precision=dpf.FP32R, tol=1e-6, max_iter=N1_DC_BUDGET, flat_start=0, **N1_DC, **N1_DC_START,
+                         **N1_DC_TEST)
+    opts = dpf.dpf_autotune(y, ws, opts, iters=50, n_case=K, outage=od, va_start=bva[0], vm_start=bvm[0])
+    r = _solve(y, ws, K, opts, va_start=bva[0], vm_start=bvm[0], outage=od)
+    conv = np.nonzero(r["status"] == dpf.CASE_CONVERGED)[0]
+    assert conv.size >= 150, conv.size
+    assert (r["max_mismatch"][conv] <= 1e-6).all()
+    assert (r["iters"][conv] <= N1_DC_BUDGET).all()
+    pvpq, pq = oracle.learnable_sets(g.bus_type)
+    for k in conv[:: max(1, conv.size // 5)][:5]:
+        Yk = _ybus_without(g, int(outs[k]))
+        f, _ = oracle.mismatch(Yk, r["va"][k], r["vm"][k], g.p_spec, g.q_spec, g.bus_type)
+        assert abs(np.abs(f).max() - r["max_mismatch"][k]) <= 1e-12, k
+        nr = oracle.nr_solve(Yk, g.p_spec, g.q_spec, g.bus_type, g.vm_set, va_slack=g.va_slack)
+        assert nr["converged"], k
+        dx = np.concatenate([r["va"][k][pvpq] - nr["va"][pvpq], r["vm"][k][pq] - nr["vm"][pq]])
+        lin = spla.spsolve(oracle.jacobian_f(Yk, nr["va"], nr["vm"], g.bus_type), f)
+        assert np.abs(dx - lin).max() <= 1e-7, (k, np.abs(dx - lin).max(), np.abs(dx).max())
+    rest = np.setdiff1d(np.arange(K), conv)
+    for k in rest[:: max(1, rest.size // 3)][:3]:
+        f, _ = oracle.mismatch(_ybus_without(g, int(outs[k])), r["va"][k], r["vm"][k], g.p_spec, g.q_spec,
+                               g.bus_type)
+        assert abs(np.abs(f).max() - r["max_mismatch"][k]) <= 1e-12 * max(1.0, np.abs(f).max()), k
+
+
 @pytest.mark.parametrize("outages", [False, True])
 def test_pair_kernels_match_single(outages):
     """FP32R batches of >= 64 cases run two cases per thread: the same
@@ -236,6 +284,13 @@ def test_refined_option_checks():
         dpf.dpf_power(y, ws, va, va + 1, precision=dpf.FP32R)
     with pytest.raises(dpf.DPFError):
         dpf.dpf_loss_backward(y, ws, va, va + 1, precision=dpf.FP32R)
+    with pytest.raises(dpf.DPFError):  # a negative renewal interval
+        dpf.dpf_solve_batch(y, ws, dpf.SolveOpts(precision=dpf.FP32R, refresh_every=-1), n_case=2, va=va,
+                            vm=va + 1)
+    with pytest.raises(dpf.DPFError):  # the DC start needs a positive tolerance and iteration cap
+        dpf.dpf_solve_batch(y, ws, dpf.SolveOpts(dc_start=1, dc_tol=0.0), n_case=2, va=va, vm=va + 1)
+    with pytest.raises(dpf.DPFError):
+        dpf.dpf_solve_batch(y, ws, dpf.SolveOpts(dc_start=1, dc_max_iter=0), n_case=2, va=va, vm=va + 1)
 
 
 def test_300_bus_n1_converged_cases_within_state_bar():
