@@ -756,7 +756,9 @@ def timeseries_record(dpf, torch, T, newton=False, precision=None):
     snapshots from the returned voltages.  `newton`: the series again with the
     first window solved by Newton-Raphson from the flat start, the later
     windows by Alg. 1 from it, with the oracle's mismatch of sampled later
-    snapshots at their start and at their end."""
+    snapshots at their start and at their end.  Then the series with the other
+    warm-start reading (every snapshot of a window from the previous window's
+    last solution)."""
     import gridgen
     import oracle
     from oracle.ybus import grid_ybus
@@ -852,6 +854,17 @@ def timeseries_record(dpf, torch, T, newton=False, precision=None):
             "max_mismatch_p50_later_windows": float(np.median(out_n["max_mismatch"][96:])) if T > 96 else None,
             "sampled_later_snapshots": later,
             "sampled_start_max_mismatch_oracle": start_mm, "sampled_end_max_mismatch_oracle": end_mm}
+    # the other warm-start reading: a window's every snapshot from the previous
+    # window's last solution
+    solve_time_series(y, ws, P[:96], Q[:96], window=96, precision=precision, warm_from="last")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out_l = solve_time_series(y, ws, P, Q, window=96, precision=precision, warm_from="last")
+    torch.cuda.synchronize()
+    wall_l = time.perf_counter() - t0
+    rec["warm_from_last_snapshot"] = {
+        "wall_s": wall_l, "snapshots_per_s": T / wall_l, "converged": int((out_l["status"] == 0).sum()),
+        "max_mismatch_p50_later_windows": float(np.median(out_l["max_mismatch"][96:])) if T > 96 else None}
     ws.free()
     y.free()
     return rec

@@ -7,8 +7,11 @@ every later window starts from the solutions of the previous window,
 snapshot by snapshot (snapshot t from snapshot t - window, the same hour of
 day for a 96-hour window), with the t > 0 settings (Adam lr 0.00027, betas
 (0.7847, 0.6624), ReduceLROnPlateau 0.8 / 2 / 0.0388 / 4, <= 300 iterations).
-The solutions stay on the device between windows; only the window's
-injections are copied in.  All arithmetic runs in the library's kernels.
+With `warm_from="last"` (the other reading of Sec. 5.4.2's warm start) every
+snapshot of a window starts from the solution of the previous window's last
+snapshot instead (one shared start, dpf_batch.va_start).  The solutions stay
+on the device between windows; only the window's injections are copied in.
+All arithmetic runs in the library's kernels.
 
 With `first_newton`, the first window's Alg. 1 solutions are handed to
 Newton-Raphson on the GPU (dpf_nr_solve, FP32 factor, to 1e-10 p.u.) as
@@ -46,13 +49,15 @@ TABLE3_T1 = dict(lr=0.00027, beta1=0.7847, beta2=0.6624, sched=_abi.SCHED_PLATEA
                  threshold=0.0388, cooldown=4, max_iter=300)
 
 
-def _fingerprint(p, q, precision, tol, check_every, settings, first_newton, w0, window, newton_from="dpf"):
+def _fingerprint(p, q, precision, tol, check_every, settings, first_newton, w0, window, newton_from="dpf",
+                 warm_from="same_hour"):
     h = hashlib.sha256()
     h.update(np.ascontiguousarray(p.cpu().numpy()).tobytes())
     h.update(np.ascontiguousarray(q.cpu().numpy()).tobytes())
     h.update(json.dumps(dict(precision=int(precision), tol=float(tol), check_every=int(check_every),
                              settings={k: settings[k] for k in sorted(settings)},
-                             newton=(newton_from if first_newton is not None and w0 == 0 else False), warm=w0 > 0,
+                             newton=(newton_from if first_newton is not None and w0 == 0 else False),
+                             warm=(warm_from if w0 > 0 else False),
                              window=int(window)), sort_keys=True).encode())
     return h.hexdigest()
 
@@ -60,7 +65,7 @@ def _fingerprint(p, q, precision, tol, check_every, settings, first_newton, w0, 
 def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 96, precision=_abi.FP32,
                       first=None, later=None, check_every: int = 25, tol: float = 1e-6, stream=None,
                       first_newton: NewtonSolver | None = None, newton_from: str = "dpf",
-                      checkpoint: str | None = None, resume: bool = False):
+                      checkpoint: str | None = None, resume: bool = False, warm_from: str = "same_hour"):
     """Solve T snapshots ([T][N] injections, numpy or torch); returns numpy arrays.
 
     `first` / `later` override the Table 3 settings (dicts of SolveOpts fields).
@@ -70,9 +75,13 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
     `newton_from="flat"` Newton-Raphson alone solves the first window from
     the flat start.
     `checkpoint` / `resume`: per-window save and restart (module docstring).
+    `warm_from`: "same_hour" (snapshot t from snapshot t - window) or "last"
+    (a window's every snapshot from the previous window's last snapshot).
     """
     if newton_from not in ("dpf", "flat"):
         raise ValueError(f"newton_from must be 'dpf' or 'flat', not {newton_from!r}")
+    if warm_from not in ("same_hour", "last"):
+        raise ValueError(f"warm_from must be 'same_hour' or 'last', not {warm_from!r}")
     import torch
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -98,7 +107,7 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
         settings = dict(TABLE3_T0 if w0 == 0 else TABLE3_T1)
         settings.update((first if w0 == 0 else later) or {})
         fp = _fingerprint(P[w0:w0 + K], Q[w0:w0 + K], precision, tol, check_every, settings, first_newton, w0,
-                          window, newton_from) if path else None
+                          window, newton_from, warm_from) if path else None
         if resume and path and os.path.exists(path):
             with np.load(path) as z:
                 if z["va"].shape != (K, N):
@@ -109,21 +118,26 @@ def solve_time_series(y: Ybus, ws: Workspace, p_series, q_series, window: int = 
                     out[k][w0:w0 + K] = z[k]
             va[:K] = torch.as_tensor(out["va"][w0:w0 + K], device=dev)
             vm[:K] = torch.as_tensor(out["vm"][w0:w0 + K], device=dev)
+            last = K
             continue
         p = P[w0:w0 + K].to(dev).contiguous()
         q = Q[w0:w0 + K].to(dev).contiguous()
         opts = SolveOpts(precision=precision, check_every=check_every, tol=tol, flat_start=1 if w0 == 0 else 0,
                          **settings)
         newton_only = w0 == 0 and first_newton is not None and newton_from == "flat"
+        shared = {}
+        if w0 > 0 and warm_from == "last":  # the previous window's last solution, for every snapshot
+            shared = dict(va_start=va[last - 1].clone(), vm_start=vm[last - 1].clone())
         if not newton_only:
             dpf_solve_batch(y, ws, opts, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K], vm=vm[:K],
-                            **{k: v[:K] for k, v in res.items()})
+                            **shared, **{k: v[:K] for k, v in res.items()})
         if w0 == 0 and first_newton is not None:
             dpf_nr_solve(first_newton, precision=_abi.FP32, tol=1e-10, max_iter=20, flat_start=newton_only,
                          fallback=not newton_only, stream=stream, n_case=K, p_spec=p, q_spec=q, va=va[:K],
                          vm=vm[:K], **{k: v[:K] for k, v in res.items()})
         out["va"][w0:w0 + K] = va[:K].cpu().numpy()
         out["vm"][w0:w0 + K] = vm[:K].cpu().numpy()
+        last = K
         for k, v in res.items():
             out[k][w0:w0 + K] = v[:K].cpu().numpy()
         if path:

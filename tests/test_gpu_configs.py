@@ -83,7 +83,7 @@ def test_c2_adjoint_fd_and_oracle():
         assert np.abs(gg["vm"] - d_vm).max() <= rel * scale
 
 
-def _oracle_series(g, P, Q, window, first, later, check_every=1):
+def _oracle_series(g, P, Q, window, first, later, check_every=1, warm_from="same_hour"):
     Y = grid_ybus(g)
     T = P.shape[0]
     out = []
@@ -96,11 +96,43 @@ def _oracle_series(g, P, Q, window, first, later, check_every=1):
                               factor=s.get("factor", 0.547), patience=s.get("patience", 41),
                               threshold=s.get("threshold", 0.0673), cooldown=s.get("cooldown", 97),
                               max_iter=s["max_iter"], tol=1e-6, check_every=check_every)
-        warm = out[t - window] if t >= window else None
+        if t < window:
+            warm = None
+        elif warm_from == "last":
+            warm = out[(t // window) * window - 1]
+        else:
+            warm = out[t - window]
         r = oracle.dpf_solve(Y, P[t], Q[t], g.bus_type, g.vm_set, o,
                              va0=None if warm is None else warm["va"], vm0=None if warm is None else warm["vm"])
         out.append(r)
     return out
+
+
+def test_c4_time_series_warm_from_last_snapshot_parity():
+    """The other warm-start reading: every snapshot of a window starts from
+    the previous window's last solution (a shared start).  FP64 iterations
+    against the oracle's Alg. 1 run snapshot by snapshot from the oracle's
+    own previous solutions: same iterations and statuses, states to 1e-4
+    (the Table 3 t > 0 reason of the same-hour test), first window to 1e-9."""
+    g = gridgen.make_grid(300, 3, load_scale=0.1)
+    T, window = 20, 8
+    P, Q = gridgen.time_series(g, T, seed=4)
+    first, later = dict(max_iter=250), dict(max_iter=60)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, window)
+    r = solve_time_series(y, ws, P, Q, window=window, precision=dpf.FP64, first=first, later=later, check_every=1,
+                          warm_from="last")
+    ref = _oracle_series(g, P, Q, window, first, later, warm_from="last")
+    for t in range(T):
+        tol = 1e-9 if t < window else 1e-4
+        assert r["iters"][t] == ref[t]["iters"] and r["status"][t] == ref[t]["status"], t
+        assert np.abs(r["va"][t] - ref[t]["va"]).max() < tol, t
+        assert np.abs(r["vm"][t] - ref[t]["vm"]).max() < tol, t
+        assert abs(r["max_mismatch"][t] - ref[t]["max_mismatch"]) <= 1e-6 * ref[t]["max_mismatch"], t
+    # the two readings start the later windows differently
+    same = solve_time_series(y, ws, P, Q, window=window, precision=dpf.FP64, first=first, later=later,
+                             check_every=1)
+    assert np.abs(same["va"][window:] - r["va"][window:]).max() > 1e-6
 
 
 def test_c4_time_series_warm_start_parity():

@@ -19,6 +19,8 @@ def test_newton_from_is_validated_before_any_device_work():
     P = np.zeros((2, 3))
     with pytest.raises(ValueError, match="newton_from"):
         solve_time_series(None, None, P, P, window=2, newton_from="newton")
+    with pytest.raises(ValueError, match="warm_from"):
+        solve_time_series(None, None, P, P, window=2, warm_from="previous")
 
 
 def test_fingerprint_tells_the_first_window_starts_apart():
@@ -29,8 +31,11 @@ def test_fingerprint_tells_the_first_window_starts_apart():
     via_dpf = _fingerprint(*base, marker, 0, 96, "dpf")
     via_flat = _fingerprint(*base, marker, 0, 96, "flat")
     assert len({plain, via_dpf, via_flat}) == 3
-    # later windows start from the previous window whatever solved the first
+    # later windows start from the previous window whatever solved the first,
+    # but the two warm-start readings differ
     assert _fingerprint(*base, marker, 96, 96, "dpf") == _fingerprint(*base, marker, 96, 96, "flat")
+    assert _fingerprint(*base, None, 96, 96, "dpf", "same_hour") != _fingerprint(*base, None, 96, 96, "dpf", "last")
+    assert _fingerprint(*base, None, 0, 96, "dpf", "same_hour") == _fingerprint(*base, None, 0, 96, "dpf", "last")
 
 
 def test_time_series_grid_solves_at_its_peak_hour():
