@@ -199,6 +199,36 @@ def test_dc_outage_shift_of_a_warm_start(precision, shared):
         assert abs(np.abs(f).max() - mm[k]) <= 1e-10 * max(1.0, np.abs(f).max()), k
 
 
+def test_dc_outage_shift_through_host_buffers():
+    """The shifted start through host_io (outage list and shared start from
+    pinned host memory, results back to it: the benchmark's e2e path) equals
+    the device-buffer call bit for bit, 200 refined FP32 iterations."""
+    g = gridgen.make_grid(300, 5, load_scale=0.1)
+    outs = gridgen.n1_outages(g)[:40].astype(np.int32)
+    K, N = outs.size, g.n_bus
+    va0, vm0 = _base_state(g)
+    y = dpf.dpf_build_ybus(g)
+    ws = dpf.dpf_workspace_create(y, K)
+    o = dpf.SolveOpts(precision=dpf.FP32R, max_iter=200, flat_start=0, dc_start=1, dc_tol=1e-4, dc_max_iter=100,
+                      check_every=50, gate=5e-6)
+
+    def outs_on(dev):
+        mk = (lambda shape, dt: torch.zeros(shape, dtype=dt).pin_memory()) if dev == "cpu" else \
+             (lambda shape, dt: torch.zeros(shape, dtype=dt, device=DEV))
+        return dict(va=mk((K, N), torch.float64), vm=mk((K, N), torch.float64), iters=mk(K, torch.int32),
+                    status=mk(K, torch.int32), max_mismatch=mk(K, torch.float64))
+
+    d = outs_on("cuda")
+    dpf.dpf_solve_batch(y, ws, o, n_case=K, outage=_t(outs, torch.int32), va_start=_t(va0), vm_start=_t(vm0), **d)
+    h = outs_on("cpu")
+    pin = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt).pin_memory()
+    dpf.dpf_solve_batch(y, ws, o, n_case=K, host_io=True, outage=pin(outs, torch.int32), va_start=pin(va0),
+                        vm_start=pin(vm0), **h)
+    torch.cuda.synchronize()
+    for k in d:
+        assert torch.equal(d[k].cpu(), h[k]), k
+
+
 def test_dc_outage_shift_full_n1_batch_in_the_benchmark_settings():
     """The whole 2,000-bus N-1 batch started as the benchmark starts it (the
     base case's Newton state shared, refined FP32, the shift's CG stopped at
