@@ -39,7 +39,6 @@ import math
 import os
 import statistics
 import subprocess
-import sys
 import tempfile
 import time
 
