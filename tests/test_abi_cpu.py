@@ -194,3 +194,37 @@ def test_newton_handle_needs_an_uploaded_ybus(dpf):
     with pytest.raises(dpf.DPFError) as e:
         dpf.dpf_nr_create(y, 0)
     assert e.value.code == dpf._abi.DPF_E_INVALID
+
+
+def test_binding_structs_match_the_header_layout(dpf, tmp_path):
+    """The ctypes mirrors of the ABI structs (dpf_grid, dpf_batch,
+    dpf_solve_opts, dpf_nr_opts) have the C compiler's size and the offset
+    of every field, so a field added to the header without the binding (or
+    in another order) fails here rather than shifting every later field."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2603_28203_gb300 import _abi
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"dpf_grid": _abi.DpfGrid, "dpf_batch": _abi.DpfBatch, "dpf_solve_opts": _abi.DpfSolveOpts,
+               "dpf_nr_opts": _abi.DpfNrOpts}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dpf.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I" + inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, fname, v = line.split()
+        got[(cname, fname)] = int(v)
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
