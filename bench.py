@@ -1096,19 +1096,26 @@ def _nr_point_worker(item):
 def run_paramid(args):
     """Parameter identification against the ground truth (the uneven-batch
     experiment at a size the FP64 oracle can measure): `--pid-grids` synthetic
-    grids of log-uniform 300-3,000 buses in one block-diagonal batch, 16 hourly
-    operating points measured by the oracle's Newton-Raphson at the true branch
-    parameters, branch r and x perturbed by U(-10%, +10%), then Adam on the
-    series g, b of every branch from the branch adjoint (dpf_paramid_step).
-    Reports the relative errors of r and x before and after, the loss, and the
-    time per step.  One JSON line."""
+    grids of log-uniform 300-3,000 buses in one block-diagonal batch,
+    `--pid-points` (16) hourly operating points measured by the oracle's
+    Newton-Raphson at the true branch parameters -- the first hours of the
+    load model at which every grid has a solution (`--pid-hours first`), or
+    hours spread over the year (`spread`: 64 candidates evenly spaced) --
+    branch r and x perturbed by U(-10%, +10%), then Adam on the series g, b
+    of every branch from the branch adjoint (dpf_paramid_step).  Reports the
+    relative errors of r and x before and after, the loss, and the time per
+    step.  One JSON line."""
     import multiprocessing as mp
     import gridgen
     sizes = gridgen.uneven_sizes(args.pid_grids, 200, lo=300, hi=3000)
     grids = [gridgen.make_grid(int(n), 2000 + i, load_scale=0.1) for i, n in enumerate(sizes)]
     cat = gridgen.concat_grids(grids)
-    K, H = 16, 48  # 16 operating points: the first hours at which every grid has a power-flow solution
-    P, Q = gridgen.time_series(cat, H, seed=5)
+    K = args.pid_points  # operating points: the first candidate hours at which every grid has a solution
+    hours = np.arange(48) if args.pid_hours == "first" else np.linspace(0, 8759, 64).round().astype(int)
+    H = hours.size
+    PQ = [gridgen.time_series(cat, 1, seed=5, t0=int(h)) for h in hours]
+    P = np.concatenate([a for a, _ in PQ])
+    Q = np.concatenate([b for _, b in PQ])
     off = np.cumsum([0] + [g.n_bus for g in grids])
     items = []
     for gi, g in enumerate(grids):
@@ -1169,7 +1176,8 @@ def run_paramid(args):
         "workload": "paramid",
         "config": {"grids": int(len(sizes)), "bus_sizes": "log-uniform 300-3,000 (seed 200)",
                    "n_bus": int(cat.n_bus), "n_branch": int(cat.n_branch), "operating_points": int(len(kk)),
-                   "hours_with_a_solution": f"{int(ok.sum())} of the first {H}",
+                   "hours_with_a_solution": f"{int(ok.sum())} of {H} candidates ({args.pid_hours})",
+                   "hours_used": [int(h) for h in hours[kk]],
                    "measurements": "FP64 oracle Newton-Raphson at the true parameters",
                    "perturbation": "r, x x U(0.9, 1.1) per branch (seed 5)",
                    "steps": n, "lr": args.pid_lr, "precision": f"{args.pid_precision} forward and adjoint, FP64 loss"},
@@ -1590,6 +1598,9 @@ def main():
     ap.add_argument("--pid-steps", type=int, default=4000)
     ap.add_argument("--pid-lr", type=float, default=3e-3)
     ap.add_argument("--pid-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--pid-points", type=int, default=16, help="operating points of the identification")
+    ap.add_argument("--pid-hours", default="first", choices=["first", "spread"],
+                    help="candidate hours: the first 48, or 64 spread over the year")
     ap.add_argument("--uneven-pid-steps", type=int, default=10)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
