@@ -58,3 +58,22 @@ def test_refined_byte_model_and_presets():
     assert bench.n1_settings("dc")[1]["dc_start"] == 1 and "dc_start" not in bench.n1_settings("base")[1]
     for start in ("dc", "base"):
         assert set(bench.n1_settings(start)[1]) <= names
+
+
+def test_oracle_legs_run_a_shifted_case():
+    """The oracle legs (cpu_baseline, --impl reference) run one N-1 case: the
+    oracle's DC outage shift of the base case's angles, then Alg. 1 with the
+    benchmark's settings; a short budget here.  The shifted start lowers the
+    starting mismatch, as on the GPU."""
+    import oracle
+    from oracle.ybus import grid_ybus
+    g, outages = bench._workload()
+    ell = int(outages[100])
+    it, dt, st = bench._oracle_case((ell, 20, "dc"))
+    assert it == 20 and st == 1 and dt > 0.0  # budget spent (not converged in 20 iterations)
+    _, base = bench._oracle_base()
+    Yk = grid_ybus(g.without_branch(ell))
+    f0, _ = oracle.mismatch(Yk, base["va"], base["vm"], g.p_spec, g.q_spec, g.bus_type)
+    d = oracle.dc_outage_shift(g.n_bus, g.f_bus, g.t_bus, g.x, g.tap, g.bus_type, base["va"], ell)
+    f1, _ = oracle.mismatch(Yk, base["va"] + d, base["vm"], g.p_spec, g.q_spec, g.bus_type)
+    assert np.abs(f1).max() < np.abs(f0).max()
